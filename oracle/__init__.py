@@ -1,0 +1,201 @@
+"""Python access to the plain FP64 CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the benchmark's CPU-baseline
+leg use this module; the product library never does. The C source is compiled on first use
+with the system C compiler (plain -O2, no fast-math) into oracle/liboracle.so.
+
+Each wrapper names the part of the paper it follows: the forward step of inverse mean
+curvature flow (§7.1, (M - tau L) v' = M v, here written A = M + t L with L positive
+semidefinite) and the adjoint rule for linear solves (§5.2, built on Eq. 3 of §3.1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_SO = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_INDEX, ERR_DEGENERATE, ERR_NOT_CONVERGED, ERR_NONFINITE, ERR_OOM, ERR_NOT_SPD = (
+    0, 1, 2, 3, 4, 5, 6, 8)
+
+
+class OracleError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__(f"oracle {what} failed with status {status}")
+        self.status = status
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (only when missing or older than the source)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+            L.orc_validate.argtypes = [i64, i64, vp]
+            L.orc_face_geometry.argtypes = [i64, vp, i64, vp, vp, vp]
+            L.orc_laplacian_csr.argtypes = [i64, vp, i64, vp, vp, vp, vp, i64]
+            L.orc_laplacian_csr.restype = i64
+            L.orc_mass.argtypes = [i64, vp, i64, vp, vp]
+            L.orc_operator.argtypes = [i64, vp, vp, vp, vp, dbl, vp]
+            L.orc_spmv.argtypes = [i64, vp, vp, vp, i32, vp, vp]
+            L.orc_spmv.restype = None
+            L.orc_dense_cholesky_solve.argtypes = [i64, vp, vp, vp, i32, vp, vp]
+            L.orc_pcg_solve.argtypes = [i64, vp, vp, vp, i32, vp, vp, dbl, i32, vp, vp]
+            L.orc_vjp.argtypes = [i64, vp, i64, vp, dbl, i32, vp, vp, vp, i32, vp, vp, vp]
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def validate(F, n):
+    F = _i32(F)
+    return lib().orc_validate(n, F.shape[0], _p(F))
+
+
+def face_geometry(V, F):
+    """Per-face corner cotangents [m][3] and areas [m] (§7.1's L(v), M(v) ingredients)."""
+    V, F = _f64(V), _i32(F)
+    m = F.shape[0]
+    cot = np.empty((m, 3)); area = np.empty(m)
+    st = lib().orc_face_geometry(V.shape[0], _p(V), m, _p(F), _p(cot), _p(area))
+    if st:
+        raise OracleError(st, "face_geometry")
+    return cot, area
+
+
+def laplacian(V, F):
+    """Cotangent Laplacian (PSD convention) as CSR: (rowptr int64[n+1], col int32, val f64)."""
+    V, F = _f64(V), _i32(F)
+    n, m = V.shape[0], F.shape[0]
+    cap = n + 6 * m
+    rowptr = np.empty(n + 1, dtype=np.int64)
+    col = np.empty(cap, dtype=np.int32)
+    val = np.empty(cap)
+    nnz = lib().orc_laplacian_csr(n, _p(V), m, _p(F), _p(rowptr), _p(col), _p(val), cap)
+    if nnz < 0:
+        raise OracleError(-nnz, "laplacian_csr")
+    return rowptr, col[:nnz].copy(), val[:nnz].copy()
+
+
+def mass(V, F):
+    """Barycentric lumped mass diagonal M_ii = sum of incident face areas / 3."""
+    V, F = _f64(V), _i32(F)
+    M = np.empty(V.shape[0])
+    st = lib().orc_mass(V.shape[0], _p(V), F.shape[0], _p(F), _p(M))
+    if st:
+        raise OracleError(st, "mass")
+    return M
+
+
+def operator(V, F, t):
+    """A = M + t L on L's pattern. Returns (rowptr, col, Aval, Lval, M)."""
+    rowptr, col, Lval = laplacian(V, F)
+    M = mass(V, F)
+    Aval = np.empty_like(Lval)
+    lib().orc_operator(M.shape[0], _p(rowptr), _p(col), _p(Lval), _p(M), float(t), _p(Aval))
+    return rowptr, col, Aval, Lval, M
+
+
+def spmv(rowptr, col, val, X):
+    X = _f64(X)
+    X2 = X.reshape(X.shape[0], -1)
+    Y = np.empty_like(X2)
+    lib().orc_spmv(X2.shape[0], _p(rowptr), _p(col), _p(_f64(val)), X2.shape[1], _p(X2), _p(Y))
+    return Y.reshape(X.shape)
+
+
+def dense_cholesky_solve(rowptr, col, Aval, R):
+    R = _f64(R)
+    R2 = R.reshape(R.shape[0], -1)
+    X = np.empty_like(R2)
+    st = lib().orc_dense_cholesky_solve(R2.shape[0], _p(rowptr), _p(col), _p(_f64(Aval)), R2.shape[1], _p(R2),
+                                        _p(X))
+    if st:
+        raise OracleError(st, "dense_cholesky_solve")
+    return X.reshape(R.shape)
+
+
+def pcg_solve(rowptr, col, Aval, R, tol=1e-14, max_iter=100000):
+    """Textbook Jacobi-PCG per column, x0 = 0. Returns (X, iters, true relres, status)."""
+    R = _f64(R)
+    R2 = R.reshape(R.shape[0], -1)
+    k = R2.shape[1]
+    X = np.empty_like(R2)
+    iters = np.zeros(k, dtype=np.int32)
+    rel = np.zeros(k)
+    st = lib().orc_pcg_solve(R2.shape[0], _p(rowptr), _p(col), _p(_f64(Aval)), k, _p(R2), _p(X), float(tol),
+                             int(max_iter), _p(iters), _p(rel))
+    if st not in (OK, ERR_NOT_CONVERGED):
+        raise OracleError(st, "pcg_solve")
+    return X.reshape(R.shape), iters, rel, st
+
+
+def solve(rowptr, col, Aval, R, tol=1e-14, method="auto", max_iter=100000):
+    """Dense Cholesky when n <= 3000 (method 'auto' or 'dense'), else Jacobi-PCG to tol."""
+    n = rowptr.shape[0] - 1
+    if method == "dense" or (method == "auto" and n <= 3000):
+        return dense_cholesky_solve(rowptr, col, Aval, R)
+    X, _, _, st = pcg_solve(rowptr, col, Aval, R, tol=tol, max_iter=max_iter)
+    return X
+
+
+def vjp(V, F, t, U, Lam, B, b_is_V):
+    """Closed-form per-face gradient of the loss w.r.t. V (see orc_vjp). Returns (gV, gB, gt)."""
+    V, F, U, Lam = _f64(V), _i32(F), _f64(U), _f64(Lam)
+    n, k = U.shape
+    Bc = None if b_is_V else _f64(B)
+    gV = np.empty((n, 3))
+    gB = None if b_is_V else np.empty((n, k))
+    gt = ctypes.c_double(0.0)
+    st = lib().orc_vjp(n, _p(V), F.shape[0], _p(F), float(t), k, _p(U), _p(Lam), _p(Bc), int(bool(b_is_V)),
+                       _p(gV), _p(gB), ctypes.byref(gt))
+    if st:
+        raise OracleError(st, "vjp")
+    return gV, gB, gt.value
+
+
+def forward_adjoint(V, F, B, t, T, b_is_V, tol=1e-14, method="auto"):
+    """The whole path for loss l = 0.5 ||U - T||^2: assemble, solve A U = M B, adjoint
+    A Lambda = U - T, gradient. Returns a dict with U, Lam, gV, gB, gt, loss and the operator."""
+    rowptr, col, Aval, Lval, M = operator(V, F, t)
+    Bv = _f64(V) if b_is_V else _f64(B)
+    R = M[:, None] * Bv
+    U = solve(rowptr, col, Aval, R, tol=tol, method=method)
+    G = U - T
+    Lam = solve(rowptr, col, Aval, G, tol=tol, method=method)
+    gV, gB, gt = vjp(V, F, t, U, Lam, B, b_is_V)
+    return dict(U=U, Lam=Lam, gV=gV, gB=gB, gt=gt, loss=0.5 * float(np.sum(G * G)), rowptr=rowptr, col=col,
+                Aval=Aval, Lval=Lval, M=M, R=R, G=G)
+
+
+def num_threads():
+    return 1
