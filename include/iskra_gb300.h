@@ -1,0 +1,163 @@
+/*
+ * iskra_gb300.h -- C ABI of the GB300 (sm_103a) implicit mesh-smoothing library.
+ *
+ * The library computes one step of the paper's inverse mean-curvature flow (§7.1) and its
+ * gradient by the adjoint rule for linear solves (§5.2, "Differentiating linear solvers",
+ * which applies Eq. 3 of §3.1 to f(A, b; y) = A y - b):
+ *
+ *   assemble : per-face cotangents and areas of the triangle mesh (V, F) give the cotangent
+ *              Laplacian L(V) and the diagonal (barycentric, area/3) mass M(V), and the
+ *              operator A = M + t L. L uses the positive-semidefinite sign convention
+ *              (L_ab = -(cot alpha_ab + cot beta_ab)/2, L_aa = -sum_b L_ab), so A is the
+ *              paper's M - tau L_paper with L_paper = -L and tau = t.
+ *   solve    : A U = M B, the paper's (M - tau L) v' = M v when B = V (§7.1).
+ *   adjoint  : A Lambda = G with G = dl/dU (A is symmetric), then the vector-Jacobian product
+ *              dl/dV = <Lambda, d(M B)/dV - (dA/dV) U> gathered per face, plus
+ *              dl/dB = M Lambda and dl/dt = -<Lambda, L U>.
+ *
+ * Conventions for every call:
+ *   - All array arguments are DEVICE pointers on the context's device, contiguous, row-major.
+ *     V is [n][3] double; F is [m][3] int32 (counter-clockwise faces); B, U, G, Lambda are
+ *     [n][k] double with 1 <= k <= 4; gV is [n][3] double.
+ *   - The caller owns every array it passes and must keep it alive and unchanged until the
+ *     work queued on the context's stream has finished. The library owns every object it
+ *     creates (contexts, meshes, batches) and all memory behind them; free them with the
+ *     matching *_free / ig_destroy call.
+ *   - Every call is asynchronous on the context's stream unless its description says it
+ *     synchronises. Calls that fill an ig_solve_info synchronise.
+ *   - Errors are reported by the return code (never by exceptions or aborts);
+ *     ig_last_error() gives a one-line description of the last failure on a context.
+ *   - Integer offsets are 32-bit: n, m and nnz must each stay below 2^31 - 1.
+ */
+#ifndef ISKRA_GB300_H
+#define ISKRA_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IG_OK = 0,
+  IG_ERR_INVALID_ARG = 1,        /* bad size, null pointer, unsupported k or option, unused vertex */
+  IG_ERR_INDEX_OUT_OF_RANGE = 2, /* a face index outside [0, n) */
+  IG_ERR_DEGENERATE_FACE = 3,    /* a face repeats a vertex or has zero area */
+  IG_ERR_NOT_CONVERGED = 4,      /* a solve reached max_iter above rel_tol; the best iterate is written */
+  IG_ERR_NONFINITE = 5,          /* a NaN/Inf in the inputs or a breakdown of the iteration */
+  IG_ERR_OOM = 6,                /* device allocation failed */
+  IG_ERR_CUDA = 7,               /* any other CUDA runtime error */
+  IG_ERR_STATE = 8               /* call out of order (e.g. solve before assemble) */
+} ig_status;
+
+enum { IG_PRECISION_FP64 = 0, IG_PRECISION_MIXED = 1 };
+enum { IG_LAUNCH_GRAPH = 0, IG_LAUNCH_HOST = 1 };
+
+typedef struct ig_ctx ig_ctx;
+typedef struct ig_mesh ig_mesh;
+
+/* Solver options. ig_default_opts() fills the defaults shown. */
+typedef struct {
+  double rel_tol;   /* stop when, for every column, ||rhs - A x||_2 / ||rhs||_2 <= rel_tol (1e-10) */
+  int max_iter;     /* cap on conjugate-gradient iterations per solve (20000) */
+  int launch;       /* IG_LAUNCH_GRAPH: device-side loop in a CUDA graph (default);
+                       IG_LAUNCH_HOST: the host launches every iteration and polls every 16 */
+  double inner_tol; /* mixed precision: relative tolerance of each FP32 inner solve (1e-5) */
+  int max_refine;   /* mixed precision: cap on FP64 residual refinements (30) */
+} ig_solve_opts;
+
+/* Per-solve report (filled only when a non-NULL pointer is passed; the call then synchronises). */
+typedef struct {
+  int status;                /* ig_status of the solve */
+  int k;                     /* number of right-hand-side columns */
+  int iterations;            /* conjugate-gradient iterations performed (all refinements) */
+  int refinements;           /* FP64 residual refinements performed (mixed precision) */
+  double rel_residual[4];    /* final relative residual per column as seen by the stopping test */
+  double true_rel_residual[4]; /* ||rhs - A x|| / ||rhs|| recomputed in FP64 after the solve */
+} ig_solve_info;
+
+/* One-line description of a status code (static storage). */
+const char* ig_status_str(ig_status s);
+
+/* Fill opts with the defaults listed in ig_solve_opts. */
+void ig_default_opts(ig_solve_opts* opts);
+
+/* Create a context on CUDA device `device`, issuing all work on `cuda_stream` (a cudaStream_t;
+ * NULL means the legacy default stream). The context owns its scratch buffers.
+ * Errors: IG_ERR_INVALID_ARG (ctx NULL), IG_ERR_CUDA (bad device). */
+ig_status ig_create(ig_ctx** ctx, int device, void* cuda_stream);
+
+/* Change the stream later calls are issued on. Work already queued stays on the old stream. */
+ig_status ig_set_stream(ig_ctx* ctx, void* cuda_stream);
+
+/* Destroy a context. Every mesh created on it must have been freed first. */
+ig_status ig_destroy(ig_ctx* ctx);
+
+/* Last error message recorded on ctx (empty string if none). */
+const char* ig_last_error(ig_ctx* ctx);
+
+/* Upload the topology of a triangle mesh and build, on the device, everything that depends
+ * on it alone (the paper reuses the sparsity pattern across iterations because it does not
+ * change with V, §7.1): the CSR pattern of L (sorted columns, diagonal included), the
+ * vertex->(face, corner) incidence used by the atomic-free assembly and gradient gathers.
+ * F_dev is [m][3] int32 on the device; the library copies it (the caller keeps F_dev).
+ * Synchronises (the pattern size must be known before allocating).
+ * Errors: IG_ERR_INVALID_ARG (n < 3, m < 1, a vertex used by no face, a vertex with more
+ * than 65535 neighbours), IG_ERR_INDEX_OUT_OF_RANGE, IG_ERR_DEGENERATE_FACE (repeated vertex),
+ * IG_ERR_OOM, IG_ERR_CUDA. On error *out is NULL. */
+ig_status ig_mesh_upload(ig_ctx* ctx, const int32_t* F_dev, int64_t m, int64_t n, ig_mesh** out);
+
+/* Release a mesh and all device memory it owns (after the stream's queued work on it). */
+ig_status ig_mesh_free(ig_mesh* mesh);
+
+/* Sizes of a mesh: vertices, faces, stored nonzeros of L / A, device bytes owned. Any output
+ * pointer may be NULL. */
+ig_status ig_mesh_info(ig_mesh* mesh, int64_t* n, int64_t* m, int64_t* nnz, int64_t* device_bytes);
+
+/* Copy the CSR pattern into caller device buffers rowptr_dev [n+1] and col_dev [nnz] (int32). */
+ig_status ig_mesh_pattern(ig_mesh* mesh, int32_t* rowptr_dev, int32_t* col_dev);
+
+/* Assemble A = M(V) + t L(V) for positions V_dev [n][3] (§7.1: L(v), M(v) recomputed
+ * whenever v changes). precision = IG_PRECISION_FP64 keeps A in FP64; IG_PRECISION_MIXED also
+ * keeps an FP32 copy of A and its diagonal for the inner iterations (the FP64 operator is
+ * still the one every residual is measured against). Asynchronous; a zero-area face or a
+ * non-finite coordinate is reported by the next synchronising call (ig_solve with info, or
+ * ig_check), as IG_ERR_DEGENERATE_FACE / IG_ERR_NONFINITE.
+ * Errors: IG_ERR_INVALID_ARG (t < 0 or not finite, bad precision), IG_ERR_OOM, IG_ERR_CUDA. */
+ig_status ig_assemble(ig_mesh* mesh, const double* V_dev, double t, int precision);
+
+/* Synchronise and return the first error the device recorded for this mesh since upload
+ * (assembly or solve), or IG_OK. */
+ig_status ig_check(ig_mesh* mesh);
+
+/* Copy the assembled operator: Aval_dev [nnz] (values of A on the pattern, FP64) and
+ * M_dev [n] (the lumped mass). Either pointer may be NULL. */
+ig_status ig_operator(ig_mesh* mesh, double* Aval_dev, double* M_dev);
+
+/* Solve A U = M B (the forward smoothing step of §7.1) by Jacobi-preconditioned conjugate
+ * gradients, x0 = 0, every column to opts->rel_tol (FP64 operator; in mixed precision the
+ * iterations run in FP32 and the residual is recomputed in FP64 between refinements).
+ * B_dev, U_dev are [n][k], 1 <= k <= 4, and may not overlap. opts may be NULL (defaults).
+ * Errors: IG_ERR_STATE (not assembled), IG_ERR_INVALID_ARG, and -- only when info is given --
+ * IG_ERR_NOT_CONVERGED / IG_ERR_NONFINITE / IG_ERR_DEGENERATE_FACE from the device. */
+ig_status ig_solve(ig_mesh* mesh, const double* B_dev, int k, double* U_dev, const ig_solve_opts* opts,
+                   ig_solve_info* info);
+
+/* Reverse pass of ig_solve for the loss l(U): solves A Lambda = G_dev (G = dl/dU, [n][k]) and
+ * writes the vector-Jacobian products
+ *   gV_dev [n][3] : dl/dV (NULL not allowed),
+ *   gB_dev [n][k] : dl/dB = M Lambda (may be NULL),
+ *   gt_dev [1]    : dl/dt = -<Lambda, L U> (device double; may be NULL).
+ * V_dev must hold the positions the operator was assembled with, U_dev the forward solution.
+ * b_is_V != 0 means the forward right-hand side was B = V itself (k must be 3): the explicit
+ * term M Lambda is then added to gV and B_dev is ignored. The gradient is gathered per vertex
+ * from per-face contributions, without atomics. Errors as for ig_solve. */
+ig_status ig_adjoint(ig_mesh* mesh, const double* V_dev, const double* B_dev, int b_is_V, const double* U_dev,
+                     const double* G_dev, int k, double* gV_dev, double* gB_dev, double* gt_dev,
+                     const ig_solve_opts* opts, ig_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISKRA_GB300_H */

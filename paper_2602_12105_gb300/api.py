@@ -1,0 +1,212 @@
+"""Python API over the native library: contexts, meshes and a differentiable smoothing step.
+
+PyTorch supplies device memory and the CUDA stream; every step of the computation runs in the
+library's kernels (assemble, solve, adjoint). The differentiable entry point `smooth` follows the
+paper's "differentiable linear_solve with a non-differentiable solver" pattern (§5.2): the forward
+solves (M + tL) U = M B (§7.1) and the backward solves the adjoint system with the same operator.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import torch
+
+from . import _native as N
+
+_PREC = {"fp64": N.IG_PRECISION_FP64, "mixed": N.IG_PRECISION_MIXED}
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise N.NativeLibraryError("a CUDA device is required: this library has no CPU path")
+
+
+def make_opts(rel_tol=1e-10, max_iter=20000, launch="graph", inner_tol=1e-5, max_refine=30):
+    o = N.SolveOpts()
+    N.load().ig_default_opts(ctypes.byref(o))
+    o.rel_tol = float(rel_tol)
+    o.max_iter = int(max_iter)
+    o.launch = N.IG_LAUNCH_GRAPH if launch == "graph" else N.IG_LAUNCH_HOST
+    o.inner_tol = float(inner_tol)
+    o.max_refine = int(max_refine)
+    return o
+
+
+class Context:
+    """One library context on one CUDA device (work goes on torch's current stream)."""
+
+    def __init__(self, device=None):
+        _require_cuda()
+        self.lib = N.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self.h = ctypes.c_void_p()
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        N.check(self.lib.ig_create(ctypes.byref(self.h), self.device.index, ctypes.c_void_p(stream)))
+
+    def sync_stream(self):
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        self.lib.ig_set_stream(self.h, ctypes.c_void_p(stream))
+
+    def check(self, status):
+        N.check(status, self.h)
+
+    def close(self):
+        if self.h:
+            self.lib.ig_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+
+_default_ctx: dict = {}
+
+
+def default_context(device=None) -> Context:
+    _require_cuda()
+    idx = torch.cuda.current_device() if device is None else (torch.device(device).index or 0)
+    if idx not in _default_ctx:
+        _default_ctx[idx] = Context(idx)
+    return _default_ctx[idx]
+
+
+class Mesh:
+    """A triangle mesh uploaded to the library: the CSR pattern and incidence are built once from
+    F and reused by every assemble / solve / adjoint (the sparsity pattern does not change with
+    the positions, §7.1)."""
+
+    def __init__(self, F: torch.Tensor, n: int, ctx: Optional[Context] = None):
+        self.ctx = ctx or default_context(F.device if F.is_cuda else None)
+        F = F.to(device=self.ctx.device, dtype=torch.int32).contiguous()
+        if F.dim() != 2 or F.shape[1] != 3:
+            raise ValueError("F must be [m][3]")
+        self.n, self.m = int(n), int(F.shape[0])
+        self.h = ctypes.c_void_p()
+        self.ctx.sync_stream()
+        self.ctx.check(self.ctx.lib.ig_mesh_upload(self.ctx.h, _ptr(F), self.m, self.n, ctypes.byref(self.h)))
+        nnz, nbytes = ctypes.c_int64(), ctypes.c_int64()
+        self.ctx.lib.ig_mesh_info(self.h, None, None, ctypes.byref(nnz), ctypes.byref(nbytes))
+        self.nnz, self.device_bytes = nnz.value, nbytes.value
+        self.t = None
+        self.precision = None
+        self._token = None
+
+    # -- helpers
+    def _dev(self, x: torch.Tensor, cols=None, name="array"):
+        if x.device != self.ctx.device or x.dtype != torch.float64:
+            raise ValueError(f"{name} must be a float64 tensor on {self.ctx.device}")
+        x = x.contiguous()
+        if x.dim() != 2 or x.shape[0] != self.n or (cols is not None and x.shape[1] != cols):
+            raise ValueError(f"{name} must be [{self.n}][{cols or 'k'}]")
+        return x
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.ig_mesh_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    # -- library calls
+    def assemble(self, V: torch.Tensor, t: float, precision: str = "fp64"):
+        V = self._dev(V, 3, "V")
+        self.ctx.sync_stream()
+        self.ctx.check(self.ctx.lib.ig_assemble(self.h, _ptr(V), float(t), _PREC[precision]))
+        self.t, self.precision = float(t), precision
+        self._token = (V.data_ptr(), V._version, float(t), precision)
+        self._V = V
+        return self
+
+    def check(self):
+        self.ctx.check(self.ctx.lib.ig_check(self.h))
+
+    def operator(self):
+        A = torch.empty(self.nnz, dtype=torch.float64, device=self.ctx.device)
+        M = torch.empty(self.n, dtype=torch.float64, device=self.ctx.device)
+        self.ctx.sync_stream()
+        self.ctx.check(self.ctx.lib.ig_operator(self.h, _ptr(A), _ptr(M)))
+        return A, M
+
+    def pattern(self):
+        rowptr = torch.empty(self.n + 1, dtype=torch.int32, device=self.ctx.device)
+        col = torch.empty(self.nnz, dtype=torch.int32, device=self.ctx.device)
+        self.ctx.sync_stream()
+        self.ctx.check(self.ctx.lib.ig_mesh_pattern(self.h, _ptr(rowptr), _ptr(col)))
+        return rowptr, col
+
+    def solve(self, B: torch.Tensor, opts=None, info: bool = False, out: Optional[torch.Tensor] = None):
+        B = self._dev(B, None, "B")
+        k = B.shape[1]
+        U = out if out is not None else torch.empty_like(B)
+        inf = N.SolveInfo() if info else None
+        self.ctx.sync_stream()
+        st = self.ctx.lib.ig_solve(self.h, _ptr(B), k, _ptr(U), ctypes.byref(opts) if opts is not None else None,
+                                   ctypes.byref(inf) if inf is not None else None)
+        if info:
+            if st not in (N.IG_OK, N.IG_ERR_NOT_CONVERGED):
+                self.ctx.check(st)
+            return U, inf.as_dict()
+        self.ctx.check(st)
+        return U
+
+    def adjoint(self, V, B, b_is_V, U, G, want_gB=False, want_gt=False, opts=None, info: bool = False):
+        V = self._dev(V, 3, "V")
+        G = self._dev(G, None, "G")
+        k = G.shape[1]
+        U = self._dev(U, k, "U")
+        B = None if b_is_V else self._dev(B, k, "B")
+        gV = torch.empty((self.n, 3), dtype=torch.float64, device=self.ctx.device)
+        gB = torch.empty((self.n, k), dtype=torch.float64, device=self.ctx.device) if want_gB else None
+        gt = torch.empty(1, dtype=torch.float64, device=self.ctx.device) if want_gt else None
+        inf = N.SolveInfo() if info else None
+        self.ctx.sync_stream()
+        st = self.ctx.lib.ig_adjoint(self.h, _ptr(V), _ptr(B), int(bool(b_is_V)), _ptr(U), _ptr(G), k, _ptr(gV),
+                                     _ptr(gB), _ptr(gt), ctypes.byref(opts) if opts is not None else None,
+                                     ctypes.byref(inf) if inf is not None else None)
+        if info:
+            if st not in (N.IG_OK, N.IG_ERR_NOT_CONVERGED):
+                self.ctx.check(st)
+            return gV, gB, gt, inf.as_dict()
+        self.ctx.check(st)
+        return gV, gB, gt
+
+
+class SmoothSolve(torch.autograd.Function):
+    """U = (M(V) + t L(V))^-1 M(V) B, differentiable in V, B and t (adjoint rule of §5.2)."""
+
+    @staticmethod
+    def forward(ctx, V, B, t, mesh: Mesh, precision: str, opts):
+        b_is_V = B is None
+        tval = float(t)
+        mesh.assemble(V, tval, precision)
+        U = mesh.solve(V if b_is_V else B, opts=opts)
+        ctx.mesh, ctx.b_is_V, ctx.t, ctx.precision, ctx.opts = mesh, b_is_V, tval, precision, opts
+        ctx.t_is_tensor = isinstance(t, torch.Tensor)
+        ctx.save_for_backward(V, U, *(() if b_is_V else (B,)))
+        return U
+
+    @staticmethod
+    def backward(ctx, gU):
+        mesh: Mesh = ctx.mesh
+        V, U = ctx.saved_tensors[:2]
+        B = None if ctx.b_is_V else ctx.saved_tensors[2]
+        if mesh._token != (V.data_ptr(), V._version, ctx.t, ctx.precision):
+            mesh.assemble(V, ctx.t, ctx.precision)
+        want_gB = (not ctx.b_is_V) and ctx.needs_input_grad[1]
+        want_gt = ctx.t_is_tensor and ctx.needs_input_grad[2]
+        gV, gB, gt = mesh.adjoint(V, B, ctx.b_is_V, U, gU.to(torch.float64).contiguous(), want_gB=want_gB,
+                                  want_gt=want_gt, opts=ctx.opts)
+        gt_out = gt.reshape(()) if want_gt else None
+        return gV, gB, gt_out, None, None, None
+
+
+def smooth(mesh: Mesh, V: torch.Tensor, B: Optional[torch.Tensor], t, precision: str = "fp64", opts=None):
+    """Differentiable implicit smoothing step: solve (M(V) + t L(V)) U = M(V) B (B = V if None)."""
+    return SmoothSolve.apply(V, B, t, mesh, precision, opts)

@@ -1,0 +1,479 @@
+// ig_api.cu -- the C ABI (include/iskra_gb300.h): argument checks, device memory ownership and
+// the order of kernel launches. No arithmetic of the method happens here.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "ig_internal.cuh"
+
+namespace ig {
+
+void set_error(ig_ctx* ctx, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+}
+
+}  // namespace ig
+
+using namespace ig;
+
+namespace {
+
+ig_status from_cuda(ig_ctx* ctx, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return IG_OK;
+  set_error(ctx, std::string(where) + ": " + cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return IG_ERR_OOM;
+  }
+  return IG_ERR_CUDA;
+}
+
+#define IG_CK(ctx, call, where)                                        \
+  do {                                                                 \
+    cudaError_t e_ = (call);                                           \
+    if (e_ != cudaSuccess) return from_cuda((ctx), e_, (where));       \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+ig_status bad_arg(ig_ctx* ctx, const char* msg) {
+  set_error(ctx, msg);
+  return IG_ERR_INVALID_ARG;
+}
+
+template <typename T>
+cudaError_t mesh_alloc(ig_mesh* mesh, T** out, size_t count) {
+  void* p = nullptr;
+  const size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return e;
+  mesh->allocs.push_back(p);
+  mesh->bytes += (int64_t)bytes;
+  *out = static_cast<T*>(p);
+  return cudaSuccess;
+}
+
+void mesh_release(ig_mesh* mesh) {
+  group_destroy(mesh->group);
+  for (void* p : mesh->allocs) cudaFree(p);
+  mesh->allocs.clear();
+}
+
+ig_status err_bits_to_status(int bits) {
+  if (bits & kErrIndex) return IG_ERR_INDEX_OUT_OF_RANGE;
+  if (bits & kErrRepeated) return IG_ERR_DEGENERATE_FACE;
+  if (bits & kErrNonfinite) return IG_ERR_NONFINITE;
+  if (bits & kErrDegenerate) return IG_ERR_DEGENERATE_FACE;
+  if (bits & (kErrUnused | kErrValence)) return IG_ERR_INVALID_ARG;
+  return IG_OK;
+}
+
+const char* err_bits_message(int bits) {
+  if (bits & kErrIndex) return "a face index is outside [0, n)";
+  if (bits & kErrRepeated) return "a face repeats a vertex";
+  if (bits & kErrNonfinite) return "a vertex position is not finite";
+  if (bits & kErrDegenerate) return "a face has zero area";
+  if (bits & kErrUnused) return "a vertex is used by no face";
+  if (bits & kErrValence) return "a vertex has more than 65535 neighbours";
+  return "";
+}
+
+// Device temporaries released when the owner goes out of scope.
+struct TmpAllocs {
+  std::vector<void*> v;
+  ~TmpAllocs() {
+    for (void* p : v) cudaFree(p);
+  }
+  template <typename T>
+  cudaError_t get(T** out, size_t count) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(T) * (count > 0 ? count : 1));
+    if (e == cudaSuccess) {
+      v.push_back(p);
+      *out = static_cast<T*>(p);
+    }
+    return e;
+  }
+};
+
+ig_solve_opts resolve_opts(const ig_solve_opts* o) {
+  ig_solve_opts d;
+  ig_default_opts(&d);
+  return o ? *o : d;
+}
+
+ig_status check_opts(ig_ctx* ctx, const ig_solve_opts& o) {
+  if (!(o.rel_tol >= 0.0) || !std::isfinite(o.rel_tol)) return bad_arg(ctx, "rel_tol must be finite and >= 0");
+  if (o.max_iter < 1 || o.max_iter > 100000000) return bad_arg(ctx, "max_iter must be in [1, 1e8]");
+  if (o.launch != IG_LAUNCH_GRAPH && o.launch != IG_LAUNCH_HOST) return bad_arg(ctx, "unknown launch mode");
+  if (!(o.inner_tol > 0.0) || !(o.inner_tol < 1.0)) return bad_arg(ctx, "inner_tol must be in (0, 1)");
+  if (o.max_refine < 1) return bad_arg(ctx, "max_refine must be >= 1");
+  return IG_OK;
+}
+
+// Synchronise, then report the solve state of the mesh into info and as a status.
+ig_status collect_info(ig_mesh* mesh, int k, ig_solve_info* info) {
+  ig_ctx* ctx = mesh->ctx;
+  SolveScal s;
+  int bits = 0;
+  IG_CK(ctx, cudaMemcpyAsync(&s, mesh->md.s, sizeof(SolveScal), cudaMemcpyDeviceToHost, ctx->stream), "read state");
+  IG_CK(ctx, cudaMemcpyAsync(&bits, mesh->md.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "read state");
+  IG_CK(ctx, cudaStreamSynchronize(ctx->stream), "solve");
+  ig_status st = (ig_status)s.status;
+  if (bits) {
+    st = err_bits_to_status(bits);
+    set_error(ctx, err_bits_message(bits));
+  } else if (st == IG_ERR_NOT_CONVERGED) {
+    set_error(ctx, "conjugate gradients reached max_iter above rel_tol");
+  } else if (st == IG_ERR_NONFINITE) {
+    set_error(ctx, "non-finite value or breakdown in conjugate gradients");
+  }
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->status = st;
+    info->k = k;
+    info->iterations = s.iter;
+    info->refinements = s.refine;
+    for (int c = 0; c < kMaxK; ++c) {
+      info->rel_residual[c] = c < k ? s.relres[c] : 0.0;
+      info->true_rel_residual[c] = c < k ? s.trueres[c] : 0.0;
+    }
+  }
+  return st;
+}
+
+}  // namespace
+
+// =============================================================================================
+extern "C" {
+
+const char* ig_status_str(ig_status s) {
+  switch (s) {
+    case IG_OK: return "ok";
+    case IG_ERR_INVALID_ARG: return "invalid argument";
+    case IG_ERR_INDEX_OUT_OF_RANGE: return "face index out of range";
+    case IG_ERR_DEGENERATE_FACE: return "degenerate face";
+    case IG_ERR_NOT_CONVERGED: return "solver did not converge";
+    case IG_ERR_NONFINITE: return "non-finite value";
+    case IG_ERR_OOM: return "out of device memory";
+    case IG_ERR_CUDA: return "CUDA error";
+    case IG_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+void ig_default_opts(ig_solve_opts* o) {
+  if (!o) return;
+  o->rel_tol = 1e-10;
+  o->max_iter = 20000;
+  o->launch = IG_LAUNCH_GRAPH;
+  o->inner_tol = 1e-5;
+  o->max_refine = 30;
+}
+
+ig_status ig_create(ig_ctx** out, int device, void* cuda_stream) {
+  if (!out) return IG_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return IG_ERR_CUDA;
+  }
+  ig_ctx* ctx = new (std::nothrow) ig_ctx();
+  if (!ctx) return IG_ERR_OOM;
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  DeviceGuard g(device);
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete ctx;
+    return IG_ERR_CUDA;
+  }
+  *out = ctx;
+  return IG_OK;
+}
+
+ig_status ig_set_stream(ig_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return IG_ERR_INVALID_ARG;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  return IG_OK;
+}
+
+ig_status ig_destroy(ig_ctx* ctx) {
+  if (!ctx) return IG_ERR_INVALID_ARG;
+  if (ctx->live_meshes != 0) return bad_arg(ctx, "meshes still alive on this context");
+  delete ctx;
+  return IG_OK;
+}
+
+const char* ig_last_error(ig_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+ig_status ig_mesh_upload(ig_ctx* ctx, const int32_t* F_dev, int64_t m, int64_t n, ig_mesh** out) {
+  if (!ctx || !out) return IG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!F_dev) return bad_arg(ctx, "F is NULL");
+  if (n < 3 || m < 1) return bad_arg(ctx, "need n >= 3 and m >= 1");
+  if (n > (1ll << 30) || m > (1ll << 29)) return bad_arg(ctx, "mesh too large for 32-bit offsets");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t st = ctx->stream;
+  std::unique_ptr<ig_mesh> mesh(new (std::nothrow) ig_mesh());
+  if (!mesh) return IG_ERR_OOM;
+  ig_mesh* M = mesh.get();
+  M->ctx = ctx;
+  M->n = n;
+  M->m = m;
+  const int ni = (int)n, mi = (int)m;
+
+  TmpAllocs tmp;  // temporaries, freed before returning
+
+  int *F = nullptr, *incptr = nullptr, *rowptr = nullptr, *diagpos = nullptr, *err = nullptr, *col = nullptr;
+  int2* inc = nullptr;
+  int *deg = nullptr, *fill = nullptr, *inc_fc = nullptr, *nbr = nullptr, *rowlen = nullptr, *scratch = nullptr,
+      *totals = nullptr;
+  ig_status rs = IG_OK;
+  auto fail = [&](cudaError_t e, const char* where) {
+    rs = from_cuda(ctx, e, where);
+    mesh_release(M);
+    return rs;
+  };
+#define UP_CK(call, where)                          \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return fail(e_, where);  \
+  } while (0)
+
+  const size_t scan_ints = scan_scratch_ints(std::max(ni, 3 * mi) + 1);
+  UP_CK(mesh_alloc(M, &F, 3 * (size_t)m), "alloc F");
+  UP_CK(mesh_alloc(M, &incptr, (size_t)n + 1), "alloc incptr");
+  UP_CK(mesh_alloc(M, &rowptr, (size_t)n + 1), "alloc rowptr");
+  UP_CK(mesh_alloc(M, &diagpos, (size_t)n), "alloc diagpos");
+  UP_CK(mesh_alloc(M, &inc, 3 * (size_t)m), "alloc incidence");
+  UP_CK(mesh_alloc(M, &err, 1), "alloc err");
+  UP_CK(tmp.get(&deg, (size_t)n), "alloc tmp");
+  UP_CK(tmp.get(&fill, (size_t)n), "alloc tmp");
+  UP_CK(tmp.get(&inc_fc, 3 * (size_t)m), "alloc tmp");
+  UP_CK(tmp.get(&nbr, 6 * (size_t)m + (size_t)n), "alloc tmp");
+  UP_CK(tmp.get(&rowlen, (size_t)n), "alloc tmp");
+  UP_CK(tmp.get(&scratch, scan_ints), "alloc tmp");
+  UP_CK(tmp.get(&totals, 2), "alloc tmp");
+
+  UP_CK(cudaMemcpyAsync(F, F_dev, sizeof(int) * 3 * (size_t)m, cudaMemcpyDeviceToDevice, st), "copy F");
+  UP_CK(cudaMemsetAsync(deg, 0, sizeof(int) * (size_t)n, st), "memset");
+  UP_CK(cudaMemsetAsync(fill, 0, sizeof(int) * (size_t)n, st), "memset");
+  UP_CK(cudaMemsetAsync(err, 0, sizeof(int), st), "memset");
+  UP_CK(launch_pattern_count(F, mi, ni, deg, err, st), "pattern count");
+  UP_CK(exclusive_scan_int(deg, incptr, ni, totals, scratch, scan_ints, st), "scan");
+  int host_err = 0;
+  UP_CK(cudaMemcpyAsync(&host_err, err, sizeof(int), cudaMemcpyDeviceToHost, st), "read err");
+  UP_CK(cudaStreamSynchronize(st), "pattern count");
+  if (host_err) {
+    set_error(ctx, err_bits_message(host_err));
+    mesh_release(M);
+    return err_bits_to_status(host_err);
+  }
+  UP_CK(launch_pattern_fill(F, mi, incptr, fill, inc_fc, st), "pattern fill");
+  UP_CK(launch_pattern_rows(F, ni, incptr, inc_fc, nbr, rowlen, err, st), "pattern rows");
+  UP_CK(exclusive_scan_int(rowlen, rowptr, ni, totals + 1, scratch, scan_ints, st), "scan");
+  int host_tot[2] = {0, 0};
+  UP_CK(cudaMemcpyAsync(&host_err, err, sizeof(int), cudaMemcpyDeviceToHost, st), "read err");
+  UP_CK(cudaMemcpyAsync(host_tot, totals, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "read totals");
+  UP_CK(cudaStreamSynchronize(st), "pattern rows");
+  if (host_err) {
+    set_error(ctx, err_bits_message(host_err));
+    mesh_release(M);
+    return err_bits_to_status(host_err);
+  }
+  const int nnz = host_tot[1];
+  M->nnz = nnz;
+  UP_CK(mesh_alloc(M, &col, (size_t)nnz), "alloc col");
+  UP_CK(launch_pattern_cols(F, ni, incptr, inc_fc, nbr, rowptr, col, diagpos, inc, err, st), "pattern cols");
+
+  // operator and solver workspace
+  MeshDev& md = M->md;
+  std::memset(&md, 0, sizeof(md));
+  md.n = ni;
+  md.m = mi;
+  md.nnz = nnz;
+  md.ntiles = (ni + kTileRows - 1) / kTileRows;
+  md.F = F;
+  md.rowptr = rowptr;
+  md.col = col;
+  md.diagpos = diagpos;
+  md.incptr = incptr;
+  md.inc = inc;
+  md.err = err;
+  const size_t nv = (size_t)n * kMaxK;
+  const size_t npart = std::max((size_t)md.ntiles * kPartStride, (size_t)(mi + 255) / 256) + 8;
+  UP_CK(mesh_alloc(M, &md.facew, 4 * (size_t)m), "alloc");
+  UP_CK(mesh_alloc(M, &md.A, (size_t)nnz), "alloc");
+  UP_CK(mesh_alloc(M, &md.M, (size_t)n), "alloc");
+  UP_CK(mesh_alloc(M, &md.Dinv, (size_t)n), "alloc");
+  UP_CK(mesh_alloc(M, &md.x, nv), "alloc");
+  UP_CK(mesh_alloc(M, &md.r, nv), "alloc");
+  UP_CK(mesh_alloc(M, &md.p, nv), "alloc");
+  UP_CK(mesh_alloc(M, &md.q, nv), "alloc");
+  UP_CK(mesh_alloc(M, &md.lam, nv), "alloc");
+  UP_CK(mesh_alloc(M, &md.gface, 9 * (size_t)m), "alloc");
+  UP_CK(mesh_alloc(M, &md.part, npart), "alloc");
+  UP_CK(mesh_alloc(M, &md.s, 1), "alloc");
+  UP_CK(cudaMemsetAsync(md.s, 0, sizeof(SolveScal), st), "memset");
+  UP_CK(cudaMemsetAsync(md.p, 0, sizeof(double) * nv, st), "memset");
+  UP_CK(group_init(M->group, &md, 1, st), "group");
+  UP_CK(cudaStreamSynchronize(st), "upload");
+#undef UP_CK
+  ctx->live_meshes += 1;
+  *out = mesh.release();
+  return IG_OK;
+}
+
+ig_status ig_mesh_free(ig_mesh* mesh) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  DeviceGuard guard(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  mesh_release(mesh);
+  ctx->live_meshes -= 1;
+  delete mesh;
+  return IG_OK;
+}
+
+ig_status ig_mesh_info(ig_mesh* mesh, int64_t* n, int64_t* m, int64_t* nnz, int64_t* device_bytes) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  if (n) *n = mesh->n;
+  if (m) *m = mesh->m;
+  if (nnz) *nnz = mesh->nnz;
+  if (device_bytes) *device_bytes = mesh->bytes;
+  return IG_OK;
+}
+
+ig_status ig_mesh_pattern(ig_mesh* mesh, int32_t* rowptr_dev, int32_t* col_dev) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  DeviceGuard guard(ctx->device);
+  if (rowptr_dev)
+    IG_CK(ctx, cudaMemcpyAsync(rowptr_dev, mesh->md.rowptr, sizeof(int) * (mesh->n + 1), cudaMemcpyDeviceToDevice,
+                               ctx->stream), "copy rowptr");
+  if (col_dev)
+    IG_CK(ctx, cudaMemcpyAsync(col_dev, mesh->md.col, sizeof(int) * mesh->nnz, cudaMemcpyDeviceToDevice, ctx->stream),
+          "copy col");
+  return IG_OK;
+}
+
+ig_status ig_assemble(ig_mesh* mesh, const double* V_dev, double t, int precision) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (!V_dev) return bad_arg(ctx, "V is NULL");
+  if (!(t >= 0.0) || !std::isfinite(t)) return bad_arg(ctx, "t must be finite and >= 0");
+  if (precision != IG_PRECISION_FP64 && precision != IG_PRECISION_MIXED) return bad_arg(ctx, "unknown precision");
+  DeviceGuard guard(ctx->device);
+  MeshDev& md = mesh->md;
+  const int mixed = precision == IG_PRECISION_MIXED;
+  if (mixed && !md.A32) {
+    const size_t nv = (size_t)mesh->n * kMaxK;
+    IG_CK(ctx, mesh_alloc(mesh, &md.A32, (size_t)mesh->nnz), "alloc");
+    IG_CK(ctx, mesh_alloc(mesh, &md.Dinv32, (size_t)mesh->n), "alloc");
+    IG_CK(ctx, mesh_alloc(mesh, &md.x32, nv), "alloc");
+    IG_CK(ctx, mesh_alloc(mesh, &md.r32, nv), "alloc");
+    IG_CK(ctx, mesh_alloc(mesh, &md.p32, nv), "alloc");
+    IG_CK(ctx, mesh_alloc(mesh, &md.q32, nv), "alloc");
+    IG_CK(ctx, cudaMemsetAsync(md.p32, 0, sizeof(float) * nv, ctx->stream), "memset");
+  }
+  md.t = t;
+  IG_CK(ctx, cudaMemcpyAsync(mesh->group.mds, &md, sizeof(MeshDev), cudaMemcpyHostToDevice, ctx->stream), "upload");
+  IG_CK(ctx, cudaMemsetAsync(md.err, 0, sizeof(int), ctx->stream), "memset");
+  IG_CK(ctx, launch_assemble(md, V_dev, t, mixed, ctx->stream), "assemble");
+  mesh->assembled = mixed ? 2 : 1;
+  mesh->t = t;
+  return IG_OK;
+}
+
+ig_status ig_check(ig_mesh* mesh) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  DeviceGuard guard(ctx->device);
+  int bits = 0;
+  IG_CK(ctx, cudaMemcpyAsync(&bits, mesh->md.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "read err");
+  IG_CK(ctx, cudaStreamSynchronize(ctx->stream), "check");
+  if (bits) set_error(ctx, err_bits_message(bits));
+  return err_bits_to_status(bits);
+}
+
+ig_status ig_operator(ig_mesh* mesh, double* Aval_dev, double* M_dev) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (!mesh->assembled) {
+    set_error(ctx, "operator requested before assemble");
+    return IG_ERR_STATE;
+  }
+  DeviceGuard guard(ctx->device);
+  if (Aval_dev)
+    IG_CK(ctx, cudaMemcpyAsync(Aval_dev, mesh->md.A, sizeof(double) * mesh->nnz, cudaMemcpyDeviceToDevice,
+                               ctx->stream), "copy A");
+  if (M_dev)
+    IG_CK(ctx, cudaMemcpyAsync(M_dev, mesh->md.M, sizeof(double) * mesh->n, cudaMemcpyDeviceToDevice, ctx->stream),
+          "copy M");
+  return IG_OK;
+}
+
+ig_status ig_solve(ig_mesh* mesh, const double* B_dev, int k, double* U_dev, const ig_solve_opts* opts,
+                   ig_solve_info* info) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (!mesh->assembled) {
+    set_error(ctx, "solve before assemble");
+    return IG_ERR_STATE;
+  }
+  if (!B_dev || !U_dev) return bad_arg(ctx, "B and U must be non-NULL");
+  if (k < 1 || k > kMaxK) return bad_arg(ctx, "k must be in [1, 4]");
+  if ((const void*)B_dev == (const void*)U_dev) return bad_arg(ctx, "B and U must not overlap");
+  const ig_solve_opts o = resolve_opts(opts);
+  ig_status cs = check_opts(ctx, o);
+  if (cs != IG_OK) return cs;
+  DeviceGuard guard(ctx->device);
+  auto io = std::make_unique<IoTable>();
+  io->in[0] = B_dev;
+  io->out[0] = U_dev;
+  IG_CK(ctx, group_solve(mesh->group, k, mesh->assembled == 2, *io, 1, o, ctx->stream), "solve");
+  if (!info) return IG_OK;
+  IG_CK(ctx, group_true_residual(mesh->group, k, *io, 1, ctx->stream), "residual");
+  return collect_info(mesh, k, info);
+}
+
+ig_status ig_adjoint(ig_mesh* mesh, const double* V_dev, const double* B_dev, int b_is_V, const double* U_dev,
+                     const double* G_dev, int k, double* gV_dev, double* gB_dev, double* gt_dev,
+                     const ig_solve_opts* opts, ig_solve_info* info) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (!mesh->assembled) {
+    set_error(ctx, "adjoint before assemble");
+    return IG_ERR_STATE;
+  }
+  if (!V_dev || !U_dev || !G_dev || !gV_dev) return bad_arg(ctx, "V, U, G and gV must be non-NULL");
+  if (!b_is_V && !B_dev) return bad_arg(ctx, "B must be non-NULL unless b_is_V");
+  if (k < 1 || k > kMaxK) return bad_arg(ctx, "k must be in [1, 4]");
+  if (b_is_V && k != 3) return bad_arg(ctx, "b_is_V needs k == 3");
+  const ig_solve_opts o = resolve_opts(opts);
+  ig_status cs = check_opts(ctx, o);
+  if (cs != IG_OK) return cs;
+  DeviceGuard guard(ctx->device);
+  auto io = std::make_unique<IoTable>();
+  io->in[0] = G_dev;
+  io->out[0] = mesh->md.lam;
+  IG_CK(ctx, group_solve(mesh->group, k, mesh->assembled == 2, *io, 0, o, ctx->stream), "adjoint solve");
+  IG_CK(ctx, launch_vjp(mesh->md, V_dev, B_dev, b_is_V, U_dev, k, gV_dev, gB_dev, gt_dev, ctx->stream), "vjp");
+  if (!info) return IG_OK;
+  IG_CK(ctx, group_true_residual(mesh->group, k, *io, 0, ctx->stream), "residual");
+  return collect_info(mesh, k, info);
+}
+
+}  // extern "C"

@@ -1,0 +1,203 @@
+// ig_internal.cuh -- shared definitions of the sm_103a implicit-smoothing library.
+//
+// Layout conventions on the device (all row-major, 32-bit indices):
+//   F        [m][3]  int32      faces (copied at upload)
+//   rowptr   [n+1]   int32      CSR row offsets of L / A (diagonal included, columns sorted)
+//   col      [nnz]   int32      CSR columns
+//   diagpos  [n]     int32      absolute index of the diagonal entry of each row
+//   incptr   [n+1]   int32      vertex -> (face, corner) incidence offsets (3m entries)
+//   inc      [3m]    int2       .x = face*4 + corner (sorted by face within a vertex),
+//                               .y = slot of the edge to the next corner | slot of the edge
+//                                    to the previous corner << 16 (slots relative to rowptr[v])
+//   facew    [m][4]  double     per face: t*cot_c/2 for the three corners, area/3
+//   A        [nnz]   double     A = M + t L;   A32 [nnz] float (mixed precision)
+//   M, Dinv  [n]     double     lumped mass and 1/A_ii;  Dinv32 [n] float
+//   vectors  [n][K]  (p: [n][KP], KP = 4 when K = 3 so that a row is one aligned 32-byte load)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/iskra_gb300.h"
+
+namespace ig {
+
+constexpr int kBlock = 256;          // threads per CTA of every row- or face-parallel kernel
+constexpr int kRowsPerThread = 4;    // rows per thread in the solver kernels
+constexpr int kTileRows = kBlock * kRowsPerThread;
+constexpr int kMaxK = 4;
+constexpr int kPartStride = 8;       // doubles per tile in the partial-sum arrays
+
+// Device error word bits (OR-ed by kernels, decoded on the host).
+enum : int {
+  kErrIndex = 1,
+  kErrRepeated = 2,
+  kErrUnused = 4,
+  kErrValence = 8,
+  kErrDegenerate = 16,
+  kErrNonfinite = 32,
+};
+
+// Solver state of one mesh, resident in device memory. The "last CTA" of each reduction
+// (detected with a counter) writes the scalars; every other field is read-only for kernels.
+struct SolveScal {
+  double rz[kMaxK];      // r . z of the current iterate (inner iterate in mixed precision)
+  double alpha[kMaxK];
+  double beta[kMaxK];
+  double bnorm2[kMaxK];  // ||rhs||^2 of the system being iterated
+  double rhs2[kMaxK];    // ||rhs||^2 of the outer (FP64) system
+  double relres[kMaxK];  // last relative residual seen by the stopping test
+  double trueres[kMaxK]; // FP64 recomputed relative residual (filled on request)
+  double scale[kMaxK];   // mixed precision: norm of the residual the inner system was scaled by
+  int active[kMaxK];
+  int k;
+  int done;              // 1 once every column converged, failed or hit the cap
+  int status;            // ig_status of this solve
+  int iter;              // conjugate-gradient iterations so far
+  int refine;            // mixed precision: refinements so far
+  int phase;             // mixed precision: 0 inner iterations, 1 refinement pending
+  int max_iter, max_refine;
+  double tol, inner_tol;
+  unsigned int cnt[4];   // last-CTA counters (spmv, update, init/residual, vjp)
+};
+
+// Everything a kernel needs about one mesh (plain device pointers, passed in device arrays so
+// that a batch of meshes is a list of these).
+struct MeshDev {
+  int n, m, nnz, ntiles;   // ntiles = ceil(n / kTileRows)
+  int k;
+  double t;
+  const int* F;
+  const int* rowptr;
+  const int* col;
+  const int* diagpos;
+  const int* incptr;
+  const int2* inc;
+  double* facew;
+  double* A;
+  float* A32;
+  double* M;
+  double* Dinv;
+  float* Dinv32;
+  // FP64 solver vectors
+  double* x;
+  double* r;
+  double* p;
+  double* q;
+  // mixed-precision inner vectors
+  float* x32;
+  float* r32;
+  float* p32;
+  float* q32;
+  // right-hand side of the outer system (caller buffer for the forward solve), and its mode
+  const double* rhs_src;
+  int rhs_mass;            // 1: rhs = M * rhs_src, 0: rhs = rhs_src
+  double* lam;             // adjoint solution [n][k]
+  double* gface;           // per-face gradient contributions [m][9]
+  double* part;            // [ntiles][kPartStride] partial sums
+  SolveScal* s;
+  int* err;
+};
+
+// Host-side helpers (ig_api.cu).
+void set_error(ig_ctx* ctx, const std::string& msg);
+
+}  // namespace ig
+
+// ---------------------------------------------------------------------------------------------
+// Opaque types of the C ABI.
+struct ig_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int live_meshes = 0;
+  std::string last_error;
+};
+
+namespace ig {
+
+// Loop control shared by every mesh of one launch group (a single mesh or a batch).
+struct LoopCtl {
+  unsigned int cnt;   // CTAs of the update kernel that have finished this iteration
+  int iter;           // iterations of the device-side loop so far
+  int cap;            // hard cap on iterations of the device-side loop
+  int all_done;       // 1 once every mesh of the group is done
+};
+
+// Per-launch pointers that change from call to call (kept out of the cached graphs).
+constexpr int kMaxIo = 1024;
+struct IoTable {
+  const double* in[kMaxIo];
+  double* out[kMaxIo];
+};
+
+// A cached solver launch for one (k, precision): a CUDA graph whose WHILE node runs the
+// iteration body until the device sets the loop condition to 0.
+struct SolvePlan {
+  int k = 0;
+  int mixed = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+// A group of meshes solved by the same kernel launches (a single mesh is a group of one).
+struct Group {
+  int nmesh = 0;
+  int ntiles = 0;                 // total tiles over all meshes
+  MeshDev* mds = nullptr;         // device array [nmesh]
+  int2* tiles = nullptr;          // device array [ntiles]: (mesh, local tile)
+  LoopCtl* ctl = nullptr;         // device
+  int* done_host = nullptr;       // pinned host word for the host-driven loop
+  SolvePlan plans[2][kMaxK + 1];  // [mixed][k]
+  cudaStream_t capture_stream = nullptr;
+};
+
+cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, cudaStream_t st);
+void group_destroy(Group& g);
+cudaError_t group_solve(Group& g, int k, int mixed, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
+                        cudaStream_t st);
+cudaError_t group_true_residual(Group& g, int k, const IoTable& io, int rhs_mass, cudaStream_t st);
+
+}  // namespace ig
+
+// A mesh: topology, operator, solver workspace and its own launch group.
+struct ig_mesh {
+  ig_ctx* ctx = nullptr;
+  int64_t n = 0, m = 0, nnz = 0;
+  int64_t bytes = 0;
+  int assembled = 0;        // 0 none, 1 FP64, 2 mixed
+  double t = 0.0;
+  int ws_k = 0;             // solver vectors allocated for this many columns
+  ig::MeshDev md{};         // host copy of the device pointers
+  ig::Group group;          // this mesh alone
+  std::vector<void*> allocs;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Kernel launchers (each file defines its own).
+namespace ig {
+
+// ig_pattern.cu
+cudaError_t exclusive_scan_int(const int* in, int* out, int count, int* total_out_dev, int* scratch,
+                               size_t scratch_ints, cudaStream_t st);
+size_t scan_scratch_ints(int count);
+cudaError_t launch_pattern_count(const int* F, int m, int n, int* deg, int* err, cudaStream_t st);
+cudaError_t launch_pattern_fill(const int* F, int m, const int* incptr, int* fill, int* inc_fc, cudaStream_t st);
+cudaError_t launch_pattern_rows(const int* F, int n, const int* incptr, int* inc_fc, int* nbr, int* rowlen,
+                                int* err, cudaStream_t st);
+cudaError_t launch_pattern_cols(const int* F, int n, const int* incptr, const int* inc_fc, const int* nbr,
+                                const int* rowptr, int* col, int* diagpos, int2* inc, int* err, cudaStream_t st);
+
+// ig_assemble.cu
+cudaError_t launch_assemble(const MeshDev& md, const double* V, double t, int mixed, cudaStream_t st);
+
+// ig_pcg.cu: see Group above
+
+// ig_vjp.cu
+cudaError_t launch_vjp(const MeshDev& md, const double* V, const double* B, int b_is_V, const double* U, int k,
+                       double* gV, double* gB, double* gt, cudaStream_t st);
+
+}  // namespace ig

@@ -1,0 +1,538 @@
+// ig_pcg.cu -- Jacobi-preconditioned conjugate gradients for A X = RHS with k <= 4 columns
+// solved together (the matrix is read once per iteration for all columns), on a group of one or
+// more meshes (the forward solve of §7.1 and the adjoint solve of §5.2 use the same operator).
+//
+// One iteration is three kernels over tiles of kTileRows rows (a tile belongs to one mesh):
+//   spmv   : q = A p for the tile's rows, partial p.q  -> last tile of the mesh: alpha = rz / pq
+//   update : x += alpha p, r -= alpha q, partial r.z and r.r with z = D^-1 r recomputed
+//            -> last tile of the mesh: convergence test, beta = rz_new / rz
+//            -> last CTA of the launch: loop control (all meshes done or the cap reached)
+//   pupdate: p = D^-1 r + beta p
+// Reductions are deterministic: every CTA writes its partial sums, the last CTA of a mesh (found
+// with a counter) adds the partials in tile order. No atomics touch floating-point data, so a mesh
+// gives the same bits alone and inside a batch.
+//
+// The loop runs on the device: a CUDA graph holds a WHILE node whose body is one iteration; the
+// update kernel's last CTA clears the condition when the group is done, so the host neither
+// polls nor synchronises per iteration. Every loop is bounded by a hard cap.
+//
+// FP64 instructions are the scarce resource of this GPU (2 FP64 FMA per clock per SM). Each thread
+// handles kRowsPerThread rows so the block reductions, which cost FP64 adds, are amortised.
+#include "ig_internal.cuh"
+
+namespace ig {
+
+namespace {
+
+template <int K>
+struct KP {
+  static constexpr int v = (K == 3) ? 4 : K;
+};
+
+__device__ __forceinline__ bool positive_finite(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && (b & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool is_finite(double x) {
+  return (__double_as_longlong(x) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+
+// Sum v[0..NV) over the CTA; thread 0 receives the totals. sh holds NV*kBlock doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i) sh[i * kBlock + threadIdx.x] = v[i];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double a = sh[i * kBlock + threadIdx.x];
+#pragma unroll
+      for (int w = 1; w < kBlock / 32; ++w) a += sh[i * kBlock + threadIdx.x + 32 * w];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      v[i] = a;
+    }
+  }
+  __syncthreads();
+}
+
+// Block-sum v, publish the tile's partials, and return true in the last CTA of the mesh, whose
+// thread 0 then holds the mesh totals (partials added in tile order, so the result does not
+// depend on which CTA finished last).
+template <int NV>
+__device__ __forceinline__ bool reduce_tiles(double (&v)[NV], double* part, int tile, int ntiles, unsigned int* cnt,
+                                             double* sh) {
+  __shared__ int s_last;
+  block_sum<NV>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) part[tile * kPartStride + i] = v[i];
+    __threadfence();
+    const unsigned prev = atomicAdd(cnt, 1u);
+    s_last = (prev == (unsigned)ntiles - 1u);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = 0.0;
+  for (int t = threadIdx.x; t < ntiles; t += kBlock)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += __ldcg(part + t * kPartStride + i);
+  block_sum<NV>(v, sh);
+  if (threadIdx.x == 0) *cnt = 0u;
+  return true;
+}
+
+template <int K>
+__device__ __forceinline__ void load_row(const double* __restrict__ p, long row, double (&v)[K]) {
+  if constexpr (K == 3 || K == 4) {
+    const double2* q = reinterpret_cast<const double2*>(p + row * KP<K>::v);
+    const double2 a = q[0], b = q[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x;
+    if constexpr (K == 4) v[3] = b.y;
+  } else if constexpr (K == 2) {
+    const double2 a = reinterpret_cast<const double2*>(p + row * 2)[0];
+    v[0] = a.x; v[1] = a.y;
+  } else {
+    v[0] = p[row];
+  }
+}
+
+// ------------------------------------------------------------------------------- init
+// rhs = M * in (rhs_mass) or in; x = 0; r = rhs; p = z = D^-1 r; per mesh: rz, ||rhs||^2.
+template <int K>
+__global__ void __launch_bounds__(kBlock) init_kernel(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles,
+                                                      IoTable io, int rhs_mass, LoopCtl* ctl, double tol,
+                                                      int max_iter, int cap) {
+  __shared__ double sh[2 * K * kBlock];
+  const int2 tl = tiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->cnt = 0u;
+    ctl->iter = 0;
+    ctl->all_done = 0;
+    ctl->cap = cap;
+  }
+  const double* __restrict__ src = io.in[tl.x];
+  double acc[2 * K];
+#pragma unroll
+  for (int i = 0; i < 2 * K; ++i) acc[i] = 0.0;
+#pragma unroll
+  for (int rr = 0; rr < kRowsPerThread; ++rr) {
+    const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
+    if (row < md.n) {
+      const double dinv = md.Dinv[row];
+      const double mass = rhs_mass ? md.M[row] : 1.0;
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        const double b = rhs_mass ? mass * src[row * K + c] : src[row * K + c];
+        const double z = dinv * b;
+        md.x[row * K + c] = 0.0;
+        md.r[row * K + c] = b;
+        md.p[row * KP<K>::v + c] = z;
+        acc[c] = fma(b, z, acc[c]);
+        acc[K + c] = fma(b, b, acc[K + c]);
+      }
+    }
+  }
+  if (reduce_tiles<2 * K>(acc, md.part, tl.y, md.ntiles, &md.s->cnt[2], sh) && threadIdx.x == 0) {
+    SolveScal* s = md.s;
+    int any = 0, bad = 0;
+    for (int c = 0; c < kMaxK; ++c) {
+      const bool in = c < K;
+      const double bb = in ? acc[K + c] : 0.0;
+      const double rz = in ? acc[c] : 0.0;
+      if (in && (!is_finite(bb) || !is_finite(rz))) bad = 1;
+      const int act = in && positive_finite(bb);
+      s->rz[c] = rz;
+      s->bnorm2[c] = bb;
+      s->rhs2[c] = bb;
+      s->alpha[c] = 0.0;
+      s->beta[c] = 0.0;
+      s->scale[c] = 1.0;
+      s->active[c] = act;
+      s->relres[c] = act ? 1.0 : 0.0;
+      s->trueres[c] = -1.0;
+      any |= act;
+    }
+    s->k = K;
+    s->cnt[0] = 0u;
+    s->cnt[1] = 0u;
+    s->iter = 0;
+    s->refine = 0;
+    s->phase = 0;
+    s->tol = tol;
+    s->max_iter = max_iter;
+    s->status = bad ? IG_ERR_NONFINITE : IG_OK;
+    s->done = (bad || !any) ? 1 : 0;
+  }
+}
+
+// ------------------------------------------------------------------------------- spmv
+template <int K>
+__global__ void __launch_bounds__(kBlock) spmv_kernel(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles) {
+  __shared__ double sh[K * kBlock];
+  const int2 tl = tiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  SolveScal* s = md.s;
+  if (__ldcg(&s->done)) return;
+  const double* __restrict__ A = md.A;
+  const int* __restrict__ col = md.col;
+  const int* __restrict__ rowptr = md.rowptr;
+  const double* __restrict__ p = md.p;
+  double pq[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) pq[c] = 0.0;
+#pragma unroll
+  for (int rr = 0; rr < kRowsPerThread; ++rr) {
+    const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
+    if (row < md.n) {
+      const int e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
+      double acc[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) acc[c] = 0.0;
+      for (int e = e0; e < e1; ++e) {
+        const double a = __ldg(A + e);
+        double pj[K];
+        load_row<K>(p, __ldg(col + e), pj);
+#pragma unroll
+        for (int c = 0; c < K; ++c) acc[c] = fma(a, pj[c], acc[c]);
+      }
+      double pi[K];
+      load_row<K>(p, row, pi);
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        md.q[row * K + c] = acc[c];
+        pq[c] = fma(pi[c], acc[c], pq[c]);
+      }
+    }
+  }
+  if (reduce_tiles<K>(pq, md.part, tl.y, md.ntiles, &s->cnt[0], sh) && threadIdx.x == 0) {
+    for (int c = 0; c < K; ++c) {
+      if (s->active[c]) {
+        if (!positive_finite(pq[c])) {
+          s->status = IG_ERR_NONFINITE;
+          s->done = 1;
+          s->alpha[c] = 0.0;
+        } else {
+          s->alpha[c] = s->rz[c] / pq[c];
+        }
+      } else {
+        s->alpha[c] = 0.0;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------- update
+template <int K>
+__global__ void __launch_bounds__(kBlock) update_kernel(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles,
+                                                        LoopCtl* ctl, cudaGraphConditionalHandle handle, int use_graph,
+                                                        int nmesh) {
+  __shared__ double sh[2 * K * kBlock];
+  const int2 tl = tiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  SolveScal* s = md.s;
+  if (!__ldcg(&s->done)) {
+    double alpha[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) alpha[c] = __ldcg(&s->alpha[c]);
+    double acc[2 * K];
+#pragma unroll
+    for (int i = 0; i < 2 * K; ++i) acc[i] = 0.0;
+#pragma unroll
+    for (int rr = 0; rr < kRowsPerThread; ++rr) {
+      const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
+      if (row < md.n) {
+        const double dinv = md.Dinv[row];
+        double pi[K];
+        load_row<K>(md.p, row, pi);
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+          const double xv = fma(alpha[c], pi[c], md.x[row * K + c]);
+          const double rv = fma(-alpha[c], md.q[row * K + c], md.r[row * K + c]);
+          md.x[row * K + c] = xv;
+          md.r[row * K + c] = rv;
+          const double z = dinv * rv;
+          acc[c] = fma(rv, z, acc[c]);
+          acc[K + c] = fma(rv, rv, acc[K + c]);
+        }
+      }
+    }
+    if (reduce_tiles<2 * K>(acc, md.part, tl.y, md.ntiles, &s->cnt[1], sh) && threadIdx.x == 0) {
+      int any = 0, bad = 0;
+      for (int c = 0; c < K; ++c) {
+        if (!s->active[c]) continue;
+        const double rzn = acc[c], rr = acc[K + c];
+        if (!is_finite(rzn) || !is_finite(rr)) {
+          bad = 1;
+          continue;
+        }
+        const double rel = sqrt(rr / s->bnorm2[c]);
+        s->relres[c] = rel;
+        if (rel <= s->tol) {
+          s->active[c] = 0;
+          s->beta[c] = 0.0;
+        } else {
+          s->beta[c] = rzn / s->rz[c];
+          s->rz[c] = rzn;
+          any = 1;
+        }
+      }
+      const int it = s->iter + 1;
+      s->iter = it;
+      if (bad) {
+        s->status = IG_ERR_NONFINITE;
+        s->done = 1;
+      } else if (!any) {
+        s->done = 1;
+      } else if (it >= s->max_iter) {
+        s->status = IG_ERR_NOT_CONVERGED;
+        s->done = 1;
+      }
+    }
+  }
+  // Loop control: the last CTA of the launch decides whether the device-side loop goes on.
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&ctl->cnt, 1u);
+    if (prev == gridDim.x - 1u) {
+      __threadfence();
+      int all = 1;
+      for (int i = 0; i < nmesh; ++i) all &= (__ldcg(&mds[i].s->done) != 0);
+      const int it = ctl->iter + 1;
+      ctl->iter = it;
+      if (all || it >= ctl->cap) {
+        ctl->all_done = 1;
+        if (use_graph) cudaGraphSetConditional(handle, 0u);
+      }
+      ctl->cnt = 0u;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------- pupdate
+template <int K>
+__global__ void __launch_bounds__(kBlock) pupdate_kernel(const MeshDev* __restrict__ mds,
+                                                         const int2* __restrict__ tiles) {
+  const int2 tl = tiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  SolveScal* s = md.s;
+  if (__ldcg(&s->done)) return;
+  double beta[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) beta[c] = __ldcg(&s->beta[c]);
+#pragma unroll
+  for (int rr = 0; rr < kRowsPerThread; ++rr) {
+    const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
+    if (row < md.n) {
+      const double dinv = md.Dinv[row];
+      double pi[K];
+      load_row<K>(md.p, row, pi);
+#pragma unroll
+      for (int c = 0; c < K; ++c) md.p[row * KP<K>::v + c] = fma(beta[c], pi[c], dinv * md.r[row * K + c]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------- finalize
+template <int K>
+__global__ void __launch_bounds__(kBlock) finalize_kernel(const MeshDev* __restrict__ mds,
+                                                          const int2* __restrict__ tiles, IoTable io) {
+  const int2 tl = tiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  double* __restrict__ out = io.out[tl.x];
+#pragma unroll
+  for (int rr = 0; rr < kRowsPerThread; ++rr) {
+    const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
+    if (row < md.n) {
+#pragma unroll
+      for (int c = 0; c < K; ++c) out[row * K + c] = md.x[row * K + c];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------- true residual
+// trueres = ||rhs - A x|| / ||rhs|| per column with x = io.out (the written solution).
+template <int K>
+__global__ void __launch_bounds__(kBlock) residual_kernel(const MeshDev* __restrict__ mds,
+                                                          const int2* __restrict__ tiles, IoTable io, int rhs_mass) {
+  __shared__ double sh[K * kBlock];
+  const int2 tl = tiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  const double* __restrict__ src = io.in[tl.x];
+  const double* __restrict__ xs = io.out[tl.x];
+  double acc[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) acc[c] = 0.0;
+#pragma unroll
+  for (int rr = 0; rr < kRowsPerThread; ++rr) {
+    const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
+    if (row < md.n) {
+      double ax[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) ax[c] = 0.0;
+      for (int e = md.rowptr[row]; e < md.rowptr[row + 1]; ++e) {
+        const double a = md.A[e];
+        const long j = md.col[e];
+#pragma unroll
+        for (int c = 0; c < K; ++c) ax[c] = fma(a, xs[j * K + c], ax[c]);
+      }
+      const double mass = rhs_mass ? md.M[row] : 1.0;
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        const double b = rhs_mass ? mass * src[row * K + c] : src[row * K + c];
+        const double res = b - ax[c];
+        acc[c] = fma(res, res, acc[c]);
+      }
+    }
+  }
+  if (reduce_tiles<K>(acc, md.part, tl.y, md.ntiles, &md.s->cnt[2], sh) && threadIdx.x == 0) {
+    for (int c = 0; c < K; ++c) {
+      const double r2 = md.s->rhs2[c];
+      md.s->trueres[c] = r2 > 0.0 ? sqrt(acc[c] / r2) : sqrt(acc[c]);
+    }
+  }
+}
+
+template <int K>
+cudaError_t build_plan(Group& g, SolvePlan& pl) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle handle;
+  e = cudaGraphConditionalHandleCreate(&handle, graph, 1u, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t cs = g.capture_stream;
+  e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  spmv_kernel<K><<<g.ntiles, kBlock, 0, cs>>>(g.mds, g.tiles);
+  update_kernel<K><<<g.ntiles, kBlock, 0, cs>>>(g.mds, g.tiles, g.ctl, handle, 1, g.nmesh);
+  pupdate_kernel<K><<<g.ntiles, kBlock, 0, cs>>>(g.mds, g.tiles);
+  cudaError_t le = cudaGetLastError();
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(cs, &captured);
+  if (le != cudaSuccess) e = le;
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  pl.k = K;
+  pl.mixed = 0;
+  pl.graph = graph;
+  pl.exec = exec;
+  return cudaSuccess;
+}
+
+template <int K>
+cudaError_t solve_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_opts& o, cudaStream_t st) {
+  const int cap = o.max_iter + 2;
+  init_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io, rhs_mass, g.ctl, o.rel_tol, o.max_iter, cap);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (o.launch == IG_LAUNCH_GRAPH) {
+    SolvePlan& pl = g.plans[0][K];
+    if (!pl.exec) {
+      e = build_plan<K>(g, pl);
+      if (e != cudaSuccess) return e;
+    }
+    e = cudaGraphLaunch(pl.exec, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    for (int it = 0; it < cap; ++it) {
+      spmv_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles);
+      update_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, g.ctl, cudaGraphConditionalHandle{}, 0, g.nmesh);
+      pupdate_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      if ((it & 15) == 15 || it == cap - 1) {
+        e = cudaMemcpyAsync(g.done_host, &g.ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        if (*g.done_host) break;
+      }
+    }
+  }
+  finalize_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, cudaStream_t st) {
+  g.nmesh = nmesh;
+  std::vector<int2> tiles;
+  for (int i = 0; i < nmesh; ++i)
+    for (int t = 0; t < host_mds[i].ntiles; ++t) tiles.push_back(make_int2(i, t));
+  g.ntiles = (int)tiles.size();
+  cudaError_t e = cudaMalloc(&g.mds, sizeof(MeshDev) * nmesh);
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&g.tiles, sizeof(int2) * tiles.size());
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&g.ctl, sizeof(LoopCtl));
+  if (e != cudaSuccess) return e;
+  e = cudaMallocHost(&g.done_host, sizeof(int));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(g.mds, host_mds, sizeof(MeshDev) * nmesh, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(g.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(g.ctl, 0, sizeof(LoopCtl), st);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamCreateWithFlags(&g.capture_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
+}
+
+void group_destroy(Group& g) {
+  for (auto& row : g.plans)
+    for (auto& pl : row) {
+      if (pl.exec) cudaGraphExecDestroy(pl.exec);
+      if (pl.graph) cudaGraphDestroy(pl.graph);
+      pl = SolvePlan{};
+    }
+  if (g.capture_stream) cudaStreamDestroy(g.capture_stream);
+  if (g.mds) cudaFree(g.mds);
+  if (g.tiles) cudaFree(g.tiles);
+  if (g.ctl) cudaFree(g.ctl);
+  if (g.done_host) cudaFreeHost(g.done_host);
+  g = Group{};
+}
+
+cudaError_t group_solve(Group& g, int k, int mixed, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
+                        cudaStream_t st) {
+  (void)mixed;
+  switch (k) {
+    case 1: return solve_k<1>(g, io, rhs_mass, o, st);
+    case 2: return solve_k<2>(g, io, rhs_mass, o, st);
+    case 3: return solve_k<3>(g, io, rhs_mass, o, st);
+    case 4: return solve_k<4>(g, io, rhs_mass, o, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t group_true_residual(Group& g, int k, const IoTable& io, int rhs_mass, cudaStream_t st) {
+  switch (k) {
+    case 1: residual_kernel<1><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io, rhs_mass); break;
+    case 2: residual_kernel<2><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io, rhs_mass); break;
+    case 3: residual_kernel<3><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io, rhs_mass); break;
+    case 4: residual_kernel<4><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io, rhs_mass); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ig
