@@ -156,6 +156,25 @@ ig_status ig_adjoint(ig_mesh* mesh, const double* V_dev, const double* B_dev, in
                      const double* G_dev, int k, double* gV_dev, double* gB_dev, double* gt_dev,
                      const ig_solve_opts* opts, ig_solve_info* info);
 
+/* ---- kernel timing (tracing) -------------------------------------------------------------- */
+
+/* Per-kernel device time accumulated while profiling is on. */
+typedef struct {
+  char name[48];      /* kernel name */
+  int64_t launches;   /* launches timed */
+  double total_ms;    /* summed device time between the CUDA events around each launch */
+} ig_kernel_stat;
+
+/* Turn process-wide kernel timing on (enable != 0) or off, clearing the accumulated figures.
+ * While it is on, every launch is bracketed by CUDA events on the stream it is issued on, and
+ * the conjugate-gradient loop is launched from the host (one launch per kernel) so that each
+ * iteration's kernels are timed individually. It changes no result. */
+ig_status ig_profile_enable(int enable);
+
+/* Synchronise on the recorded events and copy up to max per-kernel records into out; returns
+ * the number of kernel names recorded (which may exceed max). */
+int ig_profile_read(ig_kernel_stat* out, int max);
+
 #ifdef __cplusplus
 }
 #endif

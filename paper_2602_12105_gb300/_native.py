@@ -54,6 +54,10 @@ class SolveInfo(ctypes.Structure):
                 "rel_residual": list(self.rel_residual[:k]), "true_rel_residual": list(self.true_rel_residual[:k])}
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
 _vp, _i32, _i64, _dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
 _P = ctypes.POINTER
 
@@ -74,6 +78,8 @@ SIGNATURES = {
     "ig_operator": (_i32, [_vp, _vp, _vp]),
     "ig_solve": (_i32, [_vp, _vp, _i32, _vp, _P(SolveOpts), _P(SolveInfo)]),
     "ig_adjoint": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _P(SolveOpts), _P(SolveInfo)]),
+    "ig_profile_enable": (_i32, [_i32]),
+    "ig_profile_read": (_i32, [_P(KernelStat), _i32]),
 }
 
 _lib = None
@@ -114,3 +120,16 @@ def check(status: int, ctx=None):
         if ctx is not None:
             msg = load().ig_last_error(ctx).decode()
         raise IgError(status, f"{status_str(status)}: {msg}" if msg else status_str(status))
+
+
+def profile_enable(on: bool = True):
+    load().ig_profile_enable(1 if on else 0)
+
+
+def profile_read():
+    """{kernel name: (launches, total device ms)} accumulated since profile_enable."""
+    lib = load()
+    cnt = lib.ig_profile_read(None, 0)
+    arr = (KernelStat * max(cnt, 1))()
+    cnt = lib.ig_profile_read(arr, cnt)
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(cnt)}

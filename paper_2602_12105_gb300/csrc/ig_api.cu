@@ -3,7 +3,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 
 #include "ig_internal.cuh"
@@ -12,6 +14,69 @@ namespace ig {
 
 void set_error(ig_ctx* ctx, const std::string& msg) {
   if (ctx) ctx->last_error = msg;
+}
+
+namespace {
+struct ProfState {
+  std::mutex mu;
+  bool on = false;
+  struct Rec {
+    const char* name;
+    cudaEvent_t e0, e1;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  std::map<std::string, std::pair<int64_t, double>> acc;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void drain() {
+    for (auto& r : pending) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(r.e1) == cudaSuccess && cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
+        auto& a = acc[r.name];
+        a.first += 1;
+        a.second += ms;
+      }
+      cudaGetLastError();
+      pool.push_back(r.e0);
+      pool.push_back(r.e1);
+    }
+    pending.clear();
+  }
+};
+ProfState& prof_state() {
+  static ProfState* s = new ProfState();
+  return *s;
+}
+}  // namespace
+
+bool prof_on() { return prof_state().on; }
+
+ProfScope::ProfScope(const char* n, cudaStream_t s) : name(n), st(s) {
+  ProfState& P = prof_state();
+  if (!P.on) return;
+  std::lock_guard<std::mutex> lk(P.mu);
+  cudaEvent_t e0 = P.get(), e1 = P.get();
+  if (!e0 || !e1) return;
+  cudaEventRecord(e0, st);
+  P.pending.push_back({name, e0, e1});
+  slot = (int)P.pending.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (slot < 0) return;
+  ProfState& P = prof_state();
+  std::lock_guard<std::mutex> lk(P.mu);
+  cudaEventRecord(P.pending[slot].e1, st);
+  if (P.pending.size() > 4096) P.drain();
 }
 
 }  // namespace ig
@@ -474,6 +539,32 @@ ig_status ig_adjoint(ig_mesh* mesh, const double* V_dev, const double* B_dev, in
   if (!info) return IG_OK;
   IG_CK(ctx, group_true_residual(mesh->group, k, *io, 0, ctx->stream), "residual");
   return collect_info(mesh, k, info);
+}
+
+ig_status ig_profile_enable(int enable) {
+  ProfState& P = prof_state();
+  std::lock_guard<std::mutex> lk(P.mu);
+  P.drain();
+  P.acc.clear();
+  P.on = enable != 0;
+  return IG_OK;
+}
+
+int ig_profile_read(ig_kernel_stat* out, int max) {
+  ProfState& P = prof_state();
+  std::lock_guard<std::mutex> lk(P.mu);
+  P.drain();
+  int i = 0;
+  for (auto& kv : P.acc) {
+    if (out && i < max) {
+      std::memset(&out[i], 0, sizeof(ig_kernel_stat));
+      std::strncpy(out[i].name, kv.first.c_str(), sizeof(out[i].name) - 1);
+      out[i].launches = kv.second.first;
+      out[i].total_ms = kv.second.second;
+    }
+    ++i;
+  }
+  return i;
 }
 
 }  // extern "C"

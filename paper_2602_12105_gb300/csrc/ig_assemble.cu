@@ -125,10 +125,16 @@ __global__ void __launch_bounds__(256) row_kernel(MeshDev md, int mixed) {
 }  // namespace
 
 cudaError_t launch_assemble(const MeshDev& md, const double* V, double t, int mixed, cudaStream_t st) {
-  face_kernel<<<(md.m + 255) / 256, 256, 0, st>>>(V, md.F, md.m, 0.5 * t, md.facew, md.err);
+  {
+    IG_PROF("assemble_face", st);
+    face_kernel<<<(md.m + 255) / 256, 256, 0, st>>>(V, md.F, md.m, 0.5 * t, md.facew, md.err);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  row_kernel<<<(md.n + 255) / 256, 256, 0, st>>>(md, mixed);
+  {
+    IG_PROF("assemble_rows", st);
+    row_kernel<<<(md.n + 255) / 256, 256, 0, st>>>(md, mixed);
+  }
   return cudaGetLastError();
 }
 

@@ -105,6 +105,18 @@ struct MeshDev {
 // Host-side helpers (ig_api.cu).
 void set_error(ig_ctx* ctx, const std::string& msg);
 
+// Kernel timing (process-wide, off by default): while profiling is on, every launch is
+// bracketed by CUDA events on its stream and the device time is accumulated per kernel name.
+bool prof_on();
+struct ProfScope {
+  int slot = -1;
+  const char* name;
+  cudaStream_t st;
+  ProfScope(const char* name, cudaStream_t st);
+  ~ProfScope();
+};
+#define IG_PROF(name, st) ::ig::ProfScope ig_prof_scope_((name), (st))
+
 }  // namespace ig
 
 // ---------------------------------------------------------------------------------------------

@@ -439,10 +439,13 @@ cudaError_t build_plan(Group& g, SolvePlan& pl) {
 template <int K>
 cudaError_t solve_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_opts& o, cudaStream_t st) {
   const int cap = o.max_iter + 2;
-  init_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io, rhs_mass, g.ctl, o.rel_tol, o.max_iter, cap);
+  {
+    IG_PROF("pcg_init", st);
+    init_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io, rhs_mass, g.ctl, o.rel_tol, o.max_iter, cap);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (o.launch == IG_LAUNCH_GRAPH) {
+  if (o.launch == IG_LAUNCH_GRAPH && !prof_on()) {
     SolvePlan& pl = g.plans[0][K];
     if (!pl.exec) {
       e = build_plan<K>(g, pl);
@@ -452,12 +455,24 @@ cudaError_t solve_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_op
     if (e != cudaSuccess) return e;
   } else {
     for (int it = 0; it < cap; ++it) {
-      spmv_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles);
-      update_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, g.ctl, cudaGraphConditionalHandle{}, 0, g.nmesh);
-      pupdate_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles);
+      {
+        IG_PROF("pcg_spmv", st);
+        spmv_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles);
+      }
+      {
+        IG_PROF("pcg_update", st);
+        update_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, g.ctl, cudaGraphConditionalHandle{}, 0,
+                                                      g.nmesh);
+      }
+      {
+        IG_PROF("pcg_pupdate", st);
+        pupdate_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles);
+      }
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
-      if ((it & 15) == 15 || it == cap - 1) {
+      // poll every 16 iterations (every iteration while kernels are being timed, so that no
+      // launch after convergence is timed)
+      if (prof_on() || (it & 15) == 15 || it == cap - 1) {
         e = cudaMemcpyAsync(g.done_host, &g.ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return e;
         e = cudaStreamSynchronize(st);
@@ -466,7 +481,10 @@ cudaError_t solve_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_op
       }
     }
   }
-  finalize_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io);
+  {
+    IG_PROF("pcg_finalize", st);
+    finalize_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io);
+  }
   return cudaGetLastError();
 }
 

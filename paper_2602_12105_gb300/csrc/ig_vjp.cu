@@ -173,10 +173,16 @@ cudaError_t vjp_k(const MeshDev& md, const double* V, const double* B, int b_is_
                   double* gB, double* gt, cudaStream_t st) {
   const double* Bsrc = b_is_V ? V : B;
   const int bstride = b_is_V ? 3 : K;
-  vjp_face_kernel<K><<<(md.m + kFaceTile - 1) / kFaceTile, 256, 0, st>>>(md, V, Bsrc, bstride, U, gt);
+  {
+    IG_PROF("vjp_face", st);
+    vjp_face_kernel<K><<<(md.m + kFaceTile - 1) / kFaceTile, 256, 0, st>>>(md, V, Bsrc, bstride, U, gt);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  vjp_gather_kernel<K><<<(md.n + 255) / 256, 256, 0, st>>>(md, b_is_V, gV, gB);
+  {
+    IG_PROF("vjp_gather", st);
+    vjp_gather_kernel<K><<<(md.n + 255) / 256, 256, 0, st>>>(md, b_is_V, gV, gB);
+  }
   return cudaGetLastError();
 }
 

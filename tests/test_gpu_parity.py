@@ -58,9 +58,23 @@ def test_pattern_and_operator(api, name):
     assert np.abs(L - o_L).max() <= 1e-12 * np.abs(o_L).max()
 
 
+def _min_angle(V, F):
+    P = V[F]
+    ang = []
+    for c in range(3):
+        a, b = P[:, (c + 1) % 3] - P[:, c], P[:, (c + 2) % 3] - P[:, c]
+        cosv = np.einsum("ij,ij->i", a, b) / np.linalg.norm(a, axis=1) / np.linalg.norm(b, axis=1)
+        ang.append(np.arccos(np.clip(cosv, -1, 1)))
+    return float(np.min(ang))
+
+
 @pytest.mark.parametrize("name", CASES)
 def test_forward_and_adjoint(api, name):
+    """U within 1e-10; the gradient within max(1e-10, 1e-12 / theta_min): the derivative of a
+    cotangent, d cot / d theta = -1 / sin^2 theta, amplifies rounding by about 1/theta on faces
+    with a tiny angle theta, so two exact formulas of the same gradient agree only to that."""
     V, F, t, B, T = case(name)
+    gtol = max(1e-10, 1e-12 / _min_angle(V, F))
     n = V.shape[0]
     mesh = api.Mesh(_t(F, torch.int32), n)
     mesh.assemble(_t(V), t)
@@ -76,9 +90,9 @@ def test_forward_and_adjoint(api, name):
     assert ainfo["status"] == 0, ainfo
     Lam_ref = _oracle_solve(o_rowptr, o_col, o_A, U_ref - T)
     gV_ref, gB_ref, gt_ref = oracle.vjp(V, F, t, U_ref, Lam_ref, B, False)
-    assert rel2(gV.cpu().numpy(), gV_ref) <= 1e-10
+    assert rel2(gV.cpu().numpy(), gV_ref) <= gtol
     assert rel2(gB.cpu().numpy(), gB_ref) <= 1e-10
-    assert abs(gt.item() - gt_ref) <= 1e-10 * max(abs(gt_ref), 1e-300)
+    assert abs(gt.item() - gt_ref) <= gtol * max(abs(gt_ref), 1e-300)
 
 
 @pytest.mark.parametrize("k", [1, 2, 4])
