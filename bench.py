@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--launch", default="graph", choices=["graph", "host"],
+                    help="graph: device-side solver loop (default); host: one launch per kernel")
+    ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel timing pass")
     return ap.parse_args()
 
 
@@ -184,7 +187,7 @@ def run_ours(args, rank, world, local_rank):
     B = torch.from_numpy(p.B).to(dev)
     T = torch.from_numpy(p.T).to(dev)
     U = torch.empty_like(B)
-    opts = api.make_opts(rel_tol=args.tol)
+    opts = api.make_opts(rel_tol=args.tol, launch=args.launch)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -230,12 +233,14 @@ def run_ours(args, rank, world, local_rank):
     value = world * args.steps / (total_ms / 1000.0)
 
     # per-kernel device times (CUDA events around each launch, host-launched loop)
-    _native.profile_enable(True)
-    for _ in range(3):
-        step()
-    torch.cuda.synchronize()
-    prof = _native.profile_read()
-    _native.profile_enable(False)
+    prof = {}
+    if not args.no_profile:
+        _native.profile_enable(True)
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        prof = _native.profile_read()
+        _native.profile_enable(False)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -279,7 +284,7 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernel
     its_f, its_a = finfo["iterations"], ainfo["iterations"]
-    dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
     hbm_peak, peak_kind = peaks()
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     fp64_peak_tflops = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12     # 2 FP64 FMA / clk / SM

@@ -100,6 +100,89 @@ __device__ __forceinline__ void load_row(const double* __restrict__ p, long row,
   }
 }
 
+// ------------------------------------------------------------------------------- last-CTA steps
+// The per-mesh scalar updates run on one thread of the last CTA of a reduction. They are kept
+// out of line (and count active columns explicitly) so that this bookkeeping is compiled on its
+// own, apart from the unrolled arithmetic of the kernels.
+__device__ __noinline__ void finish_init(SolveScal* s, int k, const double* acc, double tol, int max_iter) {
+  int nact = 0, bad = 0;
+  for (int c = 0; c < kMaxK; ++c) {
+    const double rz = c < k ? acc[c] : 0.0;
+    const double bb = c < k ? acc[k + c] : 0.0;
+    if (c < k && (!is_finite(bb) || !is_finite(rz))) bad = 1;
+    const int act = (c < k && positive_finite(bb)) ? 1 : 0;
+    s->rz[c] = rz;
+    s->bnorm2[c] = bb;
+    s->rhs2[c] = bb;
+    s->active[c] = act;
+    s->relres[c] = act ? 1.0 : 0.0;
+    s->alpha[c] = 0.0;
+    s->beta[c] = 0.0;
+    s->scale[c] = 1.0;
+    s->trueres[c] = -1.0;
+    nact += act;
+  }
+  s->k = k;
+  s->cnt[0] = 0u;
+  s->cnt[1] = 0u;
+  s->iter = 0;
+  s->refine = 0;
+  s->phase = 0;
+  s->tol = tol;
+  s->max_iter = max_iter;
+  s->status = bad ? IG_ERR_NONFINITE : IG_OK;
+  s->done = (bad != 0 || nact == 0) ? 1 : 0;
+}
+
+// alpha_c = rz_c / (p_c . q_c) for active columns.
+__device__ __noinline__ void finish_spmv(SolveScal* s, int k, const double* pq) {
+  for (int c = 0; c < k; ++c) {
+    if (s->active[c] == 0) {
+      s->alpha[c] = 0.0;
+    } else if (!positive_finite(pq[c])) {
+      s->alpha[c] = 0.0;
+      s->status = IG_ERR_NONFINITE;
+      s->done = 1;
+    } else {
+      s->alpha[c] = s->rz[c] / pq[c];
+    }
+  }
+}
+
+// Convergence test per column (recursive residual), beta_c = rz_new / rz, iteration count.
+__device__ __noinline__ void finish_update(SolveScal* s, int k, const double* acc) {
+  int nact = 0, bad = 0;
+  for (int c = 0; c < k; ++c) {
+    if (s->active[c] == 0) continue;
+    const double rzn = acc[c], rr = acc[k + c];
+    if (!is_finite(rzn) || !is_finite(rr)) {
+      bad = 1;
+      continue;
+    }
+    const double rel = sqrt(rr / s->bnorm2[c]);
+    s->relres[c] = rel;
+    if (rel <= s->tol) {
+      s->active[c] = 0;
+      s->beta[c] = 0.0;
+    } else {
+      s->beta[c] = rzn / s->rz[c];
+      s->rz[c] = rzn;
+      nact += 1;
+    }
+  }
+  const int it = s->iter + 1;
+  s->iter = it;
+  if (bad) {
+    s->status = IG_ERR_NONFINITE;
+    s->done = 1;
+  } else if (nact == 0) {
+    s->done = 1;
+  } else if (it >= s->max_iter) {
+    s->status = IG_ERR_NOT_CONVERGED;
+    s->done = 1;
+  }
+}
+
 // ------------------------------------------------------------------------------- init
 // rhs = M * in (rhs_mass) or in; x = 0; r = rhs; p = z = D^-1 r; per mesh: rz, ||rhs||^2.
 template <int K>
@@ -137,37 +220,8 @@ __global__ void __launch_bounds__(kBlock) init_kernel(const MeshDev* __restrict_
       }
     }
   }
-  if (reduce_tiles<2 * K>(acc, md.part, tl.y, md.ntiles, &md.s->cnt[2], sh) && threadIdx.x == 0) {
-    SolveScal* s = md.s;
-    int any = 0, bad = 0;
-    for (int c = 0; c < kMaxK; ++c) {
-      const bool in = c < K;
-      const double bb = in ? acc[K + c] : 0.0;
-      const double rz = in ? acc[c] : 0.0;
-      if (in && (!is_finite(bb) || !is_finite(rz))) bad = 1;
-      const int act = in && positive_finite(bb);
-      s->rz[c] = rz;
-      s->bnorm2[c] = bb;
-      s->rhs2[c] = bb;
-      s->alpha[c] = 0.0;
-      s->beta[c] = 0.0;
-      s->scale[c] = 1.0;
-      s->active[c] = act;
-      s->relres[c] = act ? 1.0 : 0.0;
-      s->trueres[c] = -1.0;
-      any |= act;
-    }
-    s->k = K;
-    s->cnt[0] = 0u;
-    s->cnt[1] = 0u;
-    s->iter = 0;
-    s->refine = 0;
-    s->phase = 0;
-    s->tol = tol;
-    s->max_iter = max_iter;
-    s->status = bad ? IG_ERR_NONFINITE : IG_OK;
-    s->done = (bad || !any) ? 1 : 0;
-  }
+  if (reduce_tiles<2 * K>(acc, md.part, tl.y, md.ntiles, &md.s->cnt[2], sh) && threadIdx.x == 0)
+    finish_init(md.s, K, acc, tol, max_iter);
 }
 
 // ------------------------------------------------------------------------------- spmv
@@ -209,21 +263,7 @@ __global__ void __launch_bounds__(kBlock) spmv_kernel(const MeshDev* __restrict_
       }
     }
   }
-  if (reduce_tiles<K>(pq, md.part, tl.y, md.ntiles, &s->cnt[0], sh) && threadIdx.x == 0) {
-    for (int c = 0; c < K; ++c) {
-      if (s->active[c]) {
-        if (!positive_finite(pq[c])) {
-          s->status = IG_ERR_NONFINITE;
-          s->done = 1;
-          s->alpha[c] = 0.0;
-        } else {
-          s->alpha[c] = s->rz[c] / pq[c];
-        }
-      } else {
-        s->alpha[c] = 0.0;
-      }
-    }
-  }
+  if (reduce_tiles<K>(pq, md.part, tl.y, md.ntiles, &s->cnt[0], sh) && threadIdx.x == 0) finish_spmv(s, K, pq);
 }
 
 // ------------------------------------------------------------------------------- update
@@ -261,38 +301,8 @@ __global__ void __launch_bounds__(kBlock) update_kernel(const MeshDev* __restric
         }
       }
     }
-    if (reduce_tiles<2 * K>(acc, md.part, tl.y, md.ntiles, &s->cnt[1], sh) && threadIdx.x == 0) {
-      int any = 0, bad = 0;
-      for (int c = 0; c < K; ++c) {
-        if (!s->active[c]) continue;
-        const double rzn = acc[c], rr = acc[K + c];
-        if (!is_finite(rzn) || !is_finite(rr)) {
-          bad = 1;
-          continue;
-        }
-        const double rel = sqrt(rr / s->bnorm2[c]);
-        s->relres[c] = rel;
-        if (rel <= s->tol) {
-          s->active[c] = 0;
-          s->beta[c] = 0.0;
-        } else {
-          s->beta[c] = rzn / s->rz[c];
-          s->rz[c] = rzn;
-          any = 1;
-        }
-      }
-      const int it = s->iter + 1;
-      s->iter = it;
-      if (bad) {
-        s->status = IG_ERR_NONFINITE;
-        s->done = 1;
-      } else if (!any) {
-        s->done = 1;
-      } else if (it >= s->max_iter) {
-        s->status = IG_ERR_NOT_CONVERGED;
-        s->done = 1;
-      }
-    }
+    if (reduce_tiles<2 * K>(acc, md.part, tl.y, md.ntiles, &s->cnt[1], sh) && threadIdx.x == 0)
+      finish_update(s, K, acc);
   }
   // Loop control: the last CTA of the launch decides whether the device-side loop goes on.
   __syncthreads();
