@@ -156,6 +156,42 @@ ig_status ig_adjoint(ig_mesh* mesh, const double* V_dev, const double* B_dev, in
                      const double* G_dev, int k, double* gV_dev, double* gB_dev, double* gt_dev,
                      const ig_solve_opts* opts, ig_solve_info* info);
 
+/* ---- allocation-free solve ----------------------------------------------------------------- */
+
+/* Largest number of rows ig_solve_csr_noalloc accepts. */
+#define IG_NOALLOC_MAX_ROWS 65536
+
+/* Solve A X = M B (or A X = B when M_dev is NULL) for a CSR operator the caller already holds,
+ * by the same Jacobi-preconditioned conjugate gradients as ig_solve, WITHOUT ALLOCATING: no
+ * cudaMalloc, cudaFree, graph or other allocating call is made. It is meant for callers that
+ * cannot allocate device memory -- a host running under a fixed memory plan or pre-reserved
+ * arena that forbids new device allocations after start-up, or a process whose device memory
+ * belongs to another framework's allocator. The paper has no counterpart to this call; it is a
+ * service of this library.
+ *
+ * Inputs (device pointers on the CURRENT CUDA device): rowptr_dev [n+1] and col_dev [nnz] int32
+ * (CSR, each row holding its diagonal), Aval_dev [nnz] double (symmetric positive definite
+ * values, e.g. from ig_operator), M_dev [n] double or NULL, B_dev [n][k] double. Output: U_dev
+ * [n][k] double (must not overlap B). 1 <= k <= 4, 1 <= n <= IG_NOALLOC_MAX_ROWS. Work goes on
+ * cuda_stream (a cudaStream_t; NULL = legacy default stream); the call returns after the
+ * solve's loop has finished (it waits for a 4-byte flag every 16 iterations). opts may be NULL
+ * (defaults; the launch mode is always one launch per kernel). info, if given, is filled as by
+ * ig_solve (status IG_ERR_INVALID_ARG there means a missing or non-positive diagonal).
+ *
+ * Scratch: all workspace lives in one static device array of about 9 MB, which every GPU that
+ * loads this library holds until the process exits. The first call on a device looks up that
+ * array's device address (once per device), so make the first call outside any stream capture.
+ * Every call reuses the same array and overwrites what the previous call left there (the call
+ * clears its counters itself); two calls that overlap on the GPU -- on different streams or
+ * from different host threads -- race on the array and give wrong results.
+ *
+ * Errors: IG_ERR_INVALID_ARG for a NULL pointer, n > IG_NOALLOC_MAX_ROWS, nnz < n, k outside
+ * [1, 4], overlapping B and U or bad options; IG_ERR_CUDA for a failed launch; with info,
+ * IG_ERR_NOT_CONVERGED / IG_ERR_NONFINITE as for ig_solve. */
+ig_status ig_solve_csr_noalloc(const int32_t* rowptr_dev, const int32_t* col_dev, const double* Aval_dev,
+                               const double* M_dev, int64_t n, int64_t nnz, const double* B_dev, int k,
+                               double* U_dev, void* cuda_stream, const ig_solve_opts* opts, ig_solve_info* info);
+
 /* ---- kernel timing (tracing) -------------------------------------------------------------- */
 
 /* Per-kernel device time accumulated while profiling is on. */

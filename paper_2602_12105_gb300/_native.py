@@ -78,6 +78,8 @@ SIGNATURES = {
     "ig_operator": (_i32, [_vp, _vp, _vp]),
     "ig_solve": (_i32, [_vp, _vp, _i32, _vp, _P(SolveOpts), _P(SolveInfo)]),
     "ig_adjoint": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _P(SolveOpts), _P(SolveInfo)]),
+    "ig_solve_csr_noalloc": (_i32, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, _i32, _vp, _vp, _P(SolveOpts),
+                                     _P(SolveInfo)]),
     "ig_profile_enable": (_i32, [_i32]),
     "ig_profile_read": (_i32, [_P(KernelStat), _i32]),
 }

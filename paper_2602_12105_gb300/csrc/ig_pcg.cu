@@ -18,6 +18,10 @@
 //
 // FP64 instructions are the scarce resource of this GPU (2 FP64 FMA per clock per SM). Each thread
 // handles kRowsPerThread rows so the block reductions, which cost FP64 adds, are amortised.
+#include <cstring>
+#include <mutex>
+#include <new>
+
 #include "ig_internal.cuh"
 
 namespace ig {
@@ -564,3 +568,150 @@ cudaError_t group_true_residual(Group& g, int k, const IoTable& io, int rhs_mass
 }
 
 }  // namespace ig
+
+// =============================================================================================
+// Allocation-free solve on a caller-provided CSR operator.
+//
+// Some callers cannot allocate device memory at all: code that runs under a fixed memory plan
+// or a pre-reserved arena (an embedded or real-time host that forbids cudaMalloc after start-up,
+// a process whose allocator belongs to another framework), or code that must not add new
+// allocations between two points of a stream. ig_solve_csr_noalloc serves them: it runs the same
+// Jacobi-PCG kernels as ig_solve, with every piece of solver workspace (vectors, partial sums,
+// loop state, the preconditioner) in one file-scope device array of fixed size, and the caller
+// passes only inputs and outputs.
+namespace ig {
+namespace {
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr int kNoAllocMaxRows = IG_NOALLOC_MAX_ROWS;
+constexpr int kNoAllocMaxTiles = (kNoAllocMaxRows + kTileRows - 1) / kTileRows;
+constexpr size_t kNaMd = 0;
+constexpr size_t kNaTiles = align256(kNaMd + sizeof(MeshDev));
+constexpr size_t kNaCtl = align256(kNaTiles + sizeof(int2) * kNoAllocMaxTiles);
+constexpr size_t kNaScal = align256(kNaCtl + sizeof(LoopCtl));
+constexpr size_t kNaErr = align256(kNaScal + sizeof(SolveScal));
+constexpr size_t kNaPart = align256(kNaErr + sizeof(int));
+constexpr size_t kNaDinv = align256(kNaPart + sizeof(double) * kPartStride * kNoAllocMaxTiles);
+constexpr size_t kNaVec = sizeof(double) * kMaxK * kNoAllocMaxRows;
+constexpr size_t kNaX = align256(kNaDinv + sizeof(double) * kNoAllocMaxRows);
+constexpr size_t kNaR = align256(kNaX + kNaVec);
+constexpr size_t kNaP = align256(kNaR + kNaVec);
+constexpr size_t kNaQ = align256(kNaP + kNaVec);
+constexpr size_t kNoAllocBytes = align256(kNaQ + kNaVec);
+
+// Per-device base address of the scratch array, looked up once per device.
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[64] = {};
+
+// Preconditioner from the operator's diagonal, solver state cleared, tile table written.
+__global__ void __launch_bounds__(256) noalloc_setup_kernel(MeshDev md, MeshDev* md_out, int2* tiles, int ntiles,
+                                                            LoopCtl* ctl, SolveScal* s) {
+  const long row = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row < md.n) {
+    double d = 0.0;
+    for (int e = md.rowptr[row]; e < md.rowptr[row + 1]; ++e)
+      if (md.col[e] == row) d = md.A[e];
+    if (!positive_finite(d)) atomicOr(md.err, kErrDegenerate);
+    md.Dinv[row] = positive_finite(d) ? 1.0 / d : 0.0;
+#pragma unroll
+    for (int c = 0; c < kMaxK; ++c) md.p[row * kMaxK + c] = 0.0;
+  }
+  if (blockIdx.x == 0) {
+    if (threadIdx.x < ntiles) tiles[threadIdx.x] = make_int2(0, threadIdx.x);
+    if (threadIdx.x == 0) {
+      *md_out = md;
+      *ctl = LoopCtl{};
+      *s = SolveScal{};
+    }
+  }
+}
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+}  // namespace ig
+
+extern "C" ig_status ig_solve_csr_noalloc(const int32_t* rowptr_dev, const int32_t* col_dev, const double* Aval_dev,
+                                          const double* M_dev, int64_t n, int64_t nnz, const double* B_dev, int k,
+                                          double* U_dev, void* cuda_stream, const ig_solve_opts* opts,
+                                          ig_solve_info* info) {
+  using namespace ig;
+  if (!rowptr_dev || !col_dev || !Aval_dev || !B_dev || !U_dev) return IG_ERR_INVALID_ARG;
+  if (n < 1 || n > kNoAllocMaxRows || nnz < n || nnz > (int64_t)INT32_MAX) return IG_ERR_INVALID_ARG;
+  if (k < 1 || k > kMaxK || (const void*)B_dev == (const void*)U_dev) return IG_ERR_INVALID_ARG;
+  ig_solve_opts o;
+  ig_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.rel_tol >= 0.0) || !(o.rel_tol < 1e300) || o.max_iter < 1 || o.max_iter > 100000000)
+    return IG_ERR_INVALID_ARG;
+  o.launch = IG_LAUNCH_HOST;  // no graph objects are created on this path
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return IG_ERR_CUDA;
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return IG_ERR_CUDA;
+      }
+      g_noalloc_base[dev] = p;
+    }
+    base = static_cast<unsigned char*>(g_noalloc_base[dev]);
+  }
+  MeshDev md{};
+  md.n = (int)n;
+  md.nnz = (int)nnz;
+  md.ntiles = (int)((n + kTileRows - 1) / kTileRows);
+  md.k = k;
+  md.rowptr = rowptr_dev;
+  md.col = col_dev;
+  md.A = const_cast<double*>(Aval_dev);
+  md.M = const_cast<double*>(M_dev);
+  md.Dinv = reinterpret_cast<double*>(base + kNaDinv);
+  md.x = reinterpret_cast<double*>(base + kNaX);
+  md.r = reinterpret_cast<double*>(base + kNaR);
+  md.p = reinterpret_cast<double*>(base + kNaP);
+  md.q = reinterpret_cast<double*>(base + kNaQ);
+  md.part = reinterpret_cast<double*>(base + kNaPart);
+  md.s = reinterpret_cast<SolveScal*>(base + kNaScal);
+  md.err = reinterpret_cast<int*>(base + kNaErr);
+  Group g;
+  g.nmesh = 1;
+  g.ntiles = md.ntiles;
+  g.mds = reinterpret_cast<MeshDev*>(base + kNaMd);
+  g.tiles = reinterpret_cast<int2*>(base + kNaTiles);
+  g.ctl = reinterpret_cast<LoopCtl*>(base + kNaCtl);
+  int done_word = 0;
+  g.done_host = &done_word;
+  if (cudaMemsetAsync(md.err, 0, sizeof(int), st) != cudaSuccess) return IG_ERR_CUDA;
+  noalloc_setup_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(md, g.mds, g.tiles, g.ntiles, g.ctl, md.s);
+  if (cudaGetLastError() != cudaSuccess) return IG_ERR_CUDA;
+  IoTable* io = new (std::nothrow) IoTable;
+  if (!io) return IG_ERR_OOM;
+  io->in[0] = B_dev;
+  io->out[0] = U_dev;
+  cudaError_t e = group_solve(g, k, 0, *io, M_dev ? 1 : 0, o, st);
+  if (e == cudaSuccess && info) e = group_true_residual(g, k, *io, M_dev ? 1 : 0, st);
+  delete io;
+  if (e != cudaSuccess) return IG_ERR_CUDA;
+  if (!info) return IG_OK;
+  SolveScal s;
+  int bits = 0;
+  if (cudaMemcpyAsync(&s, md.s, sizeof(SolveScal), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&bits, md.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return IG_ERR_CUDA;
+  std::memset(info, 0, sizeof(*info));
+  info->status = bits ? IG_ERR_INVALID_ARG : s.status;
+  info->k = k;
+  info->iterations = s.iter;
+  for (int c = 0; c < k; ++c) {
+    info->rel_residual[c] = s.relres[c];
+    info->true_rel_residual[c] = s.trueres[c];
+  }
+  return (ig_status)info->status;
+}
