@@ -387,6 +387,7 @@ ig_status ig_mesh_upload(ig_ctx* ctx, const int32_t* F_dev, int64_t m, int64_t n
   UP_CK(mesh_alloc(M, &md.r, nv), "alloc");
   UP_CK(mesh_alloc(M, &md.p, nv), "alloc");
   UP_CK(mesh_alloc(M, &md.q, nv), "alloc");
+  md.rhs = md.q;  // the FP64 q vector is unused in mixed precision, where it keeps the rhs
   UP_CK(mesh_alloc(M, &md.lam, nv), "alloc");
   UP_CK(mesh_alloc(M, &md.gface, 9 * (size_t)m), "alloc");
   UP_CK(mesh_alloc(M, &md.part, npart), "alloc");

@@ -52,16 +52,27 @@ struct SolveScal {
   double relres[kMaxK];  // last relative residual seen by the stopping test
   double trueres[kMaxK]; // FP64 recomputed relative residual (filled on request)
   double scale[kMaxK];   // mixed precision: norm of the residual the inner system was scaled by
-  int active[kMaxK];
+  int active[kMaxK];     // columns still iterating (the inner FP32 system in mixed precision)
+  int active64[kMaxK];   // mixed precision: columns whose FP64 residual is still above tol
+  double relres_inner[kMaxK];
+  int inner_iter;        // mixed precision: iterations of the current inner solve
+  int inner_cap;         // mixed precision: cap on iterations of one inner solve
   int k;
   int done;              // 1 once every column converged, failed or hit the cap
   int status;            // ig_status of this solve
   int iter;              // conjugate-gradient iterations so far
   int refine;            // mixed precision: refinements so far
-  int phase;             // mixed precision: 0 inner iterations, 1 refinement pending
+  int phase;             // mixed precision: kPhaseInner / kPhaseApply / kPhaseRestart
   int max_iter, max_refine;
   double tol, inner_tol;
   unsigned int cnt[4];   // last-CTA counters (spmv, update, init/residual, vjp)
+};
+
+// Phases of a mixed-precision solve (per mesh).
+enum : int {
+  kPhaseInner = 0,    // FP32 conjugate-gradient iterations on A32 d = r32
+  kPhaseApply = 1,    // x64 += scale * d, then the next spmv recomputes r64 = rhs - A64 x64
+  kPhaseRestart = 2,  // r32 = r64 / scale, d = 0, new inner solve
 };
 
 // Everything a kernel needs about one mesh (plain device pointers, passed in device arrays so
@@ -92,6 +103,7 @@ struct MeshDev {
   float* r32;
   float* p32;
   float* q32;
+  double* rhs;             // mixed precision: the outer right-hand side, kept for residuals
   // right-hand side of the outer system (caller buffer for the forward solve), and its mode
   const double* rhs_src;
   int rhs_mass;            // 1: rhs = M * rhs_src, 0: rhs = rhs_src
@@ -172,6 +184,8 @@ void group_destroy(Group& g);
 cudaError_t group_solve(Group& g, int k, int mixed, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
                         cudaStream_t st);
 cudaError_t group_true_residual(Group& g, int k, const IoTable& io, int rhs_mass, cudaStream_t st);
+cudaError_t group_solve_mixed(Group& g, int k, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
+                              cudaStream_t st);
 
 }  // namespace ig
 

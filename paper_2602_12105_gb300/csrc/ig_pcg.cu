@@ -22,87 +22,11 @@
 #include <mutex>
 #include <new>
 
-#include "ig_internal.cuh"
+#include "ig_device.cuh"
 
 namespace ig {
 
 namespace {
-
-template <int K>
-struct KP {
-  static constexpr int v = (K == 3) ? 4 : K;
-};
-
-__device__ __forceinline__ bool positive_finite(double x) {
-  const long long b = __double_as_longlong(x);
-  return b > 0 && (b & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
-}
-__device__ __forceinline__ bool is_finite(double x) {
-  return (__double_as_longlong(x) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
-}
-
-// Sum v[0..NV) over the CTA; thread 0 receives the totals. sh holds NV*kBlock doubles.
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
-#pragma unroll
-  for (int i = 0; i < NV; ++i) sh[i * kBlock + threadIdx.x] = v[i];
-  __syncthreads();
-  if (threadIdx.x < 32) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      double a = sh[i * kBlock + threadIdx.x];
-#pragma unroll
-      for (int w = 1; w < kBlock / 32; ++w) a += sh[i * kBlock + threadIdx.x + 32 * w];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      v[i] = a;
-    }
-  }
-  __syncthreads();
-}
-
-// Block-sum v, publish the tile's partials, and return true in the last CTA of the mesh, whose
-// thread 0 then holds the mesh totals (partials added in tile order, so the result does not
-// depend on which CTA finished last).
-template <int NV>
-__device__ __forceinline__ bool reduce_tiles(double (&v)[NV], double* part, int tile, int ntiles, unsigned int* cnt,
-                                             double* sh) {
-  __shared__ int s_last;
-  block_sum<NV>(v, sh);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) part[tile * kPartStride + i] = v[i];
-    __threadfence();
-    const unsigned prev = atomicAdd(cnt, 1u);
-    s_last = (prev == (unsigned)ntiles - 1u);
-  }
-  __syncthreads();
-  if (!s_last) return false;
-  __threadfence();
-#pragma unroll
-  for (int i = 0; i < NV; ++i) v[i] = 0.0;
-  for (int t = threadIdx.x; t < ntiles; t += kBlock)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] += __ldcg(part + t * kPartStride + i);
-  block_sum<NV>(v, sh);
-  if (threadIdx.x == 0) *cnt = 0u;
-  return true;
-}
-
-template <int K>
-__device__ __forceinline__ void load_row(const double* __restrict__ p, long row, double (&v)[K]) {
-  if constexpr (K == 3 || K == 4) {
-    const double2* q = reinterpret_cast<const double2*>(p + row * KP<K>::v);
-    const double2 a = q[0], b = q[1];
-    v[0] = a.x; v[1] = a.y; v[2] = b.x;
-    if constexpr (K == 4) v[3] = b.y;
-  } else if constexpr (K == 2) {
-    const double2 a = reinterpret_cast<const double2*>(p + row * 2)[0];
-    v[0] = a.x; v[1] = a.y;
-  } else {
-    v[0] = p[row];
-  }
-}
 
 // ------------------------------------------------------------------------------- last-CTA steps
 // The per-mesh scalar updates run on one thread of the last CTA of a reduction. They are kept
@@ -136,21 +60,6 @@ __device__ __noinline__ void finish_init(SolveScal* s, int k, const double* acc,
   s->max_iter = max_iter;
   s->status = bad ? IG_ERR_NONFINITE : IG_OK;
   s->done = (bad != 0 || nact == 0) ? 1 : 0;
-}
-
-// alpha_c = rz_c / (p_c . q_c) for active columns.
-__device__ __noinline__ void finish_spmv(SolveScal* s, int k, const double* pq) {
-  for (int c = 0; c < k; ++c) {
-    if (s->active[c] == 0) {
-      s->alpha[c] = 0.0;
-    } else if (!positive_finite(pq[c])) {
-      s->alpha[c] = 0.0;
-      s->status = IG_ERR_NONFINITE;
-      s->done = 1;
-    } else {
-      s->alpha[c] = s->rz[c] / pq[c];
-    }
-  }
 }
 
 // Convergence test per column (recursive residual), beta_c = rz_new / rz, iteration count.
@@ -308,24 +217,7 @@ __global__ void __launch_bounds__(kBlock) update_kernel(const MeshDev* __restric
     if (reduce_tiles<2 * K>(acc, md.part, tl.y, md.ntiles, &s->cnt[1], sh) && threadIdx.x == 0)
       finish_update(s, K, acc);
   }
-  // Loop control: the last CTA of the launch decides whether the device-side loop goes on.
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned prev = atomicAdd(&ctl->cnt, 1u);
-    if (prev == gridDim.x - 1u) {
-      __threadfence();
-      int all = 1;
-      for (int i = 0; i < nmesh; ++i) all &= (__ldcg(&mds[i].s->done) != 0);
-      const int it = ctl->iter + 1;
-      ctl->iter = it;
-      if (all || it >= ctl->cap) {
-        ctl->all_done = 1;
-        if (use_graph) cudaGraphSetConditional(handle, 0u);
-      }
-      ctl->cnt = 0u;
-    }
-  }
+  loop_control(mds, ctl, handle, use_graph, nmesh);
 }
 
 // ------------------------------------------------------------------------------- pupdate
@@ -348,23 +240,6 @@ __global__ void __launch_bounds__(kBlock) pupdate_kernel(const MeshDev* __restri
       load_row<K>(md.p, row, pi);
 #pragma unroll
       for (int c = 0; c < K; ++c) md.p[row * KP<K>::v + c] = fma(beta[c], pi[c], dinv * md.r[row * K + c]);
-    }
-  }
-}
-
-// ------------------------------------------------------------------------------- finalize
-template <int K>
-__global__ void __launch_bounds__(kBlock) finalize_kernel(const MeshDev* __restrict__ mds,
-                                                          const int2* __restrict__ tiles, IoTable io) {
-  const int2 tl = tiles[blockIdx.x];
-  const MeshDev& md = mds[tl.x];
-  double* __restrict__ out = io.out[tl.x];
-#pragma unroll
-  for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
-    if (row < md.n) {
-#pragma unroll
-      for (int c = 0; c < K; ++c) out[row * K + c] = md.x[row * K + c];
     }
   }
 }
@@ -546,7 +421,7 @@ void group_destroy(Group& g) {
 
 cudaError_t group_solve(Group& g, int k, int mixed, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
                         cudaStream_t st) {
-  (void)mixed;
+  if (mixed) return group_solve_mixed(g, k, io, rhs_mass, o, st);
   switch (k) {
     case 1: return solve_k<1>(g, io, rhs_mass, o, st);
     case 2: return solve_k<2>(g, io, rhs_mass, o, st);

@@ -1,0 +1,480 @@
+// ig_pcg_mixed.cu -- mixed-precision solve of A X = RHS (forward and adjoint systems of §7.1 /
+// §5.2) to an FP64 relative residual: FP32 Jacobi-PCG on the FP32 copy of A inside an FP64
+// iterative refinement whose residuals use the FP64 operator.
+//
+//   x64 = 0, r64 = rhs
+//   repeat:  r32 = r64 / ||r64||            (per column; unit-norm inner right-hand side)
+//            solve A32 d = r32 by FP32 Jacobi-PCG to inner_tol (dot products summed in FP64)
+//            x64 += ||r64|| d
+//            r64 = rhs - A64 x64 in FP64; stop when ||r64|| / ||rhs|| <= rel_tol
+//
+// It runs inside the same three-kernel iteration as the FP64 solver, with a per-mesh phase:
+//   Inner   : spmv q32 = A32 p32 | update x32, r32, (r.z, r.r) | pupdate p32
+//   Apply   : set by update when the inner solve converged; pupdate adds ||r64|| d into x64
+//   (next)  : spmv computes r64 = rhs - A64 x64 and its norms (the refinement residual)
+//   Restart : update forms r32 = r64 / ||r64||, d = 0; pupdate sets p32 = z32
+// so a refinement costs one iteration slot whose SpMV runs in FP64, and no extra launches.
+// FP64 arithmetic is used only for the residual SpMV, the x64 update and the reductions.
+#include "ig_device.cuh"
+
+namespace ig {
+
+namespace {
+
+template <int K>
+struct KPm {
+  static constexpr int v = (K == 3) ? 4 : K;
+};
+
+// ------------------------------------------------------------------------------- bookkeeping
+__device__ __noinline__ void finish_init_mixed(SolveScal* s, int k, const double* acc, double tol, double inner_tol,
+                                               int max_iter, int max_refine) {
+  int nact = 0, bad = 0;
+  for (int c = 0; c < kMaxK; ++c) {
+    const double bb = c < k ? acc[c] : 0.0;
+    if (c < k && !is_finite(bb)) bad = 1;
+    const int act = (c < k && positive_finite(bb)) ? 1 : 0;
+    s->rhs2[c] = bb;
+    s->bnorm2[c] = 0.0;
+    s->active64[c] = act;
+    s->active[c] = 0;
+    s->relres[c] = act ? 1.0 : 0.0;
+    s->relres_inner[c] = 0.0;
+    s->scale[c] = act ? sqrt(bb) : 1.0;
+    s->rz[c] = 0.0;
+    s->alpha[c] = 0.0;
+    s->beta[c] = 0.0;
+    s->trueres[c] = -1.0;
+    nact += act;
+  }
+  s->k = k;
+  s->cnt[0] = 0u;
+  s->cnt[1] = 0u;
+  s->iter = 0;
+  s->refine = 0;
+  s->inner_iter = 0;
+  s->inner_cap = max_iter < 4000 ? max_iter : 4000;
+  s->phase = kPhaseRestart;
+  s->tol = tol;
+  s->inner_tol = inner_tol;
+  s->max_iter = max_iter;
+  s->max_refine = max_refine;
+  s->status = bad ? IG_ERR_NONFINITE : IG_OK;
+  s->done = (bad || nact == 0) ? 1 : 0;
+}
+
+// After r64 = rhs - A64 x64: FP64 convergence test per column, the scale of the next inner
+// right-hand side, and the refinement cap.
+__device__ __noinline__ void finish_residual(SolveScal* s, int k, const double* res2) {
+  int nact = 0, bad = 0;
+  s->refine = s->refine + 1;
+  for (int c = 0; c < k; ++c) {
+    if (s->active64[c] == 0) continue;
+    if (!is_finite(res2[c])) {
+      bad = 1;
+      continue;
+    }
+    const double rel = sqrt(res2[c] / s->rhs2[c]);
+    s->relres[c] = rel;
+    if (rel <= s->tol || !positive_finite(res2[c])) {
+      s->active64[c] = 0;
+    } else {
+      s->scale[c] = sqrt(res2[c]);
+      nact += 1;
+    }
+  }
+  if (bad) {
+    s->status = IG_ERR_NONFINITE;
+    s->done = 1;
+  } else if (nact == 0) {
+    s->done = 1;
+  } else if (s->refine >= s->max_refine || s->iter >= s->max_iter) {
+    s->status = IG_ERR_NOT_CONVERGED;
+    s->done = 1;
+  } else {
+    s->phase = kPhaseRestart;
+  }
+}
+
+// After forming r32 = r64 / scale: start a new inner solve.
+__device__ __noinline__ void finish_restart(SolveScal* s, int k, const double* acc) {
+  int nact = 0;
+  for (int c = 0; c < k; ++c) {
+    const int act = (s->active64[c] && positive_finite(acc[k + c])) ? 1 : 0;
+    s->active[c] = act;
+    s->rz[c] = acc[c];
+    s->bnorm2[c] = acc[k + c];
+    s->alpha[c] = 0.0;
+    s->beta[c] = 0.0;
+    s->relres_inner[c] = act ? 1.0 : 0.0;
+    nact += act;
+  }
+  s->inner_iter = 0;
+  s->phase = nact ? kPhaseInner : kPhaseApply;
+}
+
+// Inner FP32 iteration: inner convergence test, beta, switch to Apply when the inner solve is done.
+__device__ __noinline__ void finish_update_mixed(SolveScal* s, int k, const double* acc) {
+  int nact = 0, bad = 0;
+  for (int c = 0; c < k; ++c) {
+    if (s->active[c] == 0) continue;
+    const double rzn = acc[c], rr = acc[k + c];
+    if (!is_finite(rzn) || !is_finite(rr)) {
+      bad = 1;
+      continue;
+    }
+    const double rel = sqrt(rr / s->bnorm2[c]);
+    s->relres_inner[c] = rel;
+    if (rel <= s->inner_tol || !positive_finite(rzn)) {
+      s->active[c] = 0;
+      s->beta[c] = 0.0;
+    } else {
+      s->beta[c] = rzn / s->rz[c];
+      s->rz[c] = rzn;
+      nact += 1;
+    }
+  }
+  s->iter = s->iter + 1;
+  s->inner_iter = s->inner_iter + 1;
+  if (bad) {
+    s->status = IG_ERR_NONFINITE;
+    s->done = 1;
+  } else if (nact == 0 || s->inner_iter >= s->inner_cap || s->iter >= s->max_iter) {
+    s->phase = kPhaseApply;
+  }
+}
+
+// ------------------------------------------------------------------------------- kernels
+template <int K>
+__global__ void __launch_bounds__(kBlock) init_mixed_kernel(const MeshDev* __restrict__ mds,
+                                                            const int2* __restrict__ tiles, IoTable io, int rhs_mass,
+                                                            LoopCtl* ctl, double tol, double inner_tol, int max_iter,
+                                                            int max_refine, int cap) {
+  __shared__ double sh[K * kBlock];
+  const int2 tl = tiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->cnt = 0u;
+    ctl->iter = 0;
+    ctl->all_done = 0;
+    ctl->cap = cap;
+  }
+  const double* __restrict__ src = io.in[tl.x];
+  double acc[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) acc[c] = 0.0;
+#pragma unroll
+  for (int rr = 0; rr < kRowsPerThread; ++rr) {
+    const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
+    if (row < md.n) {
+      const double mass = rhs_mass ? md.M[row] : 1.0;
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        const double b = rhs_mass ? mass * src[row * K + c] : src[row * K + c];
+        md.rhs[row * K + c] = b;
+        md.r[row * K + c] = b;
+        md.x[row * K + c] = 0.0;
+        acc[c] = fma(b, b, acc[c]);
+      }
+    }
+  }
+  if (reduce_tiles<K>(acc, md.part, tl.y, md.ntiles, &md.s->cnt[2], sh) && threadIdx.x == 0)
+    finish_init_mixed(md.s, K, acc, tol, inner_tol, max_iter, max_refine);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) spmv_mixed_kernel(const MeshDev* __restrict__ mds,
+                                                            const int2* __restrict__ tiles) {
+  __shared__ double sh[K * kBlock];
+  const int2 tl = tiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  SolveScal* s = md.s;
+  if (__ldcg(&s->done)) return;
+  const int phase = __ldcg(&s->phase);
+  if (phase == kPhaseRestart) return;
+  const int* __restrict__ rowptr = md.rowptr;
+  const int* __restrict__ col = md.col;
+  double acc[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) acc[c] = 0.0;
+  if (phase == kPhaseInner) {
+    const float* __restrict__ A = md.A32;
+    const float* __restrict__ p = md.p32;
+    float pq[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) pq[c] = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < kRowsPerThread; ++rr) {
+      const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
+      if (row < md.n) {
+        const int e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
+        float q[K];
+#pragma unroll
+        for (int c = 0; c < K; ++c) q[c] = 0.f;
+        for (int e = e0; e < e1; ++e) {
+          const float a = __ldg(A + e);
+          float pj[K];
+          load_row32<K>(p, __ldg(col + e), pj);
+#pragma unroll
+          for (int c = 0; c < K; ++c) q[c] = fmaf(a, pj[c], q[c]);
+        }
+        float pi[K];
+        load_row32<K>(p, row, pi);
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+          md.q32[row * K + c] = q[c];
+          pq[c] = fmaf(pi[c], q[c], pq[c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < K; ++c) acc[c] = (double)pq[c];
+    if (reduce_tiles<K>(acc, md.part, tl.y, md.ntiles, &s->cnt[0], sh) && threadIdx.x == 0) finish_spmv(s, K, acc);
+  } else {
+    // Apply: r64 = rhs - A64 x64 in FP64 and its squared norms
+    const double* __restrict__ A = md.A;
+    const double* __restrict__ x = md.x;
+#pragma unroll
+    for (int rr = 0; rr < kRowsPerThread; ++rr) {
+      const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
+      if (row < md.n) {
+        const int e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
+        double ax[K];
+#pragma unroll
+        for (int c = 0; c < K; ++c) ax[c] = 0.0;
+        for (int e = e0; e < e1; ++e) {
+          const double a = __ldg(A + e);
+          const long j = __ldg(col + e);
+#pragma unroll
+          for (int c = 0; c < K; ++c) ax[c] = fma(a, x[j * K + c], ax[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+          const double res = md.rhs[row * K + c] - ax[c];
+          md.r[row * K + c] = res;
+          acc[c] = fma(res, res, acc[c]);
+        }
+      }
+    }
+    if (reduce_tiles<K>(acc, md.part, tl.y, md.ntiles, &s->cnt[0], sh) && threadIdx.x == 0)
+      finish_residual(s, K, acc);
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) update_mixed_kernel(const MeshDev* __restrict__ mds,
+                                                              const int2* __restrict__ tiles, LoopCtl* ctl,
+                                                              cudaGraphConditionalHandle handle, int use_graph,
+                                                              int nmesh) {
+  __shared__ double sh[2 * K * kBlock];
+  const int2 tl = tiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  SolveScal* s = md.s;
+  const int phase = __ldcg(&s->phase);
+  if (!__ldcg(&s->done) && phase != kPhaseApply) {
+    float rz[K], rr2[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) rz[c] = rr2[c] = 0.f;
+    if (phase == kPhaseInner) {
+      float alpha[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) alpha[c] = (float)__ldcg(&s->alpha[c]);
+#pragma unroll
+      for (int rr = 0; rr < kRowsPerThread; ++rr) {
+        const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
+        if (row < md.n) {
+          const float dinv = md.Dinv32[row];
+          float pi[K];
+          load_row32<K>(md.p32, row, pi);
+#pragma unroll
+          for (int c = 0; c < K; ++c) {
+            const float xv = fmaf(alpha[c], pi[c], md.x32[row * K + c]);
+            const float rv = fmaf(-alpha[c], md.q32[row * K + c], md.r32[row * K + c]);
+            md.x32[row * K + c] = xv;
+            md.r32[row * K + c] = rv;
+            rz[c] = fmaf(rv, dinv * rv, rz[c]);
+            rr2[c] = fmaf(rv, rv, rr2[c]);
+          }
+        }
+      }
+    } else {
+      // Restart: r32 = r64 / ||r64|| for columns still above tol, d = 0
+      double inv[K];
+      int act[K];
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        act[c] = __ldcg(&s->active64[c]);
+        inv[c] = 1.0 / __ldcg(&s->scale[c]);
+      }
+#pragma unroll
+      for (int rr = 0; rr < kRowsPerThread; ++rr) {
+        const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
+        if (row < md.n) {
+          const float dinv = md.Dinv32[row];
+#pragma unroll
+          for (int c = 0; c < K; ++c) {
+            const float rv = act[c] ? (float)(md.r[row * K + c] * inv[c]) : 0.f;
+            md.r32[row * K + c] = rv;
+            md.x32[row * K + c] = 0.f;
+            rz[c] = fmaf(rv, dinv * rv, rz[c]);
+            rr2[c] = fmaf(rv, rv, rr2[c]);
+          }
+        }
+      }
+    }
+    double acc[2 * K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      acc[c] = (double)rz[c];
+      acc[K + c] = (double)rr2[c];
+    }
+    if (reduce_tiles<2 * K>(acc, md.part, tl.y, md.ntiles, &s->cnt[1], sh) && threadIdx.x == 0) {
+      if (phase == kPhaseInner) finish_update_mixed(s, K, acc);
+      else finish_restart(s, K, acc);
+    }
+  }
+  loop_control(mds, ctl, handle, use_graph, nmesh);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) pupdate_mixed_kernel(const MeshDev* __restrict__ mds,
+                                                               const int2* __restrict__ tiles) {
+  const int2 tl = tiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  SolveScal* s = md.s;
+  if (__ldcg(&s->done)) return;
+  const int phase = __ldcg(&s->phase);
+  if (phase == kPhaseInner) {
+    float beta[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) beta[c] = (float)__ldcg(&s->beta[c]);
+#pragma unroll
+    for (int rr = 0; rr < kRowsPerThread; ++rr) {
+      const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
+      if (row < md.n) {
+        const float dinv = md.Dinv32[row];
+        float pi[K];
+        load_row32<K>(md.p32, row, pi);
+#pragma unroll
+        for (int c = 0; c < K; ++c) md.p32[row * KPm<K>::v + c] = fmaf(beta[c], pi[c], dinv * md.r32[row * K + c]);
+      }
+    }
+  } else if (phase == kPhaseApply) {
+    double sc[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) sc[c] = __ldcg(&s->scale[c]);
+#pragma unroll
+    for (int rr = 0; rr < kRowsPerThread; ++rr) {
+      const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
+      if (row < md.n) {
+#pragma unroll
+        for (int c = 0; c < K; ++c)
+          md.x[row * K + c] = fma(sc[c], (double)md.x32[row * K + c], md.x[row * K + c]);
+      }
+    }
+  }
+}
+
+template <int K>
+cudaError_t build_plan_mixed(Group& g, SolvePlan& pl) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle handle;
+  e = cudaGraphConditionalHandleCreate(&handle, graph, 1u, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t cs = g.capture_stream;
+  e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  spmv_mixed_kernel<K><<<g.ntiles, kBlock, 0, cs>>>(g.mds, g.tiles);
+  update_mixed_kernel<K><<<g.ntiles, kBlock, 0, cs>>>(g.mds, g.tiles, g.ctl, handle, 1, g.nmesh);
+  pupdate_mixed_kernel<K><<<g.ntiles, kBlock, 0, cs>>>(g.mds, g.tiles);
+  cudaError_t le = cudaGetLastError();
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(cs, &captured);
+  if (le != cudaSuccess) e = le;
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  pl.k = K;
+  pl.mixed = 1;
+  pl.graph = graph;
+  pl.exec = exec;
+  return cudaSuccess;
+}
+
+template <int K>
+cudaError_t solve_mixed_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_opts& o, cudaStream_t st) {
+  const int cap = o.max_iter + 3 * o.max_refine + 4;
+  {
+    IG_PROF("pcg_init", st);
+    init_mixed_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io, rhs_mass, g.ctl, o.rel_tol, o.inner_tol,
+                                                      o.max_iter, o.max_refine, cap);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (o.launch == IG_LAUNCH_GRAPH && !prof_on()) {
+    SolvePlan& pl = g.plans[1][K];
+    if (!pl.exec) {
+      e = build_plan_mixed<K>(g, pl);
+      if (e != cudaSuccess) return e;
+    }
+    e = cudaGraphLaunch(pl.exec, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    for (int it = 0; it < cap; ++it) {
+      {
+        IG_PROF("pcg32_spmv", st);
+        spmv_mixed_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles);
+      }
+      {
+        IG_PROF("pcg32_update", st);
+        update_mixed_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, g.ctl, cudaGraphConditionalHandle{}, 0,
+                                                            g.nmesh);
+      }
+      {
+        IG_PROF("pcg32_pupdate", st);
+        pupdate_mixed_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles);
+      }
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      if (prof_on() || (it & 15) == 15 || it == cap - 1) {
+        e = cudaMemcpyAsync(g.done_host, &g.ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        if (*g.done_host) break;
+      }
+    }
+  }
+  {
+    IG_PROF("pcg_finalize", st);
+    finalize_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t group_solve_mixed(Group& g, int k, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
+                              cudaStream_t st) {
+  switch (k) {
+    case 1: return solve_mixed_k<1>(g, io, rhs_mass, o, st);
+    case 2: return solve_mixed_k<2>(g, io, rhs_mass, o, st);
+    case 3: return solve_mixed_k<3>(g, io, rhs_mass, o, st);
+    case 4: return solve_mixed_k<4>(g, io, rhs_mass, o, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ig
