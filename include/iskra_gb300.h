@@ -55,6 +55,7 @@ enum { IG_LAUNCH_GRAPH = 0, IG_LAUNCH_HOST = 1 };
 
 typedef struct ig_ctx ig_ctx;
 typedef struct ig_mesh ig_mesh;
+typedef struct ig_batch ig_batch;
 
 /* Solver options. ig_default_opts() fills the defaults shown. */
 typedef struct {
@@ -155,6 +156,39 @@ ig_status ig_solve(ig_mesh* mesh, const double* B_dev, int k, double* U_dev, con
 ig_status ig_adjoint(ig_mesh* mesh, const double* V_dev, const double* B_dev, int b_is_V, const double* U_dev,
                      const double* G_dev, int k, double* gV_dev, double* gB_dev, double* gt_dev,
                      const ig_solve_opts* opts, ig_solve_info* info);
+
+/* ---- batches ------------------------------------------------------------------------------ */
+/* A batch runs the assembly, the solves and the gradient of many meshes in the same kernel
+ * launches: the block-diagonal system of independent smoothing steps (§7.1 applied to each
+ * mesh), every mesh with its own t, its own conjugate-gradient scalars and its own convergence
+ * test. A mesh gives the same bits alone and inside a batch. Array-of-pointer arguments are HOST
+ * arrays with one device pointer per mesh, in the order the meshes were given; per-mesh arrays
+ * follow the single-mesh conventions. A mesh may belong to several batches but must not be used
+ * by two calls at once. */
+
+/* Create a batch over count (1..1024) meshes of ctx. The batch does not own the meshes; free the
+ * batch before them. Errors: IG_ERR_INVALID_ARG (bad count, repeated or foreign mesh), IG_ERR_OOM. */
+ig_status ig_batch_create(ig_ctx* ctx, ig_mesh* const* meshes, int count, ig_batch** out);
+
+/* Release a batch (not its meshes). */
+ig_status ig_batch_free(ig_batch* batch);
+
+/* Assemble every mesh: V_dev[i] [n_i][3] and t[i] (host array of doubles). Same semantics and
+ * errors as ig_assemble, for all meshes in two launches. */
+ig_status ig_batch_assemble(ig_batch* batch, const double* const* V_dev, const double* t, int precision);
+
+/* Solve A_i U_i = M_i B_i for every mesh (k columns each, shared options). infos, if given, is
+ * a host array of count records; the call then synchronises and returns the first failing
+ * status (or IG_OK). Errors as ig_solve. */
+ig_status ig_batch_solve(ig_batch* batch, const double* const* B_dev, int k, double* const* U_dev,
+                         const ig_solve_opts* opts, ig_solve_info* infos);
+
+/* Reverse pass of ig_batch_solve (as ig_adjoint, per mesh): G_dev[i] = dl/dU_i; writes gV_dev[i],
+ * gB_dev[i] (gB_dev may be NULL) and gt_dev[i] (gt_dev is a DEVICE array of count doubles or
+ * NULL). */
+ig_status ig_batch_adjoint(ig_batch* batch, const double* const* V_dev, const double* const* B_dev, int b_is_V,
+                           const double* const* U_dev, const double* const* G_dev, int k, double* const* gV_dev,
+                           double* const* gB_dev, double* gt_dev, const ig_solve_opts* opts, ig_solve_info* infos);
 
 /* ---- allocation-free solve ----------------------------------------------------------------- */
 

@@ -78,6 +78,12 @@ SIGNATURES = {
     "ig_operator": (_i32, [_vp, _vp, _vp]),
     "ig_solve": (_i32, [_vp, _vp, _i32, _vp, _P(SolveOpts), _P(SolveInfo)]),
     "ig_adjoint": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _P(SolveOpts), _P(SolveInfo)]),
+    "ig_batch_create": (_i32, [_vp, _P(_vp), _i32, _P(_vp)]),
+    "ig_batch_free": (_i32, [_vp]),
+    "ig_batch_assemble": (_i32, [_vp, _P(_vp), _P(_dbl), _i32]),
+    "ig_batch_solve": (_i32, [_vp, _P(_vp), _i32, _P(_vp), _P(SolveOpts), _P(SolveInfo)]),
+    "ig_batch_adjoint": (_i32, [_vp, _P(_vp), _P(_vp), _i32, _P(_vp), _P(_vp), _i32, _P(_vp), _P(_vp), _vp,
+                                _P(SolveOpts), _P(SolveInfo)]),
     "ig_solve_csr_noalloc": (_i32, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, _i32, _vp, _vp, _P(SolveOpts),
                                      _P(SolveInfo)]),
     "ig_profile_enable": (_i32, [_i32]),

@@ -210,3 +210,127 @@ class SmoothSolve(torch.autograd.Function):
 def smooth(mesh: Mesh, V: torch.Tensor, B: Optional[torch.Tensor], t, precision: str = "fp64", opts=None):
     """Differentiable implicit smoothing step: solve (M(V) + t L(V)) U = M(V) B (B = V if None)."""
     return SmoothSolve.apply(V, B, t, mesh, precision, opts)
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = t.data_ptr() if t is not None else None
+    return arr
+
+
+class Batch:
+    """Many meshes assembled, solved and differentiated by the same kernel launches (each mesh
+    keeps its own t, scalars and convergence test; results equal those of the meshes alone)."""
+
+    def __init__(self, meshes, ctx: Optional[Context] = None):
+        self.meshes = list(meshes)
+        self.ctx = ctx or self.meshes[0].ctx
+        self.h = ctypes.c_void_p()
+        handles = (ctypes.c_void_p * len(self.meshes))(*[m.h.value for m in self.meshes])
+        self.ctx.sync_stream()
+        self.ctx.check(self.ctx.lib.ig_batch_create(self.ctx.h, handles, len(self.meshes), ctypes.byref(self.h)))
+        self.ts = None
+        self.precision = None
+
+    def __len__(self):
+        return len(self.meshes)
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.ig_batch_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def assemble(self, Vs, ts, precision: str = "fp64"):
+        Vs = [m._dev(V, 3, "V") for m, V in zip(self.meshes, Vs)]
+        tarr = (ctypes.c_double * len(Vs))(*[float(t) for t in ts])
+        self.ctx.sync_stream()
+        self.ctx.check(self.ctx.lib.ig_batch_assemble(self.h, _ptr_array(Vs), tarr, _PREC[precision]))
+        self.ts, self.precision = [float(t) for t in ts], precision
+        for m, V, t in zip(self.meshes, Vs, ts):
+            m.t, m.precision = float(t), precision
+            m._token = (V.data_ptr(), V._version, float(t), precision)
+        return self
+
+    def solve(self, Bs, opts=None, info: bool = False, outs=None):
+        Bs = [m._dev(B, None, "B") for m, B in zip(self.meshes, Bs)]
+        k = Bs[0].shape[1]
+        Us = outs if outs is not None else [torch.empty_like(B) for B in Bs]
+        infos = (N.SolveInfo * len(Bs))() if info else None
+        self.ctx.sync_stream()
+        st = self.ctx.lib.ig_batch_solve(self.h, _ptr_array(Bs), k, _ptr_array(Us),
+                                         ctypes.byref(opts) if opts is not None else None, infos)
+        if info:
+            if st not in (N.IG_OK, N.IG_ERR_NOT_CONVERGED):
+                self.ctx.check(st)
+            return Us, [i.as_dict() for i in infos]
+        self.ctx.check(st)
+        return Us
+
+    def adjoint(self, Vs, Bs, b_is_V, Us, Gs, want_gB=False, want_gt=False, opts=None, info: bool = False):
+        n = len(self.meshes)
+        k = Gs[0].shape[1]
+        Vs = [m._dev(V, 3, "V") for m, V in zip(self.meshes, Vs)]
+        Gs = [m._dev(G, k, "G") for m, G in zip(self.meshes, Gs)]
+        Us = [m._dev(U, k, "U") for m, U in zip(self.meshes, Us)]
+        Bs = None if b_is_V else [m._dev(B, k, "B") for m, B in zip(self.meshes, Bs)]
+        dev = self.ctx.device
+        gVs = [torch.empty((m.n, 3), dtype=torch.float64, device=dev) for m in self.meshes]
+        gBs = [torch.empty((m.n, k), dtype=torch.float64, device=dev) for m in self.meshes] if want_gB else None
+        gt = torch.empty(n, dtype=torch.float64, device=dev) if want_gt else None
+        infos = (N.SolveInfo * n)() if info else None
+        self.ctx.sync_stream()
+        st = self.ctx.lib.ig_batch_adjoint(self.h, _ptr_array(Vs), _ptr_array(Bs) if Bs else None, int(bool(b_is_V)),
+                                           _ptr_array(Us), _ptr_array(Gs), k, _ptr_array(gVs),
+                                           _ptr_array(gBs) if gBs else None, _ptr(gt),
+                                           ctypes.byref(opts) if opts is not None else None, infos)
+        if info:
+            if st not in (N.IG_OK, N.IG_ERR_NOT_CONVERGED):
+                self.ctx.check(st)
+            return gVs, gBs, gt, [i.as_dict() for i in infos]
+        self.ctx.check(st)
+        return gVs, gBs, gt
+
+
+class SmoothBatch(torch.autograd.Function):
+    """U_i = (M(V_i) + t_i L(V_i))^-1 M(V_i) B_i for every mesh of a batch (B_i = V_i when no B
+    is given), differentiable in the V_i (and B_i) by one batched adjoint pass."""
+
+    @staticmethod
+    def forward(ctx, batch: "Batch", ts, precision, opts, nB, *tensors):
+        n = len(batch)
+        Vs = list(tensors[:n])
+        Bs = list(tensors[n:n + nB]) if nB else None
+        batch.assemble(Vs, ts, precision)
+        Us = batch.solve(Vs if Bs is None else Bs, opts=opts)
+        ctx.batch, ctx.ts, ctx.precision, ctx.opts, ctx.nB = batch, list(ts), precision, opts, nB
+        ctx.save_for_backward(*Vs, *(Bs or []), *Us)
+        return tuple(Us)
+
+    @staticmethod
+    def backward(ctx, *gUs):
+        batch: Batch = ctx.batch
+        n = len(batch)
+        saved = ctx.saved_tensors
+        Vs = list(saved[:n])
+        Bs = list(saved[n:n + ctx.nB]) if ctx.nB else None
+        Us = list(saved[n + ctx.nB:])
+        if any(m._token != (V.data_ptr(), V._version, t, ctx.precision)
+               for m, V, t in zip(batch.meshes, Vs, ctx.ts)):
+            batch.assemble(Vs, ctx.ts, ctx.precision)
+        Gs = [(g if g is not None else torch.zeros_like(U)).to(torch.float64).contiguous() for g, U in zip(gUs, Us)]
+        want_gB = ctx.nB > 0 and any(ctx.needs_input_grad[5 + n:5 + n + ctx.nB])
+        gVs, gBs, _ = batch.adjoint(Vs, Bs, Bs is None, Us, Gs, want_gB=want_gB, opts=ctx.opts)
+        return (None, None, None, None, None, *gVs, *(gBs if gBs else [None] * ctx.nB))
+
+
+def smooth_batch(batch: Batch, Vs, Bs, ts, precision: str = "fp64", opts=None):
+    """Differentiable batched smoothing step; returns the list of U_i."""
+    nB = 0 if Bs is None else len(Bs)
+    return list(SmoothBatch.apply(batch, list(ts), precision, opts, nB, *Vs, *(Bs or [])))

@@ -220,6 +220,28 @@ ig_status collect_info(ig_mesh* mesh, int k, ig_solve_info* info) {
 
 }  // namespace
 
+namespace ig {
+
+// Allocate the FP32 copies used by mixed precision (once per mesh) and refresh the mesh's own
+// descriptor on the device.
+cudaError_t mesh_ensure_mixed(ig_mesh* mesh, cudaStream_t st) {
+  MeshDev& md = mesh->md;
+  if (md.A32) return cudaSuccess;
+  const size_t nv = (size_t)mesh->n * kMaxK;
+  cudaError_t e;
+  if ((e = mesh_alloc(mesh, &md.A32, (size_t)mesh->nnz)) != cudaSuccess) return e;
+  if ((e = mesh_alloc(mesh, &md.Dinv32, (size_t)mesh->n)) != cudaSuccess) return e;
+  if ((e = mesh_alloc(mesh, &md.x32, nv)) != cudaSuccess) return e;
+  if ((e = mesh_alloc(mesh, &md.r32, nv)) != cudaSuccess) return e;
+  if ((e = mesh_alloc(mesh, &md.p32, nv)) != cudaSuccess) return e;
+  if ((e = mesh_alloc(mesh, &md.q32, nv)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(md.p32, 0, sizeof(float) * nv, st)) != cudaSuccess) return e;
+  mesh->group.host_mds[0] = md;
+  return group_upload_mds(mesh->group, st);
+}
+
+}  // namespace ig
+
 // =============================================================================================
 extern "C" {
 
@@ -442,22 +464,14 @@ ig_status ig_assemble(ig_mesh* mesh, const double* V_dev, double t, int precisio
   if (!(t >= 0.0) || !std::isfinite(t)) return bad_arg(ctx, "t must be finite and >= 0");
   if (precision != IG_PRECISION_FP64 && precision != IG_PRECISION_MIXED) return bad_arg(ctx, "unknown precision");
   DeviceGuard guard(ctx->device);
-  MeshDev& md = mesh->md;
   const int mixed = precision == IG_PRECISION_MIXED;
-  if (mixed && !md.A32) {
-    const size_t nv = (size_t)mesh->n * kMaxK;
-    IG_CK(ctx, mesh_alloc(mesh, &md.A32, (size_t)mesh->nnz), "alloc");
-    IG_CK(ctx, mesh_alloc(mesh, &md.Dinv32, (size_t)mesh->n), "alloc");
-    IG_CK(ctx, mesh_alloc(mesh, &md.x32, nv), "alloc");
-    IG_CK(ctx, mesh_alloc(mesh, &md.r32, nv), "alloc");
-    IG_CK(ctx, mesh_alloc(mesh, &md.p32, nv), "alloc");
-    IG_CK(ctx, mesh_alloc(mesh, &md.q32, nv), "alloc");
-    IG_CK(ctx, cudaMemsetAsync(md.p32, 0, sizeof(float) * nv, ctx->stream), "memset");
-  }
-  md.t = t;
-  IG_CK(ctx, cudaMemcpyAsync(mesh->group.mds, &md, sizeof(MeshDev), cudaMemcpyHostToDevice, ctx->stream), "upload");
-  IG_CK(ctx, cudaMemsetAsync(md.err, 0, sizeof(int), ctx->stream), "memset");
-  IG_CK(ctx, launch_assemble(md, V_dev, t, mixed, ctx->stream), "assemble");
+  if (mixed) IG_CK(ctx, mesh_ensure_mixed(mesh, ctx->stream), "alloc");
+  CallDev call{};
+  call.V = V_dev;
+  call.t = t;
+  IG_CK(ctx, group_set_calls(mesh->group, &call, ctx->stream), "upload");
+  IG_CK(ctx, cudaMemsetAsync(mesh->md.err, 0, sizeof(int), ctx->stream), "memset");
+  IG_CK(ctx, launch_assemble(mesh->group, mixed, ctx->stream), "assemble");
   mesh->assembled = mixed ? 2 : 1;
   mesh->t = t;
   return IG_OK;
@@ -536,7 +550,18 @@ ig_status ig_adjoint(ig_mesh* mesh, const double* V_dev, const double* B_dev, in
   io->in[0] = G_dev;
   io->out[0] = mesh->md.lam;
   IG_CK(ctx, group_solve(mesh->group, k, mesh->assembled == 2, *io, 0, o, ctx->stream), "adjoint solve");
-  IG_CK(ctx, launch_vjp(mesh->md, V_dev, B_dev, b_is_V, U_dev, k, gV_dev, gB_dev, gt_dev, ctx->stream), "vjp");
+  CallDev call{};
+  call.V = V_dev;
+  call.B = b_is_V ? V_dev : B_dev;
+  call.U = U_dev;
+  call.gV = gV_dev;
+  call.gB = gB_dev;
+  call.gt = gt_dev;
+  call.t = mesh->t;
+  call.b_is_V = b_is_V ? 1 : 0;
+  call.bstride = b_is_V ? 3 : k;
+  IG_CK(ctx, group_set_calls(mesh->group, &call, ctx->stream), "upload");
+  IG_CK(ctx, launch_vjp(mesh->group, k, ctx->stream), "vjp");
   if (!info) return IG_OK;
   IG_CK(ctx, group_true_residual(mesh->group, k, *io, 0, ctx->stream), "residual");
   return collect_info(mesh, k, info);

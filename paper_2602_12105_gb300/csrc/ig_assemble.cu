@@ -25,10 +25,17 @@ __device__ __forceinline__ bool positive_finite(double x) {
   return b > 0 && (b & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
 }
 
-__global__ void __launch_bounds__(256) face_kernel(const double* __restrict__ V, const int* __restrict__ F, int m,
-                                                   double half_t, double* __restrict__ facew, int* __restrict__ err) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= m) return;
+__global__ void __launch_bounds__(256) face_kernel(const MeshDev* __restrict__ mds, const CallDev* __restrict__ calls,
+                                                   const int2* __restrict__ ftiles) {
+  const int2 tl = ftiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  const int f = tl.y * 256 + threadIdx.x;
+  if (f >= md.m) return;
+  const double* __restrict__ V = calls[tl.x].V;
+  const double half_t = 0.5 * calls[tl.x].t;
+  const int* __restrict__ F = md.F;
+  double* __restrict__ facew = md.facew;
+  int* err = md.err;
   const int i0 = __ldg(F + 3 * f), i1 = __ldg(F + 3 * f + 1), i2 = __ldg(F + 3 * f + 2);
   double p0[3], p1[3], p2[3];
 #pragma unroll
@@ -68,9 +75,12 @@ __global__ void __launch_bounds__(256) face_kernel(const double* __restrict__ V,
 
 constexpr int kSmemSlots = 16;  // rows up to this length accumulate in shared memory
 
-__global__ void __launch_bounds__(256) row_kernel(MeshDev md, int mixed) {
+__global__ void __launch_bounds__(256) row_kernel(const MeshDev* __restrict__ mds, const int2* __restrict__ rtiles,
+                                                  int mixed) {
   __shared__ double acc[kSmemSlots][256];
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int2 tl = rtiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  const int v = tl.y * 256 + threadIdx.x;
   if (v >= md.n) return;
   const int r0 = __ldg(md.rowptr + v);
   const int len = __ldg(md.rowptr + v + 1) - r0;
@@ -124,16 +134,16 @@ __global__ void __launch_bounds__(256) row_kernel(MeshDev md, int mixed) {
 
 }  // namespace
 
-cudaError_t launch_assemble(const MeshDev& md, const double* V, double t, int mixed, cudaStream_t st) {
+cudaError_t launch_assemble(Group& g, int mixed, cudaStream_t st) {
   {
     IG_PROF("assemble_face", st);
-    face_kernel<<<(md.m + 255) / 256, 256, 0, st>>>(V, md.F, md.m, 0.5 * t, md.facew, md.err);
+    face_kernel<<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   {
     IG_PROF("assemble_rows", st);
-    row_kernel<<<(md.n + 255) / 256, 256, 0, st>>>(md, mixed);
+    row_kernel<<<g.nrow_tiles, 256, 0, st>>>(g.mds, g.row_tiles, mixed);
   }
   return cudaGetLastError();
 }

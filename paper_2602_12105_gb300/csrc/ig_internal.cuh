@@ -158,6 +158,20 @@ struct IoTable {
   double* out[kMaxIo];
 };
 
+// Per-call arguments of one mesh for the assembly and gradient kernels (caller buffers change
+// from call to call; they reach the kernels through this small device table).
+struct CallDev {
+  const double* V;   // positions [n][3]
+  const double* B;   // right-hand side [n][k] (or V when b_is_V)
+  const double* U;   // forward solution [n][k]
+  double* gV;        // dl/dV [n][3]
+  double* gB;        // dl/dB [n][k] or null
+  double* gt;        // dl/dt (one double) or null
+  double t;          // time step of the assembled operator
+  int b_is_V;
+  int bstride;       // columns of B (3 when b_is_V)
+};
+
 // A cached solver launch for one (k, precision): a CUDA graph whose WHILE node runs the
 // iteration body until the device sets the loop condition to 0.
 struct SolvePlan {
@@ -177,13 +191,24 @@ struct Group {
   int* done_host = nullptr;       // pinned host word for the host-driven loop
   SolvePlan plans[2][kMaxK + 1];  // [mixed][k]
   cudaStream_t capture_stream = nullptr;
+  // 256-element tiles for the face- and row-parallel kernels: (mesh, local tile)
+  int nface_tiles = 0, nrow_tiles = 0;
+  int2* face_tiles = nullptr;
+  int2* row_tiles = nullptr;
+  CallDev* calls_dev = nullptr;   // [nmesh]
+  CallDev* calls_host = nullptr;  // pinned staging for calls_dev
+  cudaEvent_t calls_ev = nullptr; // the last upload of calls_host has been read
+  std::vector<MeshDev> host_mds;  // host copy of mds
 };
 
 cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, cudaStream_t st);
+cudaError_t group_upload_mds(Group& g, cudaStream_t st);
+cudaError_t group_set_calls(Group& g, const CallDev* calls, cudaStream_t st);
 void group_destroy(Group& g);
 cudaError_t group_solve(Group& g, int k, int mixed, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
                         cudaStream_t st);
 cudaError_t group_true_residual(Group& g, int k, const IoTable& io, int rhs_mass, cudaStream_t st);
+cudaError_t mesh_ensure_mixed(ig_mesh* mesh, cudaStream_t st);
 cudaError_t group_solve_mixed(Group& g, int k, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
                               cudaStream_t st);
 
@@ -217,13 +242,12 @@ cudaError_t launch_pattern_rows(const int* F, int n, const int* incptr, int* inc
 cudaError_t launch_pattern_cols(const int* F, int n, const int* incptr, const int* inc_fc, const int* nbr,
                                 const int* rowptr, int* col, int* diagpos, int2* inc, int* err, cudaStream_t st);
 
-// ig_assemble.cu
-cudaError_t launch_assemble(const MeshDev& md, const double* V, double t, int mixed, cudaStream_t st);
+// ig_assemble.cu (per-call V and t come from g.calls_dev)
+cudaError_t launch_assemble(Group& g, int mixed, cudaStream_t st);
 
 // ig_pcg.cu: see Group above
 
 // ig_vjp.cu
-cudaError_t launch_vjp(const MeshDev& md, const double* V, const double* B, int b_is_V, const double* U, int k,
-                       double* gV, double* gB, double* gt, cudaStream_t st);
+cudaError_t launch_vjp(Group& g, int k, cudaStream_t st);
 
 }  // namespace ig

@@ -381,27 +381,56 @@ cudaError_t solve_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_op
 
 cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, cudaStream_t st) {
   g.nmesh = nmesh;
-  std::vector<int2> tiles;
-  for (int i = 0; i < nmesh; ++i)
+  g.host_mds.assign(host_mds, host_mds + nmesh);
+  std::vector<int2> tiles, ftiles, rtiles;
+  for (int i = 0; i < nmesh; ++i) {
     for (int t = 0; t < host_mds[i].ntiles; ++t) tiles.push_back(make_int2(i, t));
+    for (int t = 0; t < (host_mds[i].m + 255) / 256; ++t) ftiles.push_back(make_int2(i, t));
+    for (int t = 0; t < (host_mds[i].n + 255) / 256; ++t) rtiles.push_back(make_int2(i, t));
+  }
   g.ntiles = (int)tiles.size();
-  cudaError_t e = cudaMalloc(&g.mds, sizeof(MeshDev) * nmesh);
-  if (e != cudaSuccess) return e;
-  e = cudaMalloc(&g.tiles, sizeof(int2) * tiles.size());
-  if (e != cudaSuccess) return e;
-  e = cudaMalloc(&g.ctl, sizeof(LoopCtl));
-  if (e != cudaSuccess) return e;
-  e = cudaMallocHost(&g.done_host, sizeof(int));
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(g.mds, host_mds, sizeof(MeshDev) * nmesh, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(g.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(g.ctl, 0, sizeof(LoopCtl), st);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamCreateWithFlags(&g.capture_stream, cudaStreamNonBlocking);
-  if (e != cudaSuccess) return e;
+  g.nface_tiles = (int)ftiles.size();
+  g.nrow_tiles = (int)rtiles.size();
+  cudaError_t e;
+  if ((e = cudaMalloc(&g.mds, sizeof(MeshDev) * nmesh)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&g.tiles, sizeof(int2) * tiles.size())) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&g.face_tiles, sizeof(int2) * ftiles.size())) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&g.row_tiles, sizeof(int2) * rtiles.size())) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&g.ctl, sizeof(LoopCtl))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&g.calls_dev, sizeof(CallDev) * nmesh)) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&g.calls_host, sizeof(CallDev) * nmesh)) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&g.done_host, sizeof(int))) != cudaSuccess) return e;
+  if ((e = cudaEventCreateWithFlags(&g.calls_ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(g.mds, host_mds, sizeof(MeshDev) * nmesh, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(g.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(g.face_tiles, ftiles.data(), sizeof(int2) * ftiles.size(), cudaMemcpyHostToDevice, st)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(g.row_tiles, rtiles.data(), sizeof(int2) * rtiles.size(), cudaMemcpyHostToDevice, st)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemsetAsync(g.ctl, 0, sizeof(LoopCtl), st)) != cudaSuccess) return e;
+  if ((e = cudaStreamCreateWithFlags(&g.capture_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(g.calls_ev, st)) != cudaSuccess) return e;
   return cudaStreamSynchronize(st);
+}
+
+// Refresh the device copy of the mesh descriptors from g.host_mds.
+cudaError_t group_upload_mds(Group& g, cudaStream_t st) {
+  return cudaMemcpyAsync(g.mds, g.host_mds.data(), sizeof(MeshDev) * g.nmesh, cudaMemcpyHostToDevice, st);
+}
+
+// Upload per-call arguments; waits until the previous upload from the pinned staging is done.
+cudaError_t group_set_calls(Group& g, const CallDev* calls, cudaStream_t st) {
+  cudaError_t e = cudaEventSynchronize(g.calls_ev);
+  if (e != cudaSuccess) return e;
+  std::memcpy(g.calls_host, calls, sizeof(CallDev) * g.nmesh);
+  e = cudaMemcpyAsync(g.calls_dev, g.calls_host, sizeof(CallDev) * g.nmesh, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  return cudaEventRecord(g.calls_ev, st);
 }
 
 void group_destroy(Group& g) {
@@ -411,11 +440,17 @@ void group_destroy(Group& g) {
       if (pl.graph) cudaGraphDestroy(pl.graph);
       pl = SolvePlan{};
     }
+  if (g.calls_ev) cudaEventSynchronize(g.calls_ev);
   if (g.capture_stream) cudaStreamDestroy(g.capture_stream);
   if (g.mds) cudaFree(g.mds);
   if (g.tiles) cudaFree(g.tiles);
+  if (g.face_tiles) cudaFree(g.face_tiles);
+  if (g.row_tiles) cudaFree(g.row_tiles);
   if (g.ctl) cudaFree(g.ctl);
+  if (g.calls_dev) cudaFree(g.calls_dev);
+  if (g.calls_host) cudaFreeHost(g.calls_host);
   if (g.done_host) cudaFreeHost(g.done_host);
+  if (g.calls_ev) cudaEventDestroy(g.calls_ev);
   g = Group{};
 }
 

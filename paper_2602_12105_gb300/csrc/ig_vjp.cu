@@ -26,12 +26,22 @@ namespace {
 constexpr int kFaceTile = 256;
 
 template <int K>
-__global__ void __launch_bounds__(256) vjp_face_kernel(MeshDev md, const double* __restrict__ V,
-                                                       const double* __restrict__ Bsrc, int bstride,
-                                                       const double* __restrict__ U, double* __restrict__ gt) {
+__global__ void __launch_bounds__(256) vjp_face_kernel(const MeshDev* __restrict__ mds,
+                                                       const CallDev* __restrict__ calls,
+                                                       const int2* __restrict__ ftiles) {
   __shared__ double sh[8];
   __shared__ int s_last;
-  const int f = blockIdx.x * kFaceTile + threadIdx.x;
+  const int2 tl = ftiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  const CallDev& cl = calls[tl.x];
+  const double* __restrict__ V = cl.V;
+  const double* __restrict__ Bsrc = cl.b_is_V ? cl.V : cl.B;
+  const int bstride = cl.bstride;
+  const double* __restrict__ U = cl.U;
+  double* __restrict__ gt = cl.gt;
+  const double tval = cl.t;
+  const int ntl = (md.m + kFaceTile - 1) / kFaceTile;
+  const int f = tl.y * kFaceTile + threadIdx.x;
   const double* __restrict__ lam = md.lam;
   double gt_part = 0.0;
   if (f < md.m) {
@@ -76,7 +86,7 @@ __global__ void __launch_bounds__(256) vjp_face_kernel(MeshDev md, const double*
     }
     wa *= (1.0 / 3.0);
     double omega[3];
-    const double mt2 = -0.5 * md.t;
+    const double mt2 = -0.5 * tval;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const int a = (c + 1) % 3, b = (c + 2) % 3;
@@ -116,16 +126,16 @@ __global__ void __launch_bounds__(256) vjp_face_kernel(MeshDev md, const double*
   if (threadIdx.x == 0) {
     double tot = 0.0;
     for (int w = 0; w < 8; ++w) tot += sh[w];
-    md.part[blockIdx.x] = tot;
+    md.part[tl.y] = tot;
     __threadfence();
     const unsigned prev = atomicAdd(&md.s->cnt[3], 1u);
-    s_last = (prev == gridDim.x - 1u);
+    s_last = (prev == (unsigned)ntl - 1u);
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
   double tot = 0.0;
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) tot += __ldcg(md.part + b);
+  for (int b = threadIdx.x; b < ntl; b += blockDim.x) tot += __ldcg(md.part + b);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
   __syncthreads();
@@ -140,10 +150,16 @@ __global__ void __launch_bounds__(256) vjp_face_kernel(MeshDev md, const double*
 }
 
 template <int K>
-__global__ void __launch_bounds__(256) vjp_gather_kernel(MeshDev md, int b_is_V, double* __restrict__ gV,
-                                                         double* __restrict__ gB) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) vjp_gather_kernel(const MeshDev* __restrict__ mds,
+                                                         const CallDev* __restrict__ calls,
+                                                         const int2* __restrict__ rtiles) {
+  const int2 tl = rtiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  const int v = tl.y * 256 + threadIdx.x;
   if (v >= md.n) return;
+  const int b_is_V = calls[tl.x].b_is_V;
+  double* __restrict__ gV = calls[tl.x].gV;
+  double* __restrict__ gB = calls[tl.x].gB;
   double g0 = 0.0, g1 = 0.0, g2 = 0.0;
   const int e0 = __ldg(md.incptr + v), e1 = __ldg(md.incptr + v + 1);
   for (int e = e0; e < e1; ++e) {
@@ -169,32 +185,28 @@ __global__ void __launch_bounds__(256) vjp_gather_kernel(MeshDev md, int b_is_V,
 }
 
 template <int K>
-cudaError_t vjp_k(const MeshDev& md, const double* V, const double* B, int b_is_V, const double* U, double* gV,
-                  double* gB, double* gt, cudaStream_t st) {
-  const double* Bsrc = b_is_V ? V : B;
-  const int bstride = b_is_V ? 3 : K;
+cudaError_t vjp_k(Group& g, cudaStream_t st) {
   {
     IG_PROF("vjp_face", st);
-    vjp_face_kernel<K><<<(md.m + kFaceTile - 1) / kFaceTile, 256, 0, st>>>(md, V, Bsrc, bstride, U, gt);
+    vjp_face_kernel<K><<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   {
     IG_PROF("vjp_gather", st);
-    vjp_gather_kernel<K><<<(md.n + 255) / 256, 256, 0, st>>>(md, b_is_V, gV, gB);
+    vjp_gather_kernel<K><<<g.nrow_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.row_tiles);
   }
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_vjp(const MeshDev& md, const double* V, const double* B, int b_is_V, const double* U, int k,
-                       double* gV, double* gB, double* gt, cudaStream_t st) {
+cudaError_t launch_vjp(Group& g, int k, cudaStream_t st) {
   switch (k) {
-    case 1: return vjp_k<1>(md, V, B, b_is_V, U, gV, gB, gt, st);
-    case 2: return vjp_k<2>(md, V, B, b_is_V, U, gV, gB, gt, st);
-    case 3: return vjp_k<3>(md, V, B, b_is_V, U, gV, gB, gt, st);
-    case 4: return vjp_k<4>(md, V, B, b_is_V, U, gV, gB, gt, st);
+    case 1: return vjp_k<1>(g, st);
+    case 2: return vjp_k<2>(g, st);
+    case 3: return vjp_k<3>(g, st);
+    case 4: return vjp_k<4>(g, st);
     default: return cudaErrorInvalidValue;
   }
 }
