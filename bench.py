@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="grid1024", choices=["grid1024", "ico3", "grid4096x2048"])
+    ap.add_argument("--workload", default="grid1024", choices=["grid1024", "ico3", "grid2048", "grid4096x2048"])
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"])
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -55,6 +55,8 @@ def make_problem(name, seed):
         return mg.config_grid1024(seed)
     if name == "grid4096x2048":
         return mg.config_grid4096x2048(seed)
+    if name == "grid2048":
+        return mg.config_grid(2048, 2048, seed)
     return mg.config_ico3(seed)
 
 

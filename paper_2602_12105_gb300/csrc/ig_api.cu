@@ -229,7 +229,8 @@ cudaError_t mesh_ensure_mixed(ig_mesh* mesh, cudaStream_t st) {
   if (md.A32) return cudaSuccess;
   const size_t nv = (size_t)mesh->n * kMaxK;
   cudaError_t e;
-  if ((e = mesh_alloc(mesh, &md.A32, (size_t)mesh->nnz)) != cudaSuccess) return e;
+  if ((e = mesh_alloc(mesh, &md.A32, (size_t)md.nnz_sell)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(md.A32, 0, sizeof(float) * (size_t)md.nnz_sell, st)) != cudaSuccess) return e;
   if ((e = mesh_alloc(mesh, &md.Dinv32, (size_t)mesh->n)) != cudaSuccess) return e;
   if ((e = mesh_alloc(mesh, &md.x32, nv)) != cudaSuccess) return e;
   if ((e = mesh_alloc(mesh, &md.r32, nv)) != cudaSuccess) return e;
@@ -286,6 +287,9 @@ ig_status ig_create(ig_ctx** out, int device, void* cuda_stream) {
     delete ctx;
     return IG_ERR_CUDA;
   }
+  ctx->solver_slots = ctx->num_sms * solver_blocks_per_sm();
+  ctx->solver_slots32 = ctx->num_sms * solver_blocks_per_sm_mixed();
+  cudaGetLastError();
   *out = ctx;
   return IG_OK;
 }
@@ -385,13 +389,45 @@ ig_status ig_mesh_upload(ig_ctx* ctx, const int32_t* F_dev, int64_t m, int64_t n
   UP_CK(mesh_alloc(M, &col, (size_t)nnz), "alloc col");
   UP_CK(launch_pattern_cols(F, ni, incptr, inc_fc, nbr, rowptr, col, diagpos, inc, err, st), "pattern cols");
 
+  // sliced-ELL copy of the pattern for the solver's SpMV (slices of 32 rows)
+  const int nsl = (ni + 31) / 32;
+  int *width32 = nullptr, *sell_ptr = nullptr, *sell_col = nullptr;
+  UP_CK(tmp.get(&width32, (size_t)nsl), "alloc tmp");
+  UP_CK(mesh_alloc(M, &sell_ptr, (size_t)nsl + 1), "alloc sell");
+  UP_CK(launch_sell_width(rowptr, ni, width32, st), "sell width");
+  UP_CK(exclusive_scan_int(width32, sell_ptr, nsl, totals, scratch, scan_ints, st), "scan");
+  int nnz_sell = 0;
+  UP_CK(cudaMemcpyAsync(&nnz_sell, totals, sizeof(int), cudaMemcpyDeviceToHost, st), "read totals");
+  UP_CK(cudaStreamSynchronize(st), "sell width");
+  UP_CK(mesh_alloc(M, &sell_col, (size_t)nnz_sell), "alloc sell");
+  UP_CK(launch_sell_fill(rowptr, col, ni, sell_ptr, sell_col, st), "sell fill");
+
   // operator and solver workspace
   MeshDev& md = M->md;
   std::memset(&md, 0, sizeof(md));
   md.n = ni;
   md.m = mi;
   md.nnz = nnz;
-  md.ntiles = (ni + kTileRows - 1) / kTileRows;
+  // Solver tiles (256..1024 rows, whole warps): a mesh that fills the GPU gets a tile count that
+  // is a whole multiple of the resident CTA slots S of the solver kernels, so every launch ends in
+  // full waves; a smaller mesh gets tiles of 256 rows so that it still spreads over the SMs. The
+  // choice depends on n and the device only, never on a batch.
+  auto choose_tiles = [ni](long S, int& tile_rows, int& ntiles) {
+    if (S < 1) S = 1;
+    long waves = ((long)ni + S * kTileRows - 1) / (S * kTileRows);
+    if (waves < 1) waves = 1;
+    long rows = ((long)ni + S * waves - 1) / (S * waves);
+    if (rows < kBlock) rows = kBlock;
+    if (rows > kTileRows) rows = kTileRows;
+    rows = (rows + 31) / 32 * 32;
+    tile_rows = (int)rows;
+    ntiles = (int)(((long)ni + rows - 1) / rows);
+  };
+  choose_tiles(ctx->solver_slots, md.tile_rows, md.ntiles);
+  choose_tiles(ctx->solver_slots32, md.tile_rows32, md.ntiles32);
+  md.nnz_sell = nnz_sell;
+  md.sell_ptr = sell_ptr;
+  md.sell_col = sell_col;
   md.F = F;
   md.rowptr = rowptr;
   md.col = col;
@@ -400,9 +436,11 @@ ig_status ig_mesh_upload(ig_ctx* ctx, const int32_t* F_dev, int64_t m, int64_t n
   md.inc = inc;
   md.err = err;
   const size_t nv = (size_t)n * kMaxK;
-  const size_t npart = std::max((size_t)md.ntiles * kPartStride, (size_t)(mi + 255) / 256) + 8;
+  const size_t npart = std::max(std::max((size_t)md.ntiles, (size_t)md.ntiles32) * kPartStride,
+                                (size_t)(mi + 255) / 256) + 8;
   UP_CK(mesh_alloc(M, &md.facew, 4 * (size_t)m), "alloc");
-  UP_CK(mesh_alloc(M, &md.A, (size_t)nnz), "alloc");
+  UP_CK(mesh_alloc(M, &md.A, (size_t)nnz_sell), "alloc");
+  UP_CK(cudaMemsetAsync(md.A, 0, sizeof(double) * (size_t)nnz_sell, st), "memset");
   UP_CK(mesh_alloc(M, &md.M, (size_t)n), "alloc");
   UP_CK(mesh_alloc(M, &md.Dinv, (size_t)n), "alloc");
   UP_CK(mesh_alloc(M, &md.x, nv), "alloc");
@@ -496,9 +534,7 @@ ig_status ig_operator(ig_mesh* mesh, double* Aval_dev, double* M_dev) {
     return IG_ERR_STATE;
   }
   DeviceGuard guard(ctx->device);
-  if (Aval_dev)
-    IG_CK(ctx, cudaMemcpyAsync(Aval_dev, mesh->md.A, sizeof(double) * mesh->nnz, cudaMemcpyDeviceToDevice,
-                               ctx->stream), "copy A");
+  if (Aval_dev) IG_CK(ctx, launch_operator_csr(mesh->md, Aval_dev, ctx->stream), "copy A");
   if (M_dev)
     IG_CK(ctx, cudaMemcpyAsync(M_dev, mesh->md.M, sizeof(double) * mesh->n, cudaMemcpyDeviceToDevice, ctx->stream),
           "copy M");

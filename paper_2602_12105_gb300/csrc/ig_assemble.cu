@@ -75,6 +75,8 @@ __global__ void __launch_bounds__(256) face_kernel(const MeshDev* __restrict__ m
 
 constexpr int kSmemSlots = 16;  // rows up to this length accumulate in shared memory
 
+// Values of row v go to the sliced layout: slot j at sell_ptr[v/32] + 32 j + v%32; slots between
+// the row's length and the slice width are written as 0.
 __global__ void __launch_bounds__(256) row_kernel(const MeshDev* __restrict__ mds, const int2* __restrict__ rtiles,
                                                   int mixed) {
   __shared__ double acc[kSmemSlots][256];
@@ -85,12 +87,15 @@ __global__ void __launch_bounds__(256) row_kernel(const MeshDev* __restrict__ md
   const int r0 = __ldg(md.rowptr + v);
   const int len = __ldg(md.rowptr + v + 1) - r0;
   const int dslot = __ldg(md.diagpos + v) - r0;
+  const int sl = v >> 5;
+  const int sbase = __ldg(md.sell_ptr + sl) + (v & 31);
+  const int width = (__ldg(md.sell_ptr + sl + 1) - __ldg(md.sell_ptr + sl)) >> 5;
   const bool in_smem = len <= kSmemSlots;
-  double* gA = md.A + r0;
+  double* gA = md.A;
   if (in_smem) {
     for (int j = 0; j < len; ++j) acc[j][threadIdx.x] = 0.0;
   } else {
-    for (int j = 0; j < len; ++j) gA[j] = 0.0;
+    for (int j = 0; j < len; ++j) gA[sbase + 32 * j] = 0.0;
   }
   double mass = 0.0, diag = 0.0;
   const int e0 = __ldg(md.incptr + v), e1 = __ldg(md.incptr + v + 1);
@@ -107,8 +112,8 @@ __global__ void __launch_bounds__(256) row_kernel(const MeshDev* __restrict__ md
       acc[sn][threadIdx.x] -= w_next;
       acc[sp][threadIdx.x] -= w_prev;
     } else {
-      gA[sn] -= w_next;
-      gA[sp] -= w_prev;
+      gA[sbase + 32 * sn] -= w_next;
+      gA[sbase + 32 * sp] -= w_prev;
     }
     diag += w_next + w_prev;
     mass += b.y;
@@ -119,17 +124,30 @@ __global__ void __launch_bounds__(256) row_kernel(const MeshDev* __restrict__ md
     acc[dslot][threadIdx.x] = aii;
     for (int j = 0; j < len; ++j) {
       const double x = acc[j][threadIdx.x];
-      gA[j] = x;
-      if (mixed) md.A32[r0 + j] = (float)x;
+      gA[sbase + 32 * j] = x;
+      if (mixed) md.A32[sbase + 32 * j] = (float)x;
     }
   } else {
-    gA[dslot] = aii;
+    gA[sbase + 32 * dslot] = aii;
     if (mixed)
-      for (int j = 0; j < len; ++j) md.A32[r0 + j] = (float)gA[j];
+      for (int j = 0; j < len; ++j) md.A32[sbase + 32 * j] = (float)gA[sbase + 32 * j];
+  }
+  for (int j = len; j < width; ++j) {
+    gA[sbase + 32 * j] = 0.0;
+    if (mixed) md.A32[sbase + 32 * j] = 0.f;
   }
   md.M[v] = mass;
   md.Dinv[v] = dinv;
   if (mixed) md.Dinv32[v] = (float)dinv;
+}
+
+// Copy of A in CSR order (the order of ig_mesh_pattern).
+__global__ void __launch_bounds__(256) operator_csr_kernel(MeshDev md, double* __restrict__ out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= md.n) return;
+  const int r0 = md.rowptr[v], len = md.rowptr[v + 1] - r0;
+  const int sbase = md.sell_ptr[v >> 5] + (v & 31);
+  for (int j = 0; j < len; ++j) out[r0 + j] = md.A[sbase + 32 * j];
 }
 
 }  // namespace
@@ -145,6 +163,11 @@ cudaError_t launch_assemble(Group& g, int mixed, cudaStream_t st) {
     IG_PROF("assemble_rows", st);
     row_kernel<<<g.nrow_tiles, 256, 0, st>>>(g.mds, g.row_tiles, mixed);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_operator_csr(const MeshDev& md, double* Acsr, cudaStream_t st) {
+  operator_csr_kernel<<<(md.n + 255) / 256, 256, 0, st>>>(md, Acsr);
   return cudaGetLastError();
 }
 

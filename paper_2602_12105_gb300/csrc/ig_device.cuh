@@ -40,6 +40,58 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
   __syncthreads();
 }
 
+// Mixed precision: sum float per-thread partials over the CTA. Each warp adds its 32 lanes in FP32
+// with shuffles (the FP32 pipe is fast); the 8 warp sums are added in FP64. Thread 0 receives the
+// totals in v64. sh holds NV*8 doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum_f32(const float (&v)[NV], double (&v64)[NV], double* sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    float a = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) sh[i * 8 + warp] = (double)a;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double a = lane < kBlock / 32 ? sh[i * 8 + lane] : 0.0;
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      v64[i] = a;
+    }
+  }
+  __syncthreads();
+}
+
+// Publish a tile's partials (already CTA-summed in thread 0's v) and return true in the last CTA
+// of the mesh, whose thread 0 then holds the mesh totals (tile order, deterministic).
+template <int NV>
+__device__ __forceinline__ bool publish_tiles(double (&v)[NV], double* part, int tile, int ntiles,
+                                              unsigned int* cnt, double* sh) {
+  __shared__ int s_last2;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) part[tile * kPartStride + i] = v[i];
+    __threadfence();
+    const unsigned prev = atomicAdd(cnt, 1u);
+    s_last2 = (prev == (unsigned)ntiles - 1u);
+  }
+  __syncthreads();
+  if (!s_last2) return false;
+  __threadfence();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = 0.0;
+  for (int t = threadIdx.x; t < ntiles; t += kBlock)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += __ldcg(part + t * kPartStride + i);
+  block_sum<NV>(v, sh);
+  if (threadIdx.x == 0) *cnt = 0u;
+  return true;
+}
+
 // Block-sum v, publish the tile's partials, and return true in the last CTA of the mesh, whose
 // thread 0 then holds the mesh totals (partials added in tile order, so the result does not
 // depend on which CTA finished last).
@@ -81,6 +133,104 @@ __device__ __forceinline__ void load_row(const double* __restrict__ p, long row,
   } else {
     v[0] = p[row];
   }
+}
+
+template <int K>
+__device__ __forceinline__ void load_row32(const float* __restrict__ p, long row, float (&v)[K]);
+
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
+// acc[c] = sum over the stored entries of row `row` of A[e] * X(col_e, c), where X is read by
+// the gather functor (x(col, v) fills v[0..K)). Uses the sliced-ELL layout when the mesh has one
+// (a warp's rows share one slice, so the loop count is uniform and each slot is one contiguous
+// load for the warp) and plain CSR otherwise.
+template <int K, typename TA, typename TX, typename G>
+__device__ __forceinline__ void row_product(const MeshDev& md, const TA* __restrict__ A, long row, const G& gather,
+                                            TX (&acc)[K]) {
+#pragma unroll
+  for (int c = 0; c < K; ++c) acc[c] = TX(0);
+  if (md.sell_ptr) {
+    const int sl = (int)(row >> 5);
+    const int b0 = __ldg(md.sell_ptr + sl), b1 = __ldg(md.sell_ptr + sl + 1);
+    const int w = (b1 - b0) >> 5;
+    const int base = b0 + (int)(row & 31);
+    const int* __restrict__ sc = md.sell_col;
+#pragma unroll 4
+    for (int j = 0; j < w; ++j) {
+      const int e = base + 32 * j;
+      const TA a = __ldg(A + e);
+      TX v[K];
+      gather(__ldg(sc + e), v);
+#pragma unroll
+      for (int c = 0; c < K; ++c) acc[c] = fma_t((TX)a, v[c], acc[c]);
+    }
+  } else {
+    const int e0 = __ldg(md.rowptr + row), e1 = __ldg(md.rowptr + row + 1);
+    for (int e = e0; e < e1; ++e) {
+      const TA a = __ldg(A + e);
+      TX v[K];
+      gather(__ldg(md.col + e), v);
+#pragma unroll
+      for (int c = 0; c < K; ++c) acc[c] = fma_t((TX)a, v[c], acc[c]);
+    }
+  }
+}
+
+// Gathers: rows of the padded p vectors, columns of an [K][n] vector, rows of an [n][K] vector.
+template <int K>
+struct GatherP64 {
+  const double* p;
+  __device__ __forceinline__ void operator()(int j, double (&v)[K]) const { load_row<K>(p, j, v); }
+};
+template <int K>
+struct GatherP32 {
+  const float* p;
+  __device__ __forceinline__ void operator()(int j, float (&v)[K]) const { load_row32<K>(p, j, v); }
+};
+template <int K>
+struct GatherSoA64 {
+  const double* x;
+  long n;
+  __device__ __forceinline__ void operator()(int j, double (&v)[K]) const {
+#pragma unroll
+    for (int c = 0; c < K; ++c) v[c] = x[c * n + j];
+  }
+};
+template <int K>
+struct GatherAoS64 {
+  const double* x;
+  __device__ __forceinline__ void operator()(int j, double (&v)[K]) const {
+#pragma unroll
+    for (int c = 0; c < K; ++c) v[c] = x[(long)j * K + c];
+  }
+};
+
+// Per-CTA snapshot of the per-mesh scalars a kernel needs. One thread reads them (one L2
+// request per CTA instead of one per warp: every CTA of a launch reads the same few words, so
+// per-warp reads would queue on a single L2 line) and the CTA shares them through shared memory.
+struct ScalSnap {
+  double alpha[kMaxK];
+  double beta[kMaxK];
+  double scale[kMaxK];
+  int act64[kMaxK];
+  int done;
+  int phase;
+};
+
+__device__ __forceinline__ void snap_scalars(const SolveScal* s, ScalSnap& sn) {
+  if (threadIdx.x == 0) {
+    sn.done = s->done;
+    sn.phase = s->phase;
+#pragma unroll
+    for (int c = 0; c < kMaxK; ++c) {
+      sn.alpha[c] = s->alpha[c];
+      sn.beta[c] = s->beta[c];
+      sn.scale[c] = s->scale[c];
+      sn.act64[c] = s->active64[c];
+    }
+  }
+  __syncthreads();
 }
 
 // The last CTA of an update launch decides whether the device-side loop goes on: it stops when
@@ -142,13 +292,16 @@ __global__ void __launch_bounds__(kBlock) finalize_kernel(const MeshDev* __restr
                                                           const int2* __restrict__ tiles, IoTable io) {
   const int2 tl = tiles[blockIdx.x];
   const MeshDev& md = mds[tl.x];
+  const long nn = md.n;
+  const long t0 = (long)tl.y * md.tile_rows;
+  const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
   double* __restrict__ out = io.out[tl.x];
 #pragma unroll
   for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
-    if (row < md.n) {
+    const long row = t0 + rr * kBlock + threadIdx.x;
+    if (row < t1) {
 #pragma unroll
-      for (int c = 0; c < K; ++c) out[row * K + c] = md.x[row * K + c];
+      for (int c = 0; c < K; ++c) out[row * K + c] = md.x[c * nn + row];
     }
   }
 }

@@ -10,9 +10,15 @@
 //                               .y = slot of the edge to the next corner | slot of the edge
 //                                    to the previous corner << 16 (slots relative to rowptr[v])
 //   facew    [m][4]  double     per face: t*cot_c/2 for the three corners, area/3
-//   A        [nnz]   double     A = M + t L;   A32 [nnz] float (mixed precision)
+//   sell_ptr [nslices+1] int32  sliced-ELL layout of the same pattern, slices of 32 rows: entry j
+//   sell_col [nnz_sell] int32   of row r sits at sell_ptr[r/32] + 32 j + r%32 (column-major in the
+//                               slice, so a warp's 32 rows read slot j with one contiguous load);
+//                               rows shorter than the slice width are padded with value 0
+//   A        [nnz_sell] double  A = M + t L in the sliced layout; A32 [nnz_sell] float (mixed)
 //   M, Dinv  [n]     double     lumped mass and 1/A_ii;  Dinv32 [n] float
-//   vectors  [n][K]  (p: [n][KP], KP = 4 when K = 3 so that a row is one aligned 32-byte load)
+//   solver vectors x, r, q (and their FP32 copies, rhs): column-major [K][n] so that a warp's
+//   accesses to consecutive rows are contiguous; p: [n][KP] (KP = 4 when K = 3) because it is
+//   gathered by rows in the SpMV (one aligned 32-byte FP64 or 16-byte FP32 load per row)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -78,7 +84,12 @@ enum : int {
 // Everything a kernel needs about one mesh (plain device pointers, passed in device arrays so
 // that a batch of meshes is a list of these).
 struct MeshDev {
-  int n, m, nnz, ntiles;   // ntiles = ceil(n / kTileRows)
+  int n, m, nnz, ntiles;   // ntiles = ceil(n / tile_rows)
+  int tile_rows;           // rows per FP64 solver tile (<= kTileRows, a multiple of 32), chosen at upload
+  int ntiles32, tile_rows32;  // the same for the mixed-precision kernels (their own occupancy)
+  int nnz_sell;            // stored entries of the sliced layout (0: A is plain CSR on rowptr/col)
+  const int* sell_ptr;     // [ceil(n/32)+1] slice offsets, or null for plain CSR
+  const int* sell_col;     // [nnz_sell]
   int k;
   double t;
   const int* F;
@@ -137,6 +148,8 @@ struct ig_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   int num_sms = 0;
+  int solver_slots = 0;    // CTAs of the FP64 solver kernels resident at once on the device
+  int solver_slots32 = 0;  // same for the mixed-precision solver kernels
   int live_meshes = 0;
   std::string last_error;
 };
@@ -187,6 +200,8 @@ struct Group {
   int ntiles = 0;                 // total tiles over all meshes
   MeshDev* mds = nullptr;         // device array [nmesh]
   int2* tiles = nullptr;          // device array [ntiles]: (mesh, local tile)
+  int ntiles32 = 0;
+  int2* tiles32 = nullptr;        // the tiling of the mixed-precision kernels
   LoopCtl* ctl = nullptr;         // device
   int* done_host = nullptr;       // pinned host word for the host-driven loop
   SolvePlan plans[2][kMaxK + 1];  // [mixed][k]
@@ -209,6 +224,8 @@ cudaError_t group_solve(Group& g, int k, int mixed, const IoTable& io, int rhs_m
                         cudaStream_t st);
 cudaError_t group_true_residual(Group& g, int k, const IoTable& io, int rhs_mass, cudaStream_t st);
 cudaError_t mesh_ensure_mixed(ig_mesh* mesh, cudaStream_t st);
+int solver_blocks_per_sm();        // ig_pcg.cu: min resident CTAs per SM of the FP64 loop kernels
+int solver_blocks_per_sm_mixed();  // ig_pcg_mixed.cu: same for the mixed-precision loop kernels
 cudaError_t group_solve_mixed(Group& g, int k, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
                               cudaStream_t st);
 
@@ -241,9 +258,13 @@ cudaError_t launch_pattern_rows(const int* F, int n, const int* incptr, int* inc
                                 int* err, cudaStream_t st);
 cudaError_t launch_pattern_cols(const int* F, int n, const int* incptr, const int* inc_fc, const int* nbr,
                                 const int* rowptr, int* col, int* diagpos, int2* inc, int* err, cudaStream_t st);
+cudaError_t launch_sell_width(const int* rowptr, int n, int* width32, cudaStream_t st);
+cudaError_t launch_sell_fill(const int* rowptr, const int* col, int n, const int* sell_ptr, int* sell_col,
+                             cudaStream_t st);
 
 // ig_assemble.cu (per-call V and t come from g.calls_dev)
 cudaError_t launch_assemble(Group& g, int mixed, cudaStream_t st);
+cudaError_t launch_operator_csr(const MeshDev& md, double* Acsr, cudaStream_t st);
 
 // ig_pcg.cu: see Group above
 

@@ -213,6 +213,41 @@ __global__ void __launch_bounds__(256) cols_kernel(const int* __restrict__ F, in
   }
 }
 
+// Sliced-ELL: 32 x (widest row of the slice) entries per slice of 32 rows.
+__global__ void __launch_bounds__(256) sell_width_kernel(const int* __restrict__ rowptr, int n,
+                                                         int* __restrict__ width32) {
+  const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nsl = (n + 31) / 32;
+  if (sl >= nsl) return;
+  int w = 0;
+  for (int r = sl * 32; r < sl * 32 + 32 && r < n; ++r) {
+    const int len = rowptr[r + 1] - rowptr[r];
+    w = len > w ? len : w;
+  }
+  width32[sl] = 32 * w;
+}
+
+// One thread per (slice, lane): copy the row's columns, pad with the row itself (value 0 later).
+// Lanes past n (last slice) are padded with the slice's first row.
+__global__ void __launch_bounds__(256) sell_fill_kernel(const int* __restrict__ rowptr, const int* __restrict__ col,
+                                                        int n, const int* __restrict__ sell_ptr,
+                                                        int* __restrict__ sell_col) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nsl = (n + 31) / 32;
+  if (t >= (long)nsl * 32) return;
+  const int sl = (int)(t >> 5), lane = (int)(t & 31);
+  const int r = (int)t;
+  const int base = sell_ptr[sl] + lane;
+  const int w = (sell_ptr[sl + 1] - sell_ptr[sl]) >> 5;
+  int len = 0, r0 = 0;
+  if (r < n) {
+    r0 = rowptr[r];
+    len = rowptr[r + 1] - r0;
+  }
+  const int pad = r < n ? r : sl * 32;
+  for (int j = 0; j < w; ++j) sell_col[base + 32 * j] = j < len ? col[r0 + j] : pad;
+}
+
 inline int blocks_for(long work) { return (int)((work + 255) / 256); }
 
 }  // namespace
@@ -237,6 +272,17 @@ cudaError_t launch_pattern_cols(const int* F, int n, const int* incptr, const in
                                 const int* rowptr, int* col, int* diagpos, int2* inc, int* err, cudaStream_t st) {
   (void)err;
   cols_kernel<<<blocks_for(n), 256, 0, st>>>(F, n, incptr, inc_fc, nbr, rowptr, col, diagpos, inc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sell_width(const int* rowptr, int n, int* width32, cudaStream_t st) {
+  sell_width_kernel<<<blocks_for((n + 31) / 32), 256, 0, st>>>(rowptr, n, width32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sell_fill(const int* rowptr, const int* col, int n, const int* sell_ptr, int* sell_col,
+                             cudaStream_t st) {
+  sell_fill_kernel<<<blocks_for((long)((n + 31) / 32) * 32), 256, 0, st>>>(rowptr, col, n, sell_ptr, sell_col);
   return cudaGetLastError();
 }
 

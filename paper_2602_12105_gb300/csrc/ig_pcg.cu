@@ -105,6 +105,9 @@ __global__ void __launch_bounds__(kBlock) init_kernel(const MeshDev* __restrict_
   __shared__ double sh[2 * K * kBlock];
   const int2 tl = tiles[blockIdx.x];
   const MeshDev& md = mds[tl.x];
+  const long nn = md.n;
+  const long t0 = (long)tl.y * md.tile_rows;
+  const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->cnt = 0u;
     ctl->iter = 0;
@@ -117,16 +120,16 @@ __global__ void __launch_bounds__(kBlock) init_kernel(const MeshDev* __restrict_
   for (int i = 0; i < 2 * K; ++i) acc[i] = 0.0;
 #pragma unroll
   for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
-    if (row < md.n) {
+    const long row = t0 + rr * kBlock + threadIdx.x;
+    if (row < t1) {
       const double dinv = md.Dinv[row];
       const double mass = rhs_mass ? md.M[row] : 1.0;
 #pragma unroll
       for (int c = 0; c < K; ++c) {
         const double b = rhs_mass ? mass * src[row * K + c] : src[row * K + c];
         const double z = dinv * b;
-        md.x[row * K + c] = 0.0;
-        md.r[row * K + c] = b;
+        md.x[c * nn + row] = 0.0;
+        md.r[c * nn + row] = b;
         md.p[row * KP<K>::v + c] = z;
         acc[c] = fma(b, z, acc[c]);
         acc[K + c] = fma(b, b, acc[K + c]);
@@ -141,37 +144,32 @@ __global__ void __launch_bounds__(kBlock) init_kernel(const MeshDev* __restrict_
 template <int K>
 __global__ void __launch_bounds__(kBlock) spmv_kernel(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles) {
   __shared__ double sh[K * kBlock];
+  __shared__ ScalSnap sn;
   const int2 tl = tiles[blockIdx.x];
   const MeshDev& md = mds[tl.x];
+  const long nn = md.n;
+  const long t0 = (long)tl.y * md.tile_rows;
+  const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
   SolveScal* s = md.s;
-  if (__ldcg(&s->done)) return;
+  snap_scalars(s, sn);
+  if (sn.done) return;
   const double* __restrict__ A = md.A;
-  const int* __restrict__ col = md.col;
-  const int* __restrict__ rowptr = md.rowptr;
   const double* __restrict__ p = md.p;
+  double* __restrict__ q = md.q;
   double pq[K];
 #pragma unroll
   for (int c = 0; c < K; ++c) pq[c] = 0.0;
 #pragma unroll
   for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
-    if (row < md.n) {
-      const int e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
+    const long row = t0 + rr * kBlock + threadIdx.x;
+    if (row < t1) {
       double acc[K];
-#pragma unroll
-      for (int c = 0; c < K; ++c) acc[c] = 0.0;
-      for (int e = e0; e < e1; ++e) {
-        const double a = __ldg(A + e);
-        double pj[K];
-        load_row<K>(p, __ldg(col + e), pj);
-#pragma unroll
-        for (int c = 0; c < K; ++c) acc[c] = fma(a, pj[c], acc[c]);
-      }
+      row_product<K>(md, A, row, GatherP64<K>{p}, acc);
       double pi[K];
       load_row<K>(p, row, pi);
 #pragma unroll
       for (int c = 0; c < K; ++c) {
-        md.q[row * K + c] = acc[c];
+        q[c * nn + row] = acc[c];
         pq[c] = fma(pi[c], acc[c], pq[c]);
       }
     }
@@ -181,36 +179,45 @@ __global__ void __launch_bounds__(kBlock) spmv_kernel(const MeshDev* __restrict_
 
 // ------------------------------------------------------------------------------- update
 template <int K>
-__global__ void __launch_bounds__(kBlock) update_kernel(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles,
+__global__ void __launch_bounds__(kBlock, 5) update_kernel(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles,
                                                         LoopCtl* ctl, cudaGraphConditionalHandle handle, int use_graph,
                                                         int nmesh) {
   __shared__ double sh[2 * K * kBlock];
+  __shared__ ScalSnap sn;
   const int2 tl = tiles[blockIdx.x];
   const MeshDev& md = mds[tl.x];
+  const long nn = md.n;
+  const long t0 = (long)tl.y * md.tile_rows;
+  const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
   SolveScal* s = md.s;
-  if (!__ldcg(&s->done)) {
+  snap_scalars(s, sn);
+  if (!sn.done) {
     double alpha[K];
 #pragma unroll
-    for (int c = 0; c < K; ++c) alpha[c] = __ldcg(&s->alpha[c]);
+    for (int c = 0; c < K; ++c) alpha[c] = sn.alpha[c];
     double acc[2 * K];
 #pragma unroll
     for (int i = 0; i < 2 * K; ++i) acc[i] = 0.0;
+    const double* __restrict__ Dinv = md.Dinv;
+    const double* __restrict__ p = md.p;
+    const double* __restrict__ q = md.q;
+    double* __restrict__ x = md.x;
+    double* __restrict__ r = md.r;
 #pragma unroll
     for (int rr = 0; rr < kRowsPerThread; ++rr) {
-      const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
-      if (row < md.n) {
-        const double dinv = md.Dinv[row];
+      const long row = t0 + rr * kBlock + threadIdx.x;
+      if (row < t1) {
+        const double dinv = Dinv[row];
         double pi[K];
-        load_row<K>(md.p, row, pi);
+        load_row<K>(p, row, pi);
 #pragma unroll
         for (int c = 0; c < K; ++c) {
-          const double xv = fma(alpha[c], pi[c], md.x[row * K + c]);
-          const double rv = fma(-alpha[c], md.q[row * K + c], md.r[row * K + c]);
-          md.x[row * K + c] = xv;
-          md.r[row * K + c] = rv;
-          const double z = dinv * rv;
-          acc[c] = fma(rv, z, acc[c]);
-          acc[K + c] = fma(rv, rv, acc[K + c]);
+          const double xn = fma(alpha[c], pi[c], x[c * nn + row]);
+          const double rn = fma(-alpha[c], q[c * nn + row], r[c * nn + row]);
+          x[c * nn + row] = xn;
+          r[c * nn + row] = rn;
+          acc[c] = fma(rn, dinv * rn, acc[c]);
+          acc[K + c] = fma(rn, rn, acc[K + c]);
         }
       }
     }
@@ -224,22 +231,30 @@ __global__ void __launch_bounds__(kBlock) update_kernel(const MeshDev* __restric
 template <int K>
 __global__ void __launch_bounds__(kBlock) pupdate_kernel(const MeshDev* __restrict__ mds,
                                                          const int2* __restrict__ tiles) {
+  __shared__ ScalSnap sn;
   const int2 tl = tiles[blockIdx.x];
   const MeshDev& md = mds[tl.x];
+  const long nn = md.n;
+  const long t0 = (long)tl.y * md.tile_rows;
+  const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
   SolveScal* s = md.s;
-  if (__ldcg(&s->done)) return;
+  snap_scalars(s, sn);
+  if (sn.done) return;
   double beta[K];
 #pragma unroll
-  for (int c = 0; c < K; ++c) beta[c] = __ldcg(&s->beta[c]);
+  for (int c = 0; c < K; ++c) beta[c] = sn.beta[c];
+  const double* __restrict__ Dinv = md.Dinv;
+  const double* __restrict__ r = md.r;
+  double* __restrict__ p = md.p;
 #pragma unroll
   for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
-    if (row < md.n) {
-      const double dinv = md.Dinv[row];
+    const long row = t0 + rr * kBlock + threadIdx.x;
+    if (row < t1) {
+      const double dinv = Dinv[row];
       double pi[K];
-      load_row<K>(md.p, row, pi);
+      load_row<K>(p, row, pi);
 #pragma unroll
-      for (int c = 0; c < K; ++c) md.p[row * KP<K>::v + c] = fma(beta[c], pi[c], dinv * md.r[row * K + c]);
+      for (int c = 0; c < K; ++c) p[row * KP<K>::v + c] = fma(beta[c], pi[c], dinv * r[c * nn + row]);
     }
   }
 }
@@ -252,6 +267,9 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(const MeshDev* __restr
   __shared__ double sh[K * kBlock];
   const int2 tl = tiles[blockIdx.x];
   const MeshDev& md = mds[tl.x];
+  const long nn = md.n;
+  const long t0 = (long)tl.y * md.tile_rows;
+  const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
   const double* __restrict__ src = io.in[tl.x];
   const double* __restrict__ xs = io.out[tl.x];
   double acc[K];
@@ -259,17 +277,10 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(const MeshDev* __restr
   for (int c = 0; c < K; ++c) acc[c] = 0.0;
 #pragma unroll
   for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
-    if (row < md.n) {
+    const long row = t0 + rr * kBlock + threadIdx.x;
+    if (row < t1) {
       double ax[K];
-#pragma unroll
-      for (int c = 0; c < K; ++c) ax[c] = 0.0;
-      for (int e = md.rowptr[row]; e < md.rowptr[row + 1]; ++e) {
-        const double a = md.A[e];
-        const long j = md.col[e];
-#pragma unroll
-        for (int c = 0; c < K; ++c) ax[c] = fma(a, xs[j * K + c], ax[c]);
-      }
+      row_product<K>(md, md.A, row, GatherAoS64<K>{xs}, ax);
       const double mass = rhs_mass ? md.M[row] : 1.0;
 #pragma unroll
       for (int c = 0; c < K; ++c) {
@@ -379,21 +390,34 @@ cudaError_t solve_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_op
 
 }  // namespace
 
+int solver_blocks_per_sm() {
+  int a = 0, b = 0, c = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, spmv_kernel<3>, kBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, update_kernel<3>, kBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, pupdate_kernel<3>, kBlock, 0);
+  int m = a < b ? a : b;
+  m = m < c ? m : c;
+  return m > 0 ? m : 1;
+}
+
 cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, cudaStream_t st) {
   g.nmesh = nmesh;
   g.host_mds.assign(host_mds, host_mds + nmesh);
-  std::vector<int2> tiles, ftiles, rtiles;
+  std::vector<int2> tiles, tiles32, ftiles, rtiles;
   for (int i = 0; i < nmesh; ++i) {
     for (int t = 0; t < host_mds[i].ntiles; ++t) tiles.push_back(make_int2(i, t));
+    for (int t = 0; t < host_mds[i].ntiles32; ++t) tiles32.push_back(make_int2(i, t));
     for (int t = 0; t < (host_mds[i].m + 255) / 256; ++t) ftiles.push_back(make_int2(i, t));
     for (int t = 0; t < (host_mds[i].n + 255) / 256; ++t) rtiles.push_back(make_int2(i, t));
   }
   g.ntiles = (int)tiles.size();
+  g.ntiles32 = (int)tiles32.size();
   g.nface_tiles = (int)ftiles.size();
   g.nrow_tiles = (int)rtiles.size();
   cudaError_t e;
   if ((e = cudaMalloc(&g.mds, sizeof(MeshDev) * nmesh)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&g.tiles, sizeof(int2) * tiles.size())) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&g.tiles32, sizeof(int2) * (tiles32.size() ? tiles32.size() : 1))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&g.face_tiles, sizeof(int2) * ftiles.size())) != cudaSuccess) return e;
   if ((e = cudaMalloc(&g.row_tiles, sizeof(int2) * rtiles.size())) != cudaSuccess) return e;
   if ((e = cudaMalloc(&g.ctl, sizeof(LoopCtl))) != cudaSuccess) return e;
@@ -405,6 +429,9 @@ cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, cudaStream_
     return e;
   if ((e = cudaMemcpyAsync(g.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, st)) !=
       cudaSuccess)
+    return e;
+  if (!tiles32.empty() && (e = cudaMemcpyAsync(g.tiles32, tiles32.data(), sizeof(int2) * tiles32.size(),
+                                               cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return e;
   if ((e = cudaMemcpyAsync(g.face_tiles, ftiles.data(), sizeof(int2) * ftiles.size(), cudaMemcpyHostToDevice, st)) !=
       cudaSuccess)
@@ -444,6 +471,7 @@ void group_destroy(Group& g) {
   if (g.capture_stream) cudaStreamDestroy(g.capture_stream);
   if (g.mds) cudaFree(g.mds);
   if (g.tiles) cudaFree(g.tiles);
+  if (g.tiles32) cudaFree(g.tiles32);
   if (g.face_tiles) cudaFree(g.face_tiles);
   if (g.row_tiles) cudaFree(g.row_tiles);
   if (g.ctl) cudaFree(g.ctl);
@@ -575,6 +603,7 @@ extern "C" ig_status ig_solve_csr_noalloc(const int32_t* rowptr_dev, const int32
   MeshDev md{};
   md.n = (int)n;
   md.nnz = (int)nnz;
+  md.tile_rows = kTileRows;
   md.ntiles = (int)((n + kTileRows - 1) / kTileRows);
   md.k = k;
   md.rowptr = rowptr_dev;

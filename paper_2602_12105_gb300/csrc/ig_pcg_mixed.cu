@@ -153,6 +153,9 @@ __global__ void __launch_bounds__(kBlock) init_mixed_kernel(const MeshDev* __res
   __shared__ double sh[K * kBlock];
   const int2 tl = tiles[blockIdx.x];
   const MeshDev& md = mds[tl.x];
+  const long nn = md.n;
+  const long t0 = (long)tl.y * md.tile_rows32;
+  const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->cnt = 0u;
     ctl->iter = 0;
@@ -165,39 +168,41 @@ __global__ void __launch_bounds__(kBlock) init_mixed_kernel(const MeshDev* __res
   for (int c = 0; c < K; ++c) acc[c] = 0.0;
 #pragma unroll
   for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
-    if (row < md.n) {
+    const long row = t0 + rr * kBlock + threadIdx.x;
+    if (row < t1) {
       const double mass = rhs_mass ? md.M[row] : 1.0;
 #pragma unroll
       for (int c = 0; c < K; ++c) {
         const double b = rhs_mass ? mass * src[row * K + c] : src[row * K + c];
-        md.rhs[row * K + c] = b;
-        md.r[row * K + c] = b;
-        md.x[row * K + c] = 0.0;
+        md.rhs[c * nn + row] = b;
+        md.r[c * nn + row] = b;
+        md.x[c * nn + row] = 0.0;
         acc[c] = fma(b, b, acc[c]);
       }
     }
   }
-  if (reduce_tiles<K>(acc, md.part, tl.y, md.ntiles, &md.s->cnt[2], sh) && threadIdx.x == 0)
+  if (reduce_tiles<K>(acc, md.part, tl.y, md.ntiles32, &md.s->cnt[2], sh) && threadIdx.x == 0)
     finish_init_mixed(md.s, K, acc, tol, inner_tol, max_iter, max_refine);
 }
 
 template <int K>
-__global__ void __launch_bounds__(kBlock) spmv_mixed_kernel(const MeshDev* __restrict__ mds,
+__global__ void __launch_bounds__(kBlock, 6) spmv_mixed_kernel(const MeshDev* __restrict__ mds,
                                                             const int2* __restrict__ tiles) {
   __shared__ double sh[K * kBlock];
   const int2 tl = tiles[blockIdx.x];
   const MeshDev& md = mds[tl.x];
+  const long nn = md.n;
+  const long t0 = (long)tl.y * md.tile_rows32;
+  const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
   SolveScal* s = md.s;
-  if (__ldcg(&s->done)) return;
-  const int phase = __ldcg(&s->phase);
-  if (phase == kPhaseRestart) return;
-  const int* __restrict__ rowptr = md.rowptr;
-  const int* __restrict__ col = md.col;
+  __shared__ ScalSnap sn;
+  snap_scalars(s, sn);
+  if (sn.done) return;
+  if (sn.phase != kPhaseInner) return;
   double acc[K];
 #pragma unroll
   for (int c = 0; c < K; ++c) acc[c] = 0.0;
-  if (phase == kPhaseInner) {
+  {
     const float* __restrict__ A = md.A32;
     const float* __restrict__ p = md.p32;
     float pq[K];
@@ -205,93 +210,98 @@ __global__ void __launch_bounds__(kBlock) spmv_mixed_kernel(const MeshDev* __res
     for (int c = 0; c < K; ++c) pq[c] = 0.f;
 #pragma unroll
     for (int rr = 0; rr < kRowsPerThread; ++rr) {
-      const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
-      if (row < md.n) {
-        const int e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
+      const long row = t0 + rr * kBlock + threadIdx.x;
+      if (row < t1) {
         float q[K];
-#pragma unroll
-        for (int c = 0; c < K; ++c) q[c] = 0.f;
-        for (int e = e0; e < e1; ++e) {
-          const float a = __ldg(A + e);
-          float pj[K];
-          load_row32<K>(p, __ldg(col + e), pj);
-#pragma unroll
-          for (int c = 0; c < K; ++c) q[c] = fmaf(a, pj[c], q[c]);
-        }
+        row_product<K>(md, A, row, GatherP32<K>{p}, q);
         float pi[K];
         load_row32<K>(p, row, pi);
 #pragma unroll
         for (int c = 0; c < K; ++c) {
-          md.q32[row * K + c] = q[c];
+          md.q32[c * nn + row] = q[c];
           pq[c] = fmaf(pi[c], q[c], pq[c]);
         }
       }
     }
-#pragma unroll
-    for (int c = 0; c < K; ++c) acc[c] = (double)pq[c];
-    if (reduce_tiles<K>(acc, md.part, tl.y, md.ntiles, &s->cnt[0], sh) && threadIdx.x == 0) finish_spmv(s, K, acc);
-  } else {
-    // Apply: r64 = rhs - A64 x64 in FP64 and its squared norms
-    const double* __restrict__ A = md.A;
-    const double* __restrict__ x = md.x;
-#pragma unroll
-    for (int rr = 0; rr < kRowsPerThread; ++rr) {
-      const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
-      if (row < md.n) {
-        const int e0 = __ldg(rowptr + row), e1 = __ldg(rowptr + row + 1);
-        double ax[K];
-#pragma unroll
-        for (int c = 0; c < K; ++c) ax[c] = 0.0;
-        for (int e = e0; e < e1; ++e) {
-          const double a = __ldg(A + e);
-          const long j = __ldg(col + e);
-#pragma unroll
-          for (int c = 0; c < K; ++c) ax[c] = fma(a, x[j * K + c], ax[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < K; ++c) {
-          const double res = md.rhs[row * K + c] - ax[c];
-          md.r[row * K + c] = res;
-          acc[c] = fma(res, res, acc[c]);
-        }
-      }
-    }
-    if (reduce_tiles<K>(acc, md.part, tl.y, md.ntiles, &s->cnt[0], sh) && threadIdx.x == 0)
-      finish_residual(s, K, acc);
+    block_sum_f32<K>(pq, acc, sh);
+    if (publish_tiles<K>(acc, md.part, tl.y, md.ntiles32, &s->cnt[0], sh) && threadIdx.x == 0) finish_spmv(s, K, acc);
   }
 }
 
+// Apply phase: r64 = rhs - A64 x64 in FP64 and its squared norms (the refinement residual).
+// Kept out of the FP32 SpMV kernel so that the hot FP32 kernel stays small.
 template <int K>
-__global__ void __launch_bounds__(kBlock) update_mixed_kernel(const MeshDev* __restrict__ mds,
+__global__ void __launch_bounds__(kBlock) resid_mixed_kernel(const MeshDev* __restrict__ mds,
+                                                             const int2* __restrict__ tiles) {
+  __shared__ double sh[K * kBlock];
+  __shared__ ScalSnap sn;
+  const int2 tl = tiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  const long nn = md.n;
+  const long t0 = (long)tl.y * md.tile_rows32;
+  const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
+  SolveScal* s = md.s;
+  snap_scalars(s, sn);
+  if (sn.done || sn.phase != kPhaseApply) return;
+  double acc[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) acc[c] = 0.0;
+  const double* __restrict__ A = md.A;
+  const double* __restrict__ x = md.x;
+#pragma unroll
+  for (int rr = 0; rr < kRowsPerThread; ++rr) {
+    const long row = t0 + rr * kBlock + threadIdx.x;
+    if (row < t1) {
+      double ax[K];
+      row_product<K>(md, A, row, GatherSoA64<K>{x, nn}, ax);
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        const double res = md.rhs[c * nn + row] - ax[c];
+        md.r[c * nn + row] = res;
+        acc[c] = fma(res, res, acc[c]);
+      }
+    }
+  }
+  if (reduce_tiles<K>(acc, md.part, tl.y, md.ntiles32, &s->cnt[0], sh) && threadIdx.x == 0)
+    finish_residual(s, K, acc);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock, 8) update_mixed_kernel(const MeshDev* __restrict__ mds,
                                                               const int2* __restrict__ tiles, LoopCtl* ctl,
                                                               cudaGraphConditionalHandle handle, int use_graph,
                                                               int nmesh) {
   __shared__ double sh[2 * K * kBlock];
   const int2 tl = tiles[blockIdx.x];
   const MeshDev& md = mds[tl.x];
+  const long nn = md.n;
+  const long t0 = (long)tl.y * md.tile_rows32;
+  const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
   SolveScal* s = md.s;
-  const int phase = __ldcg(&s->phase);
-  if (!__ldcg(&s->done) && phase != kPhaseApply) {
+  __shared__ ScalSnap sn;
+  snap_scalars(s, sn);
+  const int phase = sn.phase;
+  if (!sn.done && phase != kPhaseApply) {
     float rz[K], rr2[K];
 #pragma unroll
     for (int c = 0; c < K; ++c) rz[c] = rr2[c] = 0.f;
     if (phase == kPhaseInner) {
       float alpha[K];
 #pragma unroll
-      for (int c = 0; c < K; ++c) alpha[c] = (float)__ldcg(&s->alpha[c]);
+      for (int c = 0; c < K; ++c) alpha[c] = (float)sn.alpha[c];
 #pragma unroll
       for (int rr = 0; rr < kRowsPerThread; ++rr) {
-        const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
-        if (row < md.n) {
+        const long row = t0 + rr * kBlock + threadIdx.x;
+        if (row < t1) {
           const float dinv = md.Dinv32[row];
           float pi[K];
           load_row32<K>(md.p32, row, pi);
 #pragma unroll
           for (int c = 0; c < K; ++c) {
-            const float xv = fmaf(alpha[c], pi[c], md.x32[row * K + c]);
-            const float rv = fmaf(-alpha[c], md.q32[row * K + c], md.r32[row * K + c]);
-            md.x32[row * K + c] = xv;
-            md.r32[row * K + c] = rv;
+            const float xv = fmaf(alpha[c], pi[c], md.x32[c * nn + row]);
+            const float rv = fmaf(-alpha[c], md.q32[c * nn + row], md.r32[c * nn + row]);
+            md.x32[c * nn + row] = xv;
+            md.r32[c * nn + row] = rv;
             rz[c] = fmaf(rv, dinv * rv, rz[c]);
             rr2[c] = fmaf(rv, rv, rr2[c]);
           }
@@ -303,32 +313,34 @@ __global__ void __launch_bounds__(kBlock) update_mixed_kernel(const MeshDev* __r
       int act[K];
 #pragma unroll
       for (int c = 0; c < K; ++c) {
-        act[c] = __ldcg(&s->active64[c]);
-        inv[c] = 1.0 / __ldcg(&s->scale[c]);
+        act[c] = sn.act64[c];
+        inv[c] = 1.0 / sn.scale[c];
       }
 #pragma unroll
       for (int rr = 0; rr < kRowsPerThread; ++rr) {
-        const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
-        if (row < md.n) {
+        const long row = t0 + rr * kBlock + threadIdx.x;
+        if (row < t1) {
           const float dinv = md.Dinv32[row];
 #pragma unroll
           for (int c = 0; c < K; ++c) {
-            const float rv = act[c] ? (float)(md.r[row * K + c] * inv[c]) : 0.f;
-            md.r32[row * K + c] = rv;
-            md.x32[row * K + c] = 0.f;
+            const float rv = act[c] ? (float)(md.r[c * nn + row] * inv[c]) : 0.f;
+            md.r32[c * nn + row] = rv;
+            md.x32[c * nn + row] = 0.f;
             rz[c] = fmaf(rv, dinv * rv, rz[c]);
             rr2[c] = fmaf(rv, rv, rr2[c]);
           }
         }
       }
     }
-    double acc[2 * K];
+    float accf[2 * K];
 #pragma unroll
     for (int c = 0; c < K; ++c) {
-      acc[c] = (double)rz[c];
-      acc[K + c] = (double)rr2[c];
+      accf[c] = rz[c];
+      accf[K + c] = rr2[c];
     }
-    if (reduce_tiles<2 * K>(acc, md.part, tl.y, md.ntiles, &s->cnt[1], sh) && threadIdx.x == 0) {
+    double acc[2 * K];
+    block_sum_f32<2 * K>(accf, acc, sh);
+    if (publish_tiles<2 * K>(acc, md.part, tl.y, md.ntiles32, &s->cnt[1], sh) && threadIdx.x == 0) {
       if (phase == kPhaseInner) finish_update_mixed(s, K, acc);
       else finish_restart(s, K, acc);
     }
@@ -337,39 +349,44 @@ __global__ void __launch_bounds__(kBlock) update_mixed_kernel(const MeshDev* __r
 }
 
 template <int K>
-__global__ void __launch_bounds__(kBlock) pupdate_mixed_kernel(const MeshDev* __restrict__ mds,
+__global__ void __launch_bounds__(kBlock, 8) pupdate_mixed_kernel(const MeshDev* __restrict__ mds,
                                                                const int2* __restrict__ tiles) {
   const int2 tl = tiles[blockIdx.x];
   const MeshDev& md = mds[tl.x];
+  const long nn = md.n;
+  const long t0 = (long)tl.y * md.tile_rows32;
+  const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
   SolveScal* s = md.s;
-  if (__ldcg(&s->done)) return;
-  const int phase = __ldcg(&s->phase);
+  __shared__ ScalSnap sn;
+  snap_scalars(s, sn);
+  if (sn.done) return;
+  const int phase = sn.phase;
   if (phase == kPhaseInner) {
     float beta[K];
 #pragma unroll
-    for (int c = 0; c < K; ++c) beta[c] = (float)__ldcg(&s->beta[c]);
+    for (int c = 0; c < K; ++c) beta[c] = (float)sn.beta[c];
 #pragma unroll
     for (int rr = 0; rr < kRowsPerThread; ++rr) {
-      const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
-      if (row < md.n) {
+      const long row = t0 + rr * kBlock + threadIdx.x;
+      if (row < t1) {
         const float dinv = md.Dinv32[row];
         float pi[K];
         load_row32<K>(md.p32, row, pi);
 #pragma unroll
-        for (int c = 0; c < K; ++c) md.p32[row * KPm<K>::v + c] = fmaf(beta[c], pi[c], dinv * md.r32[row * K + c]);
+        for (int c = 0; c < K; ++c) md.p32[row * KPm<K>::v + c] = fmaf(beta[c], pi[c], dinv * md.r32[c * nn + row]);
       }
     }
   } else if (phase == kPhaseApply) {
     double sc[K];
 #pragma unroll
-    for (int c = 0; c < K; ++c) sc[c] = __ldcg(&s->scale[c]);
+    for (int c = 0; c < K; ++c) sc[c] = sn.scale[c];
 #pragma unroll
     for (int rr = 0; rr < kRowsPerThread; ++rr) {
-      const long row = (long)tl.y * kTileRows + rr * kBlock + threadIdx.x;
-      if (row < md.n) {
+      const long row = t0 + rr * kBlock + threadIdx.x;
+      if (row < t1) {
 #pragma unroll
         for (int c = 0; c < K; ++c)
-          md.x[row * K + c] = fma(sc[c], (double)md.x32[row * K + c], md.x[row * K + c]);
+          md.x[c * nn + row] = fma(sc[c], (double)md.x32[c * nn + row], md.x[c * nn + row]);
       }
     }
   }
@@ -395,9 +412,10 @@ cudaError_t build_plan_mixed(Group& g, SolvePlan& pl) {
   cudaStream_t cs = g.capture_stream;
   e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
-  spmv_mixed_kernel<K><<<g.ntiles, kBlock, 0, cs>>>(g.mds, g.tiles);
-  update_mixed_kernel<K><<<g.ntiles, kBlock, 0, cs>>>(g.mds, g.tiles, g.ctl, handle, 1, g.nmesh);
-  pupdate_mixed_kernel<K><<<g.ntiles, kBlock, 0, cs>>>(g.mds, g.tiles);
+  resid_mixed_kernel<K><<<g.ntiles32, kBlock, 0, cs>>>(g.mds, g.tiles32);
+  spmv_mixed_kernel<K><<<g.ntiles32, kBlock, 0, cs>>>(g.mds, g.tiles32);
+  update_mixed_kernel<K><<<g.ntiles32, kBlock, 0, cs>>>(g.mds, g.tiles32, g.ctl, handle, 1, g.nmesh);
+  pupdate_mixed_kernel<K><<<g.ntiles32, kBlock, 0, cs>>>(g.mds, g.tiles32);
   cudaError_t le = cudaGetLastError();
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(cs, &captured);
@@ -418,7 +436,7 @@ cudaError_t solve_mixed_k(Group& g, const IoTable& io, int rhs_mass, const ig_so
   const int cap = o.max_iter + 3 * o.max_refine + 4;
   {
     IG_PROF("pcg_init", st);
-    init_mixed_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io, rhs_mass, g.ctl, o.rel_tol, o.inner_tol,
+    init_mixed_kernel<K><<<g.ntiles32, kBlock, 0, st>>>(g.mds, g.tiles32, io, rhs_mass, g.ctl, o.rel_tol, o.inner_tol,
                                                       o.max_iter, o.max_refine, cap);
   }
   cudaError_t e = cudaGetLastError();
@@ -434,17 +452,21 @@ cudaError_t solve_mixed_k(Group& g, const IoTable& io, int rhs_mass, const ig_so
   } else {
     for (int it = 0; it < cap; ++it) {
       {
+        IG_PROF("pcg32_resid64", st);
+        resid_mixed_kernel<K><<<g.ntiles32, kBlock, 0, st>>>(g.mds, g.tiles32);
+      }
+      {
         IG_PROF("pcg32_spmv", st);
-        spmv_mixed_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles);
+        spmv_mixed_kernel<K><<<g.ntiles32, kBlock, 0, st>>>(g.mds, g.tiles32);
       }
       {
         IG_PROF("pcg32_update", st);
-        update_mixed_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, g.ctl, cudaGraphConditionalHandle{}, 0,
+        update_mixed_kernel<K><<<g.ntiles32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ctl, cudaGraphConditionalHandle{}, 0,
                                                             g.nmesh);
       }
       {
         IG_PROF("pcg32_pupdate", st);
-        pupdate_mixed_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles);
+        pupdate_mixed_kernel<K><<<g.ntiles32, kBlock, 0, st>>>(g.mds, g.tiles32);
       }
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
@@ -465,6 +487,16 @@ cudaError_t solve_mixed_k(Group& g, const IoTable& io, int rhs_mass, const ig_so
 }
 
 }  // namespace
+
+int solver_blocks_per_sm_mixed() {
+  int a = 0, b = 0, c = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, spmv_mixed_kernel<3>, kBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, update_mixed_kernel<3>, kBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, pupdate_mixed_kernel<3>, kBlock, 0);
+  int m = a < b ? a : b;
+  m = m < c ? m : c;
+  return m > 0 ? m : 1;
+}
 
 cudaError_t group_solve_mixed(Group& g, int k, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
                               cudaStream_t st) {
