@@ -120,7 +120,7 @@ ig_status ig_batch_create(ig_ctx* ctx, ig_mesh* const* meshes, int count, ig_bat
   b->meshes.assign(meshes, meshes + count);
   std::vector<MeshDev> mds(count);
   for (int i = 0; i < count; ++i) mds[i] = meshes[i]->md;
-  cudaError_t e = group_init(b->group, mds.data(), count, ctx->stream);
+  cudaError_t e = group_init(b->group, mds.data(), count, ctx->solver_slots, ctx->solver_slots32, ctx->stream);
   if (e != cudaSuccess) {
     group_destroy(b->group);
     return batch_cuda(ctx, e, "batch create");

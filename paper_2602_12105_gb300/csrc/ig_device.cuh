@@ -20,6 +20,39 @@ __device__ __forceinline__ bool is_finite(double x) {
   return (__double_as_longlong(x) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
 }
 
+// Thread j of the CTA adds the partials of tiles j, j + kBlock, j + 2 kBlock, ... in that order
+// (the association is fixed by the tile count alone, so the result is deterministic). Loads go in
+// batches of 4 tiles so that a thread has several L2 requests in flight.
+template <int NV>
+__device__ __noinline__ void gather_partials_impl(const double* __restrict__ part, int ntiles, double* out) {
+  double v[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = 0.0;
+  int t = threadIdx.x;
+  for (; t + 3 * kBlock < ntiles; t += 4 * kBlock) {
+    double b[4][NV];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) b[u][i] = __ldcg(part + (t + u * kBlock) * kPartStride + i);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) v[i] += b[u][i];
+  }
+  for (; t < ntiles; t += kBlock)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += __ldcg(part + t * kPartStride + i);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) out[i] = v[i];
+}
+
+// (kept out of line: only the last CTA of a reduction runs it)
+template <int NV>
+__device__ __forceinline__ void gather_partials(const double* __restrict__ part, int ntiles, double (&v)[NV]) {
+  gather_partials_impl<NV>(part, ntiles, v);
+}
+
 // Sum v[0..NV) over the CTA; thread 0 receives the totals. sh holds NV*kBlock doubles.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
@@ -82,11 +115,7 @@ __device__ __forceinline__ bool publish_tiles(double (&v)[NV], double* part, int
   __syncthreads();
   if (!s_last2) return false;
   __threadfence();
-#pragma unroll
-  for (int i = 0; i < NV; ++i) v[i] = 0.0;
-  for (int t = threadIdx.x; t < ntiles; t += kBlock)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] += __ldcg(part + t * kPartStride + i);
+  gather_partials<NV>(part, ntiles, v);
   block_sum<NV>(v, sh);
   if (threadIdx.x == 0) *cnt = 0u;
   return true;
@@ -110,11 +139,7 @@ __device__ __forceinline__ bool reduce_tiles(double (&v)[NV], double* part, int 
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-#pragma unroll
-  for (int i = 0; i < NV; ++i) v[i] = 0.0;
-  for (int t = threadIdx.x; t < ntiles; t += kBlock)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] += __ldcg(part + t * kPartStride + i);
+  gather_partials<NV>(part, ntiles, v);
   block_sum<NV>(v, sh);
   if (threadIdx.x == 0) *cnt = 0u;
   return true;
@@ -156,14 +181,36 @@ __device__ __forceinline__ void row_product(const MeshDev& md, const TA* __restr
     const int w = (b1 - b0) >> 5;
     const int base = b0 + (int)(row & 31);
     const int* __restrict__ sc = md.sell_col;
-#pragma unroll 4
-    for (int j = 0; j < w; ++j) {
-      const int e = base + 32 * j;
-      const TA a = __ldg(A + e);
-      TX v[K];
-      gather(__ldg(sc + e), v);
+    if constexpr (sizeof(TX) == 4) {
+      // FP32: up to 8 slots at once (a mesh row has ~7): all column/value loads, then the gathers
+      for (int j0 = 0; j0 < w; j0 += 8) {
+        int cj[8];
+        TA aj[8];
 #pragma unroll
-      for (int c = 0; c < K; ++c) acc[c] = fma_t((TX)a, v[c], acc[c]);
+        for (int u = 0; u < 8; ++u)
+          if (j0 + u < w) {
+            cj[u] = __ldg(sc + base + 32 * (j0 + u));
+            aj[u] = __ldg(A + base + 32 * (j0 + u));
+          }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (j0 + u < w) {
+            TX v[K];
+            gather(cj[u], v);
+#pragma unroll
+            for (int c = 0; c < K; ++c) acc[c] = fma_t((TX)aj[u], v[c], acc[c]);
+          }
+      }
+    } else {
+#pragma unroll 4
+      for (int j = 0; j < w; ++j) {
+        const int e = base + 32 * j;
+        const TA a = __ldg(A + e);
+        TX v[K];
+        gather(__ldg(sc + e), v);
+#pragma unroll
+        for (int c = 0; c < K; ++c) acc[c] = fma_t((TX)a, v[c], acc[c]);
+      }
     }
   } else {
     const int e0 = __ldg(md.rowptr + row), e1 = __ldg(md.rowptr + row + 1);
@@ -219,6 +266,7 @@ struct ScalSnap {
 };
 
 __device__ __forceinline__ void snap_scalars(const SolveScal* s, ScalSnap& sn) {
+  __syncthreads();  // every thread is done with the previous snapshot
   if (threadIdx.x == 0) {
     sn.done = s->done;
     sn.phase = s->phase;
@@ -233,6 +281,89 @@ __device__ __forceinline__ void snap_scalars(const SolveScal* s, ScalSnap& sn) {
   __syncthreads();
 }
 
+// ------------------------------------------------------------------------------- persistent tiles
+// The loop kernels run one CTA per resident slot; CTA b takes the flat tiles b, b + G, b + 2G, ...
+// (G = gridDim.x). A tile's partial sums (already summed over the CTA, in thread 0) go to the
+// mesh's part[tile]; each CTA counts the tiles it did per run of consecutive tiles of one mesh
+// and adds that count to the mesh's counter with one atomic. The CTA whose addition completes
+// the mesh adds the partials in tile order (deterministic, independent of G and of any batch)
+// and calls finish(md, totals) on thread 0.
+template <int NV, typename Finish>
+__device__ __forceinline__ void flush_tiles(const MeshDev& md, int ntiles, unsigned run, unsigned int* cnt,
+                                            double* sh, const Finish& finish) {
+  __shared__ int s_done;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(cnt, run);
+    s_done = (prev + run == (unsigned)ntiles);
+  }
+  __syncthreads();
+  if (s_done) {
+    __threadfence();
+    double v[NV];
+    gather_partials<NV>(md.part, ntiles, v);
+    block_sum<NV>(v, sh);
+    if (threadIdx.x == 0) {
+      *cnt = 0u;
+      finish(md, v);
+    }
+  }
+  __syncthreads();
+}
+
+// body(md, tile, v) does the tile's work and leaves its CTA-summed partials in thread 0's v;
+// active(sn) says whether a mesh takes part in this launch (uniform per CTA). tiling 0: FP64
+// solver tiles, 1: mixed-precision tiles; cnt_idx selects the mesh counter.
+template <int NV, typename Active, typename Body, typename Finish>
+__device__ __forceinline__ void tile_loop(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles,
+                                          int ntiles_total, int tiling, int cnt_idx, double* sh, ScalSnap& sn,
+                                          const Active& active, const Body& body, const Finish& finish) {
+  int cur = -1;
+  unsigned run = 0;
+  for (int t = blockIdx.x; t < ntiles_total; t += gridDim.x) {
+    const int2 tl = tiles[t];
+    if (tl.x != cur) {
+      if (run) {
+        const MeshDev& pm = mds[cur];
+        flush_tiles<NV>(pm, tiling ? pm.ntiles32 : pm.ntiles, run, &pm.s->cnt[cnt_idx], sh, finish);
+      }
+      cur = tl.x;
+      run = 0;
+      snap_scalars(mds[cur].s, sn);
+    }
+    if (!active(sn)) continue;
+    const MeshDev& md = mds[cur];
+    double v[NV];
+    body(md, tl.y, v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) md.part[tl.y * kPartStride + i] = v[i];
+    }
+    ++run;
+  }
+  if (run) {
+    const MeshDev& pm = mds[cur];
+    flush_tiles<NV>(pm, tiling ? pm.ntiles32 : pm.ntiles, run, &pm.s->cnt[cnt_idx], sh, finish);
+  }
+}
+
+// Tile loop without reductions.
+template <typename Active, typename Body>
+__device__ __forceinline__ void tile_loop_plain(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles,
+                                                int ntiles_total, ScalSnap& sn, const Active& active,
+                                                const Body& body) {
+  int cur = -1;
+  for (int t = blockIdx.x; t < ntiles_total; t += gridDim.x) {
+    const int2 tl = tiles[t];
+    if (tl.x != cur) {
+      cur = tl.x;
+      snap_scalars(mds[cur].s, sn);
+    }
+    if (!active(sn)) continue;
+    body(mds[cur], tl.y);
+  }
+}
+
 // The last CTA of an update launch decides whether the device-side loop goes on: it stops when
 // every mesh of the group is done or the hard cap on iterations is reached.
 __device__ __forceinline__ void loop_control(const MeshDev* __restrict__ mds, LoopCtl* ctl,
@@ -243,8 +374,13 @@ __device__ __forceinline__ void loop_control(const MeshDev* __restrict__ mds, Lo
     const unsigned prev = atomicAdd(&ctl->cnt, 1u);
     if (prev == gridDim.x - 1u) {
       __threadfence();
-      int all = 1;
-      for (int i = 0; i < nmesh; ++i) all &= (__ldcg(&mds[i].s->done) != 0);
+      int all = 1, apply = 0;
+      for (int i = 0; i < nmesh; ++i) {
+        const int d = __ldcg(&mds[i].s->done);
+        all &= (d != 0);
+        apply |= (!d && __ldcg(&mds[i].s->phase) == kPhaseApply);
+      }
+      ctl->any_apply = apply;
       const int it = ctl->iter + 1;
       ctl->iter = it;
       if (all || it >= ctl->cap) {

@@ -162,6 +162,7 @@ struct LoopCtl {
   int iter;           // iterations of the device-side loop so far
   int cap;            // hard cap on iterations of the device-side loop
   int all_done;       // 1 once every mesh of the group is done
+  int any_apply;      // mixed precision: some mesh will recompute its FP64 residual next
 };
 
 // Per-launch pointers that change from call to call (kept out of the cached graphs).
@@ -202,6 +203,7 @@ struct Group {
   int2* tiles = nullptr;          // device array [ntiles]: (mesh, local tile)
   int ntiles32 = 0;
   int2* tiles32 = nullptr;        // the tiling of the mixed-precision kernels
+  int grid64 = 0, grid32 = 0;     // persistent grid of the loop kernels: min(tiles, resident slots)
   LoopCtl* ctl = nullptr;         // device
   int* done_host = nullptr;       // pinned host word for the host-driven loop
   SolvePlan plans[2][kMaxK + 1];  // [mixed][k]
@@ -216,7 +218,7 @@ struct Group {
   std::vector<MeshDev> host_mds;  // host copy of mds
 };
 
-cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, cudaStream_t st);
+cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, int slots64, int slots32, cudaStream_t st);
 cudaError_t group_upload_mds(Group& g, cudaStream_t st);
 cudaError_t group_set_calls(Group& g, const CallDev* calls, cudaStream_t st);
 void group_destroy(Group& g);

@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(kBlock) init_kernel(const MeshDev* __restrict_
     ctl->cnt = 0u;
     ctl->iter = 0;
     ctl->all_done = 0;
+    ctl->any_apply = 0;
     ctl->cap = cap;
   }
   const double* __restrict__ src = io.in[tl.x];
@@ -141,22 +142,15 @@ __global__ void __launch_bounds__(kBlock) init_kernel(const MeshDev* __restrict_
 }
 
 // ------------------------------------------------------------------------------- spmv
+// q = A p and the partial sums p.q, over the rows of one tile (t0..t1).
 template <int K>
-__global__ void __launch_bounds__(kBlock) spmv_kernel(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles) {
-  __shared__ double sh[K * kBlock];
-  __shared__ ScalSnap sn;
-  const int2 tl = tiles[blockIdx.x];
-  const MeshDev& md = mds[tl.x];
+__device__ __forceinline__ void spmv_tile(const MeshDev& md, int tile, double (&pq)[K], double* sh) {
   const long nn = md.n;
-  const long t0 = (long)tl.y * md.tile_rows;
+  const long t0 = (long)tile * md.tile_rows;
   const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
-  SolveScal* s = md.s;
-  snap_scalars(s, sn);
-  if (sn.done) return;
   const double* __restrict__ A = md.A;
   const double* __restrict__ p = md.p;
   double* __restrict__ q = md.q;
-  double pq[K];
 #pragma unroll
   for (int c = 0; c < K; ++c) pq[c] = 0.0;
 #pragma unroll
@@ -174,78 +168,37 @@ __global__ void __launch_bounds__(kBlock) spmv_kernel(const MeshDev* __restrict_
       }
     }
   }
-  if (reduce_tiles<K>(pq, md.part, tl.y, md.ntiles, &s->cnt[0], sh) && threadIdx.x == 0) finish_spmv(s, K, pq);
+  block_sum<K>(pq, sh);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) spmv_kernel(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles,
+                                                      int ntiles_total) {
+  __shared__ double sh[K * kBlock];
+  __shared__ ScalSnap sn;
+  tile_loop<K>(
+      mds, tiles, ntiles_total, 0, 0, sh, sn, [](const ScalSnap& x) { return !x.done; },
+      [&](const MeshDev& md, int tile, double (&v)[K]) { spmv_tile<K>(md, tile, v, sh); },
+      [](const MeshDev& md, const double* v) { finish_spmv(md.s, K, v); });
 }
 
 // ------------------------------------------------------------------------------- update
 template <int K>
-__global__ void __launch_bounds__(kBlock, 5) update_kernel(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles,
-                                                        LoopCtl* ctl, cudaGraphConditionalHandle handle, int use_graph,
-                                                        int nmesh) {
-  __shared__ double sh[2 * K * kBlock];
-  __shared__ ScalSnap sn;
-  const int2 tl = tiles[blockIdx.x];
-  const MeshDev& md = mds[tl.x];
+__device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const ScalSnap& sn, double (&acc)[2 * K],
+                                            double* sh) {
   const long nn = md.n;
-  const long t0 = (long)tl.y * md.tile_rows;
+  const long t0 = (long)tile * md.tile_rows;
   const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
-  SolveScal* s = md.s;
-  snap_scalars(s, sn);
-  if (!sn.done) {
-    double alpha[K];
+  double alpha[K];
 #pragma unroll
-    for (int c = 0; c < K; ++c) alpha[c] = sn.alpha[c];
-    double acc[2 * K];
+  for (int c = 0; c < K; ++c) alpha[c] = sn.alpha[c];
 #pragma unroll
-    for (int i = 0; i < 2 * K; ++i) acc[i] = 0.0;
-    const double* __restrict__ Dinv = md.Dinv;
-    const double* __restrict__ p = md.p;
-    const double* __restrict__ q = md.q;
-    double* __restrict__ x = md.x;
-    double* __restrict__ r = md.r;
-#pragma unroll
-    for (int rr = 0; rr < kRowsPerThread; ++rr) {
-      const long row = t0 + rr * kBlock + threadIdx.x;
-      if (row < t1) {
-        const double dinv = Dinv[row];
-        double pi[K];
-        load_row<K>(p, row, pi);
-#pragma unroll
-        for (int c = 0; c < K; ++c) {
-          const double xn = fma(alpha[c], pi[c], x[c * nn + row]);
-          const double rn = fma(-alpha[c], q[c * nn + row], r[c * nn + row]);
-          x[c * nn + row] = xn;
-          r[c * nn + row] = rn;
-          acc[c] = fma(rn, dinv * rn, acc[c]);
-          acc[K + c] = fma(rn, rn, acc[K + c]);
-        }
-      }
-    }
-    if (reduce_tiles<2 * K>(acc, md.part, tl.y, md.ntiles, &s->cnt[1], sh) && threadIdx.x == 0)
-      finish_update(s, K, acc);
-  }
-  loop_control(mds, ctl, handle, use_graph, nmesh);
-}
-
-// ------------------------------------------------------------------------------- pupdate
-template <int K>
-__global__ void __launch_bounds__(kBlock) pupdate_kernel(const MeshDev* __restrict__ mds,
-                                                         const int2* __restrict__ tiles) {
-  __shared__ ScalSnap sn;
-  const int2 tl = tiles[blockIdx.x];
-  const MeshDev& md = mds[tl.x];
-  const long nn = md.n;
-  const long t0 = (long)tl.y * md.tile_rows;
-  const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
-  SolveScal* s = md.s;
-  snap_scalars(s, sn);
-  if (sn.done) return;
-  double beta[K];
-#pragma unroll
-  for (int c = 0; c < K; ++c) beta[c] = sn.beta[c];
+  for (int i = 0; i < 2 * K; ++i) acc[i] = 0.0;
   const double* __restrict__ Dinv = md.Dinv;
-  const double* __restrict__ r = md.r;
-  double* __restrict__ p = md.p;
+  const double* __restrict__ p = md.p;
+  const double* __restrict__ q = md.q;
+  double* __restrict__ x = md.x;
+  double* __restrict__ r = md.r;
 #pragma unroll
   for (int rr = 0; rr < kRowsPerThread; ++rr) {
     const long row = t0 + rr * kBlock + threadIdx.x;
@@ -254,9 +207,62 @@ __global__ void __launch_bounds__(kBlock) pupdate_kernel(const MeshDev* __restri
       double pi[K];
       load_row<K>(p, row, pi);
 #pragma unroll
-      for (int c = 0; c < K; ++c) p[row * KP<K>::v + c] = fma(beta[c], pi[c], dinv * r[c * nn + row]);
+      for (int c = 0; c < K; ++c) {
+        const double xn = fma(alpha[c], pi[c], x[c * nn + row]);
+        const double rn = fma(-alpha[c], q[c * nn + row], r[c * nn + row]);
+        x[c * nn + row] = xn;
+        r[c * nn + row] = rn;
+        acc[c] = fma(rn, dinv * rn, acc[c]);
+        acc[K + c] = fma(rn, rn, acc[K + c]);
+      }
     }
   }
+  block_sum<2 * K>(acc, sh);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock, 4) update_kernel(const MeshDev* __restrict__ mds,
+                                                           const int2* __restrict__ tiles, int ntiles_total,
+                                                           LoopCtl* ctl, cudaGraphConditionalHandle handle,
+                                                           int use_graph, int nmesh) {
+  __shared__ double sh[2 * K * kBlock];
+  __shared__ ScalSnap sn;
+  tile_loop<2 * K>(
+      mds, tiles, ntiles_total, 0, 1, sh, sn, [](const ScalSnap& x) { return !x.done; },
+      [&](const MeshDev& md, int tile, double (&v)[2 * K]) { update_tile<K>(md, tile, sn, v, sh); },
+      [](const MeshDev& md, const double* v) { finish_update(md.s, K, v); });
+  loop_control(mds, ctl, handle, use_graph, nmesh);
+}
+
+// ------------------------------------------------------------------------------- pupdate
+template <int K>
+__global__ void __launch_bounds__(kBlock) pupdate_kernel(const MeshDev* __restrict__ mds,
+                                                         const int2* __restrict__ tiles, int ntiles_total) {
+  __shared__ ScalSnap sn;
+  tile_loop_plain(mds, tiles, ntiles_total, sn, [](const ScalSnap& x) { return !x.done; },
+                  [&](const MeshDev& md, int tile) {
+                    const long nn = md.n;
+                    const long t0 = (long)tile * md.tile_rows;
+                    const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
+                    double beta[K];
+#pragma unroll
+                    for (int c = 0; c < K; ++c) beta[c] = sn.beta[c];
+                    const double* __restrict__ Dinv = md.Dinv;
+                    const double* __restrict__ r = md.r;
+                    double* __restrict__ p = md.p;
+#pragma unroll
+                    for (int rr = 0; rr < kRowsPerThread; ++rr) {
+                      const long row = t0 + rr * kBlock + threadIdx.x;
+                      if (row < t1) {
+                        const double dinv = Dinv[row];
+                        double pi[K];
+                        load_row<K>(p, row, pi);
+#pragma unroll
+                        for (int c = 0; c < K; ++c)
+                          p[row * KP<K>::v + c] = fma(beta[c], pi[c], dinv * r[c * nn + row]);
+                      }
+                    }
+                  });
 }
 
 // ------------------------------------------------------------------------------- true residual
@@ -318,9 +324,9 @@ cudaError_t build_plan(Group& g, SolvePlan& pl) {
   cudaStream_t cs = g.capture_stream;
   e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
-  spmv_kernel<K><<<g.ntiles, kBlock, 0, cs>>>(g.mds, g.tiles);
-  update_kernel<K><<<g.ntiles, kBlock, 0, cs>>>(g.mds, g.tiles, g.ctl, handle, 1, g.nmesh);
-  pupdate_kernel<K><<<g.ntiles, kBlock, 0, cs>>>(g.mds, g.tiles);
+  spmv_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.tiles, g.ntiles);
+  update_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.tiles, g.ntiles, g.ctl, handle, 1, g.nmesh);
+  pupdate_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.tiles, g.ntiles);
   cudaError_t le = cudaGetLastError();
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(cs, &captured);
@@ -357,16 +363,16 @@ cudaError_t solve_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_op
     for (int it = 0; it < cap; ++it) {
       {
         IG_PROF("pcg_spmv", st);
-        spmv_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles);
+        spmv_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.tiles, g.ntiles);
       }
       {
         IG_PROF("pcg_update", st);
-        update_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, g.ctl, cudaGraphConditionalHandle{}, 0,
-                                                      g.nmesh);
+        update_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.tiles, g.ntiles, g.ctl,
+                                                       cudaGraphConditionalHandle{}, 0, g.nmesh);
       }
       {
         IG_PROF("pcg_pupdate", st);
-        pupdate_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles);
+        pupdate_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.tiles, g.ntiles);
       }
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
@@ -400,7 +406,7 @@ int solver_blocks_per_sm() {
   return m > 0 ? m : 1;
 }
 
-cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, cudaStream_t st) {
+cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, int slots64, int slots32, cudaStream_t st) {
   g.nmesh = nmesh;
   g.host_mds.assign(host_mds, host_mds + nmesh);
   std::vector<int2> tiles, tiles32, ftiles, rtiles;
@@ -412,6 +418,9 @@ cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, cudaStream_
   }
   g.ntiles = (int)tiles.size();
   g.ntiles32 = (int)tiles32.size();
+  g.grid64 = g.ntiles < slots64 ? g.ntiles : (slots64 > 0 ? slots64 : 1);
+  g.grid32 = g.ntiles32 < slots32 ? g.ntiles32 : (slots32 > 0 ? slots32 : 1);
+  if (g.grid32 < 1) g.grid32 = 1;
   g.nface_tiles = (int)ftiles.size();
   g.nrow_tiles = (int)rtiles.size();
   cudaError_t e;
@@ -621,6 +630,12 @@ extern "C" ig_status ig_solve_csr_noalloc(const int32_t* rowptr_dev, const int32
   Group g;
   g.nmesh = 1;
   g.ntiles = md.ntiles;
+  {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return IG_ERR_CUDA;
+    const int slots = sms * solver_blocks_per_sm();
+    g.grid64 = md.ntiles < slots ? md.ntiles : slots;
+  }
   g.mds = reinterpret_cast<MeshDev*>(base + kNaMd);
   g.tiles = reinterpret_cast<int2*>(base + kNaTiles);
   g.ctl = reinterpret_cast<LoopCtl*>(base + kNaCtl);

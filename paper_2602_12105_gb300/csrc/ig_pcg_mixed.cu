@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(kBlock) init_mixed_kernel(const MeshDev* __res
     ctl->cnt = 0u;
     ctl->iter = 0;
     ctl->all_done = 0;
+    ctl->any_apply = 0;
     ctl->cap = cap;
   }
   const double* __restrict__ src = io.in[tl.x];
@@ -186,210 +187,211 @@ __global__ void __launch_bounds__(kBlock) init_mixed_kernel(const MeshDev* __res
 }
 
 template <int K>
-__global__ void __launch_bounds__(kBlock, 6) spmv_mixed_kernel(const MeshDev* __restrict__ mds,
-                                                            const int2* __restrict__ tiles) {
+__global__ void __launch_bounds__(kBlock, 4) spmv_mixed_kernel(const MeshDev* __restrict__ mds,
+                                                               const int2* __restrict__ tiles, int ntiles_total) {
   __shared__ double sh[K * kBlock];
-  const int2 tl = tiles[blockIdx.x];
-  const MeshDev& md = mds[tl.x];
-  const long nn = md.n;
-  const long t0 = (long)tl.y * md.tile_rows32;
-  const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
-  SolveScal* s = md.s;
   __shared__ ScalSnap sn;
-  snap_scalars(s, sn);
-  if (sn.done) return;
-  if (sn.phase != kPhaseInner) return;
-  double acc[K];
+  tile_loop<K>(
+      mds, tiles, ntiles_total, 1, 0, sh, sn, [](const ScalSnap& x) { return !x.done && x.phase == kPhaseInner; },
+      [&](const MeshDev& md, int tile, double (&acc)[K]) {
+        const long nn = md.n;
+        const long t0 = (long)tile * md.tile_rows32;
+        const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
+        const float* __restrict__ A = md.A32;
+        const float* __restrict__ p = md.p32;
+        float* __restrict__ q32 = md.q32;
+        float pq[K];
 #pragma unroll
-  for (int c = 0; c < K; ++c) acc[c] = 0.0;
-  {
-    const float* __restrict__ A = md.A32;
-    const float* __restrict__ p = md.p32;
-    float pq[K];
+        for (int c = 0; c < K; ++c) pq[c] = 0.f;
 #pragma unroll
-    for (int c = 0; c < K; ++c) pq[c] = 0.f;
+        for (int rr = 0; rr < kRowsPerThread; ++rr) {
+          const long row = t0 + rr * kBlock + threadIdx.x;
+          if (row < t1) {
+            float q[K];
+            row_product<K>(md, A, row, GatherP32<K>{p}, q);
+            float pi[K];
+            load_row32<K>(p, row, pi);
 #pragma unroll
-    for (int rr = 0; rr < kRowsPerThread; ++rr) {
-      const long row = t0 + rr * kBlock + threadIdx.x;
-      if (row < t1) {
-        float q[K];
-        row_product<K>(md, A, row, GatherP32<K>{p}, q);
-        float pi[K];
-        load_row32<K>(p, row, pi);
-#pragma unroll
-        for (int c = 0; c < K; ++c) {
-          md.q32[c * nn + row] = q[c];
-          pq[c] = fmaf(pi[c], q[c], pq[c]);
+            for (int c = 0; c < K; ++c) {
+              q32[c * nn + row] = q[c];
+              pq[c] = fmaf(pi[c], q[c], pq[c]);
+            }
+          }
         }
-      }
-    }
-    block_sum_f32<K>(pq, acc, sh);
-    if (publish_tiles<K>(acc, md.part, tl.y, md.ntiles32, &s->cnt[0], sh) && threadIdx.x == 0) finish_spmv(s, K, acc);
-  }
+        block_sum_f32<K>(pq, acc, sh);
+      },
+      [](const MeshDev& md, const double* v) { finish_spmv(md.s, K, v); });
 }
 
 // Apply phase: r64 = rhs - A64 x64 in FP64 and its squared norms (the refinement residual).
 // Kept out of the FP32 SpMV kernel so that the hot FP32 kernel stays small.
 template <int K>
 __global__ void __launch_bounds__(kBlock) resid_mixed_kernel(const MeshDev* __restrict__ mds,
-                                                             const int2* __restrict__ tiles) {
+                                                             const int2* __restrict__ tiles, int ntiles_total,
+                                                             const LoopCtl* __restrict__ ctl) {
   __shared__ double sh[K * kBlock];
   __shared__ ScalSnap sn;
-  const int2 tl = tiles[blockIdx.x];
-  const MeshDev& md = mds[tl.x];
-  const long nn = md.n;
-  const long t0 = (long)tl.y * md.tile_rows32;
-  const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
-  SolveScal* s = md.s;
-  snap_scalars(s, sn);
-  if (sn.done || sn.phase != kPhaseApply) return;
-  double acc[K];
+  if (!ctl->any_apply) return;  // no mesh of the group is in the Apply phase
+  tile_loop<K>(
+      mds, tiles, ntiles_total, 1, 0, sh, sn, [](const ScalSnap& x) { return !x.done && x.phase == kPhaseApply; },
+      [&](const MeshDev& md, int tile, double (&acc)[K]) {
+        const long nn = md.n;
+        const long t0 = (long)tile * md.tile_rows32;
+        const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
+        const double* __restrict__ A = md.A;
+        const double* __restrict__ x = md.x;
 #pragma unroll
-  for (int c = 0; c < K; ++c) acc[c] = 0.0;
-  const double* __restrict__ A = md.A;
-  const double* __restrict__ x = md.x;
+        for (int c = 0; c < K; ++c) acc[c] = 0.0;
 #pragma unroll
-  for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const long row = t0 + rr * kBlock + threadIdx.x;
-    if (row < t1) {
-      double ax[K];
-      row_product<K>(md, A, row, GatherSoA64<K>{x, nn}, ax);
+        for (int rr = 0; rr < kRowsPerThread; ++rr) {
+          const long row = t0 + rr * kBlock + threadIdx.x;
+          if (row < t1) {
+            double ax[K];
+            row_product<K>(md, A, row, GatherSoA64<K>{x, nn}, ax);
 #pragma unroll
-      for (int c = 0; c < K; ++c) {
-        const double res = md.rhs[c * nn + row] - ax[c];
-        md.r[c * nn + row] = res;
-        acc[c] = fma(res, res, acc[c]);
-      }
-    }
-  }
-  if (reduce_tiles<K>(acc, md.part, tl.y, md.ntiles32, &s->cnt[0], sh) && threadIdx.x == 0)
-    finish_residual(s, K, acc);
+            for (int c = 0; c < K; ++c) {
+              const double res = md.rhs[c * nn + row] - ax[c];
+              md.r[c * nn + row] = res;
+              acc[c] = fma(res, res, acc[c]);
+            }
+          }
+        }
+        block_sum<K>(acc, sh);
+      },
+      [](const MeshDev& md, const double* v) { finish_residual(md.s, K, v); });
 }
 
 template <int K>
-__global__ void __launch_bounds__(kBlock, 8) update_mixed_kernel(const MeshDev* __restrict__ mds,
-                                                              const int2* __restrict__ tiles, LoopCtl* ctl,
-                                                              cudaGraphConditionalHandle handle, int use_graph,
-                                                              int nmesh) {
+__global__ void __launch_bounds__(kBlock, 5) update_mixed_kernel(const MeshDev* __restrict__ mds,
+                                                                 const int2* __restrict__ tiles, int ntiles_total,
+                                                                 LoopCtl* ctl, cudaGraphConditionalHandle handle,
+                                                                 int use_graph, int nmesh) {
   __shared__ double sh[2 * K * kBlock];
-  const int2 tl = tiles[blockIdx.x];
-  const MeshDev& md = mds[tl.x];
-  const long nn = md.n;
-  const long t0 = (long)tl.y * md.tile_rows32;
-  const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
-  SolveScal* s = md.s;
   __shared__ ScalSnap sn;
-  snap_scalars(s, sn);
-  const int phase = sn.phase;
-  if (!sn.done && phase != kPhaseApply) {
-    float rz[K], rr2[K];
+  tile_loop<2 * K>(
+      mds, tiles, ntiles_total, 1, 1, sh, sn,
+      [](const ScalSnap& x) { return !x.done && x.phase != kPhaseApply; },
+      [&](const MeshDev& md, int tile, double (&acc)[2 * K]) {
+        const long nn = md.n;
+        const long t0 = (long)tile * md.tile_rows32;
+        const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
+        float rz[K], rr2[K];
 #pragma unroll
-    for (int c = 0; c < K; ++c) rz[c] = rr2[c] = 0.f;
-    if (phase == kPhaseInner) {
-      float alpha[K];
+        for (int c = 0; c < K; ++c) rz[c] = rr2[c] = 0.f;
+        const float* __restrict__ D32 = md.Dinv32;
+        float* __restrict__ x32 = md.x32;
+        float* __restrict__ r32 = md.r32;
+        if (sn.phase == kPhaseInner) {
+          float alpha[K];
 #pragma unroll
-      for (int c = 0; c < K; ++c) alpha[c] = (float)sn.alpha[c];
+          for (int c = 0; c < K; ++c) alpha[c] = (float)sn.alpha[c];
+          const float* __restrict__ p32 = md.p32;
+          const float* __restrict__ q32 = md.q32;
 #pragma unroll
-      for (int rr = 0; rr < kRowsPerThread; ++rr) {
-        const long row = t0 + rr * kBlock + threadIdx.x;
-        if (row < t1) {
-          const float dinv = md.Dinv32[row];
-          float pi[K];
-          load_row32<K>(md.p32, row, pi);
+          for (int rr = 0; rr < kRowsPerThread; ++rr) {
+            const long row = t0 + rr * kBlock + threadIdx.x;
+            if (row < t1) {
+              const float dinv = D32[row];
+              float pi[K];
+              load_row32<K>(p32, row, pi);
+#pragma unroll
+              for (int c = 0; c < K; ++c) {
+                const float xv = fmaf(alpha[c], pi[c], x32[c * nn + row]);
+                const float rv = fmaf(-alpha[c], q32[c * nn + row], r32[c * nn + row]);
+                x32[c * nn + row] = xv;
+                r32[c * nn + row] = rv;
+                rz[c] = fmaf(rv, dinv * rv, rz[c]);
+                rr2[c] = fmaf(rv, rv, rr2[c]);
+              }
+            }
+          }
+        } else {
+          // Restart: r32 = r64 / ||r64|| for columns still above tol, d = 0
+          double inv[K];
+          int act[K];
 #pragma unroll
           for (int c = 0; c < K; ++c) {
-            const float xv = fmaf(alpha[c], pi[c], md.x32[c * nn + row]);
-            const float rv = fmaf(-alpha[c], md.q32[c * nn + row], md.r32[c * nn + row]);
-            md.x32[c * nn + row] = xv;
-            md.r32[c * nn + row] = rv;
-            rz[c] = fmaf(rv, dinv * rv, rz[c]);
-            rr2[c] = fmaf(rv, rv, rr2[c]);
+            act[c] = sn.act64[c];
+            inv[c] = 1.0 / sn.scale[c];
+          }
+          const double* __restrict__ r64 = md.r;
+#pragma unroll
+          for (int rr = 0; rr < kRowsPerThread; ++rr) {
+            const long row = t0 + rr * kBlock + threadIdx.x;
+            if (row < t1) {
+              const float dinv = D32[row];
+#pragma unroll
+              for (int c = 0; c < K; ++c) {
+                const float rv = act[c] ? (float)(r64[c * nn + row] * inv[c]) : 0.f;
+                r32[c * nn + row] = rv;
+                x32[c * nn + row] = 0.f;
+                rz[c] = fmaf(rv, dinv * rv, rz[c]);
+                rr2[c] = fmaf(rv, rv, rr2[c]);
+              }
+            }
           }
         }
-      }
-    } else {
-      // Restart: r32 = r64 / ||r64|| for columns still above tol, d = 0
-      double inv[K];
-      int act[K];
+        float accf[2 * K];
 #pragma unroll
-      for (int c = 0; c < K; ++c) {
-        act[c] = sn.act64[c];
-        inv[c] = 1.0 / sn.scale[c];
-      }
-#pragma unroll
-      for (int rr = 0; rr < kRowsPerThread; ++rr) {
-        const long row = t0 + rr * kBlock + threadIdx.x;
-        if (row < t1) {
-          const float dinv = md.Dinv32[row];
-#pragma unroll
-          for (int c = 0; c < K; ++c) {
-            const float rv = act[c] ? (float)(md.r[c * nn + row] * inv[c]) : 0.f;
-            md.r32[c * nn + row] = rv;
-            md.x32[c * nn + row] = 0.f;
-            rz[c] = fmaf(rv, dinv * rv, rz[c]);
-            rr2[c] = fmaf(rv, rv, rr2[c]);
-          }
+        for (int c = 0; c < K; ++c) {
+          accf[c] = rz[c];
+          accf[K + c] = rr2[c];
         }
-      }
-    }
-    float accf[2 * K];
-#pragma unroll
-    for (int c = 0; c < K; ++c) {
-      accf[c] = rz[c];
-      accf[K + c] = rr2[c];
-    }
-    double acc[2 * K];
-    block_sum_f32<2 * K>(accf, acc, sh);
-    if (publish_tiles<2 * K>(acc, md.part, tl.y, md.ntiles32, &s->cnt[1], sh) && threadIdx.x == 0) {
-      if (phase == kPhaseInner) finish_update_mixed(s, K, acc);
-      else finish_restart(s, K, acc);
-    }
-  }
+        block_sum_f32<2 * K>(accf, acc, sh);
+      },
+      [](const MeshDev& md, const double* v) {
+        if (md.s->phase == kPhaseInner) finish_update_mixed(md.s, K, v);
+        else finish_restart(md.s, K, v);
+      });
   loop_control(mds, ctl, handle, use_graph, nmesh);
 }
 
 template <int K>
 __global__ void __launch_bounds__(kBlock, 8) pupdate_mixed_kernel(const MeshDev* __restrict__ mds,
-                                                               const int2* __restrict__ tiles) {
-  const int2 tl = tiles[blockIdx.x];
-  const MeshDev& md = mds[tl.x];
-  const long nn = md.n;
-  const long t0 = (long)tl.y * md.tile_rows32;
-  const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
-  SolveScal* s = md.s;
+                                                                  const int2* __restrict__ tiles, int ntiles_total) {
   __shared__ ScalSnap sn;
-  snap_scalars(s, sn);
-  if (sn.done) return;
-  const int phase = sn.phase;
-  if (phase == kPhaseInner) {
-    float beta[K];
+  tile_loop_plain(mds, tiles, ntiles_total, sn,
+                  [](const ScalSnap& x) { return !x.done && (x.phase == kPhaseInner || x.phase == kPhaseApply); },
+                  [&](const MeshDev& md, int tile) {
+                    const long nn = md.n;
+                    const long t0 = (long)tile * md.tile_rows32;
+                    const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
+                    if (sn.phase == kPhaseInner) {
+                      float beta[K];
 #pragma unroll
-    for (int c = 0; c < K; ++c) beta[c] = (float)sn.beta[c];
+                      for (int c = 0; c < K; ++c) beta[c] = (float)sn.beta[c];
+                      const float* __restrict__ D32 = md.Dinv32;
+                      const float* __restrict__ r32 = md.r32;
+                      float* __restrict__ p32 = md.p32;
 #pragma unroll
-    for (int rr = 0; rr < kRowsPerThread; ++rr) {
-      const long row = t0 + rr * kBlock + threadIdx.x;
-      if (row < t1) {
-        const float dinv = md.Dinv32[row];
-        float pi[K];
-        load_row32<K>(md.p32, row, pi);
+                      for (int rr = 0; rr < kRowsPerThread; ++rr) {
+                        const long row = t0 + rr * kBlock + threadIdx.x;
+                        if (row < t1) {
+                          const float dinv = D32[row];
+                          float pi[K];
+                          load_row32<K>(p32, row, pi);
 #pragma unroll
-        for (int c = 0; c < K; ++c) md.p32[row * KPm<K>::v + c] = fmaf(beta[c], pi[c], dinv * md.r32[c * nn + row]);
-      }
-    }
-  } else if (phase == kPhaseApply) {
-    double sc[K];
+                          for (int c = 0; c < K; ++c)
+                            p32[row * KPm<K>::v + c] = fmaf(beta[c], pi[c], dinv * r32[c * nn + row]);
+                        }
+                      }
+                    } else {
+                      double sc[K];
 #pragma unroll
-    for (int c = 0; c < K; ++c) sc[c] = sn.scale[c];
+                      for (int c = 0; c < K; ++c) sc[c] = sn.scale[c];
+                      const float* __restrict__ x32 = md.x32;
+                      double* __restrict__ x = md.x;
 #pragma unroll
-    for (int rr = 0; rr < kRowsPerThread; ++rr) {
-      const long row = t0 + rr * kBlock + threadIdx.x;
-      if (row < t1) {
+                      for (int rr = 0; rr < kRowsPerThread; ++rr) {
+                        const long row = t0 + rr * kBlock + threadIdx.x;
+                        if (row < t1) {
 #pragma unroll
-        for (int c = 0; c < K; ++c)
-          md.x[c * nn + row] = fma(sc[c], (double)md.x32[c * nn + row], md.x[c * nn + row]);
-      }
-    }
-  }
+                          for (int c = 0; c < K; ++c)
+                            x[c * nn + row] = fma(sc[c], (double)x32[c * nn + row], x[c * nn + row]);
+                        }
+                      }
+                    }
+                  });
 }
 
 template <int K>
@@ -412,10 +414,10 @@ cudaError_t build_plan_mixed(Group& g, SolvePlan& pl) {
   cudaStream_t cs = g.capture_stream;
   e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
-  resid_mixed_kernel<K><<<g.ntiles32, kBlock, 0, cs>>>(g.mds, g.tiles32);
-  spmv_mixed_kernel<K><<<g.ntiles32, kBlock, 0, cs>>>(g.mds, g.tiles32);
-  update_mixed_kernel<K><<<g.ntiles32, kBlock, 0, cs>>>(g.mds, g.tiles32, g.ctl, handle, 1, g.nmesh);
-  pupdate_mixed_kernel<K><<<g.ntiles32, kBlock, 0, cs>>>(g.mds, g.tiles32);
+  resid_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.tiles32, g.ntiles32, g.ctl);
+  spmv_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.tiles32, g.ntiles32);
+  update_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.tiles32, g.ntiles32, g.ctl, handle, 1, g.nmesh);
+  pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.tiles32, g.ntiles32);
   cudaError_t le = cudaGetLastError();
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(cs, &captured);
@@ -453,20 +455,20 @@ cudaError_t solve_mixed_k(Group& g, const IoTable& io, int rhs_mass, const ig_so
     for (int it = 0; it < cap; ++it) {
       {
         IG_PROF("pcg32_resid64", st);
-        resid_mixed_kernel<K><<<g.ntiles32, kBlock, 0, st>>>(g.mds, g.tiles32);
+        resid_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32, g.ctl);
       }
       {
         IG_PROF("pcg32_spmv", st);
-        spmv_mixed_kernel<K><<<g.ntiles32, kBlock, 0, st>>>(g.mds, g.tiles32);
+        spmv_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32);
       }
       {
         IG_PROF("pcg32_update", st);
-        update_mixed_kernel<K><<<g.ntiles32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ctl, cudaGraphConditionalHandle{}, 0,
-                                                            g.nmesh);
+        update_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32, g.ctl,
+                                                             cudaGraphConditionalHandle{}, 0, g.nmesh);
       }
       {
         IG_PROF("pcg32_pupdate", st);
-        pupdate_mixed_kernel<K><<<g.ntiles32, kBlock, 0, st>>>(g.mds, g.tiles32);
+        pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32);
       }
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
