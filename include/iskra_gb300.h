@@ -190,6 +190,32 @@ ig_status ig_batch_adjoint(ig_batch* batch, const double* const* V_dev, const do
                            const double* const* U_dev, const double* const* G_dev, int k, double* const* gV_dev,
                            double* const* gB_dev, double* gt_dev, const ig_solve_opts* opts, ig_solve_info* infos);
 
+/* ---- continuous batching (serving) ------------------------------------------------------- */
+/* A served request is one forward + adjoint solve whose iterations interleave with those of the
+ * other requests in flight. ig_solve_begin starts a solve on a mesh (its state stays on the
+ * device), ig_batch_iterate advances every running solve of a batch by up to max_iters
+ * iterations in shared launches, and ig_solve_end writes a finished solve's result. Members may
+ * be at different stages (forward or adjoint, any iteration, any refinement). */
+
+/* Start solving A X = M in (rhs_mass != 0) or A X = in (rhs_mass == 0) on one mesh: the
+ * initialisation kernel only. in_dev [n][k] must stay valid until ig_solve_end. */
+ig_status ig_solve_begin(ig_mesh* mesh, const double* in_dev, int k, int rhs_mass, const ig_solve_opts* opts);
+
+/* Advance the running solves of the batch's meshes by at most max_iters iterations (all k
+ * columns; meshes already done are skipped). The loop returns early as soon as one of the solves
+ * that were running finishes. Synchronises; done_host (host array of count ints, may be NULL)
+ * receives 1 for each mesh whose solve is finished. */
+ig_status ig_batch_iterate(ig_batch* batch, int k, int max_iters, int* done_host);
+
+/* Write the result of a finished (or interrupted) solve: X into out_dev [n][k], or, when out_dev
+ * is NULL, into the mesh's adjoint buffer used by ig_vjp. info as for ig_solve (synchronises). */
+ig_status ig_solve_end(ig_mesh* mesh, int k, double* out_dev, ig_solve_info* info);
+
+/* The gradient half of ig_adjoint: after an adjoint solve ended with out_dev == NULL, gather
+ * dl/dV (and dl/dB, dl/dt) as ig_adjoint does. Same arguments and layouts. */
+ig_status ig_vjp(ig_mesh* mesh, const double* V_dev, const double* B_dev, int b_is_V, const double* U_dev, int k,
+                 double* gV_dev, double* gB_dev, double* gt_dev);
+
 /* ---- allocation-free solve ----------------------------------------------------------------- */
 
 /* Largest number of rows ig_solve_csr_noalloc accepts. */

@@ -84,6 +84,10 @@ SIGNATURES = {
     "ig_batch_solve": (_i32, [_vp, _P(_vp), _i32, _P(_vp), _P(SolveOpts), _P(SolveInfo)]),
     "ig_batch_adjoint": (_i32, [_vp, _P(_vp), _P(_vp), _i32, _P(_vp), _P(_vp), _i32, _P(_vp), _P(_vp), _vp,
                                 _P(SolveOpts), _P(SolveInfo)]),
+    "ig_solve_begin": (_i32, [_vp, _vp, _i32, _i32, _P(SolveOpts)]),
+    "ig_batch_iterate": (_i32, [_vp, _i32, _i32, _P(_i32)]),
+    "ig_solve_end": (_i32, [_vp, _i32, _vp, _P(SolveInfo)]),
+    "ig_vjp": (_i32, [_vp, _vp, _vp, _i32, _vp, _i32, _vp, _vp, _vp]),
     "ig_solve_csr_noalloc": (_i32, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, _i32, _vp, _vp, _P(SolveOpts),
                                      _P(SolveInfo)]),
     "ig_profile_enable": (_i32, [_i32]),

@@ -603,6 +603,66 @@ ig_status ig_adjoint(ig_mesh* mesh, const double* V_dev, const double* B_dev, in
   return collect_info(mesh, k, info);
 }
 
+ig_status ig_solve_begin(ig_mesh* mesh, const double* in_dev, int k, int rhs_mass, const ig_solve_opts* opts) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (!mesh->assembled) {
+    set_error(ctx, "solve before assemble");
+    return IG_ERR_STATE;
+  }
+  if (!in_dev) return bad_arg(ctx, "right-hand side is NULL");
+  if (k < 1 || k > kMaxK) return bad_arg(ctx, "k must be in [1, 4]");
+  const ig_solve_opts o = resolve_opts(opts);
+  ig_status cs = check_opts(ctx, o);
+  if (cs != IG_OK) return cs;
+  DeviceGuard guard(ctx->device);
+  auto io = std::make_unique<IoTable>();
+  io->in[0] = in_dev;
+  io->out[0] = nullptr;
+  IG_CK(ctx, group_begin(mesh->group, k, mesh->assembled == 2, *io, rhs_mass ? 1 : 0, o, ctx->stream),
+        "solve begin");
+  return IG_OK;
+}
+
+ig_status ig_solve_end(ig_mesh* mesh, int k, double* out_dev, ig_solve_info* info) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (k < 1 || k > kMaxK) return bad_arg(ctx, "k must be in [1, 4]");
+  DeviceGuard guard(ctx->device);
+  auto io = std::make_unique<IoTable>();
+  io->in[0] = nullptr;
+  io->out[0] = out_dev ? out_dev : mesh->md.lam;
+  IG_CK(ctx, group_end(mesh->group, k, *io, ctx->stream), "solve end");
+  if (!info) return IG_OK;
+  return collect_info(mesh, k, info);
+}
+
+ig_status ig_vjp(ig_mesh* mesh, const double* V_dev, const double* B_dev, int b_is_V, const double* U_dev, int k,
+                 double* gV_dev, double* gB_dev, double* gt_dev) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (!mesh->assembled) {
+    set_error(ctx, "gradient before assemble");
+    return IG_ERR_STATE;
+  }
+  if (!V_dev || !U_dev || !gV_dev || (!b_is_V && !B_dev)) return bad_arg(ctx, "a required pointer is NULL");
+  if (k < 1 || k > kMaxK || (b_is_V && k != 3)) return bad_arg(ctx, "bad k");
+  DeviceGuard guard(ctx->device);
+  CallDev call{};
+  call.V = V_dev;
+  call.B = b_is_V ? V_dev : B_dev;
+  call.U = U_dev;
+  call.gV = gV_dev;
+  call.gB = gB_dev;
+  call.gt = gt_dev;
+  call.t = mesh->t;
+  call.b_is_V = b_is_V ? 1 : 0;
+  call.bstride = b_is_V ? 3 : k;
+  IG_CK(ctx, group_set_calls(mesh->group, &call, ctx->stream), "upload");
+  IG_CK(ctx, launch_vjp(mesh->group, k, ctx->stream), "vjp");
+  return IG_OK;
+}
+
 ig_status ig_profile_enable(int enable) {
   ProfState& P = prof_state();
   std::lock_guard<std::mutex> lk(P.mu);

@@ -254,4 +254,23 @@ ig_status ig_batch_adjoint(ig_batch* b, const double* const* V_dev, const double
   return batch_info(b, k, infos);
 }
 
+ig_status ig_batch_iterate(ig_batch* b, int k, int max_iters, int* done_host) {
+  if (!b) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = b->ctx;
+  if (k < 1 || k > kMaxK) return bad(ctx, "k must be in [1, 4]");
+  if (max_iters < 1) return bad(ctx, "max_iters must be >= 1");
+  const int prec = b->meshes[0]->assembled;
+  for (auto* m : b->meshes) {
+    if (!m->assembled) {
+      set_error(ctx, "iterate before assemble");
+      return IG_ERR_STATE;
+    }
+    if (m->assembled != prec) return bad(ctx, "meshes of a batch must share one precision");
+  }
+  BatchDevice guard(ctx->device);
+  BT_CK(ctx, refresh(b, ctx->stream), "upload");
+  BT_CK(ctx, group_iterate(b->group, k, prec == 2, max_iters, done_host, ctx->stream), "batch iterate");
+  return IG_OK;
+}
+
 }  // extern "C"

@@ -374,16 +374,17 @@ __device__ __forceinline__ void loop_control(const MeshDev* __restrict__ mds, Lo
     const unsigned prev = atomicAdd(&ctl->cnt, 1u);
     if (prev == gridDim.x - 1u) {
       __threadfence();
-      int all = 1, apply = 0;
+      int all = 1, apply = 0, ndone = 0;
       for (int i = 0; i < nmesh; ++i) {
         const int d = __ldcg(&mds[i].s->done);
         all &= (d != 0);
+        ndone += (d != 0);
         apply |= (!d && __ldcg(&mds[i].s->phase) == kPhaseApply);
       }
       ctl->any_apply = apply;
       const int it = ctl->iter + 1;
       ctl->iter = it;
-      if (all || it >= ctl->cap) {
+      if (all || it >= ctl->cap || ndone > ctl->ndone_start) {
         ctl->all_done = 1;
         if (use_graph) cudaGraphSetConditional(handle, 0u);
       }

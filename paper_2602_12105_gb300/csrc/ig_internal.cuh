@@ -163,6 +163,8 @@ struct LoopCtl {
   int cap;            // hard cap on iterations of the device-side loop
   int all_done;       // 1 once every mesh of the group is done
   int any_apply;      // mixed precision: some mesh will recompute its FP64 residual next
+  int ndone_start;    // serving: meshes already done when the loop (re)started; the loop stops
+                      // as soon as more are done (a whole solve sets it out of reach)
 };
 
 // Per-launch pointers that change from call to call (kept out of the cached graphs).
@@ -204,6 +206,7 @@ struct Group {
   int ntiles32 = 0;
   int2* tiles32 = nullptr;        // the tiling of the mixed-precision kernels
   int grid64 = 0, grid32 = 0;     // persistent grid of the loop kernels: min(tiles, resident slots)
+  int* flags_dev = nullptr;       // [nmesh] done flags gathered for the host (serving)
   LoopCtl* ctl = nullptr;         // device
   int* done_host = nullptr;       // pinned host word for the host-driven loop
   SolvePlan plans[2][kMaxK + 1];  // [mixed][k]
@@ -230,6 +233,16 @@ int solver_blocks_per_sm();        // ig_pcg.cu: min resident CTAs per SM of the
 int solver_blocks_per_sm_mixed();  // ig_pcg_mixed.cu: same for the mixed-precision loop kernels
 cudaError_t group_solve_mixed(Group& g, int k, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
                               cudaStream_t st);
+// Serving: start a solve (init), advance a group's running solves by a bounded number of
+// iterations (stopping early once a running member finishes; done flags to the host), and write
+// a finished solve's result.
+cudaError_t group_begin(Group& g, int k, int mixed, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
+                        cudaStream_t st);
+cudaError_t group_begin_mixed(Group& g, int k, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
+                              cudaStream_t st);
+cudaError_t group_iterate(Group& g, int k, int mixed, int budget, int* done_host, cudaStream_t st);
+cudaError_t group_host_loop_mixed(Group& g, int k, int budget, cudaStream_t st);
+cudaError_t group_end(Group& g, int k, const IoTable& io, cudaStream_t st);
 
 }  // namespace ig
 

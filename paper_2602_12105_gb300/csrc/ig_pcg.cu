@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(kBlock) init_kernel(const MeshDev* __restrict_
     ctl->iter = 0;
     ctl->all_done = 0;
     ctl->any_apply = 0;
+    ctl->ndone_start = 1 << 30;  // a whole solve stops only when every mesh is done
     ctl->cap = cap;
   }
   const double* __restrict__ src = io.in[tl.x];
@@ -343,58 +344,147 @@ cudaError_t build_plan(Group& g, SolvePlan& pl) {
 }
 
 template <int K>
-cudaError_t solve_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_opts& o, cudaStream_t st) {
+cudaError_t begin_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_opts& o, cudaStream_t st) {
   const int cap = o.max_iter + 2;
-  {
-    IG_PROF("pcg_init", st);
-    init_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io, rhs_mass, g.ctl, o.rel_tol, o.max_iter, cap);
-  }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (o.launch == IG_LAUNCH_GRAPH && !prof_on()) {
-    SolvePlan& pl = g.plans[0][K];
-    if (!pl.exec) {
-      e = build_plan<K>(g, pl);
-      if (e != cudaSuccess) return e;
-    }
-    e = cudaGraphLaunch(pl.exec, st);
-    if (e != cudaSuccess) return e;
-  } else {
-    for (int it = 0; it < cap; ++it) {
-      {
-        IG_PROF("pcg_spmv", st);
-        spmv_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.tiles, g.ntiles);
-      }
-      {
-        IG_PROF("pcg_update", st);
-        update_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.tiles, g.ntiles, g.ctl,
-                                                       cudaGraphConditionalHandle{}, 0, g.nmesh);
-      }
-      {
-        IG_PROF("pcg_pupdate", st);
-        pupdate_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.tiles, g.ntiles);
-      }
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-      // poll every 16 iterations (every iteration while kernels are being timed, so that no
-      // launch after convergence is timed)
-      if (prof_on() || (it & 15) == 15 || it == cap - 1) {
-        e = cudaMemcpyAsync(g.done_host, &g.ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) return e;
-        e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return e;
-        if (*g.done_host) break;
-      }
-    }
-  }
-  {
-    IG_PROF("pcg_finalize", st);
-    finalize_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io);
-  }
+  IG_PROF("pcg_init", st);
+  init_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io, rhs_mass, g.ctl, o.rel_tol, o.max_iter, cap);
   return cudaGetLastError();
 }
 
+// Host-driven loop: up to max_it iterations, polling the device's stop word every `poll`.
+template <int K>
+cudaError_t host_loop_k(Group& g, int max_it, int poll, cudaStream_t st) {
+  cudaError_t e;
+  for (int it = 0; it < max_it; ++it) {
+    {
+      IG_PROF("pcg_spmv", st);
+      spmv_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.tiles, g.ntiles);
+    }
+    {
+      IG_PROF("pcg_update", st);
+      update_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.tiles, g.ntiles, g.ctl, cudaGraphConditionalHandle{}, 0,
+                                                     g.nmesh);
+    }
+    {
+      IG_PROF("pcg_pupdate", st);
+      pupdate_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.tiles, g.ntiles);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // poll every `poll` iterations (every iteration while kernels are being timed, so that no
+    // launch after convergence is timed)
+    if (prof_on() || (it % poll) == poll - 1 || it == max_it - 1) {
+      e = cudaMemcpyAsync(g.done_host, &g.ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return e;
+      e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return e;
+      if (*g.done_host) break;
+    }
+  }
+  return cudaSuccess;
+}
+
+template <int K>
+cudaError_t loop_k(Group& g, const ig_solve_opts& o, cudaStream_t st) {
+  if (o.launch == IG_LAUNCH_GRAPH && !prof_on()) {
+    SolvePlan& pl = g.plans[0][K];
+    if (!pl.exec) {
+      cudaError_t e = build_plan<K>(g, pl);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaGraphLaunch(pl.exec, st);
+  }
+  return host_loop_k<K>(g, o.max_iter + 2, 16, st);
+}
+
+template <int K>
+cudaError_t end_k(Group& g, const IoTable& io, cudaStream_t st) {
+  IG_PROF("pcg_finalize", st);
+  finalize_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io);
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t solve_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_opts& o, cudaStream_t st) {
+  cudaError_t e = begin_k<K>(g, io, rhs_mass, o, st);
+  if (e == cudaSuccess) e = loop_k<K>(g, o, st);
+  if (e == cudaSuccess) e = end_k<K>(g, io, st);
+  return e;
+}
+
+// Serving: restart the loop counters of a group whose members may be mid-solve. The loop stops
+// after `budget` iterations, or as soon as a member that was running has finished.
+__global__ void loop_reset_kernel(const MeshDev* __restrict__ mds, int nmesh, LoopCtl* ctl, int budget) {
+  int ndone = 0, apply = 0;
+  for (int i = 0; i < nmesh; ++i) {
+    const int d = mds[i].s->done;
+    ndone += d != 0;
+    apply |= (!d && mds[i].s->phase == kPhaseApply);
+  }
+  ctl->cnt = 0u;
+  ctl->iter = 0;
+  ctl->cap = budget;
+  ctl->all_done = ndone == nmesh ? 1 : 0;
+  ctl->any_apply = apply;
+  ctl->ndone_start = ndone;
+}
+
+__global__ void collect_done_kernel(const MeshDev* __restrict__ mds, int nmesh, int* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nmesh) out[i] = mds[i].s->done;
+}
+
 }  // namespace
+
+cudaError_t group_iterate(Group& g, int k, int mixed, int budget, int* done_host, cudaStream_t st) {
+  loop_reset_kernel<<<1, 1, 0, st>>>(g.mds, g.nmesh, g.ctl, budget);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (mixed) {
+    e = group_host_loop_mixed(g, k, budget, st);
+  } else {
+    switch (k) {
+      case 1: e = host_loop_k<1>(g, budget, 8, st); break;
+      case 2: e = host_loop_k<2>(g, budget, 8, st); break;
+      case 3: e = host_loop_k<3>(g, budget, 8, st); break;
+      case 4: e = host_loop_k<4>(g, budget, 8, st); break;
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (e != cudaSuccess) return e;
+  if (!done_host) return cudaSuccess;
+  if (!g.flags_dev) {
+    e = cudaMalloc(&g.flags_dev, sizeof(int) * g.nmesh);
+    if (e != cudaSuccess) return e;
+  }
+  collect_done_kernel<<<(g.nmesh + 255) / 256, 256, 0, st>>>(g.mds, g.nmesh, g.flags_dev);
+  e = cudaMemcpyAsync(done_host, g.flags_dev, sizeof(int) * g.nmesh, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
+}
+
+cudaError_t group_begin(Group& g, int k, int mixed, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
+                        cudaStream_t st) {
+  if (mixed) return group_begin_mixed(g, k, io, rhs_mass, o, st);
+  switch (k) {
+    case 1: return begin_k<1>(g, io, rhs_mass, o, st);
+    case 2: return begin_k<2>(g, io, rhs_mass, o, st);
+    case 3: return begin_k<3>(g, io, rhs_mass, o, st);
+    case 4: return begin_k<4>(g, io, rhs_mass, o, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t group_end(Group& g, int k, const IoTable& io, cudaStream_t st) {
+  switch (k) {
+    case 1: return end_k<1>(g, io, st);
+    case 2: return end_k<2>(g, io, st);
+    case 3: return end_k<3>(g, io, st);
+    case 4: return end_k<4>(g, io, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 
 int solver_blocks_per_sm() {
   int a = 0, b = 0, c = 0;
@@ -488,6 +578,7 @@ void group_destroy(Group& g) {
   if (g.calls_host) cudaFreeHost(g.calls_host);
   if (g.done_host) cudaFreeHost(g.done_host);
   if (g.calls_ev) cudaEventDestroy(g.calls_ev);
+  if (g.flags_dev) cudaFree(g.flags_dev);
   g = Group{};
 }
 

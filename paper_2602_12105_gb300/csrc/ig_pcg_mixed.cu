@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(kBlock) init_mixed_kernel(const MeshDev* __res
     ctl->iter = 0;
     ctl->all_done = 0;
     ctl->any_apply = 0;
+    ctl->ndone_start = 1 << 30;  // a whole solve stops only when every mesh is done
     ctl->cap = cap;
   }
   const double* __restrict__ src = io.in[tl.x];
@@ -434,14 +435,51 @@ cudaError_t build_plan_mixed(Group& g, SolvePlan& pl) {
 }
 
 template <int K>
-cudaError_t solve_mixed_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_opts& o, cudaStream_t st) {
+cudaError_t begin_mixed_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_opts& o, cudaStream_t st) {
   const int cap = o.max_iter + 3 * o.max_refine + 4;
-  {
-    IG_PROF("pcg_init", st);
-    init_mixed_kernel<K><<<g.ntiles32, kBlock, 0, st>>>(g.mds, g.tiles32, io, rhs_mass, g.ctl, o.rel_tol, o.inner_tol,
+  IG_PROF("pcg_init", st);
+  init_mixed_kernel<K><<<g.ntiles32, kBlock, 0, st>>>(g.mds, g.tiles32, io, rhs_mass, g.ctl, o.rel_tol, o.inner_tol,
                                                       o.max_iter, o.max_refine, cap);
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t host_loop_mixed_k(Group& g, int max_it, int poll, cudaStream_t st) {
+  cudaError_t e;
+  for (int it = 0; it < max_it; ++it) {
+    {
+      IG_PROF("pcg32_resid64", st);
+      resid_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32, g.ctl);
+    }
+    {
+      IG_PROF("pcg32_spmv", st);
+      spmv_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32);
+    }
+    {
+      IG_PROF("pcg32_update", st);
+      update_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32, g.ctl,
+                                                           cudaGraphConditionalHandle{}, 0, g.nmesh);
+    }
+    {
+      IG_PROF("pcg32_pupdate", st);
+      pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (prof_on() || (it % poll) == poll - 1 || it == max_it - 1) {
+      e = cudaMemcpyAsync(g.done_host, &g.ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return e;
+      e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return e;
+      if (*g.done_host) break;
+    }
   }
-  cudaError_t e = cudaGetLastError();
+  return cudaSuccess;
+}
+
+template <int K>
+cudaError_t solve_mixed_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_opts& o, cudaStream_t st) {
+  cudaError_t e = begin_mixed_k<K>(g, io, rhs_mass, o, st);
   if (e != cudaSuccess) return e;
   if (o.launch == IG_LAUNCH_GRAPH && !prof_on()) {
     SolvePlan& pl = g.plans[1][K];
@@ -450,41 +488,12 @@ cudaError_t solve_mixed_k(Group& g, const IoTable& io, int rhs_mass, const ig_so
       if (e != cudaSuccess) return e;
     }
     e = cudaGraphLaunch(pl.exec, st);
-    if (e != cudaSuccess) return e;
   } else {
-    for (int it = 0; it < cap; ++it) {
-      {
-        IG_PROF("pcg32_resid64", st);
-        resid_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32, g.ctl);
-      }
-      {
-        IG_PROF("pcg32_spmv", st);
-        spmv_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32);
-      }
-      {
-        IG_PROF("pcg32_update", st);
-        update_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32, g.ctl,
-                                                             cudaGraphConditionalHandle{}, 0, g.nmesh);
-      }
-      {
-        IG_PROF("pcg32_pupdate", st);
-        pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32);
-      }
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-      if (prof_on() || (it & 15) == 15 || it == cap - 1) {
-        e = cudaMemcpyAsync(g.done_host, &g.ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) return e;
-        e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return e;
-        if (*g.done_host) break;
-      }
-    }
+    e = host_loop_mixed_k<K>(g, o.max_iter + 3 * o.max_refine + 4, 16, st);
   }
-  {
-    IG_PROF("pcg_finalize", st);
-    finalize_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io);
-  }
+  if (e != cudaSuccess) return e;
+  IG_PROF("pcg_finalize", st);
+  finalize_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io);
   return cudaGetLastError();
 }
 
@@ -498,6 +507,27 @@ int solver_blocks_per_sm_mixed() {
   int m = a < b ? a : b;
   m = m < c ? m : c;
   return m > 0 ? m : 1;
+}
+
+cudaError_t group_begin_mixed(Group& g, int k, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
+                              cudaStream_t st) {
+  switch (k) {
+    case 1: return begin_mixed_k<1>(g, io, rhs_mass, o, st);
+    case 2: return begin_mixed_k<2>(g, io, rhs_mass, o, st);
+    case 3: return begin_mixed_k<3>(g, io, rhs_mass, o, st);
+    case 4: return begin_mixed_k<4>(g, io, rhs_mass, o, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t group_host_loop_mixed(Group& g, int k, int budget, cudaStream_t st) {
+  switch (k) {
+    case 1: return host_loop_mixed_k<1>(g, budget, 8, st);
+    case 2: return host_loop_mixed_k<2>(g, budget, 8, st);
+    case 3: return host_loop_mixed_k<3>(g, budget, 8, st);
+    case 4: return host_loop_mixed_k<4>(g, budget, 8, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t group_solve_mixed(Group& g, int k, const IoTable& io, int rhs_mass, const ig_solve_opts& o,

@@ -1,0 +1,81 @@
+"""Continuous-batching server: requests that arrive while others run are admitted as memory
+allows, their iterations share launches, and each result equals the one computed alone (same
+bits: a request's reductions depend on its own tiles only; checked also against the 1e-10
+tolerance of the path)."""
+import numpy as np
+import pytest
+
+from gpu_util import rel2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_12105_gb300 import api, meshgen, serve
+    return api, meshgen, serve
+
+
+def _requests(meshgen, serve, count, spread_s, seed=0):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for r in range(count):
+        if r % 2 == 0:
+            level = int(rng.integers(2, 5))
+            n, m = meshgen.icosphere_vertex_count(level), 20 * 4 ** level
+            def make(level=level, s=seed * 1000 + r):
+                return meshgen.request_problem(meshgen.Request(r, 0.0, "ico", level, 3e-3, s))
+        else:
+            side = int(rng.integers(20, 90))
+            n, m = side * side, 2 * (side - 1) ** 2
+            def make(side=side, s=seed * 1000 + r):
+                return meshgen.request_problem(meshgen.Request(r, 0.0, "grid", side, 1e-3, s))
+        reqs.append(serve.make_request(r, float(rng.uniform(0, spread_s)), make, n, m))
+    return reqs
+
+
+def _alone(api, p, precision):
+    dev = "cuda:0"
+    mesh = api.Mesh(torch.from_numpy(p.F).to(dev), p.n)
+    V = torch.from_numpy(p.V).to(dev)
+    B = torch.from_numpy(p.B).to(dev)
+    T = torch.from_numpy(p.T).to(dev)
+    mesh.assemble(V, p.t, precision)
+    U = mesh.solve(B)
+    gV, _, _ = mesh.adjoint(V, B, False, U, U - T)
+    return U, gV
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_served_results_equal_alone(mods, precision):
+    api, meshgen, serve = mods
+    reqs = _requests(meshgen, serve, 12, 0.15, seed=1)
+    srv = serve.Server(precision=precision, quantum=8, keep_results=True)
+    done = srv.run(reqs, realtime=True)
+    assert len(done) == 12 and all(r.status == 0 for r in done), [r.status for r in done]
+    assert srv.stats["rebuilds"] >= 2
+    for r in done:
+        U, gV = _alone(api, r.make(), precision)
+        assert rel2(r.U.cpu().numpy(), U.cpu().numpy()) <= 1e-10
+        assert rel2(r.gV.cpu().numpy(), gV.cpu().numpy()) <= 1e-10
+        assert torch.equal(r.gV, gV) and torch.equal(r.U, U)
+    lat = serve.latency_summary(done, max(r.done_s for r in done))
+    assert lat["ok"] == 12 and lat["p99_ms"] >= lat["p50_ms"] > 0
+
+
+def test_budget_admission_and_rejection(mods):
+    api, meshgen, serve = mods
+    reqs = _requests(meshgen, serve, 6, 0.0, seed=2)
+    biggest = max(serve.req_bytes(r) for r in reqs)
+    # room for about one request at a time: everything still completes, one by one
+    srv = serve.Server(budget_bytes=biggest * 1.05, quantum=16, keep_results=False)
+    done = srv.run(reqs, realtime=False)
+    assert len(done) == 6 and all(r.status == 0 for r in done)
+    # a request larger than the whole budget is rejected without touching the device
+    srv = serve.Server(budget_bytes=serve.req_bytes(reqs[0]) * 0.5)
+    done = srv.run([reqs[0]], realtime=False)
+    from paper_2602_12105_gb300 import _native as N
+    assert done[0].status == N.IG_ERR_OOM and srv.stats["rejected"] == 1
