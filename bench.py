@@ -46,6 +46,12 @@ def parse():
     ap.add_argument("--launch", default="graph", choices=["graph", "host"],
                     help="graph: device-side solver loop (default); host: one launch per kernel")
     ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel timing pass")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the other workloads (mixed grid, largest mesh, 256-mesh batch, serving)")
+    ap.add_argument("--serve-requests", type=int, default=600,
+                    help="requests in the bounded sample of the serving stream")
+    ap.add_argument("--variants", default="mixed,largest,batch,serve",
+                    help="comma list of the extra workloads to run")
     return ap.parse_args()
 
 
@@ -152,6 +158,9 @@ def algorithmic(kernel, n, m, nnz, k, prec):
     """(FP64-or-FP32 flops, bytes) one launch of `kernel` must do / move (vectors [n][k])."""
     sv = 8 if prec == "fp64" else 4   # value and vector element size
     kp = 4 if k == 3 else k
+    if kernel.startswith("pcg32_"):
+        sv = 4
+        kernel = "pcg_" + kernel[len("pcg32_"):]
     if kernel == "pcg_spmv":
         flops = 2 * k * nnz + 2 * k * n
         byts = nnz * (sv + 4) + 4 * (n + 1) + sv * kp * n + sv * k * n
@@ -201,7 +210,7 @@ def run_ours(args, rank, world, local_rank):
     # correctness of this very configuration (outside the timed region)
     mesh.assemble(V, p.t, precision)
     U0, finfo = mesh.solve(B, opts=opts, info=True)
-    _, _, _, ainfo = mesh.adjoint(V, B, p.b_is_V, U0, U0 - T, opts=opts, info=True)
+    gV0, _, _, ainfo = mesh.adjoint(V, B, p.b_is_V, U0, U0 - T, opts=opts, info=True)
     if finfo["status"] != 0 or ainfo["status"] != 0:
         raise RuntimeError(f"solve failed: {finfo} {ainfo}")
 
@@ -286,36 +295,7 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernel
     its_f, its_a = finfo["iterations"], ainfo["iterations"]
-    dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
-    hbm_peak, peak_kind = peaks()
-    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    fp64_peak_tflops = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12     # 2 FP64 FMA / clk / SM
-    fp32_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12   # 128 FP32 FMA / clk / SM
-    rl_all = {}
-    for name, (cnt, ms) in prof.items():
-        fl, by = algorithmic(name, p.n, p.m, mesh.nnz, k, "fp64" if name.startswith(("assemble", "vjp")) or
-                             precision == "fp64" else "fp32")
-        if fl is None:
-            continue
-        avg_s = ms / cnt / 1000.0
-        alu_peak = fp64_peak_tflops if (precision == "fp64" or name.startswith(("assemble", "vjp"))) \
-            else fp32_peak_tflops
-        rl_all[name] = {"avg_us": avg_s * 1e6, "launches": cnt,
-                        "gbs": by / avg_s / 1e9, "hbm_frac": by / avg_s / 1e9 / hbm_peak,
-                        "tflops": fl / avg_s / 1e12, "alu_frac": fl / avg_s / 1e12 / alu_peak}
-    d = rl_all.get(dom)
-    if d is None:
-        roofline = None
-    elif d["alu_frac"] >= d["hbm_frac"]:
-        roofline = {"bound": "alu", "achieved": round(d["tflops"], 4), "peak": round(
-            fp64_peak_tflops if precision == "fp64" or dom.startswith(("assemble", "vjp")) else fp32_peak_tflops, 4),
-            "unit": "TFLOP/s", "frac": round(d["alu_frac"], 4), "traffic": measured_traffic(dom, args.workload),
-            "kernel": dom, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x median SM clock under load",
-            "hbm_gbs": round(d["gbs"], 1), "hbm_frac_of_measured": round(d["hbm_frac"], 4)}
-    else:
-        roofline = {"bound": "hbm", "achieved": round(d["gbs"], 1), "peak": hbm_peak, "unit": "GB/s",
-                    "frac": round(d["hbm_frac"], 4), "traffic": measured_traffic(dom, args.workload),
-                    "kernel": dom, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    rl_all, roofline = kernel_roofline(prof, p.n, p.m, mesh.nnz, k, precision, clocks, args.workload)
 
     # the CPU oracle on the same workload (bounded sample)
     cpu = None
@@ -338,12 +318,317 @@ def run_ours(args, rank, world, local_rank):
                        "p99": round(float(np.percentile(step_ms, 99)), 4)},
         "clocks": clocks,
         "roofline": roofline,
-        "kernels": {kname: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in kv.items()}
-                    for kname, kv in rl_all.items()},
-        "gpu_launches": int(args.steps * (2 + (2 + 3 * its_f) + (2 + 3 * its_a) + 2)),
+        "kernels": rl_all,
+        "gpu_launches": gpu_launches(prof, args.steps, its_f, its_a, args.launch),
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
+    if world == 1 and not args.no_variants:
+        out["variants"] = run_variants(args, p, U0, gV0, dev)
+    return out
+
+
+def gpu_launches(prof, steps, its_f, its_a, launch):
+    """Kernel launches of the timed region, counted from the profile pass (one host-launched
+    step, every launch bracketed by events): the kernels outside the solver loops as they were
+    counted, the loop bodies as 3 kernels per iteration of the two solves (the device-side
+    loop runs exactly the iterations the solves report)."""
+    if not prof:
+        return int(steps * (2 + (2 + 3 * its_f) + (2 + 3 * its_a) + 2))
+    loop = {"pcg_spmv", "pcg_update", "pcg_pupdate"}
+    outside = sum(c for name, (c, _) in prof.items() if name not in loop)
+    per_step = outside / 3.0 + 3 * (its_f + its_a) if launch == "graph" else \
+        sum(c for c, _ in prof.values()) / 3.0
+    return int(round(steps * per_step))
+
+
+def kernel_roofline(prof, n, m, nnz, k, precision, clocks, workload):
+    """Per-kernel achieved rates from the profile pass ({name: (launches, total ms)}) and the
+    roofline object of the kernel with the largest total time. FP64 kernels are held against the
+    FP64 ALU peak (152 SMs x 2 FMA/clk), FP32 ones against the measured HBM copy bandwidth and the
+    FP32 ALU peak; the bound is whichever fraction is higher."""
+    hbm_peak, peak_kind = peaks()
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    fp64_peak_tflops = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12     # 2 FP64 FMA / clk / SM
+    fp32_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12   # 128 FP32 FMA / clk / SM
+    rl_all = {}
+    for name, (cnt, ms) in prof.items():
+        is64 = name.startswith(("assemble", "vjp")) or (name.startswith("pcg_") and precision == "fp64")
+        fl, by = algorithmic(name, n, m, nnz, k, "fp64" if is64 else "fp32")
+        if fl is None or cnt == 0 or ms <= 0:
+            continue
+        avg_s = ms / cnt / 1000.0
+        alu_peak = fp64_peak_tflops if is64 else fp32_peak_tflops
+        rl_all[name] = {"avg_us": avg_s * 1e6, "launches": cnt, "total_ms": ms,
+                        "gbs": by / avg_s / 1e9, "hbm_frac": by / avg_s / 1e9 / hbm_peak,
+                        "tflops": fl / avg_s / 1e12, "alu_frac": fl / avg_s / 1e12 / alu_peak,
+                        "alu_peak": alu_peak, "bytes": by}
+    if not rl_all:
+        return {}, None
+    dom = max(rl_all.items(), key=lambda kv: kv[1]["total_ms"])[0]
+    d = rl_all[dom]
+    if d["alu_frac"] >= d["hbm_frac"]:
+        roofline = {"bound": "alu", "achieved": round(d["tflops"], 4), "peak": round(d["alu_peak"], 4),
+                    "unit": "TFLOP/s", "frac": round(d["alu_frac"], 4), "traffic": measured_traffic(dom, workload),
+                    "kernel": dom, "peak_source": "derived: 152 SMs x FMA/clk x 2 x median SM clock under load "
+                                                  "(2 FMA/clk FP64, 128 FP32)",
+                    "hbm_gbs": round(d["gbs"], 1), "hbm_frac_of_measured": round(d["hbm_frac"], 4),
+                    "algorithmic_bytes_per_launch": int(d["bytes"])}
+    else:
+        roofline = {"bound": "hbm", "achieved": round(d["gbs"], 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(d["hbm_frac"], 4), "traffic": measured_traffic(dom, workload),
+                    "kernel": dom, "peak_source": f"{peak_kind} (hbm_gbs copy bandwidth)",
+                    "algorithmic_bytes_per_launch": int(d["bytes"])}
+    table = {kname: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in kv.items()
+                     if kk not in ("alu_peak", "bytes")} for kname, kv in rl_all.items()}
+    return table, roofline
+
+
+# ------------------------------------------------------------------------------- other workloads
+def _rel(a, b):
+    import torch
+    den = float(torch.linalg.vector_norm(b))
+    return float(torch.linalg.vector_norm(a - b)) / (den if den > 0 else 1.0)
+
+
+def _dev_problem(p, dev):
+    import torch
+    V = torch.from_numpy(np.ascontiguousarray(p.V)).to(dev)
+    B = V if p.b_is_V else torch.from_numpy(np.ascontiguousarray(p.B)).to(dev)
+    T = torch.from_numpy(np.ascontiguousarray(p.T)).to(dev)
+    return V, B, T
+
+
+def single_mesh(api, _native, dev, p, precision, tol, steps, warmup, launch="graph", profile=True, mesh=None):
+    """Forward + adjoint of one mesh, timed over `steps` (CUDA events on the launching stream).
+    Returns timings, solver info, the per-kernel profile and the results of the last step."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    if mesh is None:
+        mesh = api.Mesh(torch.from_numpy(p.F).to(dev), p.n)
+    V, B, T = _dev_problem(p, dev)
+    U = torch.empty((p.n, B.shape[1]), dtype=torch.float64, device=dev)
+    opts = api.make_opts(rel_tol=tol, launch=launch)
+
+    def step():
+        mesh.assemble(V, p.t, precision)
+        mesh.solve(B, opts=opts, out=U)
+        gV, _, _ = mesh.adjoint(V, B, p.b_is_V, U, U - T, opts=opts)
+        return gV
+
+    mesh.assemble(V, p.t, precision)
+    U0, finfo = mesh.solve(B, opts=opts, info=True)
+    gV0, _, _, ainfo = mesh.adjoint(V, B, p.b_is_V, U0, U0 - T, opts=opts, info=True)
+    for _ in range(max(warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = float(e0.elapsed_time(e1)) / steps
+    prof = {}
+    if profile:
+        _native.profile_enable(True)
+        step()
+        torch.cuda.synchronize()
+        prof = _native.profile_read()
+        _native.profile_enable(False)
+    return {"ms_per_step": ms, "solves_per_s": 1000.0 / ms, "finfo": finfo, "ainfo": ainfo, "U": U0, "gV": gV0,
+            "prof": prof, "mesh": mesh}
+
+
+def variant_mixed_grid(api, _native, dev, p, tol, steps, fp64_U, fp64_gV, clocks):
+    """The headline grid in mixed precision (FP32 PCG inside FP64 refinement)."""
+    r = single_mesh(api, _native, dev, p, "mixed", tol, steps, 3)
+    table, roof = kernel_roofline(r["prof"], p.n, p.m, r["mesh"].nnz, p.B.shape[1], "mixed", clocks, p.name + "_mixed")
+    out = {"workload": f"{p.name} mixed: FP32 Jacobi-PCG (FP32 CSR values) inside FP64 residual refinement to {tol:g}",
+           "value": round(r["solves_per_s"], 3), "unit": UNIT, "ms_per_step": round(r["ms_per_step"], 4),
+           "steps": steps, "iterations": {"forward": r["finfo"]["iterations"], "adjoint": r["ainfo"]["iterations"]},
+           "refinements": {"forward": r["finfo"]["refinements"], "adjoint": r["ainfo"]["refinements"]},
+           "true_rel_residual": {"forward": max(r["finfo"]["true_rel_residual"]),
+                                 "adjoint": max(r["ainfo"]["true_rel_residual"])},
+           "rel_err_vs_fp64_gpu": {"U": _rel(r["U"], fp64_U), "gV": _rel(r["gV"], fp64_gV)},
+           "roofline": roof, "kernels": table}
+    r["mesh"].close()
+    return out
+
+
+def variant_largest(api, _native, dev, tol, steps, clocks):
+    """The largest single mesh (4096 x 2048 grid, 8.4M vertices) in mixed precision, with its HBM
+    roofline, and its error against the FP64 GPU path on the same mesh."""
+    from paper_2602_12105_gb300 import meshgen as mg
+    p = mg.config_grid4096x2048(0)
+    r = single_mesh(api, _native, dev, p, "mixed", tol, steps, 3)
+    mesh = r["mesh"]
+    table, roof = kernel_roofline(r["prof"], p.n, p.m, mesh.nnz, p.B.shape[1], "mixed", clocks, "grid4096x2048")
+    r64 = single_mesh(api, _native, dev, p, "fp64", tol, 1, 0, profile=False, mesh=mesh)
+    out = {"workload": f"{p.name}: {p.n} vertices, {p.m} faces, k=3, t=h^2, mixed precision to {tol:g}",
+           "value": round(r["solves_per_s"], 3), "unit": UNIT, "ms_per_step": round(r["ms_per_step"], 4),
+           "steps": steps, "fp64_gpu_ms_per_step": round(r64["ms_per_step"], 4),
+           "iterations": {"forward": r["finfo"]["iterations"], "adjoint": r["ainfo"]["iterations"]},
+           "refinements": {"forward": r["finfo"]["refinements"], "adjoint": r["ainfo"]["refinements"]},
+           "true_rel_residual": {"forward": max(r["finfo"]["true_rel_residual"]),
+                                 "adjoint": max(r["ainfo"]["true_rel_residual"])},
+           "rel_err_vs_fp64_gpu": {"U": _rel(r["U"], r64["U"]), "gV": _rel(r["gV"], r64["gV"])},
+           "resident_mb": round(mesh.device_bytes / 1e6, 1), "roofline": roof, "kernels": table}
+    mesh.close()
+    return out
+
+
+def variant_batch(api, _native, dev, tol, steps):
+    """The differentiation batch (256 icospheres, levels 2..6, per-mesh t): forward + adjoint of
+    all meshes in shared launches, FP64 and mixed, against the plain path that runs the same
+    meshes one after another in FP64."""
+    import torch
+    from paper_2602_12105_gb300 import meshgen as mg
+    probs = mg.config_batch(seed=0, count=256)
+    stream = torch.cuda.current_stream(dev)
+    meshes = [api.Mesh(torch.from_numpy(q.F).to(dev), q.n) for q in probs]
+    Vs = [torch.from_numpy(q.V).to(dev) for q in probs]
+    Ts = [torch.from_numpy(q.T).to(dev) for q in probs]
+    ts = [q.t for q in probs]
+    opts = api.make_opts(rel_tol=tol)
+    batch = api.Batch(meshes)
+
+    def bstep(prec):
+        batch.assemble(Vs, ts, prec)
+        Us = batch.solve(Vs, opts=opts)
+        gVs, _, _ = batch.adjoint(Vs, None, True, Us, [U - T for U, T in zip(Us, Ts)], opts=opts)
+        return Us, gVs
+
+    def pstep():
+        res = []
+        for m, V, T, t in zip(meshes, Vs, Ts, ts):
+            m.assemble(V, t, "fp64")
+            U = m.solve(V, opts=opts)
+            gV, _, _ = m.adjoint(V, V, True, U, U - T, opts=opts)
+            res.append((U, gV))
+        return res
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return float(e0.elapsed_time(e1)) / reps
+
+    # accuracy: every mesh's mixed result against its FP64 result (both to the same tolerance)
+    U64, g64 = bstep("fp64")
+    U32, g32 = bstep("mixed")
+    errU = max(_rel(a, b) for a, b in zip(U32, U64))
+    errG = max(_rel(a, b) for a, b in zip(g32, g64))
+    ms64 = timed(lambda: bstep("fp64"), steps)
+    ms32 = timed(lambda: bstep("mixed"), steps)
+    msp = timed(pstep, max(1, steps // 2))
+    nb = len(probs)
+    batch.close()
+    for m in meshes:
+        m.close()
+    return {"workload": f"{nb} icospheres, levels 2..6 ({min(q.n for q in probs)}..{max(q.n for q in probs)} "
+                        f"vertices, {sum(q.n for q in probs)} in all), radial N(0, 0.02), t log-uniform "
+                        f"[1e-4, 1e-2], B = V, forward + adjoint to {tol:g}",
+            "unit": UNIT, "steps": steps,
+            "batched_mixed": round(nb * 1000.0 / ms32, 2), "batched_fp64": round(nb * 1000.0 / ms64, 2),
+            "plain_fp64_one_at_a_time": round(nb * 1000.0 / msp, 2),
+            "ms_per_batch": {"batched_mixed": round(ms32, 3), "batched_fp64": round(ms64, 3),
+                             "plain_fp64": round(msp, 3)},
+            "speedup_batched_mixed_vs_plain": round(msp / ms32, 3),
+            "max_rel_err_mixed_vs_fp64": {"U": errU, "gV": errG}}
+
+
+def serving_requests(count, seed=7):
+    """A bounded sample of the serving stream: request sizes log-uniform in [1e3, 2e6] vertices,
+    half icospheres (levels 4..8), half square grids whose side is snapped to one of 32
+    log-spaced sides (so the sample's meshes are generated once), t log-uniform in [1e-4, 1e-2].
+    Arrival times are for a rate of 1/s; the caller rescales them."""
+    import dataclasses
+    from paper_2602_12105_gb300 import meshgen as mg
+    from paper_2602_12105_gb300 import serve
+    stream = mg.request_stream(count, 1.0, seed=seed)
+    sides = np.unique(np.round(np.exp(np.linspace(np.log(32), np.log(1414), 32))).astype(int))
+    bank = {}
+    reqs = []
+    for rq in stream:
+        size = rq.size if rq.kind == "ico" else int(sides[np.argmin(np.abs(np.log(sides) - np.log(rq.size)))])
+        key = (rq.kind, size)
+        if key not in bank:
+            bank[key] = mg.request_problem(mg.Request(0, 0.0, rq.kind, size, 1e-3, seed * 7919 + len(bank)))
+        base = bank[key]
+
+        def make(base=base, t=rq.t, rid=rq.rid):
+            return dataclasses.replace(base, t=t, name=f"req{rid}")
+        reqs.append(serve.make_request(rq.rid, rq.arrival_s, make, base.n, base.m))
+    return reqs
+
+
+def variant_serving(dev, tol, count):
+    """Continuous batching (mixed precision) against the plain path (one request at a time, FP64)
+    on the same request sample: closed-loop capacity of the server, then a Poisson stream at
+    0.8 x that capacity through both, with p50/p99 latency."""
+    import copy
+    from paper_2602_12105_gb300 import serve
+    reqs = serving_requests(count)
+    sizes = np.array([r.n_hint for r in reqs])
+    def fresh(r, arrival):
+        c = copy.copy(r)
+        c.arrival_s = arrival
+        c.iterations = []
+        return c
+
+    # closed loop: every request waiting at t = 0
+    srv = serve.Server(precision="mixed", rel_tol=tol)
+    t0 = time.perf_counter()
+    done = srv.run([fresh(r, 0.0) for r in reqs], realtime=False)
+    wall = time.perf_counter() - t0
+    cap = serve.latency_summary(done, wall)
+    rate = 0.8 * cap["solves_per_s"]
+    srv = serve.Server(precision="mixed", rel_tol=tol)
+    t0 = time.perf_counter()
+    done = srv.run([fresh(r, r.arrival_s / rate) for r in reqs], realtime=True)
+    served = serve.latency_summary(done, time.perf_counter() - t0)
+    served["stats"] = dict(srv.stats)
+    plain_srv = serve.PlainServer(rel_tol=tol)
+    t0 = time.perf_counter()
+    done_p = plain_srv.run([fresh(r, r.arrival_s / rate) for r in reqs], realtime=True)
+    plain = serve.latency_summary(done_p, time.perf_counter() - t0)
+    return {"workload": f"{count} requests (bounded sample of the stream): vertex counts log-uniform "
+                        f"[1e3, 2e6] (median {int(np.median(sizes))}), half icospheres (levels 4..8), half "
+                        f"square grids, t log-uniform [1e-4, 1e-2], k=3, forward + adjoint to {tol:g}, "
+                        f"150 GB HBM budget",
+            "closed_loop_capacity": cap, "offered_rate_per_s": round(rate, 3),
+            "continuous_batching_mixed": served, "plain_fp64_fifo": plain,
+            "solves_per_s_ratio_vs_plain": (served["solves_per_s"] / plain["solves_per_s"])
+            if plain["solves_per_s"] else None,
+            "p99_ratio_plain_over_served": (plain["p99_ms"] / served["p99_ms"])
+            if served["p99_ms"] and plain["p99_ms"] else None}
+
+
+def run_variants(args, p, U64, gV64, dev):
+    from paper_2602_12105_gb300 import _native, api
+    want = set(x.strip() for x in args.variants.split(",") if x.strip())
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    out = {}
+    t_start = time.perf_counter()
+    clocks_guess = {"sm_mhz": None}
+    if "mixed" in want:
+        out["grid1024_mixed"] = variant_mixed_grid(api, _native, dev, p, args.tol, 100, U64, gV64, clocks_guess)
+    if "largest" in want:
+        out["grid4096x2048_mixed"] = variant_largest(api, _native, dev, args.tol, 10, clocks_guess)
+    if "batch" in want:
+        out["batch256_icospheres"] = variant_batch(api, _native, dev, args.tol, 6)
+    if "serve" in want and args.serve_requests > 0:
+        out["serving"] = variant_serving(dev, args.tol, args.serve_requests)
+    out["clocks"] = sampler.stop()
+    out["wall_s"] = round(time.perf_counter() - t_start, 1)
     return out
 
 

@@ -11,6 +11,7 @@ closed surfaces, +z for height fields).
 """
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass, field
 
@@ -46,8 +47,14 @@ def icosphere(level: int):
     """Unit icosphere by midpoint subdivision, re-projected to the sphere after every level.
 
     Level k has 10*4^k + 2 vertices and 20*4^k faces. Returns (V float64 [n][3],
-    F int32 [m][3]) with faces CCW seen from outside.
+    F int32 [m][3]) with faces CCW seen from outside (fresh copies; the construction is cached).
     """
+    V, F = _icosphere_cached(level)
+    return V.copy(), F.copy()
+
+
+@functools.lru_cache(maxsize=16)
+def _icosphere_cached(level: int):
     if level < 0:
         raise ValueError("level must be >= 0")
     V, F = icosahedron()

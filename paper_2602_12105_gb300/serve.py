@@ -222,7 +222,9 @@ def req_bytes(req: ServeRequest) -> int:
 def latency_summary(done: List[ServeRequest], wall_s: float):
     lat = np.array([r.latency_s for r in done if r.latency_s is not None and r.status in (0,)])
     ok = int(sum(1 for r in done if r.status == 0))
+    vit = float(sum(r.n * sum(r.iterations) for r in done if r.status == 0))
     return {"requests": len(done), "ok": ok, "solves_per_s": ok / wall_s if wall_s > 0 else None,
+            "wall_s": wall_s, "vertex_iterations_per_s": vit / wall_s if wall_s > 0 else None,
             "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
             "mean_ms": float(lat.mean() * 1e3) if lat.size else None}
@@ -234,3 +236,51 @@ def make_request(rid: int, arrival_s: float, make: Callable[[], object], n: int,
     r = ServeRequest(rid, arrival_s, make)
     r.n_hint, r.m_hint = int(n), int(m)
     return r
+
+
+class PlainServer:
+    """The plain baseline: requests served one at a time, first come first served, each as a
+    whole FP64 solve + adjoint on its own (no batching, no overlap)."""
+
+    def __init__(self, ctx: Optional[Context] = None, precision: str = "fp64", rel_tol: float = 1e-10,
+                 keep_results: bool = False):
+        self.ctx = ctx or default_context()
+        self.precision = precision
+        self.opts = make_opts(rel_tol=rel_tol)
+        self.keep = keep_results
+
+    def run(self, requests: List[ServeRequest], realtime: bool = True) -> List[ServeRequest]:
+        ctx = self.ctx
+        pending = sorted(requests, key=lambda r: r.arrival_s)
+        t0 = time.perf_counter()
+        done = []
+        for req in pending:
+            if realtime:
+                wait = req.arrival_s - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+            req.admitted_s = time.perf_counter() - t0
+            p = req.make()
+            dev = ctx.device
+
+            def dev_t(a, dtype=torch.float64):
+                return a.to(device=dev, dtype=dtype).contiguous() if isinstance(a, torch.Tensor) else \
+                    torch.from_numpy(np.ascontiguousarray(a)).to(device=dev, dtype=dtype)
+
+            mesh = Mesh(dev_t(p.F, torch.int32), p.n, ctx=ctx)
+            V = dev_t(p.V)
+            B = V if p.b_is_V else dev_t(p.B)
+            T = dev_t(p.T)
+            mesh.assemble(V, p.t, self.precision)
+            U, finfo = mesh.solve(B, opts=self.opts, info=True)
+            gV, _, _, ainfo = mesh.adjoint(V, B, p.b_is_V, U, U - T, opts=self.opts, info=True)
+            torch.cuda.current_stream(dev).synchronize()
+            req.iterations = [finfo["iterations"], ainfo["iterations"]]
+            req.status = max(finfo["status"], ainfo["status"])
+            req.done_s = time.perf_counter() - t0
+            req.n = p.n
+            if self.keep:
+                req.U, req.gV = U, gV
+            mesh.close()
+            done.append(req)
+        return done
