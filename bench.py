@@ -17,6 +17,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import time
@@ -37,7 +38,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="grid1024", choices=["grid1024", "ico3", "grid2048", "grid4096x2048"])
+    ap.add_argument("--workload", default="grid1024",
+                    help="grid1024 (default), ico3, grid4096x2048, or any gridS / gridXxY of the same family")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"])
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -61,9 +63,14 @@ def make_problem(name, seed):
         return mg.config_grid1024(seed)
     if name == "grid4096x2048":
         return mg.config_grid4096x2048(seed)
-    if name == "grid2048":
-        return mg.config_grid(2048, 2048, seed)
-    return mg.config_ico3(seed)
+    if name == "ico3":
+        return mg.config_ico3(seed)
+    m = re.fullmatch(r"grid(\d+)(?:x(\d+))?", name)
+    if not m:
+        raise SystemExit(f"unknown workload {name}")
+    sx = int(m.group(1))
+    sy = int(m.group(2)) if m.group(2) else sx
+    return mg.config_grid(sx, sy, seed)
 
 
 def workload_desc(p, precision, tol):
@@ -190,7 +197,7 @@ def run_ours(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    precision = args.precision or ("mixed" if args.workload == "grid4096x2048" else "fp64")
+    precision = args.precision or "fp64"
     p = make_problem(args.workload, seed=rank)
     k = p.B.shape[1]
     mesh = api.Mesh(torch.from_numpy(p.F).to(dev), p.n)

@@ -253,9 +253,123 @@ struct GatherAoS64 {
   }
 };
 
-// Per-CTA snapshot of the per-mesh scalars a kernel needs. One thread reads them (one L2
-// request per CTA instead of one per warp: every CTA of a launch reads the same few words, so
-// per-warp reads would queue on a single L2 line) and the CTA shares them through shared memory.
+// ------------------------------------------------------------------------------- warp and tile sums
+// Transposed warp sum. In a plain butterfly every lane adds every value at each of the five
+// levels; here, at the first levels, a lane keeps half of its values and sends the other half to
+// its partner, so NV <= 8 values cost 9 shuffles and 9 adds per lane (NV <= 4: 6 and 6) instead of
+// 5 NV of each. Afterwards lane L holds the warp total of value warp_sum_index<NV>(L), and the
+// lanes selected by warp_sum_writer<NV>(L) hold each total once. The additions are in a fixed
+// order, so the sums are deterministic. (FP64 adds are scarce on this GPU: 2 per clock per SM.)
+template <int NV>
+__device__ __forceinline__ int warp_sum_index(int lane) {
+  if constexpr (NV <= 2) return 0;
+  else if constexpr (NV <= 4) return ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+  else return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+}
+template <int NV>
+__device__ __forceinline__ bool warp_sum_writer(int lane) {
+  if constexpr (NV <= 2) return lane == 0;
+  else if constexpr (NV <= 4) return (lane & 0x13) == 0;
+  else return (lane & 3) == 0;
+}
+
+template <int NV, typename T>
+__device__ __forceinline__ T warp_sum_transposed(T (&v)[NV], int lane) {
+  static_assert(NV >= 1 && NV <= 8, "at most 8 values");
+  if constexpr (NV <= 2) {
+    // plain butterfly on the (one or two) values; lane 0 returns value 0 and v[] holds both totals
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    return v[0];
+  } else if constexpr (NV <= 4) {
+    T a[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = i < NV ? v[i] : T(0);
+    const bool h8 = (lane & 8) != 0, h4 = (lane & 4) != 0;
+    T b[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const T keep = h8 ? a[2 + i] : a[i];
+      const T send = h8 ? a[i] : a[2 + i];
+      b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    T c;
+    {
+      const T keep = h4 ? b[1] : b[0];
+      const T send = h4 ? b[0] : b[1];
+      c = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    c += __shfl_xor_sync(0xffffffffu, c, 16);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+  } else {
+    T a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = i < NV ? v[i] : T(0);
+    const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0, h4 = (lane & 4) != 0;
+    T b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const T keep = h16 ? a[4 + i] : a[i];
+      const T send = h16 ? a[i] : a[4 + i];
+      b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    T c[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const T keep = h8 ? b[2 + i] : b[i];
+      const T send = h8 ? b[i] : b[2 + i];
+      c[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    T d;
+    {
+      const T keep = h4 ? c[1] : c[0];
+      const T send = h4 ? c[0] : c[1];
+      d = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    d += __shfl_xor_sync(0xffffffffu, d, 2);
+    d += __shfl_xor_sync(0xffffffffu, d, 1);
+    return d;
+  }
+}
+
+constexpr int kWarps = kBlock / 32;
+
+// Sum the per-thread values v[0..NV) over the CTA: each warp adds its lanes (in T: FP32 for the
+// mixed-precision kernels, FP64 otherwise), then threads 0..NV-1 add the kWarps warp totals in FP64
+// in warp order and write them to out[0..NV). red holds NV * kWarps doubles; a caller that sums
+// consecutive tiles alternates between two such buffers, so that one barrier per tile suffices
+// (a warp can reach the buffer again only after the next tile's barrier, which the readers of
+// this tile pass after their reads).
+template <int NV, typename T>
+__device__ __forceinline__ void tile_reduce(T (&v)[NV], double* red, double* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const T w = warp_sum_transposed<NV>(v, lane);
+  if constexpr (NV <= 2) {
+    if (lane == 0)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) red[i * kWarps + warp] = (double)v[i];
+  } else {
+    const int idx = warp_sum_index<NV>(lane);
+    if (warp_sum_writer<NV>(lane) && idx < NV) red[idx * kWarps + warp] = (double)w;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double a = red[threadIdx.x * kWarps];
+#pragma unroll
+    for (int j = 1; j < kWarps; ++j) a += red[threadIdx.x * kWarps + j];
+    out[threadIdx.x] = a;
+  }
+}
+
+// ------------------------------------------------------------------------------- persistent tiles
+// Per-CTA view of the mesh whose tiles the CTA is working on: a copy of its MeshDev and of the
+// scalars the kernels read, taken once per mesh switch. Every CTA of a launch reads the same few
+// scalars; reading them through one thread per CTA keeps them off a single hot L2 line, and the
+// copy in shared memory keeps the mesh's pointers out of the way of the kernels' global stores.
 struct ScalSnap {
   double alpha[kMaxK];
   double beta[kMaxK];
@@ -265,102 +379,115 @@ struct ScalSnap {
   int phase;
 };
 
-__device__ __forceinline__ void snap_scalars(const SolveScal* s, ScalSnap& sn) {
-  __syncthreads();  // every thread is done with the previous snapshot
+struct TileCtx {
+  MeshDev md;
+  ScalSnap sn;
+  double red[2][8 * kWarps];  // tile sums, double-buffered
+  double tot[8];              // mesh totals in the CTA that completes a mesh
+  int last;
+};
+
+__device__ __forceinline__ void load_mesh(const MeshDev* __restrict__ mds, int i, TileCtx& tc) {
+  __syncthreads();  // every thread is done with the previous mesh's view
+  static_assert(sizeof(MeshDev) % 4 == 0, "MeshDev is copied as 4-byte words");
+  const unsigned* src = reinterpret_cast<const unsigned*>(mds + i);
+  unsigned* dst = reinterpret_cast<unsigned*>(&tc.md);
+  for (int j = threadIdx.x; j < (int)(sizeof(MeshDev) / 4); j += kBlock) dst[j] = __ldg(src + j);
   if (threadIdx.x == 0) {
-    sn.done = s->done;
-    sn.phase = s->phase;
+    const SolveScal* s = mds[i].s;
+    tc.sn.done = s->done;
+    tc.sn.phase = s->phase;
 #pragma unroll
     for (int c = 0; c < kMaxK; ++c) {
-      sn.alpha[c] = s->alpha[c];
-      sn.beta[c] = s->beta[c];
-      sn.scale[c] = s->scale[c];
-      sn.act64[c] = s->active64[c];
+      tc.sn.alpha[c] = s->alpha[c];
+      tc.sn.beta[c] = s->beta[c];
+      tc.sn.scale[c] = s->scale[c];
+      tc.sn.act64[c] = s->active64[c];
     }
   }
   __syncthreads();
 }
 
-// ------------------------------------------------------------------------------- persistent tiles
 // The loop kernels run one CTA per resident slot; CTA b takes the flat tiles b, b + G, b + 2G, ...
-// (G = gridDim.x). A tile's partial sums (already summed over the CTA, in thread 0) go to the
-// mesh's part[tile]; each CTA counts the tiles it did per run of consecutive tiles of one mesh
-// and adds that count to the mesh's counter with one atomic. The CTA whose addition completes
-// the mesh adds the partials in tile order (deterministic, independent of G and of any batch)
-// and calls finish(md, totals) on thread 0.
+// (G = gridDim.x). A tile's sums go to the mesh's part[tile]; each CTA counts the tiles it did
+// per run of consecutive tiles of one mesh and adds that count to the mesh's counter with one
+// atomic. The CTA whose addition completes the mesh adds the partials in tile order
+// (deterministic, independent of G and of any batch) and calls finish(md, totals) on thread 0.
 template <int NV, typename Finish>
-__device__ __forceinline__ void flush_tiles(const MeshDev& md, int ntiles, unsigned run, unsigned int* cnt,
-                                            double* sh, const Finish& finish) {
-  __shared__ int s_done;
+__device__ __forceinline__ void flush_tiles(TileCtx& tc, int tiling, unsigned run, int cnt_idx,
+                                            const Finish& finish) {
+  const int ntiles = tiling ? tc.md.ntiles32 : tc.md.ntiles;
+  unsigned int* cnt = &tc.md.s->cnt[cnt_idx];
+  if (threadIdx.x < NV) __threadfence();  // the tile sums this thread wrote, before the count
+  __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned prev = atomicAdd(cnt, run);
-    s_done = (prev + run == (unsigned)ntiles);
+    tc.last = (prev + run == (unsigned)ntiles);
   }
   __syncthreads();
-  if (s_done) {
+  if (tc.last) {
     __threadfence();
     double v[NV];
-    gather_partials<NV>(md.part, ntiles, v);
-    block_sum<NV>(v, sh);
+    gather_partials<NV>(tc.md.part, ntiles, v);
+    tile_reduce<NV>(v, tc.red[0], tc.tot);
+    __syncthreads();
     if (threadIdx.x == 0) {
       *cnt = 0u;
-      finish(md, v);
+      finish(tc.md, tc.tot);
     }
   }
   __syncthreads();
 }
 
-// body(md, tile, v) does the tile's work and leaves its CTA-summed partials in thread 0's v;
-// active(sn) says whether a mesh takes part in this launch (uniform per CTA). tiling 0: FP64
-// solver tiles, 1: mixed-precision tiles; cnt_idx selects the mesh counter.
+// body(md, tile, red, out) does the tile's work and sums its NV values into out with
+// tile_reduce(v, red, out); active(sn) says whether a mesh takes part in this launch (uniform per
+// CTA). tiling 0: FP64 solver tiles, 1: mixed-precision tiles; cnt_idx selects the mesh counter.
+// The next tile's entry is fetched while the current one is worked on.
 template <int NV, typename Active, typename Body, typename Finish>
 __device__ __forceinline__ void tile_loop(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles,
-                                          int ntiles_total, int tiling, int cnt_idx, double* sh, ScalSnap& sn,
+                                          int ntiles_total, int tiling, int cnt_idx, TileCtx& tc,
                                           const Active& active, const Body& body, const Finish& finish) {
-  int cur = -1;
+  int cur = -1, buf = 0;
   unsigned run = 0;
-  for (int t = blockIdx.x; t < ntiles_total; t += gridDim.x) {
-    const int2 tl = tiles[t];
+  const int G = (int)gridDim.x;
+  int2 nxt = make_int2(0, 0);
+  if ((int)blockIdx.x < ntiles_total) nxt = __ldg(tiles + blockIdx.x);
+  for (int t = blockIdx.x; t < ntiles_total; t += G) {
+    const int2 tl = nxt;
+    if (t + G < ntiles_total) nxt = __ldg(tiles + t + G);
     if (tl.x != cur) {
-      if (run) {
-        const MeshDev& pm = mds[cur];
-        flush_tiles<NV>(pm, tiling ? pm.ntiles32 : pm.ntiles, run, &pm.s->cnt[cnt_idx], sh, finish);
-      }
+      if (run) flush_tiles<NV>(tc, tiling, run, cnt_idx, finish);
       cur = tl.x;
       run = 0;
-      snap_scalars(mds[cur].s, sn);
+      load_mesh(mds, cur, tc);
     }
-    if (!active(sn)) continue;
-    const MeshDev& md = mds[cur];
-    double v[NV];
-    body(md, tl.y, v);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int i = 0; i < NV; ++i) md.part[tl.y * kPartStride + i] = v[i];
-    }
+    if (!active(tc.sn)) continue;
+    body(tc.md, tl.y, tc.red[buf], tc.md.part + (long)tl.y * kPartStride);
+    buf ^= 1;
     ++run;
   }
-  if (run) {
-    const MeshDev& pm = mds[cur];
-    flush_tiles<NV>(pm, tiling ? pm.ntiles32 : pm.ntiles, run, &pm.s->cnt[cnt_idx], sh, finish);
-  }
+  if (run) flush_tiles<NV>(tc, tiling, run, cnt_idx, finish);
 }
 
-// Tile loop without reductions.
+// Tile loop without sums.
 template <typename Active, typename Body>
 __device__ __forceinline__ void tile_loop_plain(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles,
-                                                int ntiles_total, ScalSnap& sn, const Active& active,
+                                                int ntiles_total, TileCtx& tc, const Active& active,
                                                 const Body& body) {
   int cur = -1;
-  for (int t = blockIdx.x; t < ntiles_total; t += gridDim.x) {
-    const int2 tl = tiles[t];
+  const int G = (int)gridDim.x;
+  int2 nxt = make_int2(0, 0);
+  if ((int)blockIdx.x < ntiles_total) nxt = __ldg(tiles + blockIdx.x);
+  for (int t = blockIdx.x; t < ntiles_total; t += G) {
+    const int2 tl = nxt;
+    if (t + G < ntiles_total) nxt = __ldg(tiles + t + G);
     if (tl.x != cur) {
       cur = tl.x;
-      snap_scalars(mds[cur].s, sn);
+      load_mesh(mds, cur, tc);
     }
-    if (!active(sn)) continue;
-    body(mds[cur], tl.y);
+    if (!active(tc.sn)) continue;
+    body(tc.md, tl.y);
   }
 }
 

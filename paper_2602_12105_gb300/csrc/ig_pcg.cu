@@ -143,15 +143,16 @@ __global__ void __launch_bounds__(kBlock) init_kernel(const MeshDev* __restrict_
 }
 
 // ------------------------------------------------------------------------------- spmv
-// q = A p and the partial sums p.q, over the rows of one tile (t0..t1).
+// q = A p and the tile's sums p.q, over the rows of one tile (t0..t1).
 template <int K>
-__device__ __forceinline__ void spmv_tile(const MeshDev& md, int tile, double (&pq)[K], double* sh) {
+__device__ __forceinline__ void spmv_tile(const MeshDev& md, int tile, double* red, double* out) {
   const long nn = md.n;
   const long t0 = (long)tile * md.tile_rows;
   const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
   const double* __restrict__ A = md.A;
   const double* __restrict__ p = md.p;
   double* __restrict__ q = md.q;
+  double pq[K];
 #pragma unroll
   for (int c = 0; c < K; ++c) pq[c] = 0.0;
 #pragma unroll
@@ -169,30 +170,29 @@ __device__ __forceinline__ void spmv_tile(const MeshDev& md, int tile, double (&
       }
     }
   }
-  block_sum<K>(pq, sh);
+  tile_reduce<K>(pq, red, out);
 }
 
 template <int K>
-__global__ void __launch_bounds__(kBlock) spmv_kernel(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles,
-                                                      int ntiles_total) {
-  __shared__ double sh[K * kBlock];
-  __shared__ ScalSnap sn;
+__global__ void __launch_bounds__(kBlock, 4) spmv_kernel(const MeshDev* __restrict__ mds,
+                                                         const int2* __restrict__ tiles, int ntiles_total) {
+  __shared__ TileCtx tc;
   tile_loop<K>(
-      mds, tiles, ntiles_total, 0, 0, sh, sn, [](const ScalSnap& x) { return !x.done; },
-      [&](const MeshDev& md, int tile, double (&v)[K]) { spmv_tile<K>(md, tile, v, sh); },
+      mds, tiles, ntiles_total, 0, 0, tc, [](const ScalSnap& x) { return !x.done; },
+      [&](const MeshDev& md, int tile, double* red, double* out) { spmv_tile<K>(md, tile, red, out); },
       [](const MeshDev& md, const double* v) { finish_spmv(md.s, K, v); });
 }
 
 // ------------------------------------------------------------------------------- update
+// x += alpha p, r -= alpha q and the tile's sums r.z, r.r (z = D^-1 r); a row's loads are issued
+// before its stores. (FP64 arithmetic bounds this kernel, so rows are not batched further.)
 template <int K>
-__device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const ScalSnap& sn, double (&acc)[2 * K],
-                                            double* sh) {
-  const long nn = md.n;
-  const long t0 = (long)tile * md.tile_rows;
-  const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
-  double alpha[K];
-#pragma unroll
-  for (int c = 0; c < K; ++c) alpha[c] = sn.alpha[c];
+__device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const ScalSnap& sn, double* red,
+                                            double* out) {
+  const int nn = md.n;
+  const int t0 = tile * md.tile_rows;
+  const int t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
+  double acc[2 * K];
 #pragma unroll
   for (int i = 0; i < 2 * K; ++i) acc[i] = 0.0;
   const double* __restrict__ Dinv = md.Dinv;
@@ -202,23 +202,29 @@ __device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const S
   double* __restrict__ r = md.r;
 #pragma unroll
   for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const long row = t0 + rr * kBlock + threadIdx.x;
+    const int row = t0 + rr * kBlock + threadIdx.x;
     if (row < t1) {
-      const double dinv = Dinv[row];
-      double pi[K];
+      double pi[K], xs[K], qs[K], rs[K];
+      const double d = Dinv[row];
       load_row<K>(p, row, pi);
 #pragma unroll
       for (int c = 0; c < K; ++c) {
-        const double xn = fma(alpha[c], pi[c], x[c * nn + row]);
-        const double rn = fma(-alpha[c], q[c * nn + row], r[c * nn + row]);
-        x[c * nn + row] = xn;
-        r[c * nn + row] = rn;
-        acc[c] = fma(rn, dinv * rn, acc[c]);
+        xs[c] = x[(long)c * nn + row];
+        qs[c] = q[(long)c * nn + row];
+        rs[c] = r[(long)c * nn + row];
+      }
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        const double a = sn.alpha[c];
+        const double rn = fma(-a, qs[c], rs[c]);
+        x[(long)c * nn + row] = fma(a, pi[c], xs[c]);
+        r[(long)c * nn + row] = rn;
+        acc[c] = fma(rn, d * rn, acc[c]);
         acc[K + c] = fma(rn, rn, acc[K + c]);
       }
     }
   }
-  block_sum<2 * K>(acc, sh);
+  tile_reduce<2 * K>(acc, red, out);
 }
 
 template <int K>
@@ -226,41 +232,52 @@ __global__ void __launch_bounds__(kBlock, 4) update_kernel(const MeshDev* __rest
                                                            const int2* __restrict__ tiles, int ntiles_total,
                                                            LoopCtl* ctl, cudaGraphConditionalHandle handle,
                                                            int use_graph, int nmesh) {
-  __shared__ double sh[2 * K * kBlock];
-  __shared__ ScalSnap sn;
+  __shared__ TileCtx tc;
   tile_loop<2 * K>(
-      mds, tiles, ntiles_total, 0, 1, sh, sn, [](const ScalSnap& x) { return !x.done; },
-      [&](const MeshDev& md, int tile, double (&v)[2 * K]) { update_tile<K>(md, tile, sn, v, sh); },
+      mds, tiles, ntiles_total, 0, 1, tc, [](const ScalSnap& x) { return !x.done; },
+      [&](const MeshDev& md, int tile, double* red, double* out) { update_tile<K>(md, tile, tc.sn, red, out); },
       [](const MeshDev& md, const double* v) { finish_update(md.s, K, v); });
   loop_control(mds, ctl, handle, use_graph, nmesh);
 }
 
 // ------------------------------------------------------------------------------- pupdate
+// p = D^-1 r + beta p, rows in pairs with loads before stores.
 template <int K>
-__global__ void __launch_bounds__(kBlock) pupdate_kernel(const MeshDev* __restrict__ mds,
-                                                         const int2* __restrict__ tiles, int ntiles_total) {
-  __shared__ ScalSnap sn;
-  tile_loop_plain(mds, tiles, ntiles_total, sn, [](const ScalSnap& x) { return !x.done; },
+__global__ void __launch_bounds__(kBlock, 4) pupdate_kernel(const MeshDev* __restrict__ mds,
+                                                            const int2* __restrict__ tiles, int ntiles_total) {
+  __shared__ TileCtx tc;
+  tile_loop_plain(mds, tiles, ntiles_total, tc, [](const ScalSnap& x) { return !x.done; },
                   [&](const MeshDev& md, int tile) {
                     const long nn = md.n;
                     const long t0 = (long)tile * md.tile_rows;
                     const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
                     double beta[K];
 #pragma unroll
-                    for (int c = 0; c < K; ++c) beta[c] = sn.beta[c];
+                    for (int c = 0; c < K; ++c) beta[c] = tc.sn.beta[c];
                     const double* __restrict__ Dinv = md.Dinv;
                     const double* __restrict__ r = md.r;
                     double* __restrict__ p = md.p;
+                    constexpr int RB = 2;
 #pragma unroll
-                    for (int rr = 0; rr < kRowsPerThread; ++rr) {
-                      const long row = t0 + rr * kBlock + threadIdx.x;
-                      if (row < t1) {
-                        const double dinv = Dinv[row];
-                        double pi[K];
-                        load_row<K>(p, row, pi);
+                    for (int r0 = 0; r0 < kRowsPerThread; r0 += RB) {
+                      double d[RB], pi[RB][K], rs[RB][K];
 #pragma unroll
-                        for (int c = 0; c < K; ++c)
-                          p[row * KP<K>::v + c] = fma(beta[c], pi[c], dinv * r[c * nn + row]);
+                      for (int u = 0; u < RB; ++u) {
+                        const long row = t0 + (r0 + u) * kBlock + threadIdx.x;
+                        if (row < t1) {
+                          d[u] = Dinv[row];
+                          load_row<K>(p, row, pi[u]);
+#pragma unroll
+                          for (int c = 0; c < K; ++c) rs[u][c] = r[c * nn + row];
+                        }
+                      }
+#pragma unroll
+                      for (int u = 0; u < RB; ++u) {
+                        const long row = t0 + (r0 + u) * kBlock + threadIdx.x;
+                        if (row < t1) {
+#pragma unroll
+                          for (int c = 0; c < K; ++c) p[row * KP<K>::v + c] = fma(beta[c], pi[u][c], d[u] * rs[u][c]);
+                        }
                       }
                     }
                   });

@@ -190,11 +190,10 @@ __global__ void __launch_bounds__(kBlock) init_mixed_kernel(const MeshDev* __res
 template <int K>
 __global__ void __launch_bounds__(kBlock, 4) spmv_mixed_kernel(const MeshDev* __restrict__ mds,
                                                                const int2* __restrict__ tiles, int ntiles_total) {
-  __shared__ double sh[K * kBlock];
-  __shared__ ScalSnap sn;
+  __shared__ TileCtx tc;
   tile_loop<K>(
-      mds, tiles, ntiles_total, 1, 0, sh, sn, [](const ScalSnap& x) { return !x.done && x.phase == kPhaseInner; },
-      [&](const MeshDev& md, int tile, double (&acc)[K]) {
+      mds, tiles, ntiles_total, 1, 0, tc, [](const ScalSnap& x) { return !x.done && x.phase == kPhaseInner; },
+      [&](const MeshDev& md, int tile, double* red, double* out) {
         const long nn = md.n;
         const long t0 = (long)tile * md.tile_rows32;
         const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
@@ -219,7 +218,7 @@ __global__ void __launch_bounds__(kBlock, 4) spmv_mixed_kernel(const MeshDev* __
             }
           }
         }
-        block_sum_f32<K>(pq, acc, sh);
+        tile_reduce<K>(pq, red, out);
       },
       [](const MeshDev& md, const double* v) { finish_spmv(md.s, K, v); });
 }
@@ -230,17 +229,17 @@ template <int K>
 __global__ void __launch_bounds__(kBlock) resid_mixed_kernel(const MeshDev* __restrict__ mds,
                                                              const int2* __restrict__ tiles, int ntiles_total,
                                                              const LoopCtl* __restrict__ ctl) {
-  __shared__ double sh[K * kBlock];
-  __shared__ ScalSnap sn;
+  __shared__ TileCtx tc;
   if (!ctl->any_apply) return;  // no mesh of the group is in the Apply phase
   tile_loop<K>(
-      mds, tiles, ntiles_total, 1, 0, sh, sn, [](const ScalSnap& x) { return !x.done && x.phase == kPhaseApply; },
-      [&](const MeshDev& md, int tile, double (&acc)[K]) {
+      mds, tiles, ntiles_total, 1, 0, tc, [](const ScalSnap& x) { return !x.done && x.phase == kPhaseApply; },
+      [&](const MeshDev& md, int tile, double* red, double* out) {
         const long nn = md.n;
         const long t0 = (long)tile * md.tile_rows32;
         const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
         const double* __restrict__ A = md.A;
         const double* __restrict__ x = md.x;
+        double acc[K];
 #pragma unroll
         for (int c = 0; c < K; ++c) acc[c] = 0.0;
 #pragma unroll
@@ -257,52 +256,67 @@ __global__ void __launch_bounds__(kBlock) resid_mixed_kernel(const MeshDev* __re
             }
           }
         }
-        block_sum<K>(acc, sh);
+        tile_reduce<K>(acc, red, out);
       },
       [](const MeshDev& md, const double* v) { finish_residual(md.s, K, v); });
 }
 
+// Inner phase: x32 += alpha p32, r32 -= alpha q32 and the tile's sums r.z, r.r; all loads of a
+// thread's rows are issued before its stores. Restart phase: r32 = r64 / ||r64||, x32 = 0.
 template <int K>
-__global__ void __launch_bounds__(kBlock, 5) update_mixed_kernel(const MeshDev* __restrict__ mds,
+__global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* __restrict__ mds,
                                                                  const int2* __restrict__ tiles, int ntiles_total,
                                                                  LoopCtl* ctl, cudaGraphConditionalHandle handle,
                                                                  int use_graph, int nmesh) {
-  __shared__ double sh[2 * K * kBlock];
-  __shared__ ScalSnap sn;
+  __shared__ TileCtx tc;
   tile_loop<2 * K>(
-      mds, tiles, ntiles_total, 1, 1, sh, sn,
+      mds, tiles, ntiles_total, 1, 1, tc,
       [](const ScalSnap& x) { return !x.done && x.phase != kPhaseApply; },
-      [&](const MeshDev& md, int tile, double (&acc)[2 * K]) {
+      [&](const MeshDev& md, int tile, double* red, double* out) {
         const long nn = md.n;
         const long t0 = (long)tile * md.tile_rows32;
         const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
-        float rz[K], rr2[K];
+        float acc[2 * K];
 #pragma unroll
-        for (int c = 0; c < K; ++c) rz[c] = rr2[c] = 0.f;
+        for (int i = 0; i < 2 * K; ++i) acc[i] = 0.f;
         const float* __restrict__ D32 = md.Dinv32;
         float* __restrict__ x32 = md.x32;
         float* __restrict__ r32 = md.r32;
-        if (sn.phase == kPhaseInner) {
-          float alpha[K];
-#pragma unroll
-          for (int c = 0; c < K; ++c) alpha[c] = (float)sn.alpha[c];
+        if (tc.sn.phase == kPhaseInner) {
           const float* __restrict__ p32 = md.p32;
           const float* __restrict__ q32 = md.q32;
+          const int n32 = md.n;
+          constexpr int RB = 2;
 #pragma unroll
-          for (int rr = 0; rr < kRowsPerThread; ++rr) {
-            const long row = t0 + rr * kBlock + threadIdx.x;
-            if (row < t1) {
-              const float dinv = D32[row];
-              float pi[K];
-              load_row32<K>(p32, row, pi);
+          for (int r0 = 0; r0 < kRowsPerThread; r0 += RB) {
+            float d[RB], pi[RB][K], xs[RB][K], qs[RB][K], rs[RB][K];
 #pragma unroll
-              for (int c = 0; c < K; ++c) {
-                const float xv = fmaf(alpha[c], pi[c], x32[c * nn + row]);
-                const float rv = fmaf(-alpha[c], q32[c * nn + row], r32[c * nn + row]);
-                x32[c * nn + row] = xv;
-                r32[c * nn + row] = rv;
-                rz[c] = fmaf(rv, dinv * rv, rz[c]);
-                rr2[c] = fmaf(rv, rv, rr2[c]);
+            for (int u = 0; u < RB; ++u) {
+              const int row = (int)t0 + (r0 + u) * kBlock + threadIdx.x;
+              if (row < (int)t1) {
+                d[u] = D32[row];
+                load_row32<K>(p32, row, pi[u]);
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                  xs[u][c] = x32[(long)c * n32 + row];
+                  qs[u][c] = q32[(long)c * n32 + row];
+                  rs[u][c] = r32[(long)c * n32 + row];
+                }
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < RB; ++u) {
+              const int row = (int)t0 + (r0 + u) * kBlock + threadIdx.x;
+              if (row < (int)t1) {
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                  const float a = (float)tc.sn.alpha[c];
+                  const float rv = fmaf(-a, qs[u][c], rs[u][c]);
+                  x32[(long)c * n32 + row] = fmaf(a, pi[u][c], xs[u][c]);
+                  r32[(long)c * n32 + row] = rv;
+                  acc[c] = fmaf(rv, d[u] * rv, acc[c]);
+                  acc[K + c] = fmaf(rv, rv, acc[K + c]);
+                }
               }
             }
           }
@@ -312,8 +326,8 @@ __global__ void __launch_bounds__(kBlock, 5) update_mixed_kernel(const MeshDev* 
           int act[K];
 #pragma unroll
           for (int c = 0; c < K; ++c) {
-            act[c] = sn.act64[c];
-            inv[c] = 1.0 / sn.scale[c];
+            act[c] = tc.sn.act64[c];
+            inv[c] = 1.0 / tc.sn.scale[c];
           }
           const double* __restrict__ r64 = md.r;
 #pragma unroll
@@ -326,19 +340,13 @@ __global__ void __launch_bounds__(kBlock, 5) update_mixed_kernel(const MeshDev* 
                 const float rv = act[c] ? (float)(r64[c * nn + row] * inv[c]) : 0.f;
                 r32[c * nn + row] = rv;
                 x32[c * nn + row] = 0.f;
-                rz[c] = fmaf(rv, dinv * rv, rz[c]);
-                rr2[c] = fmaf(rv, rv, rr2[c]);
+                acc[c] = fmaf(rv, dinv * rv, acc[c]);
+                acc[K + c] = fmaf(rv, rv, acc[K + c]);
               }
             }
           }
         }
-        float accf[2 * K];
-#pragma unroll
-        for (int c = 0; c < K; ++c) {
-          accf[c] = rz[c];
-          accf[K + c] = rr2[c];
-        }
-        block_sum_f32<2 * K>(accf, acc, sh);
+        tile_reduce<2 * K>(acc, red, out);
       },
       [](const MeshDev& md, const double* v) {
         if (md.s->phase == kPhaseInner) finish_update_mixed(md.s, K, v);
@@ -347,39 +355,50 @@ __global__ void __launch_bounds__(kBlock, 5) update_mixed_kernel(const MeshDev* 
   loop_control(mds, ctl, handle, use_graph, nmesh);
 }
 
+// Inner phase: p32 = D^-1 r32 + beta p32 (loads of a thread's rows before its stores). Apply
+// phase: x64 += ||r64|| x32.
 template <int K>
-__global__ void __launch_bounds__(kBlock, 8) pupdate_mixed_kernel(const MeshDev* __restrict__ mds,
+__global__ void __launch_bounds__(kBlock, 4) pupdate_mixed_kernel(const MeshDev* __restrict__ mds,
                                                                   const int2* __restrict__ tiles, int ntiles_total) {
-  __shared__ ScalSnap sn;
-  tile_loop_plain(mds, tiles, ntiles_total, sn,
+  __shared__ TileCtx tc;
+  tile_loop_plain(mds, tiles, ntiles_total, tc,
                   [](const ScalSnap& x) { return !x.done && (x.phase == kPhaseInner || x.phase == kPhaseApply); },
                   [&](const MeshDev& md, int tile) {
                     const long nn = md.n;
                     const long t0 = (long)tile * md.tile_rows32;
                     const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
-                    if (sn.phase == kPhaseInner) {
+                    if (tc.sn.phase == kPhaseInner) {
                       float beta[K];
 #pragma unroll
-                      for (int c = 0; c < K; ++c) beta[c] = (float)sn.beta[c];
+                      for (int c = 0; c < K; ++c) beta[c] = (float)tc.sn.beta[c];
                       const float* __restrict__ D32 = md.Dinv32;
                       const float* __restrict__ r32 = md.r32;
                       float* __restrict__ p32 = md.p32;
+                      constexpr int R = kRowsPerThread;
+                      float d[R], pi[R][K], rs[R][K];
 #pragma unroll
-                      for (int rr = 0; rr < kRowsPerThread; ++rr) {
-                        const long row = t0 + rr * kBlock + threadIdx.x;
+                      for (int u = 0; u < R; ++u) {
+                        const long row = t0 + u * kBlock + threadIdx.x;
                         if (row < t1) {
-                          const float dinv = D32[row];
-                          float pi[K];
-                          load_row32<K>(p32, row, pi);
+                          d[u] = D32[row];
+                          load_row32<K>(p32, row, pi[u]);
+#pragma unroll
+                          for (int c = 0; c < K; ++c) rs[u][c] = r32[c * nn + row];
+                        }
+                      }
+#pragma unroll
+                      for (int u = 0; u < R; ++u) {
+                        const long row = t0 + u * kBlock + threadIdx.x;
+                        if (row < t1) {
 #pragma unroll
                           for (int c = 0; c < K; ++c)
-                            p32[row * KPm<K>::v + c] = fmaf(beta[c], pi[c], dinv * r32[c * nn + row]);
+                            p32[row * KPm<K>::v + c] = fmaf(beta[c], pi[u][c], d[u] * rs[u][c]);
                         }
                       }
                     } else {
                       double sc[K];
 #pragma unroll
-                      for (int c = 0; c < K; ++c) sc[c] = sn.scale[c];
+                      for (int c = 0; c < K; ++c) sc[c] = tc.sn.scale[c];
                       const float* __restrict__ x32 = md.x32;
                       double* __restrict__ x = md.x;
 #pragma unroll
