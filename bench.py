@@ -188,6 +188,35 @@ def algorithmic(kernel, n, m, nnz, k, prec):
     return float(flops), float(byts)
 
 
+# ------------------------------------------------------------------------------- ranks
+def max_over_ranks(x, world, device=None):
+    """The largest value of x over all ranks (the slowest rank sets a timed region); x itself on
+    one rank. Uses the process group of torch.distributed (NCCL on GPUs, gloo in the CPU tests)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, steps_per_rank, ms):
+    """Whole-job throughput: every rank ran `steps_per_rank` units of its own work (weak scaling)
+    inside a region of `ms` milliseconds (the max over ranks)."""
+    return world * steps_per_rank / (ms / 1000.0)
+
+
+def rank_seed(rank):
+    """Each rank solves its own seeded mesh of the same workload family."""
+    return rank
+
+
+def shard(items, rank, world):
+    """The independent units (meshes, requests) rank `rank` takes: every world-th one."""
+    return list(items)[rank::world]
+
+
 # ------------------------------------------------------------------------------- ours
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -198,7 +227,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     precision = args.precision or "fp64"
-    p = make_problem(args.workload, seed=rank)
+    p = make_problem(args.workload, seed=rank_seed(rank))
     k = p.B.shape[1]
     mesh = api.Mesh(torch.from_numpy(p.F).to(dev), p.n)
     V = torch.from_numpy(p.V).to(dev)
@@ -244,11 +273,8 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.stop() if sampler else None
     step_ms = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)])
     total_ms = float(evs[0].elapsed_time(evs[-1]))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1000.0)
+    total_ms = max_over_ranks(total_ms, world, dev)
+    value = aggregate_rate(world, args.steps, total_ms)
 
     # per-kernel device times (CUDA events around each launch, host-launched loop)
     prof = {}
@@ -290,11 +316,8 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         ems = float(e0.elapsed_time(e1))
-        if world > 1:
-            t = torch.tensor([ems], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * args.e2e_steps / (ems / 1000.0), "unit": UNIT,
+        ems = max_over_ranks(ems, world, dev)
+        e2e = {"value": aggregate_rate(world, args.e2e_steps, ems), "unit": UNIT,
                "h2d_bytes_per_step": int(hV.nbytes + hB.nbytes + hT.nbytes), "d2h_bytes_per_step": int(hG.nbytes)}
 
     if rank != 0:
@@ -500,8 +523,12 @@ def variant_batch(api, _native, dev, tol, steps):
     opts = api.make_opts(rel_tol=tol)
     batch = api.Batch(meshes)
 
-    def bstep(prec):
+    def bstep(prec, info=False):
         batch.assemble(Vs, ts, prec)
+        if info:
+            Us, fi = batch.solve(Vs, opts=opts, info=True)
+            gVs, _, _, ai = batch.adjoint(Vs, None, True, Us, [U - T for U, T in zip(Us, Ts)], opts=opts, info=True)
+            return Us, gVs, fi, ai
         Us = batch.solve(Vs, opts=opts)
         gVs, _, _ = batch.adjoint(Vs, None, True, Us, [U - T for U, T in zip(Us, Ts)], opts=opts)
         return Us, gVs
@@ -528,13 +555,28 @@ def variant_batch(api, _native, dev, tol, steps):
         return float(e0.elapsed_time(e1)) / reps
 
     # accuracy: every mesh's mixed result against its FP64 result (both to the same tolerance)
-    U64, g64 = bstep("fp64")
-    U32, g32 = bstep("mixed")
+    U64, g64, f64i, a64i = bstep("fp64", True)
+    U32, g32, f32i, a32i = bstep("mixed", True)
     errU = max(_rel(a, b) for a, b in zip(U32, U64))
     errG = max(_rel(a, b) for a, b in zip(g32, g64))
+    worst = int(np.argmax([_rel(a, b) for a, b in zip(g32, g64)]))
+
+    def its(infos):
+        it = np.array([i["iterations"] for i in infos])
+        return {"max": int(it.max()), "mean": round(float(it.mean()), 1),
+                "row_iterations": int(sum(q.n * i["iterations"] for q, i in zip(probs, infos)))}
+
+    def prof_step(prec):
+        _native.profile_enable(True)
+        bstep(prec)
+        torch.cuda.synchronize()
+        pr = _native.profile_read()
+        _native.profile_enable(False)
+        return {k: {"launches": c, "total_ms": round(ms, 3)} for k, (c, ms) in sorted(pr.items(), key=lambda kv: -kv[1][1])}
     ms64 = timed(lambda: bstep("fp64"), steps)
     ms32 = timed(lambda: bstep("mixed"), steps)
     msp = timed(pstep, max(1, steps // 2))
+    prof64, prof32 = prof_step("fp64"), prof_step("mixed")
     nb = len(probs)
     batch.close()
     for m in meshes:
@@ -548,7 +590,11 @@ def variant_batch(api, _native, dev, tol, steps):
             "ms_per_batch": {"batched_mixed": round(ms32, 3), "batched_fp64": round(ms64, 3),
                              "plain_fp64": round(msp, 3)},
             "speedup_batched_mixed_vs_plain": round(msp / ms32, 3),
-            "max_rel_err_mixed_vs_fp64": {"U": errU, "gV": errG}}
+            "max_rel_err_mixed_vs_fp64": {"U": errU, "gV": errG},
+            "worst_gV_mesh": {"name": probs[worst].name, "n": probs[worst].n, "t": probs[worst].t},
+            "iterations": {"fp64": {"forward": its(f64i), "adjoint": its(a64i)},
+                           "mixed": {"forward": its(f32i), "adjoint": its(a32i)}},
+            "profile_one_step_host_launch": {"fp64": prof64, "mixed": prof32}}
 
 
 def serving_requests(count, seed=7):
