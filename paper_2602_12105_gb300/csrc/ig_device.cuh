@@ -440,84 +440,258 @@ __device__ __forceinline__ void flush_tiles(TileCtx& tc, int tiling, unsigned ru
   __syncthreads();
 }
 
+// ------------------------------------------------------------------------------- active list
+// Exclusive scan of three counters over the CTA (thread order), with the CTA totals.
+__device__ __forceinline__ void block_exscan3(int a, int b, int c, int& ea, int& eb, int& ec, int& ta, int& tb,
+                                              int& tc) {
+  __shared__ int ws[3][kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int ia = a, ib = b, ic = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int xa = __shfl_up_sync(0xffffffffu, ia, o);
+    const int xb = __shfl_up_sync(0xffffffffu, ib, o);
+    const int xc = __shfl_up_sync(0xffffffffu, ic, o);
+    if (lane >= o) {
+      ia += xa;
+      ib += xb;
+      ic += xc;
+    }
+  }
+  if (lane == 31) {
+    ws[0][warp] = ia;
+    ws[1][warp] = ib;
+    ws[2][warp] = ic;
+  }
+  __syncthreads();
+  int pa = 0, pb = 0, pc = 0;
+  ta = tb = tc = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    if (w < warp) {
+      pa += ws[0][w];
+      pb += ws[1][w];
+      pc += ws[2][w];
+    }
+    ta += ws[0][w];
+    tb += ws[1][w];
+    tc += ws[2][w];
+  }
+  ea = pa + ia - a;
+  eb = pb + ib - b;
+  ec = pc + ic - c;
+  __syncthreads();
+}
+
+// Rebuild the active list from the meshes' done flags (run by every thread of one CTA, after
+// every other CTA of the launch is done with the list). The start tables give each CTA of the
+// loop kernels its first tile: CTA g takes the listed tiles [g·chunk, (g+1)·chunk).
+__device__ __noinline__ void rebuild_active(const MeshDev* __restrict__ mds, LoopCtl* ctl) {
+  const int nmesh = ctl->nmesh;
+  int nact = 0, tot64 = 0, tot32 = 0, ndone = 0;
+  for (int i0 = 0; i0 < nmesh; i0 += kBlock) {
+    const int i = i0 + threadIdx.x;
+    int live = 0, c64 = 0, c32 = 0;
+    if (i < nmesh) {
+      live = __ldcg(&mds[i].s->done) == 0;
+      if (live) {
+        c64 = mds[i].ntiles;
+        c32 = mds[i].ntiles32;
+      }
+    }
+    int e0, e1, e2, t0, t1, t2;
+    block_exscan3(live, c64, c32, e0, e1, e2, t0, t1, t2);
+    if (live) {
+      ctl->act_mesh[nact + e0] = i;
+      ctl->act_off64[nact + e0] = tot64 + e1;
+      ctl->act_off32[nact + e0] = tot32 + e2;
+    }
+    ndone += (nmesh - i0 < kBlock ? nmesh - i0 : kBlock) - t0;
+    nact += t0;
+    tot64 += t1;
+    tot32 += t2;
+  }
+  const int g64 = ctl->grid64, g32 = ctl->grid32;
+  const int ch64 = tot64 > 0 ? (tot64 + g64 - 1) / g64 : 1;
+  const int ch32 = tot32 > 0 ? (tot32 + g32 - 1) / g32 : 1;
+  if (threadIdx.x == 0) {
+    ctl->act_off64[nact] = tot64;
+    ctl->act_off32[nact] = tot32;
+    ctl->nact = nact;
+    ctl->total64 = tot64;
+    ctl->total32 = tot32;
+    ctl->chunk64 = ch64;
+    ctl->chunk32 = ch32;
+    ctl->ndone_list = ndone;
+  }
+  __syncthreads();  // the offsets above are visible to the whole CTA
+  // the thread of listed mesh j writes the start of every CTA whose chunk begins in its tiles
+  for (int j = threadIdx.x; j < nact; j += kBlock) {
+    const int mi = ctl->act_mesh[j];
+    const int a64 = ctl->act_off64[j], z64 = ctl->act_off64[j + 1];
+    for (int g = (a64 + ch64 - 1) / ch64; g < g64 && g * ch64 < z64; ++g) {
+      const int cnt = tot64 - g * ch64 < ch64 ? tot64 - g * ch64 : ch64;
+      ctl->start64[g] = make_int4(j, g * ch64 - a64, mi, cnt);
+    }
+    const int a32 = ctl->act_off32[j], z32 = ctl->act_off32[j + 1];
+    for (int g = (a32 + ch32 - 1) / ch32; g < g32 && g * ch32 < z32; ++g) {
+      const int cnt = tot32 - g * ch32 < ch32 ? tot32 - g * ch32 : ch32;
+      ctl->start32[g] = make_int4(j, g * ch32 - a32, mi, cnt);
+    }
+  }
+  // CTAs past the listed tiles get none
+  for (int g = threadIdx.x; g < g64; g += kBlock)
+    if ((long)g * ch64 >= tot64) ctl->start64[g] = make_int4(0, 0, -1, 0);
+  for (int g = threadIdx.x; g < g32; g += kBlock)
+    if ((long)g * ch32 >= tot32) ctl->start32[g] = make_int4(0, 0, -1, 0);
+}
+
+// The Apply list (mixed precision): the meshes not done and in the Apply phase, with the start
+// table of the residual kernel (mixed tiling). Run by every thread of one CTA.
+__device__ __noinline__ void rebuild_apply(const MeshDev* __restrict__ mds, LoopCtl* ctl) {
+  const int nmesh = ctl->nmesh;
+  int napp = 0, tot = 0;
+  for (int i0 = 0; i0 < nmesh; i0 += kBlock) {
+    const int i = i0 + threadIdx.x;
+    int live = 0, c32 = 0;
+    if (i < nmesh) {
+      const SolveScal* s = mds[i].s;
+      live = __ldcg(&s->done) == 0 && __ldcg(&s->phase) == kPhaseApply;
+      if (live) c32 = mds[i].ntiles32;
+    }
+    int e0, e1, e2, t0, t1, t2;
+    block_exscan3(live, c32, 0, e0, e1, e2, t0, t1, t2);
+    if (live) {
+      ctl->app_mesh[napp + e0] = i;
+      ctl->app_off32[napp + e0] = tot + e1;
+    }
+    napp += t0;
+    tot += t1;
+  }
+  const int g32 = ctl->grid32;
+  const int ch = tot > 0 ? (tot + g32 - 1) / g32 : 1;
+  if (threadIdx.x == 0) ctl->app_off32[napp] = tot;
+  __syncthreads();
+  for (int j = threadIdx.x; j < napp; j += kBlock) {
+    const int mi = ctl->app_mesh[j];
+    const int a = ctl->app_off32[j], z = ctl->app_off32[j + 1];
+    for (int g = (a + ch - 1) / ch; g < g32 && g * ch < z; ++g) {
+      const int cnt = tot - g * ch < ch ? tot - g * ch : ch;
+      ctl->app_start32[g] = make_int4(j, g * ch - a, mi, cnt);
+    }
+  }
+  for (int g = threadIdx.x; g < g32; g += kBlock)
+    if ((long)g * ch >= tot) ctl->app_start32[g] = make_int4(0, 0, -1, 0);
+}
+
 // body(md, tile, red, out) does the tile's work and sums its NV values into out with
 // tile_reduce(v, red, out); active(sn) says whether a mesh takes part in this launch (uniform per
 // CTA). tiling 0: FP64 solver tiles, 1: mixed-precision tiles; cnt_idx selects the mesh counter.
-// The next tile's entry is fetched while the current one is worked on.
+// The CTA walks its chunk of the active list's tiles (start: its entry of the start table, act:
+// the list of meshes).
 template <int NV, typename Active, typename Body, typename Finish>
-__device__ __forceinline__ void tile_loop(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles,
-                                          int ntiles_total, int tiling, int cnt_idx, TileCtx& tc,
-                                          const Active& active, const Body& body, const Finish& finish) {
-  int cur = -1, buf = 0;
+__device__ __forceinline__ void tile_loop(const MeshDev* __restrict__ mds, const int4* start, const int* act,
+                                          int tiling, int cnt_idx, TileCtx& tc, const Active& active,
+                                          const Body& body, const Finish& finish) {
+  const int4 st = start[blockIdx.x];
+  if (st.w <= 0) return;
+  int j = st.x, lt = st.y, cur = st.z, buf = 0;
   unsigned run = 0;
-  const int G = (int)gridDim.x;
-  int2 nxt = make_int2(0, 0);
-  if ((int)blockIdx.x < ntiles_total) nxt = __ldg(tiles + blockIdx.x);
-  for (int t = blockIdx.x; t < ntiles_total; t += G) {
-    const int2 tl = nxt;
-    if (t + G < ntiles_total) nxt = __ldg(tiles + t + G);
-    if (tl.x != cur) {
-      if (run) flush_tiles<NV>(tc, tiling, run, cnt_idx, finish);
-      cur = tl.x;
-      run = 0;
-      load_mesh(mds, cur, tc);
+  load_mesh(mds, cur, tc);
+  for (int t = 0; t < st.w; ++t) {
+    if (t > 0 && lt == 0) {
+      const int mi = act[j];
+      if (mi != cur) {
+        if (run) flush_tiles<NV>(tc, tiling, run, cnt_idx, finish);
+        cur = mi;
+        run = 0;
+        load_mesh(mds, cur, tc);
+      }
     }
-    if (!active(tc.sn)) continue;
-    body(tc.md, tl.y, tc.red[buf], tc.md.part + (long)tl.y * kPartStride);
-    buf ^= 1;
-    ++run;
+    if (active(tc.sn)) {
+      body(tc.md, lt, tc.red[buf], tc.md.part + (long)lt * kPartStride);
+      buf ^= 1;
+      ++run;
+    }
+    if (++lt == (tiling ? tc.md.ntiles32 : tc.md.ntiles)) {
+      ++j;
+      lt = 0;
+    }
   }
   if (run) flush_tiles<NV>(tc, tiling, run, cnt_idx, finish);
 }
 
 // Tile loop without sums.
 template <typename Active, typename Body>
-__device__ __forceinline__ void tile_loop_plain(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles,
-                                                int ntiles_total, TileCtx& tc, const Active& active,
-                                                const Body& body) {
-  int cur = -1;
-  const int G = (int)gridDim.x;
-  int2 nxt = make_int2(0, 0);
-  if ((int)blockIdx.x < ntiles_total) nxt = __ldg(tiles + blockIdx.x);
-  for (int t = blockIdx.x; t < ntiles_total; t += G) {
-    const int2 tl = nxt;
-    if (t + G < ntiles_total) nxt = __ldg(tiles + t + G);
-    if (tl.x != cur) {
-      cur = tl.x;
-      load_mesh(mds, cur, tc);
+__device__ __forceinline__ void tile_loop_plain(const MeshDev* __restrict__ mds, const int4* start, const int* act,
+                                                int tiling, TileCtx& tc, const Active& active, const Body& body) {
+  const int4 st = start[blockIdx.x];
+  if (st.w <= 0) return;
+  int j = st.x, lt = st.y, cur = st.z;
+  load_mesh(mds, cur, tc);
+  for (int t = 0; t < st.w; ++t) {
+    if (t > 0 && lt == 0) {
+      const int mi = act[j];
+      if (mi != cur) {
+        cur = mi;
+        load_mesh(mds, cur, tc);
+      }
     }
-    if (!active(tc.sn)) continue;
-    body(tc.md, tl.y);
+    if (active(tc.sn)) body(tc.md, lt);
+    if (++lt == (tiling ? tc.md.ntiles32 : tc.md.ntiles)) {
+      ++j;
+      lt = 0;
+    }
   }
 }
 
 // The last CTA of an update launch decides whether the device-side loop goes on: it stops when
-// every mesh of the group is done or the hard cap on iterations is reached.
+// every mesh of the group is done, the hard cap on iterations is reached, or (serving) a member
+// that was running has finished. It rebuilds the active list when more meshes are done.
 __device__ __forceinline__ void loop_control(const MeshDev* __restrict__ mds, LoopCtl* ctl,
-                                             cudaGraphConditionalHandle handle, int use_graph, int nmesh) {
+                                             cudaGraphConditionalHandle handle, int use_graph) {
+  __shared__ int s_last;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned prev = atomicAdd(&ctl->cnt, 1u);
-    if (prev == gridDim.x - 1u) {
-      __threadfence();
-      int all = 1, apply = 0, ndone = 0;
-      for (int i = 0; i < nmesh; ++i) {
-        const int d = __ldcg(&mds[i].s->done);
-        all &= (d != 0);
-        ndone += (d != 0);
-        apply |= (!d && __ldcg(&mds[i].s->phase) == kPhaseApply);
-      }
-      ctl->any_apply = apply;
-      const int it = ctl->iter + 1;
-      ctl->iter = it;
-      if (all || it >= ctl->cap || ndone > ctl->ndone_start) {
-        ctl->all_done = 1;
-        if (use_graph) cudaGraphSetConditional(handle, 0u);
-      }
-      ctl->cnt = 0u;
-    }
+    s_last = (prev == gridDim.x - 1u);
   }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int nmesh = ctl->nmesh;
+  int ndone = 0, apply = 0;
+  for (int i0 = 0; i0 < nmesh; i0 += kBlock) {
+    const int i = i0 + threadIdx.x;
+    int d = 0, ap = 0;
+    if (i < nmesh) {
+      const SolveScal* s = mds[i].s;
+      d = __ldcg(&s->done) != 0;
+      ap = !d && __ldcg(&s->phase) == kPhaseApply;
+    }
+    ndone += __syncthreads_count(d);
+    apply |= __syncthreads_or(ap);
+  }
+  const int rebuild = ndone > ctl->ndone_list && ndone < nmesh;
+  __syncthreads();
+  if (rebuild) rebuild_active(mds, ctl);
+  if (apply && ctl->app_mesh) rebuild_apply(mds, ctl);
+  if (threadIdx.x == 0) {
+    ctl->any_apply = apply;
+    const int it = ctl->iter + 1;
+    ctl->iter = it;
+    if (ndone == nmesh || it >= ctl->cap || ndone > ctl->ndone_start) {
+      ctl->all_done = 1;
+      if (use_graph) cudaGraphSetConditional(handle, 0u);
+    }
+    ctl->cnt = 0u;
+  }
+}
+
+// Start of a solve or of a serving round: list every mesh that is not done.
+__global__ void __launch_bounds__(kBlock) list_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl) {
+  rebuild_active(mds, ctl);
 }
 
 // Row loads of [n][KP] float vectors (KP = 4 when K = 3: one aligned 16-byte load).

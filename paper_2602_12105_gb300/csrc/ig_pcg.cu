@@ -174,11 +174,11 @@ __device__ __forceinline__ void spmv_tile(const MeshDev& md, int tile, double* r
 }
 
 template <int K>
-__global__ void __launch_bounds__(kBlock, 4) spmv_kernel(const MeshDev* __restrict__ mds,
-                                                         const int2* __restrict__ tiles, int ntiles_total) {
+__global__ void __launch_bounds__(kBlock, 4) spmv_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl,
+    const int4* start, const int* act) {
   __shared__ TileCtx tc;
   tile_loop<K>(
-      mds, tiles, ntiles_total, 0, 0, tc, [](const ScalSnap& x) { return !x.done; },
+      mds, start, act, 0, 0, tc, [](const ScalSnap& x) { return !x.done; },
       [&](const MeshDev& md, int tile, double* red, double* out) { spmv_tile<K>(md, tile, red, out); },
       [](const MeshDev& md, const double* v) { finish_spmv(md.s, K, v); });
 }
@@ -228,25 +228,23 @@ __device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const S
 }
 
 template <int K>
-__global__ void __launch_bounds__(kBlock, 4) update_kernel(const MeshDev* __restrict__ mds,
-                                                           const int2* __restrict__ tiles, int ntiles_total,
-                                                           LoopCtl* ctl, cudaGraphConditionalHandle handle,
-                                                           int use_graph, int nmesh) {
+__global__ void __launch_bounds__(kBlock, 4) update_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl,
+    const int4* start, const int* act, cudaGraphConditionalHandle handle, int use_graph) {
   __shared__ TileCtx tc;
   tile_loop<2 * K>(
-      mds, tiles, ntiles_total, 0, 1, tc, [](const ScalSnap& x) { return !x.done; },
+      mds, start, act, 0, 1, tc, [](const ScalSnap& x) { return !x.done; },
       [&](const MeshDev& md, int tile, double* red, double* out) { update_tile<K>(md, tile, tc.sn, red, out); },
       [](const MeshDev& md, const double* v) { finish_update(md.s, K, v); });
-  loop_control(mds, ctl, handle, use_graph, nmesh);
+  loop_control(mds, ctl, handle, use_graph);
 }
 
 // ------------------------------------------------------------------------------- pupdate
 // p = D^-1 r + beta p, rows in pairs with loads before stores.
 template <int K>
-__global__ void __launch_bounds__(kBlock, 4) pupdate_kernel(const MeshDev* __restrict__ mds,
-                                                            const int2* __restrict__ tiles, int ntiles_total) {
+__global__ void __launch_bounds__(kBlock, 4) pupdate_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl,
+    const int4* start, const int* act) {
   __shared__ TileCtx tc;
-  tile_loop_plain(mds, tiles, ntiles_total, tc, [](const ScalSnap& x) { return !x.done; },
+  tile_loop_plain(mds, start, act, 0, tc, [](const ScalSnap& x) { return !x.done; },
                   [&](const MeshDev& md, int tile) {
                     const long nn = md.n;
                     const long t0 = (long)tile * md.tile_rows;
@@ -342,9 +340,9 @@ cudaError_t build_plan(Group& g, SolvePlan& pl) {
   cudaStream_t cs = g.capture_stream;
   e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
-  spmv_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.tiles, g.ntiles);
-  update_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.tiles, g.ntiles, g.ctl, handle, 1, g.nmesh);
-  pupdate_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.tiles, g.ntiles);
+  spmv_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.start64, g.act_mesh);
+  update_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.start64, g.act_mesh, handle, 1);
+  pupdate_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.start64, g.act_mesh);
   cudaError_t le = cudaGetLastError();
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(cs, &captured);
@@ -365,6 +363,7 @@ cudaError_t begin_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_op
   const int cap = o.max_iter + 2;
   IG_PROF("pcg_init", st);
   init_kernel<K><<<g.ntiles, kBlock, 0, st>>>(g.mds, g.tiles, io, rhs_mass, g.ctl, o.rel_tol, o.max_iter, cap);
+  list_kernel<<<1, kBlock, 0, st>>>(g.mds, g.ctl);
   return cudaGetLastError();
 }
 
@@ -375,16 +374,15 @@ cudaError_t host_loop_k(Group& g, int max_it, int poll, cudaStream_t st) {
   for (int it = 0; it < max_it; ++it) {
     {
       IG_PROF("pcg_spmv", st);
-      spmv_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.tiles, g.ntiles);
+      spmv_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.ctl, g.start64, g.act_mesh);
     }
     {
       IG_PROF("pcg_update", st);
-      update_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.tiles, g.ntiles, g.ctl, cudaGraphConditionalHandle{}, 0,
-                                                     g.nmesh);
+      update_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.ctl, g.start64, g.act_mesh, cudaGraphConditionalHandle{}, 0);
     }
     {
       IG_PROF("pcg_pupdate", st);
-      pupdate_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.tiles, g.ntiles);
+      pupdate_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.ctl, g.start64, g.act_mesh);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -431,19 +429,30 @@ cudaError_t solve_k(Group& g, const IoTable& io, int rhs_mass, const ig_solve_op
 
 // Serving: restart the loop counters of a group whose members may be mid-solve. The loop stops
 // after `budget` iterations, or as soon as a member that was running has finished.
-__global__ void loop_reset_kernel(const MeshDev* __restrict__ mds, int nmesh, LoopCtl* ctl, int budget) {
+__global__ void __launch_bounds__(kBlock) loop_reset_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl,
+                                                             int budget) {
+  const int nmesh = ctl->nmesh;
   int ndone = 0, apply = 0;
-  for (int i = 0; i < nmesh; ++i) {
-    const int d = mds[i].s->done;
-    ndone += d != 0;
-    apply |= (!d && mds[i].s->phase == kPhaseApply);
+  for (int i0 = 0; i0 < nmesh; i0 += kBlock) {
+    const int i = i0 + threadIdx.x;
+    int d = 0, ap = 0;
+    if (i < nmesh) {
+      d = mds[i].s->done != 0;
+      ap = !d && mds[i].s->phase == kPhaseApply;
+    }
+    ndone += __syncthreads_count(d);
+    apply |= __syncthreads_or(ap);
   }
-  ctl->cnt = 0u;
-  ctl->iter = 0;
-  ctl->cap = budget;
-  ctl->all_done = ndone == nmesh ? 1 : 0;
-  ctl->any_apply = apply;
-  ctl->ndone_start = ndone;
+  if (threadIdx.x == 0) {
+    ctl->cnt = 0u;
+    ctl->iter = 0;
+    ctl->cap = budget;
+    ctl->all_done = ndone == nmesh ? 1 : 0;
+    ctl->any_apply = apply;
+    ctl->ndone_start = ndone;
+  }
+  rebuild_active(mds, ctl);
+  if (apply && ctl->app_mesh) rebuild_apply(mds, ctl);
 }
 
 __global__ void collect_done_kernel(const MeshDev* __restrict__ mds, int nmesh, int* out) {
@@ -454,7 +463,7 @@ __global__ void collect_done_kernel(const MeshDev* __restrict__ mds, int nmesh, 
 }  // namespace
 
 cudaError_t group_iterate(Group& g, int k, int mixed, int budget, int* done_host, cudaStream_t st) {
-  loop_reset_kernel<<<1, 1, 0, st>>>(g.mds, g.nmesh, g.ctl, budget);
+  loop_reset_kernel<<<1, kBlock, 0, st>>>(g.mds, g.ctl, budget);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (mixed) {
@@ -537,6 +546,11 @@ cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, int slots64
   if ((e = cudaMalloc(&g.face_tiles, sizeof(int2) * ftiles.size())) != cudaSuccess) return e;
   if ((e = cudaMalloc(&g.row_tiles, sizeof(int2) * rtiles.size())) != cudaSuccess) return e;
   if ((e = cudaMalloc(&g.ctl, sizeof(LoopCtl))) != cudaSuccess) return e;
+  // ints: act_mesh, act_off64, act_off32, app_mesh, app_off32; then (16-byte aligned) the int4
+  // start tables start64, start32, app_start32
+  const size_t list_ints = (5 * (size_t)nmesh + 3 + 3) / 4 * 4;
+  const size_t list_words = list_ints + 4 * (size_t)(g.grid64 + 2 * g.grid32);
+  if ((e = cudaMalloc(&g.act_buf, sizeof(int) * list_words)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&g.calls_dev, sizeof(CallDev) * nmesh)) != cudaSuccess) return e;
   if ((e = cudaMallocHost(&g.calls_host, sizeof(CallDev) * nmesh)) != cudaSuccess) return e;
   if ((e = cudaMallocHost(&g.done_host, sizeof(int))) != cudaSuccess) return e;
@@ -555,7 +569,27 @@ cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, int slots64
   if ((e = cudaMemcpyAsync(g.row_tiles, rtiles.data(), sizeof(int2) * rtiles.size(), cudaMemcpyHostToDevice, st)) !=
       cudaSuccess)
     return e;
-  if ((e = cudaMemsetAsync(g.ctl, 0, sizeof(LoopCtl), st)) != cudaSuccess) return e;
+  {
+    LoopCtl c{};
+    c.nmesh = nmesh;
+    c.grid64 = g.grid64;
+    c.grid32 = g.grid32;
+    c.ndone_list = -1;
+    c.act_mesh = g.act_buf;
+    c.act_off64 = g.act_buf + nmesh;
+    c.act_off32 = g.act_buf + 2 * (size_t)nmesh + 1;
+    c.app_mesh = g.act_buf + 3 * (size_t)nmesh + 2;
+    c.app_off32 = c.app_mesh + nmesh;
+    c.start64 = reinterpret_cast<int4*>(g.act_buf + list_ints);
+    c.start32 = c.start64 + g.grid64;
+    c.app_start32 = c.start32 + g.grid32;
+    g.app_mesh = c.app_mesh;
+    g.app_start32 = c.app_start32;
+    g.act_mesh = c.act_mesh;
+    g.start64 = c.start64;
+    g.start32 = c.start32;
+    if ((e = cudaMemcpyAsync(g.ctl, &c, sizeof(LoopCtl), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  }
   if ((e = cudaStreamCreateWithFlags(&g.capture_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(g.calls_ev, st)) != cudaSuccess) return e;
   return cudaStreamSynchronize(st);
@@ -591,6 +625,7 @@ void group_destroy(Group& g) {
   if (g.face_tiles) cudaFree(g.face_tiles);
   if (g.row_tiles) cudaFree(g.row_tiles);
   if (g.ctl) cudaFree(g.ctl);
+  if (g.act_buf) cudaFree(g.act_buf);
   if (g.calls_dev) cudaFree(g.calls_dev);
   if (g.calls_host) cudaFreeHost(g.calls_host);
   if (g.done_host) cudaFreeHost(g.done_host);
@@ -652,7 +687,9 @@ constexpr size_t kNaX = align256(kNaDinv + sizeof(double) * kNoAllocMaxRows);
 constexpr size_t kNaR = align256(kNaX + kNaVec);
 constexpr size_t kNaP = align256(kNaR + kNaVec);
 constexpr size_t kNaQ = align256(kNaP + kNaVec);
-constexpr size_t kNoAllocBytes = align256(kNaQ + kNaVec);
+constexpr size_t kNaList = align256(kNaQ + kNaVec);   // active list of the one mesh: 8 ints
+constexpr size_t kNaStart = align256(kNaList + sizeof(int) * 8);
+constexpr size_t kNoAllocBytes = align256(kNaStart + sizeof(int4) * (kNoAllocMaxTiles + 1));
 
 // Per-device base address of the scratch array, looked up once per device.
 std::mutex g_noalloc_mu;
@@ -660,7 +697,7 @@ void* g_noalloc_base[64] = {};
 
 // Preconditioner from the operator's diagonal, solver state cleared, tile table written.
 __global__ void __launch_bounds__(256) noalloc_setup_kernel(MeshDev md, MeshDev* md_out, int2* tiles, int ntiles,
-                                                            LoopCtl* ctl, SolveScal* s) {
+                                                            LoopCtl ctl_init, LoopCtl* ctl, SolveScal* s) {
   const long row = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (row < md.n) {
     double d = 0.0;
@@ -675,7 +712,7 @@ __global__ void __launch_bounds__(256) noalloc_setup_kernel(MeshDev md, MeshDev*
     if (threadIdx.x < ntiles) tiles[threadIdx.x] = make_int2(0, threadIdx.x);
     if (threadIdx.x == 0) {
       *md_out = md;
-      *ctl = LoopCtl{};
+      *ctl = ctl_init;
       *s = SolveScal{};
     }
   }
@@ -750,7 +787,20 @@ extern "C" ig_status ig_solve_csr_noalloc(const int32_t* rowptr_dev, const int32
   int done_word = 0;
   g.done_host = &done_word;
   if (cudaMemsetAsync(md.err, 0, sizeof(int), st) != cudaSuccess) return IG_ERR_CUDA;
-  noalloc_setup_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(md, g.mds, g.tiles, g.ntiles, g.ctl, md.s);
+  LoopCtl ctl_init{};
+  ctl_init.nmesh = 1;
+  ctl_init.grid64 = g.grid64;
+  ctl_init.grid32 = 0;
+  ctl_init.ndone_list = -1;
+  ctl_init.act_mesh = reinterpret_cast<int*>(base + kNaList);
+  ctl_init.act_off64 = ctl_init.act_mesh + 1;
+  ctl_init.act_off32 = ctl_init.act_mesh + 3;
+  ctl_init.start64 = reinterpret_cast<int4*>(base + kNaStart);
+  ctl_init.start32 = ctl_init.start64 + kNoAllocMaxTiles;
+  g.act_mesh = ctl_init.act_mesh;
+  g.start64 = ctl_init.start64;
+  g.start32 = ctl_init.start32;
+  noalloc_setup_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(md, g.mds, g.tiles, g.ntiles, ctl_init, g.ctl, md.s);
   if (cudaGetLastError() != cudaSuccess) return IG_ERR_CUDA;
   IoTable* io = new (std::nothrow) IoTable;
   if (!io) return IG_ERR_OOM;

@@ -188,11 +188,11 @@ __global__ void __launch_bounds__(kBlock) init_mixed_kernel(const MeshDev* __res
 }
 
 template <int K>
-__global__ void __launch_bounds__(kBlock, 4) spmv_mixed_kernel(const MeshDev* __restrict__ mds,
-                                                               const int2* __restrict__ tiles, int ntiles_total) {
+__global__ void __launch_bounds__(kBlock, 4) spmv_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl,
+    const int4* start, const int* act) {
   __shared__ TileCtx tc;
   tile_loop<K>(
-      mds, tiles, ntiles_total, 1, 0, tc, [](const ScalSnap& x) { return !x.done && x.phase == kPhaseInner; },
+      mds, start, act, 1, 0, tc, [](const ScalSnap& x) { return !x.done && x.phase == kPhaseInner; },
       [&](const MeshDev& md, int tile, double* red, double* out) {
         const long nn = md.n;
         const long t0 = (long)tile * md.tile_rows32;
@@ -224,15 +224,15 @@ __global__ void __launch_bounds__(kBlock, 4) spmv_mixed_kernel(const MeshDev* __
 }
 
 // Apply phase: r64 = rhs - A64 x64 in FP64 and its squared norms (the refinement residual).
-// Kept out of the FP32 SpMV kernel so that the hot FP32 kernel stays small.
+// Kept out of the FP32 SpMV kernel so that the hot FP32 kernel stays small; it walks the Apply
+// list (the meshes in that phase), which the previous update launch built.
 template <int K>
-__global__ void __launch_bounds__(kBlock) resid_mixed_kernel(const MeshDev* __restrict__ mds,
-                                                             const int2* __restrict__ tiles, int ntiles_total,
-                                                             const LoopCtl* __restrict__ ctl) {
+__global__ void __launch_bounds__(kBlock) resid_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl,
+    const int4* start, const int* act) {
   __shared__ TileCtx tc;
   if (!ctl->any_apply) return;  // no mesh of the group is in the Apply phase
   tile_loop<K>(
-      mds, tiles, ntiles_total, 1, 0, tc, [](const ScalSnap& x) { return !x.done && x.phase == kPhaseApply; },
+      mds, start, act, 1, 0, tc, [](const ScalSnap& x) { return !x.done && x.phase == kPhaseApply; },
       [&](const MeshDev& md, int tile, double* red, double* out) {
         const long nn = md.n;
         const long t0 = (long)tile * md.tile_rows32;
@@ -264,13 +264,11 @@ __global__ void __launch_bounds__(kBlock) resid_mixed_kernel(const MeshDev* __re
 // Inner phase: x32 += alpha p32, r32 -= alpha q32 and the tile's sums r.z, r.r; all loads of a
 // thread's rows are issued before its stores. Restart phase: r32 = r64 / ||r64||, x32 = 0.
 template <int K>
-__global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* __restrict__ mds,
-                                                                 const int2* __restrict__ tiles, int ntiles_total,
-                                                                 LoopCtl* ctl, cudaGraphConditionalHandle handle,
-                                                                 int use_graph, int nmesh) {
+__global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl,
+    const int4* start, const int* act, cudaGraphConditionalHandle handle, int use_graph) {
   __shared__ TileCtx tc;
   tile_loop<2 * K>(
-      mds, tiles, ntiles_total, 1, 1, tc,
+      mds, start, act, 1, 1, tc,
       [](const ScalSnap& x) { return !x.done && x.phase != kPhaseApply; },
       [&](const MeshDev& md, int tile, double* red, double* out) {
         const long nn = md.n;
@@ -352,16 +350,16 @@ __global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* 
         if (md.s->phase == kPhaseInner) finish_update_mixed(md.s, K, v);
         else finish_restart(md.s, K, v);
       });
-  loop_control(mds, ctl, handle, use_graph, nmesh);
+  loop_control(mds, ctl, handle, use_graph);
 }
 
 // Inner phase: p32 = D^-1 r32 + beta p32 (loads of a thread's rows before its stores). Apply
 // phase: x64 += ||r64|| x32.
 template <int K>
-__global__ void __launch_bounds__(kBlock, 4) pupdate_mixed_kernel(const MeshDev* __restrict__ mds,
-                                                                  const int2* __restrict__ tiles, int ntiles_total) {
+__global__ void __launch_bounds__(kBlock, 4) pupdate_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl,
+    const int4* start, const int* act) {
   __shared__ TileCtx tc;
-  tile_loop_plain(mds, tiles, ntiles_total, tc,
+  tile_loop_plain(mds, start, act, 1, tc,
                   [](const ScalSnap& x) { return !x.done && (x.phase == kPhaseInner || x.phase == kPhaseApply); },
                   [&](const MeshDev& md, int tile) {
                     const long nn = md.n;
@@ -434,10 +432,10 @@ cudaError_t build_plan_mixed(Group& g, SolvePlan& pl) {
   cudaStream_t cs = g.capture_stream;
   e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
-  resid_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.tiles32, g.ntiles32, g.ctl);
-  spmv_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.tiles32, g.ntiles32);
-  update_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.tiles32, g.ntiles32, g.ctl, handle, 1, g.nmesh);
-  pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.tiles32, g.ntiles32);
+  resid_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.app_start32, g.app_mesh);
+  spmv_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.start32, g.act_mesh);
+  update_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.start32, g.act_mesh, handle, 1);
+  pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.start32, g.act_mesh);
   cudaError_t le = cudaGetLastError();
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(cs, &captured);
@@ -459,6 +457,7 @@ cudaError_t begin_mixed_k(Group& g, const IoTable& io, int rhs_mass, const ig_so
   IG_PROF("pcg_init", st);
   init_mixed_kernel<K><<<g.ntiles32, kBlock, 0, st>>>(g.mds, g.tiles32, io, rhs_mass, g.ctl, o.rel_tol, o.inner_tol,
                                                       o.max_iter, o.max_refine, cap);
+  list_kernel<<<1, kBlock, 0, st>>>(g.mds, g.ctl);
   return cudaGetLastError();
 }
 
@@ -468,20 +467,19 @@ cudaError_t host_loop_mixed_k(Group& g, int max_it, int poll, cudaStream_t st) {
   for (int it = 0; it < max_it; ++it) {
     {
       IG_PROF("pcg32_resid64", st);
-      resid_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32, g.ctl);
+      resid_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.ctl, g.app_start32, g.app_mesh);
     }
     {
       IG_PROF("pcg32_spmv", st);
-      spmv_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32);
+      spmv_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.ctl, g.start32, g.act_mesh);
     }
     {
       IG_PROF("pcg32_update", st);
-      update_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32, g.ctl,
-                                                           cudaGraphConditionalHandle{}, 0, g.nmesh);
+      update_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.ctl, g.start32, g.act_mesh, cudaGraphConditionalHandle{}, 0);
     }
     {
       IG_PROF("pcg32_pupdate", st);
-      pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.tiles32, g.ntiles32);
+      pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.ctl, g.start32, g.act_mesh);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
