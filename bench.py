@@ -162,21 +162,25 @@ def peaks():
 
 
 def algorithmic(kernel, n, m, nnz, k, prec):
-    """(FP64-or-FP32 flops, bytes) one launch of `kernel` must do / move (vectors [n][k])."""
+    """(flops, bytes) one launch of `kernel` must do / move (vectors [n][k], p rows padded to kp).
+    FP64 path: the update kernel also writes z = D^-1 r (over q), which the p-update reads instead
+    of D^-1 and r. Mixed path (pcg32_*): 4-byte values and vectors, p-update reads D^-1 and r."""
     sv = 8 if prec == "fp64" else 4   # value and vector element size
     kp = 4 if k == 3 else k
+    z_in_q = True
     if kernel.startswith("pcg32_"):
         sv = 4
+        z_in_q = False
         kernel = "pcg_" + kernel[len("pcg32_"):]
     if kernel == "pcg_spmv":
         flops = 2 * k * nnz + 2 * k * n
         byts = nnz * (sv + 4) + 4 * (n + 1) + sv * kp * n + sv * k * n
     elif kernel == "pcg_update":
         flops = 10 * k * n + k * n
-        byts = sv * (n + 4 * k * n + kp * n - k * n) + 2 * sv * k * n
+        byts = sv * (n + 3 * k * n + kp * n) + 2 * sv * k * n + (sv * k * n if z_in_q else 0)
     elif kernel == "pcg_pupdate":
-        flops = 3 * k * n
-        byts = sv * (n + k * n + kp * n) + sv * kp * n
+        flops = (2 if z_in_q else 3) * k * n
+        byts = (sv * (k * n + kp * n) if z_in_q else sv * (n + k * n + kp * n)) + sv * kp * n
     elif kernel == "assemble_face":
         flops = 60 * m
         byts = 12 * m + 24 * n + 32 * m

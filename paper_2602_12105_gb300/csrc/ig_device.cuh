@@ -483,165 +483,206 @@ __device__ __forceinline__ void block_exscan3(int a, int b, int c, int& ea, int&
   __syncthreads();
 }
 
-// Rebuild the active list from the meshes' done flags (run by every thread of one CTA, after
-// every other CTA of the launch is done with the list). The start tables give each CTA of the
-// loop kernels its first tile: CTA g takes the listed tiles [g·chunk, (g+1)·chunk).
-__device__ __noinline__ void rebuild_active(const MeshDev* __restrict__ mds, LoopCtl* ctl) {
-  const int nmesh = ctl->nmesh;
-  int nact = 0, tot64 = 0, tot32 = 0, ndone = 0;
+// Build one list (run by every thread of one CTA, after every other CTA of the launch is done
+// with it): the meshes that are not done and satisfy sel(s). Big meshes go to `big`; the others to
+// `mesh` with their tile offsets (FP64 tiling in off64 when given, mixed tiling in off32) and the
+// start tables: CTA g of a loop kernel takes the listed tiles [g·chunk, (g+1)·chunk).
+template <typename Sel>
+__device__ __forceinline__ void build_list(const MeshDev* __restrict__ mds, int nmesh, const Sel& sel, int* mesh,
+                                           int* off64, int* off32, int4* st64, int g64, int4* st32, int g32,
+                                           int* big, int& ns, int& nbig, int& ndone) {
+  int tot64 = 0, tot32 = 0;
+  ns = nbig = ndone = 0;
   for (int i0 = 0; i0 < nmesh; i0 += kBlock) {
     const int i = i0 + threadIdx.x;
-    int live = 0, c64 = 0, c32 = 0;
+    int small = 0, isbig = 0, dn = 0, c64 = 0, c32 = 0;
     if (i < nmesh) {
-      live = __ldcg(&mds[i].s->done) == 0;
-      if (live) {
-        c64 = mds[i].ntiles;
-        c32 = mds[i].ntiles32;
+      const SolveScal* s = mds[i].s;
+      dn = __ldcg(&s->done) != 0;
+      if (!dn && sel(s)) {
+        if (mds[i].n >= kBigRows) {
+          isbig = 1;
+        } else {
+          small = 1;
+          c64 = mds[i].ntiles;
+          c32 = mds[i].ntiles32;
+        }
       }
     }
     int e0, e1, e2, t0, t1, t2;
-    block_exscan3(live, c64, c32, e0, e1, e2, t0, t1, t2);
-    if (live) {
-      ctl->act_mesh[nact + e0] = i;
-      ctl->act_off64[nact + e0] = tot64 + e1;
-      ctl->act_off32[nact + e0] = tot32 + e2;
+    block_exscan3(small, c64, c32, e0, e1, e2, t0, t1, t2);
+    if (small) {
+      mesh[ns + e0] = i;
+      if (off64) off64[ns + e0] = tot64 + e1;
+      off32[ns + e0] = tot32 + e2;
     }
-    ndone += (nmesh - i0 < kBlock ? nmesh - i0 : kBlock) - t0;
-    nact += t0;
+    int f0, f1, f2, u0, u1, u2;
+    block_exscan3(isbig, dn, 0, f0, f1, f2, u0, u1, u2);
+    if (isbig) big[nbig + f0] = i;
+    ns += t0;
     tot64 += t1;
     tot32 += t2;
+    nbig += u0;
+    ndone += u1;
   }
-  const int g64 = ctl->grid64, g32 = ctl->grid32;
-  const int ch64 = tot64 > 0 ? (tot64 + g64 - 1) / g64 : 1;
-  const int ch32 = tot32 > 0 ? (tot32 + g32 - 1) / g32 : 1;
+  const int ch64 = tot64 > 0 && g64 > 0 ? (tot64 + g64 - 1) / g64 : 1;
+  const int ch32 = tot32 > 0 && g32 > 0 ? (tot32 + g32 - 1) / g32 : 1;
   if (threadIdx.x == 0) {
-    ctl->act_off64[nact] = tot64;
-    ctl->act_off32[nact] = tot32;
-    ctl->nact = nact;
-    ctl->total64 = tot64;
-    ctl->total32 = tot32;
-    ctl->chunk64 = ch64;
-    ctl->chunk32 = ch32;
-    ctl->ndone_list = ndone;
+    if (off64) off64[ns] = tot64;
+    off32[ns] = tot32;
   }
   __syncthreads();  // the offsets above are visible to the whole CTA
   // the thread of listed mesh j writes the start of every CTA whose chunk begins in its tiles
-  for (int j = threadIdx.x; j < nact; j += kBlock) {
-    const int mi = ctl->act_mesh[j];
-    const int a64 = ctl->act_off64[j], z64 = ctl->act_off64[j + 1];
-    for (int g = (a64 + ch64 - 1) / ch64; g < g64 && g * ch64 < z64; ++g) {
-      const int cnt = tot64 - g * ch64 < ch64 ? tot64 - g * ch64 : ch64;
-      ctl->start64[g] = make_int4(j, g * ch64 - a64, mi, cnt);
+  for (int j = threadIdx.x; j < ns; j += kBlock) {
+    const int mi = mesh[j];
+    if (st64) {
+      const int a = off64[j], z = off64[j + 1];
+      for (int g = (a + ch64 - 1) / ch64; g < g64 && g * ch64 < z; ++g) {
+        const int cnt = tot64 - g * ch64 < ch64 ? tot64 - g * ch64 : ch64;
+        st64[g] = make_int4(j, g * ch64 - a, mi, cnt);
+      }
     }
-    const int a32 = ctl->act_off32[j], z32 = ctl->act_off32[j + 1];
-    for (int g = (a32 + ch32 - 1) / ch32; g < g32 && g * ch32 < z32; ++g) {
+    const int a = off32[j], z = off32[j + 1];
+    for (int g = (a + ch32 - 1) / ch32; g < g32 && g * ch32 < z; ++g) {
       const int cnt = tot32 - g * ch32 < ch32 ? tot32 - g * ch32 : ch32;
-      ctl->start32[g] = make_int4(j, g * ch32 - a32, mi, cnt);
+      st32[g] = make_int4(j, g * ch32 - a, mi, cnt);
     }
   }
   // CTAs past the listed tiles get none
-  for (int g = threadIdx.x; g < g64; g += kBlock)
-    if ((long)g * ch64 >= tot64) ctl->start64[g] = make_int4(0, 0, -1, 0);
+  if (st64)
+    for (int g = threadIdx.x; g < g64; g += kBlock)
+      if ((long)g * ch64 >= tot64) st64[g] = make_int4(0, 0, -1, 0);
   for (int g = threadIdx.x; g < g32; g += kBlock)
-    if ((long)g * ch32 >= tot32) ctl->start32[g] = make_int4(0, 0, -1, 0);
+    if ((long)g * ch32 >= tot32) st32[g] = make_int4(0, 0, -1, 0);
 }
 
-// The Apply list (mixed precision): the meshes not done and in the Apply phase, with the start
-// table of the residual kernel (mixed tiling). Run by every thread of one CTA.
-__device__ __noinline__ void rebuild_apply(const MeshDev* __restrict__ mds, LoopCtl* ctl) {
-  const int nmesh = ctl->nmesh;
-  int napp = 0, tot = 0;
-  for (int i0 = 0; i0 < nmesh; i0 += kBlock) {
-    const int i = i0 + threadIdx.x;
-    int live = 0, c32 = 0;
-    if (i < nmesh) {
-      const SolveScal* s = mds[i].s;
-      live = __ldcg(&s->done) == 0 && __ldcg(&s->phase) == kPhaseApply;
-      if (live) c32 = mds[i].ntiles32;
-    }
-    int e0, e1, e2, t0, t1, t2;
-    block_exscan3(live, c32, 0, e0, e1, e2, t0, t1, t2);
-    if (live) {
-      ctl->app_mesh[napp + e0] = i;
-      ctl->app_off32[napp + e0] = tot + e1;
-    }
-    napp += t0;
-    tot += t1;
+struct SelAll {
+  __device__ bool operator()(const SolveScal*) const { return true; }
+};
+struct SelApply {
+  __device__ bool operator()(const SolveScal* s) const { return __ldcg(&s->phase) == kPhaseApply; }
+};
+
+// The active list: every mesh that is not done.
+__device__ __noinline__ void rebuild_active(const MeshDev* __restrict__ mds, LoopCtl* ctl) {
+  int ns, nbig, ndone;
+  build_list(mds, ctl->nmesh, SelAll{}, ctl->act_mesh, ctl->act_off64, ctl->act_off32, ctl->start64, ctl->grid64,
+             ctl->start32, ctl->grid32, ctl->big_mesh, ns, nbig, ndone);
+  if (threadIdx.x == 0) {
+    ctl->nact = ns;
+    ctl->nbig = nbig;
+    ctl->ndone_list = ndone;
   }
-  const int g32 = ctl->grid32;
-  const int ch = tot > 0 ? (tot + g32 - 1) / g32 : 1;
-  if (threadIdx.x == 0) ctl->app_off32[napp] = tot;
-  __syncthreads();
-  for (int j = threadIdx.x; j < napp; j += kBlock) {
-    const int mi = ctl->app_mesh[j];
-    const int a = ctl->app_off32[j], z = ctl->app_off32[j + 1];
-    for (int g = (a + ch - 1) / ch; g < g32 && g * ch < z; ++g) {
-      const int cnt = tot - g * ch < ch ? tot - g * ch : ch;
-      ctl->app_start32[g] = make_int4(j, g * ch - a, mi, cnt);
-    }
-  }
-  for (int g = threadIdx.x; g < g32; g += kBlock)
-    if ((long)g * ch >= tot) ctl->app_start32[g] = make_int4(0, 0, -1, 0);
 }
+
+// The Apply list (mixed precision, mixed tiling): meshes not done and in the Apply phase.
+__device__ __noinline__ void rebuild_apply(const MeshDev* __restrict__ mds, LoopCtl* ctl) {
+  int ns, nbig, ndone;
+  build_list(mds, ctl->nmesh, SelApply{}, ctl->app_mesh, nullptr, ctl->app_off32, nullptr, 0, ctl->app_start32,
+             ctl->grid32, ctl->app_big, ns, nbig, ndone);
+  if (threadIdx.x == 0) ctl->napp_big = nbig;
+}
+
+// The tiles one CTA of a loop kernel takes: tiles b, b + G, ... of every big mesh (b =
+// blockIdx.x, G = gridDim.x), then its chunk of the chunked list. One walker for both parts, so
+// that a kernel's tile body is compiled once.
+struct TileWalk {
+  int nbig, bi, mi, lt, j, left;  // bi < nbig: in the big list; then the chunk (left tiles to go)
+  __device__ __forceinline__ void chunk(const ListRef& L) {
+    const int4 st = L.start[blockIdx.x];
+    bi = nbig;
+    j = st.x;
+    lt = st.y;
+    mi = st.z;
+    left = st.w;
+  }
+  __device__ __forceinline__ void begin(const ListRef& L) {
+    nbig = *L.nbig;
+    bi = 0;
+    left = 0;
+    j = 0;
+    if (nbig > 0) {
+      mi = L.big[0];
+      lt = blockIdx.x;
+    } else {
+      chunk(L);
+    }
+  }
+  __device__ __forceinline__ bool more() const { return bi < nbig || left > 0; }
+  // after the mesh mi is loaded (nt tiles): false when the current big mesh has no more tiles for
+  // this CTA (the walker then moved on; call more() again)
+  __device__ __forceinline__ bool here(const ListRef& L, int nt) {
+    if (bi < nbig && lt >= nt) {
+      if (++bi < nbig) {
+        mi = L.big[bi];
+        lt = blockIdx.x;
+      } else {
+        chunk(L);
+      }
+      return false;
+    }
+    return true;
+  }
+  __device__ __forceinline__ void next(const ListRef& L, int nt) {
+    if (bi < nbig) {
+      lt += gridDim.x;
+    } else {
+      --left;
+      if (++lt == nt) {
+        ++j;
+        lt = 0;
+        if (left > 0) mi = L.act[j];
+      }
+    }
+  }
+};
 
 // body(md, tile, red, out) does the tile's work and sums its NV values into out with
 // tile_reduce(v, red, out); active(sn) says whether a mesh takes part in this launch (uniform per
 // CTA). tiling 0: FP64 solver tiles, 1: mixed-precision tiles; cnt_idx selects the mesh counter.
-// The CTA walks its chunk of the active list's tiles (start: its entry of the start table, act:
-// the list of meshes).
 template <int NV, typename Active, typename Body, typename Finish>
-__device__ __forceinline__ void tile_loop(const MeshDev* __restrict__ mds, const int4* start, const int* act,
-                                          int tiling, int cnt_idx, TileCtx& tc, const Active& active,
-                                          const Body& body, const Finish& finish) {
-  const int4 st = start[blockIdx.x];
-  if (st.w <= 0) return;
-  int j = st.x, lt = st.y, cur = st.z, buf = 0;
+__device__ __forceinline__ void tile_loop(const MeshDev* __restrict__ mds, const ListRef& L, int tiling, int cnt_idx,
+                                          TileCtx& tc, const Active& active, const Body& body,
+                                          const Finish& finish) {
+  TileWalk w;
+  w.begin(L);
+  int cur = -1, buf = 0;
   unsigned run = 0;
-  load_mesh(mds, cur, tc);
-  for (int t = 0; t < st.w; ++t) {
-    if (t > 0 && lt == 0) {
-      const int mi = act[j];
-      if (mi != cur) {
-        if (run) flush_tiles<NV>(tc, tiling, run, cnt_idx, finish);
-        cur = mi;
-        run = 0;
-        load_mesh(mds, cur, tc);
-      }
+  while (w.more()) {
+    if (w.mi != cur) {
+      if (run) flush_tiles<NV>(tc, tiling, run, cnt_idx, finish);
+      cur = w.mi;
+      run = 0;
+      load_mesh(mds, cur, tc);
     }
+    const int nt = tiling ? tc.md.ntiles32 : tc.md.ntiles;
+    if (!w.here(L, nt)) continue;
     if (active(tc.sn)) {
-      body(tc.md, lt, tc.red[buf], tc.md.part + (long)lt * kPartStride);
+      body(tc.md, w.lt, tc.red[buf], tc.md.part + (long)w.lt * kPartStride);
       buf ^= 1;
       ++run;
     }
-    if (++lt == (tiling ? tc.md.ntiles32 : tc.md.ntiles)) {
-      ++j;
-      lt = 0;
-    }
+    w.next(L, nt);
   }
   if (run) flush_tiles<NV>(tc, tiling, run, cnt_idx, finish);
 }
 
 // Tile loop without sums.
 template <typename Active, typename Body>
-__device__ __forceinline__ void tile_loop_plain(const MeshDev* __restrict__ mds, const int4* start, const int* act,
-                                                int tiling, TileCtx& tc, const Active& active, const Body& body) {
-  const int4 st = start[blockIdx.x];
-  if (st.w <= 0) return;
-  int j = st.x, lt = st.y, cur = st.z;
-  load_mesh(mds, cur, tc);
-  for (int t = 0; t < st.w; ++t) {
-    if (t > 0 && lt == 0) {
-      const int mi = act[j];
-      if (mi != cur) {
-        cur = mi;
-        load_mesh(mds, cur, tc);
-      }
+__device__ __forceinline__ void tile_loop_plain(const MeshDev* __restrict__ mds, const ListRef& L, int tiling,
+                                                TileCtx& tc, const Active& active, const Body& body) {
+  TileWalk w;
+  w.begin(L);
+  int cur = -1;
+  while (w.more()) {
+    if (w.mi != cur) {
+      cur = w.mi;
+      load_mesh(mds, cur, tc);
     }
-    if (active(tc.sn)) body(tc.md, lt);
-    if (++lt == (tiling ? tc.md.ntiles32 : tc.md.ntiles)) {
-      ++j;
-      lt = 0;
-    }
+    const int nt = tiling ? tc.md.ntiles32 : tc.md.ntiles;
+    if (!w.here(L, nt)) continue;
+    if (active(tc.sn)) body(tc.md, w.lt);
+    w.next(L, nt);
   }
 }
 

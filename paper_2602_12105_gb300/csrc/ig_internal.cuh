@@ -165,26 +165,40 @@ struct LoopCtl {
   int any_apply;      // mixed precision: some mesh will recompute its FP64 residual next
   int ndone_start;    // serving: meshes already done when the loop (re)started; the loop stops
                       // as soon as more are done (a whole solve sets it out of reach)
-  // Active list: the meshes not yet done when it was last built, in mesh order, with the
-  // offsets of their tiles in the FP64 and mixed tilings. The loop kernels walk only these
-  // tiles, each CTA a contiguous chunk (so a CTA changes mesh rarely), and a finished mesh
+  // Active list: the meshes not yet done when it was last built, in mesh order. Meshes of at
+  // least kBigRows rows are listed apart ("big"): every CTA takes their tiles cyclically (CTAs at
+  // work at the same time then cover neighbouring rows, whose SpMV gathers share L2 lines). The
+  // others get the offsets of their tiles in the FP64 and mixed tilings and are dealt in
+  // contiguous chunks (a CTA changes mesh rarely) through per-CTA start tables. A finished mesh
   // costs nothing in later iterations. Rebuilt whenever more meshes are done.
   int nmesh;          // meshes of the group
-  int nact;           // meshes in the list
-  int total64, total32;  // tiles of the listed meshes
-  int chunk64, chunk32;  // tiles per CTA: ceil(total / grid)
+  int nact;           // meshes in the chunked list
+  int nbig;           // meshes in the big list
   int ndone_list;     // meshes done when the list was built
   int grid64, grid32; // grids of the loop kernels (the start tables have one entry per CTA)
+  int napp_big;       // big meshes in the Apply list
   int* act_mesh;      // [nmesh]
   int* act_off64;     // [nmesh + 1]
   int* act_off32;     // [nmesh + 1]
+  int* big_mesh;      // [nmesh]
   int4* start64;      // [grid64]: each CTA's (list position, local tile, mesh, tile count)
   int4* start32;      // [grid32]
   // Mixed precision: the meshes about to recompute their FP64 residual (Apply phase), listed
-  // like the active list (mixed tiling only); rebuilt in every iteration that has any.
+  // the same way (mixed tiling only); rebuilt in every iteration that has any.
   int* app_mesh;      // [nmesh]
   int* app_off32;     // [nmesh + 1]
+  int* app_big;       // [nmesh]
   int4* app_start32;  // [grid32]
+};
+
+constexpr int kBigRows = 1 << 20;
+
+// What a loop kernel walks: a chunked list with its start table and a big list with its count.
+struct ListRef {
+  const int4* start;
+  const int* act;
+  const int* big;
+  const int* nbig;
 };
 
 // Per-launch pointers that change from call to call (kept out of the cached graphs).
@@ -229,11 +243,7 @@ struct Group {
   int* flags_dev = nullptr;       // [nmesh] done flags gathered for the host (serving)
   LoopCtl* ctl = nullptr;         // device
   int* act_buf = nullptr;         // device storage of the active list and start tables (LoopCtl)
-  int* act_mesh = nullptr;        // the same pointers as in LoopCtl, for the launches
-  int4* start64 = nullptr;
-  int4* start32 = nullptr;
-  int4* app_start32 = nullptr;
-  int* app_mesh = nullptr;
+  ListRef list64{}, list32{}, listapp{};  // what the FP64, mixed and residual loop kernels walk
   int* done_host = nullptr;       // pinned host word for the host-driven loop
   SolvePlan plans[2][kMaxK + 1];  // [mixed][k]
   cudaStream_t capture_stream = nullptr;

@@ -174,18 +174,18 @@ __device__ __forceinline__ void spmv_tile(const MeshDev& md, int tile, double* r
 }
 
 template <int K>
-__global__ void __launch_bounds__(kBlock, 4) spmv_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl,
-    const int4* start, const int* act) {
+__global__ void __launch_bounds__(kBlock, 4) spmv_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L) {
   __shared__ TileCtx tc;
   tile_loop<K>(
-      mds, start, act, 0, 0, tc, [](const ScalSnap& x) { return !x.done; },
+      mds, L, 0, 0, tc, [](const ScalSnap& x) { return !x.done; },
       [&](const MeshDev& md, int tile, double* red, double* out) { spmv_tile<K>(md, tile, red, out); },
       [](const MeshDev& md, const double* v) { finish_spmv(md.s, K, v); });
 }
 
 // ------------------------------------------------------------------------------- update
-// x += alpha p, r -= alpha q and the tile's sums r.z, r.r (z = D^-1 r); a row's loads are issued
-// before its stores. (FP64 arithmetic bounds this kernel, so rows are not batched further.)
+// x += alpha p, r -= alpha q, z = D^-1 r (written over q, which the next SpMV rewrites) and the
+// tile's sums r.z, r.r; a row's loads are issued before its stores. (FP64 arithmetic bounds this
+// kernel, so rows are not batched further.)
 template <int K>
 __device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const ScalSnap& sn, double* red,
                                             double* out) {
@@ -197,7 +197,7 @@ __device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const S
   for (int i = 0; i < 2 * K; ++i) acc[i] = 0.0;
   const double* __restrict__ Dinv = md.Dinv;
   const double* __restrict__ p = md.p;
-  const double* __restrict__ q = md.q;
+  double* __restrict__ q = md.q;
   double* __restrict__ x = md.x;
   double* __restrict__ r = md.r;
 #pragma unroll
@@ -217,9 +217,11 @@ __device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const S
       for (int c = 0; c < K; ++c) {
         const double a = sn.alpha[c];
         const double rn = fma(-a, qs[c], rs[c]);
+        const double z = d * rn;
         x[(long)c * nn + row] = fma(a, pi[c], xs[c]);
         r[(long)c * nn + row] = rn;
-        acc[c] = fma(rn, d * rn, acc[c]);
+        q[(long)c * nn + row] = z;  // q is dead until the next SpMV: it carries z to pupdate
+        acc[c] = fma(rn, z, acc[c]);
         acc[K + c] = fma(rn, rn, acc[K + c]);
       }
     }
@@ -228,45 +230,40 @@ __device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const S
 }
 
 template <int K>
-__global__ void __launch_bounds__(kBlock, 4) update_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl,
-    const int4* start, const int* act, cudaGraphConditionalHandle handle, int use_graph) {
+__global__ void __launch_bounds__(kBlock, 4) update_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L,
+    cudaGraphConditionalHandle handle, int use_graph) {
   __shared__ TileCtx tc;
   tile_loop<2 * K>(
-      mds, start, act, 0, 1, tc, [](const ScalSnap& x) { return !x.done; },
+      mds, L, 0, 1, tc, [](const ScalSnap& x) { return !x.done; },
       [&](const MeshDev& md, int tile, double* red, double* out) { update_tile<K>(md, tile, tc.sn, red, out); },
       [](const MeshDev& md, const double* v) { finish_update(md.s, K, v); });
   loop_control(mds, ctl, handle, use_graph);
 }
 
 // ------------------------------------------------------------------------------- pupdate
-// p = D^-1 r + beta p, rows in pairs with loads before stores.
+// p = z + beta p with z = D^-1 r from the update kernel (kept in q); rows in pairs with loads
+// before stores.
 template <int K>
-__global__ void __launch_bounds__(kBlock, 4) pupdate_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl,
-    const int4* start, const int* act) {
+__global__ void __launch_bounds__(kBlock, 4) pupdate_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L) {
   __shared__ TileCtx tc;
-  tile_loop_plain(mds, start, act, 0, tc, [](const ScalSnap& x) { return !x.done; },
+  tile_loop_plain(mds, L, 0, tc, [](const ScalSnap& x) { return !x.done; },
                   [&](const MeshDev& md, int tile) {
                     const long nn = md.n;
                     const long t0 = (long)tile * md.tile_rows;
                     const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
-                    double beta[K];
-#pragma unroll
-                    for (int c = 0; c < K; ++c) beta[c] = tc.sn.beta[c];
-                    const double* __restrict__ Dinv = md.Dinv;
-                    const double* __restrict__ r = md.r;
+                    const double* __restrict__ z = md.q;
                     double* __restrict__ p = md.p;
                     constexpr int RB = 2;
 #pragma unroll
                     for (int r0 = 0; r0 < kRowsPerThread; r0 += RB) {
-                      double d[RB], pi[RB][K], rs[RB][K];
+                      double pi[RB][K], zs[RB][K];
 #pragma unroll
                       for (int u = 0; u < RB; ++u) {
                         const long row = t0 + (r0 + u) * kBlock + threadIdx.x;
                         if (row < t1) {
-                          d[u] = Dinv[row];
                           load_row<K>(p, row, pi[u]);
 #pragma unroll
-                          for (int c = 0; c < K; ++c) rs[u][c] = r[c * nn + row];
+                          for (int c = 0; c < K; ++c) zs[u][c] = z[c * nn + row];
                         }
                       }
 #pragma unroll
@@ -274,7 +271,7 @@ __global__ void __launch_bounds__(kBlock, 4) pupdate_kernel(const MeshDev* __res
                         const long row = t0 + (r0 + u) * kBlock + threadIdx.x;
                         if (row < t1) {
 #pragma unroll
-                          for (int c = 0; c < K; ++c) p[row * KP<K>::v + c] = fma(beta[c], pi[u][c], d[u] * rs[u][c]);
+                          for (int c = 0; c < K; ++c) p[row * KP<K>::v + c] = fma(tc.sn.beta[c], pi[u][c], zs[u][c]);
                         }
                       }
                     }
@@ -340,9 +337,9 @@ cudaError_t build_plan(Group& g, SolvePlan& pl) {
   cudaStream_t cs = g.capture_stream;
   e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
-  spmv_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.start64, g.act_mesh);
-  update_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.start64, g.act_mesh, handle, 1);
-  pupdate_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.start64, g.act_mesh);
+  spmv_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.list64);
+  update_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.list64, handle, 1);
+  pupdate_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.list64);
   cudaError_t le = cudaGetLastError();
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(cs, &captured);
@@ -374,15 +371,15 @@ cudaError_t host_loop_k(Group& g, int max_it, int poll, cudaStream_t st) {
   for (int it = 0; it < max_it; ++it) {
     {
       IG_PROF("pcg_spmv", st);
-      spmv_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.ctl, g.start64, g.act_mesh);
+      spmv_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.ctl, g.list64);
     }
     {
       IG_PROF("pcg_update", st);
-      update_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.ctl, g.start64, g.act_mesh, cudaGraphConditionalHandle{}, 0);
+      update_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.ctl, g.list64, cudaGraphConditionalHandle{}, 0);
     }
     {
       IG_PROF("pcg_pupdate", st);
-      pupdate_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.ctl, g.start64, g.act_mesh);
+      pupdate_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.ctl, g.list64);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -546,9 +543,9 @@ cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, int slots64
   if ((e = cudaMalloc(&g.face_tiles, sizeof(int2) * ftiles.size())) != cudaSuccess) return e;
   if ((e = cudaMalloc(&g.row_tiles, sizeof(int2) * rtiles.size())) != cudaSuccess) return e;
   if ((e = cudaMalloc(&g.ctl, sizeof(LoopCtl))) != cudaSuccess) return e;
-  // ints: act_mesh, act_off64, act_off32, app_mesh, app_off32; then (16-byte aligned) the int4
-  // start tables start64, start32, app_start32
-  const size_t list_ints = (5 * (size_t)nmesh + 3 + 3) / 4 * 4;
+  // ints: act_mesh, act_off64, act_off32, big_mesh, app_mesh, app_off32, app_big; then (16-byte
+  // aligned) the int4 start tables start64, start32, app_start32
+  const size_t list_ints = (7 * (size_t)nmesh + 3 + 3) / 4 * 4;
   const size_t list_words = list_ints + 4 * (size_t)(g.grid64 + 2 * g.grid32);
   if ((e = cudaMalloc(&g.act_buf, sizeof(int) * list_words)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&g.calls_dev, sizeof(CallDev) * nmesh)) != cudaSuccess) return e;
@@ -575,19 +572,20 @@ cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, int slots64
     c.grid64 = g.grid64;
     c.grid32 = g.grid32;
     c.ndone_list = -1;
-    c.act_mesh = g.act_buf;
-    c.act_off64 = g.act_buf + nmesh;
-    c.act_off32 = g.act_buf + 2 * (size_t)nmesh + 1;
-    c.app_mesh = g.act_buf + 3 * (size_t)nmesh + 2;
-    c.app_off32 = c.app_mesh + nmesh;
-    c.start64 = reinterpret_cast<int4*>(g.act_buf + list_ints);
+    int* w = g.act_buf;
+    c.act_mesh = w;
+    c.act_off64 = w + nmesh;
+    c.act_off32 = w + 2 * (size_t)nmesh + 1;
+    c.big_mesh = w + 3 * (size_t)nmesh + 2;
+    c.app_mesh = w + 4 * (size_t)nmesh + 2;
+    c.app_off32 = w + 5 * (size_t)nmesh + 2;
+    c.app_big = w + 6 * (size_t)nmesh + 3;
+    c.start64 = reinterpret_cast<int4*>(w + list_ints);
     c.start32 = c.start64 + g.grid64;
     c.app_start32 = c.start32 + g.grid32;
-    g.app_mesh = c.app_mesh;
-    g.app_start32 = c.app_start32;
-    g.act_mesh = c.act_mesh;
-    g.start64 = c.start64;
-    g.start32 = c.start32;
+    g.list64 = ListRef{c.start64, c.act_mesh, c.big_mesh, &g.ctl->nbig};
+    g.list32 = ListRef{c.start32, c.act_mesh, c.big_mesh, &g.ctl->nbig};
+    g.listapp = ListRef{c.app_start32, c.app_mesh, c.app_big, &g.ctl->napp_big};
     if ((e = cudaMemcpyAsync(g.ctl, &c, sizeof(LoopCtl), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
   }
   if ((e = cudaStreamCreateWithFlags(&g.capture_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
@@ -687,7 +685,7 @@ constexpr size_t kNaX = align256(kNaDinv + sizeof(double) * kNoAllocMaxRows);
 constexpr size_t kNaR = align256(kNaX + kNaVec);
 constexpr size_t kNaP = align256(kNaR + kNaVec);
 constexpr size_t kNaQ = align256(kNaP + kNaVec);
-constexpr size_t kNaList = align256(kNaQ + kNaVec);   // active list of the one mesh: 8 ints
+constexpr size_t kNaList = align256(kNaQ + kNaVec);   // active lists of the one mesh: 8 ints
 constexpr size_t kNaStart = align256(kNaList + sizeof(int) * 8);
 constexpr size_t kNoAllocBytes = align256(kNaStart + sizeof(int4) * (kNoAllocMaxTiles + 1));
 
@@ -795,11 +793,11 @@ extern "C" ig_status ig_solve_csr_noalloc(const int32_t* rowptr_dev, const int32
   ctl_init.act_mesh = reinterpret_cast<int*>(base + kNaList);
   ctl_init.act_off64 = ctl_init.act_mesh + 1;
   ctl_init.act_off32 = ctl_init.act_mesh + 3;
+  ctl_init.big_mesh = ctl_init.act_mesh + 5;
   ctl_init.start64 = reinterpret_cast<int4*>(base + kNaStart);
   ctl_init.start32 = ctl_init.start64 + kNoAllocMaxTiles;
-  g.act_mesh = ctl_init.act_mesh;
-  g.start64 = ctl_init.start64;
-  g.start32 = ctl_init.start32;
+  g.list64 = ListRef{ctl_init.start64, ctl_init.act_mesh, ctl_init.big_mesh,
+                     &reinterpret_cast<LoopCtl*>(base + kNaCtl)->nbig};
   noalloc_setup_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(md, g.mds, g.tiles, g.ntiles, ctl_init, g.ctl, md.s);
   if (cudaGetLastError() != cudaSuccess) return IG_ERR_CUDA;
   IoTable* io = new (std::nothrow) IoTable;

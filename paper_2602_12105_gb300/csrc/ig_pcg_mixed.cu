@@ -188,11 +188,10 @@ __global__ void __launch_bounds__(kBlock) init_mixed_kernel(const MeshDev* __res
 }
 
 template <int K>
-__global__ void __launch_bounds__(kBlock, 4) spmv_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl,
-    const int4* start, const int* act) {
+__global__ void __launch_bounds__(kBlock, 4) spmv_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L) {
   __shared__ TileCtx tc;
   tile_loop<K>(
-      mds, start, act, 1, 0, tc, [](const ScalSnap& x) { return !x.done && x.phase == kPhaseInner; },
+      mds, L, 1, 0, tc, [](const ScalSnap& x) { return !x.done && x.phase == kPhaseInner; },
       [&](const MeshDev& md, int tile, double* red, double* out) {
         const long nn = md.n;
         const long t0 = (long)tile * md.tile_rows32;
@@ -227,12 +226,11 @@ __global__ void __launch_bounds__(kBlock, 4) spmv_mixed_kernel(const MeshDev* __
 // Kept out of the FP32 SpMV kernel so that the hot FP32 kernel stays small; it walks the Apply
 // list (the meshes in that phase), which the previous update launch built.
 template <int K>
-__global__ void __launch_bounds__(kBlock) resid_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl,
-    const int4* start, const int* act) {
+__global__ void __launch_bounds__(kBlock) resid_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L) {
   __shared__ TileCtx tc;
   if (!ctl->any_apply) return;  // no mesh of the group is in the Apply phase
   tile_loop<K>(
-      mds, start, act, 1, 0, tc, [](const ScalSnap& x) { return !x.done && x.phase == kPhaseApply; },
+      mds, L, 1, 0, tc, [](const ScalSnap& x) { return !x.done && x.phase == kPhaseApply; },
       [&](const MeshDev& md, int tile, double* red, double* out) {
         const long nn = md.n;
         const long t0 = (long)tile * md.tile_rows32;
@@ -264,11 +262,11 @@ __global__ void __launch_bounds__(kBlock) resid_mixed_kernel(const MeshDev* __re
 // Inner phase: x32 += alpha p32, r32 -= alpha q32 and the tile's sums r.z, r.r; all loads of a
 // thread's rows are issued before its stores. Restart phase: r32 = r64 / ||r64||, x32 = 0.
 template <int K>
-__global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl,
-    const int4* start, const int* act, cudaGraphConditionalHandle handle, int use_graph) {
+__global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L,
+    cudaGraphConditionalHandle handle, int use_graph) {
   __shared__ TileCtx tc;
   tile_loop<2 * K>(
-      mds, start, act, 1, 1, tc,
+      mds, L, 1, 1, tc,
       [](const ScalSnap& x) { return !x.done && x.phase != kPhaseApply; },
       [&](const MeshDev& md, int tile, double* red, double* out) {
         const long nn = md.n;
@@ -356,10 +354,9 @@ __global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* 
 // Inner phase: p32 = D^-1 r32 + beta p32 (loads of a thread's rows before its stores). Apply
 // phase: x64 += ||r64|| x32.
 template <int K>
-__global__ void __launch_bounds__(kBlock, 4) pupdate_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl,
-    const int4* start, const int* act) {
+__global__ void __launch_bounds__(kBlock, 4) pupdate_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L) {
   __shared__ TileCtx tc;
-  tile_loop_plain(mds, start, act, 1, tc,
+  tile_loop_plain(mds, L, 1, tc,
                   [](const ScalSnap& x) { return !x.done && (x.phase == kPhaseInner || x.phase == kPhaseApply); },
                   [&](const MeshDev& md, int tile) {
                     const long nn = md.n;
@@ -432,10 +429,10 @@ cudaError_t build_plan_mixed(Group& g, SolvePlan& pl) {
   cudaStream_t cs = g.capture_stream;
   e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
-  resid_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.app_start32, g.app_mesh);
-  spmv_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.start32, g.act_mesh);
-  update_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.start32, g.act_mesh, handle, 1);
-  pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.start32, g.act_mesh);
+  resid_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.listapp);
+  spmv_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.list32);
+  update_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.list32, handle, 1);
+  pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.list32);
   cudaError_t le = cudaGetLastError();
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(cs, &captured);
@@ -467,19 +464,19 @@ cudaError_t host_loop_mixed_k(Group& g, int max_it, int poll, cudaStream_t st) {
   for (int it = 0; it < max_it; ++it) {
     {
       IG_PROF("pcg32_resid64", st);
-      resid_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.ctl, g.app_start32, g.app_mesh);
+      resid_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.ctl, g.listapp);
     }
     {
       IG_PROF("pcg32_spmv", st);
-      spmv_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.ctl, g.start32, g.act_mesh);
+      spmv_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.ctl, g.list32);
     }
     {
       IG_PROF("pcg32_update", st);
-      update_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.ctl, g.start32, g.act_mesh, cudaGraphConditionalHandle{}, 0);
+      update_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.ctl, g.list32, cudaGraphConditionalHandle{}, 0);
     }
     {
       IG_PROF("pcg32_pupdate", st);
-      pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.ctl, g.start32, g.act_mesh);
+      pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.ctl, g.list32);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
