@@ -161,20 +161,24 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def algorithmic(kernel, n, m, nnz, k, prec):
+def algorithmic(kernel, n, m, nnz, k, prec, idx32=4):
     """(flops, bytes) one launch of `kernel` must do / move (vectors [n][k], p rows padded to kp).
     FP64 path: the update kernel also writes z = D^-1 r (over q), which the p-update reads instead
-    of D^-1 and r. Mixed path (pcg32_*): 4-byte values and vectors, p-update reads D^-1 and r."""
+    of D^-1 and r. Mixed path (pcg32_*): 4-byte values and vectors, p-update reads D^-1 and r, and
+    the SpMV reads idx32-byte column indices (2 where every slice of 32 rows keeps its columns as
+    16-bit offsets, as on the grid workloads)."""
     sv = 8 if prec == "fp64" else 4   # value and vector element size
     kp = 4 if k == 3 else k
     z_in_q = True
+    si = 4
     if kernel.startswith("pcg32_"):
         sv = 4
+        si = idx32
         z_in_q = False
         kernel = "pcg_" + kernel[len("pcg32_"):]
     if kernel == "pcg_spmv":
         flops = 2 * k * nnz + 2 * k * n
-        byts = nnz * (sv + 4) + 4 * (n + 1) + sv * kp * n + sv * k * n
+        byts = nnz * (sv + si) + 4 * (n + 1) + sv * kp * n + sv * k * n
     elif kernel == "pcg_update":
         flops = 10 * k * n + k * n
         byts = sv * (n + 3 * k * n + kp * n) + 2 * sv * k * n + (sv * k * n if z_in_q else 0)
@@ -329,7 +333,8 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernel
     its_f, its_a = finfo["iterations"], ainfo["iterations"]
-    rl_all, roofline = kernel_roofline(prof, p.n, p.m, mesh.nnz, k, precision, clocks, args.workload)
+    rl_all, roofline = kernel_roofline(prof, p.n, p.m, mesh.nnz, k, precision, clocks, args.workload,
+                                       idx32=2 if args.workload.startswith("grid") else 4)
 
     # the CPU oracle on the same workload (bounded sample)
     cpu = None
@@ -376,7 +381,7 @@ def gpu_launches(prof, steps, its_f, its_a, launch):
     return int(round(steps * per_step))
 
 
-def kernel_roofline(prof, n, m, nnz, k, precision, clocks, workload):
+def kernel_roofline(prof, n, m, nnz, k, precision, clocks, workload, idx32=4):
     """Per-kernel achieved rates from the profile pass ({name: (launches, total ms)}) and the
     roofline object of the kernel with the largest total time. FP64 kernels are held against the
     FP64 ALU peak (152 SMs x 2 FMA/clk), FP32 ones against the measured HBM copy bandwidth and the
@@ -388,7 +393,7 @@ def kernel_roofline(prof, n, m, nnz, k, precision, clocks, workload):
     rl_all = {}
     for name, (cnt, ms) in prof.items():
         is64 = name.startswith(("assemble", "vjp")) or (name.startswith("pcg_") and precision == "fp64")
-        fl, by = algorithmic(name, n, m, nnz, k, "fp64" if is64 else "fp32")
+        fl, by = algorithmic(name, n, m, nnz, k, "fp64" if is64 else "fp32", idx32)
         if fl is None or cnt == 0 or ms <= 0:
             continue
         avg_s = ms / cnt / 1000.0
@@ -477,7 +482,8 @@ def single_mesh(api, _native, dev, p, precision, tol, steps, warmup, launch="gra
 def variant_mixed_grid(api, _native, dev, p, tol, steps, fp64_U, fp64_gV, clocks):
     """The headline grid in mixed precision (FP32 PCG inside FP64 refinement)."""
     r = single_mesh(api, _native, dev, p, "mixed", tol, steps, 3)
-    table, roof = kernel_roofline(r["prof"], p.n, p.m, r["mesh"].nnz, p.B.shape[1], "mixed", clocks, p.name + "_mixed")
+    table, roof = kernel_roofline(r["prof"], p.n, p.m, r["mesh"].nnz, p.B.shape[1], "mixed", clocks, p.name + "_mixed",
+                                  idx32=2)
     out = {"workload": f"{p.name} mixed: FP32 Jacobi-PCG (FP32 CSR values) inside FP64 residual refinement to {tol:g}",
            "value": round(r["solves_per_s"], 3), "unit": UNIT, "ms_per_step": round(r["ms_per_step"], 4),
            "steps": steps, "iterations": {"forward": r["finfo"]["iterations"], "adjoint": r["ainfo"]["iterations"]},
@@ -497,7 +503,8 @@ def variant_largest(api, _native, dev, tol, steps, clocks):
     p = mg.config_grid4096x2048(0)
     r = single_mesh(api, _native, dev, p, "mixed", tol, steps, 3)
     mesh = r["mesh"]
-    table, roof = kernel_roofline(r["prof"], p.n, p.m, mesh.nnz, p.B.shape[1], "mixed", clocks, "grid4096x2048")
+    table, roof = kernel_roofline(r["prof"], p.n, p.m, mesh.nnz, p.B.shape[1], "mixed", clocks, "grid4096x2048",
+                                  idx32=2)
     r64 = single_mesh(api, _native, dev, p, "fp64", tol, 1, 0, profile=False, mesh=mesh)
     out = {"workload": f"{p.name}: {p.n} vertices, {p.m} faces, k=3, t=h^2, mixed precision to {tol:g}",
            "value": round(r["solves_per_s"], 3), "unit": UNIT, "ms_per_step": round(r["ms_per_step"], 4),

@@ -237,6 +237,15 @@ cudaError_t mesh_ensure_mixed(ig_mesh* mesh, cudaStream_t st) {
   if ((e = mesh_alloc(mesh, &md.p32, nv)) != cudaSuccess) return e;
   if ((e = mesh_alloc(mesh, &md.q32, nv)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(md.p32, 0, sizeof(float) * nv, st)) != cudaSuccess) return e;
+  if (md.sell_ptr) {
+    short* c16 = nullptr;
+    unsigned char* ok = nullptr;
+    if ((e = mesh_alloc(mesh, &c16, (size_t)md.nnz_sell)) != cudaSuccess) return e;
+    if ((e = mesh_alloc(mesh, &ok, (size_t)(mesh->n + 31) / 32)) != cudaSuccess) return e;
+    if ((e = launch_sell_c16(md.sell_ptr, md.sell_col, mesh->n, c16, ok, st)) != cudaSuccess) return e;
+    md.sell_c16 = c16;
+    md.sell_c16ok = ok;
+  }
   mesh->group.host_mds[0] = md;
   return group_upload_mds(mesh->group, st);
 }

@@ -182,16 +182,30 @@ __device__ __forceinline__ void row_product(const MeshDev& md, const TA* __restr
     const int base = b0 + (int)(row & 31);
     const int* __restrict__ sc = md.sell_col;
     if constexpr (sizeof(TX) == 4) {
-      // FP32: up to 8 slots at once (a mesh row has ~7): all column/value loads, then the gathers
+      // FP32: up to 8 slots at once (a mesh row has ~7): all column/value loads, then the gathers.
+      // Slices flagged compact store their columns as 16-bit offsets from the slice's first row
+      // (a warp's rows are one slice, so the choice is uniform per warp).
+      const bool c16 = md.sell_c16 != nullptr && __ldg(md.sell_c16ok + sl) != 0;
+      const short* __restrict__ s16 = md.sell_c16;
+      const int rbase = sl << 5;
       for (int j0 = 0; j0 < w; j0 += 8) {
         int cj[8];
         TA aj[8];
+        if (c16) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (j0 + u < w) {
-            cj[u] = __ldg(sc + base + 32 * (j0 + u));
-            aj[u] = __ldg(A + base + 32 * (j0 + u));
-          }
+          for (int u = 0; u < 8; ++u)
+            if (j0 + u < w) {
+              cj[u] = rbase + (int)__ldg(s16 + base + 32 * (j0 + u));
+              aj[u] = __ldg(A + base + 32 * (j0 + u));
+            }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (j0 + u < w) {
+              cj[u] = __ldg(sc + base + 32 * (j0 + u));
+              aj[u] = __ldg(A + base + 32 * (j0 + u));
+            }
+        }
 #pragma unroll
         for (int u = 0; u < 8; ++u)
           if (j0 + u < w) {

@@ -241,8 +241,8 @@ __global__ void __launch_bounds__(kBlock, 4) update_kernel(const MeshDev* __rest
 }
 
 // ------------------------------------------------------------------------------- pupdate
-// p = z + beta p with z = D^-1 r from the update kernel (kept in q); rows in pairs with loads
-// before stores.
+// p = z + beta p with z = D^-1 r from the update kernel (kept in q); all of a thread's loads are
+// issued before its stores.
 template <int K>
 __global__ void __launch_bounds__(kBlock, 4) pupdate_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L) {
   __shared__ TileCtx tc;
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kBlock, 4) pupdate_kernel(const MeshDev* __res
                     const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
                     const double* __restrict__ z = md.q;
                     double* __restrict__ p = md.p;
-                    constexpr int RB = 2;
+                    constexpr int RB = kRowsPerThread;
 #pragma unroll
                     for (int r0 = 0; r0 < kRowsPerThread; r0 += RB) {
                       double pi[RB][K], zs[RB][K];

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) vjp_face_kernel(const MeshDev* __restrict
       for (int k = 0; k < K; ++k) lu = fma(L[a][k] - L[b][k], Uv[a][k] - Uv[b][k], lu);
       omega[c] = mt2 * lu;
       // dl/dt = -<Lambda, L U> = -sum_c (cot_c / 2) lu_c = sum_c (dot_c / s / 2) lu_c
-      gt_part = fma(0.5 * dot[c] * inv_s, lu, gt_part);
+      if (gt) gt_part = fma(0.5 * dot[c] * inv_s, lu, gt_part);
     }
     const double Pv = -(omega[0] * dot[0] + omega[1] * dot[1] + omega[2] * dot[2]);
     const double coef = (0.5 * wa - Pv * inv_s * inv_s) * inv_s;
