@@ -238,13 +238,17 @@ cudaError_t mesh_ensure_mixed(ig_mesh* mesh, cudaStream_t st) {
   if ((e = mesh_alloc(mesh, &md.q32, nv)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(md.p32, 0, sizeof(float) * nv, st)) != cudaSuccess) return e;
   if (md.sell_ptr) {
+    // 16-bit column offsets, kept when every slice's columns fit (one-time check on the host)
     short* c16 = nullptr;
-    unsigned char* ok = nullptr;
+    int* nfar = nullptr;
     if ((e = mesh_alloc(mesh, &c16, (size_t)md.nnz_sell)) != cudaSuccess) return e;
-    if ((e = mesh_alloc(mesh, &ok, (size_t)(mesh->n + 31) / 32)) != cudaSuccess) return e;
-    if ((e = launch_sell_c16(md.sell_ptr, md.sell_col, mesh->n, c16, ok, st)) != cudaSuccess) return e;
-    md.sell_c16 = c16;
-    md.sell_c16ok = ok;
+    if ((e = mesh_alloc(mesh, &nfar, 1)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(nfar, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if ((e = launch_sell_c16(md.sell_ptr, md.sell_col, mesh->n, c16, nfar, st)) != cudaSuccess) return e;
+    int far = 1;
+    if ((e = cudaMemcpyAsync(&far, nfar, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    md.sell_c16 = far == 0 ? c16 : nullptr;
   }
   mesh->group.host_mds[0] = md;
   return group_upload_mds(mesh->group, st);

@@ -183,9 +183,8 @@ __device__ __forceinline__ void row_product(const MeshDev& md, const TA* __restr
     const int* __restrict__ sc = md.sell_col;
     if constexpr (sizeof(TX) == 4) {
       // FP32: up to 8 slots at once (a mesh row has ~7): all column/value loads, then the gathers.
-      // Slices flagged compact store their columns as 16-bit offsets from the slice's first row
-      // (a warp's rows are one slice, so the choice is uniform per warp).
-      const bool c16 = md.sell_c16 != nullptr && __ldg(md.sell_c16ok + sl) != 0;
+      // A mesh whose columns all fit reads them as 16-bit offsets from the slice's first row.
+      const bool c16 = md.sell_c16 != nullptr;
       const short* __restrict__ s16 = md.sell_c16;
       const int rbase = sl << 5;
       for (int j0 = 0; j0 < w; j0 += 8) {

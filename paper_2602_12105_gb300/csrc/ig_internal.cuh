@@ -90,10 +90,10 @@ struct MeshDev {
   int nnz_sell;            // stored entries of the sliced layout (0: A is plain CSR on rowptr/col)
   const int* sell_ptr;     // [ceil(n/32)+1] slice offsets, or null for plain CSR
   const int* sell_col;     // [nnz_sell]
-  // mixed precision: 16-bit column offsets from the slice's first row, for the slices whose
-  // columns all lie within +-32767 of it (flag 1); the FP32 SpMV reads these instead of sell_col
-  const short* sell_c16;           // [nnz_sell] or null
-  const unsigned char* sell_c16ok; // [ceil(n/32)] or null
+  // mixed precision: the columns as 16-bit offsets from each slice's first row, kept when every
+  // stored column lies within +-32767 of its slice's first row (null otherwise); the FP32 SpMV
+  // then reads these instead of sell_col
+  const short* sell_c16;   // [nnz_sell] or null
   int k;
   double t;
   const int* F;
@@ -314,7 +314,7 @@ cudaError_t launch_pattern_rows(const int* F, int n, const int* incptr, int* inc
 cudaError_t launch_pattern_cols(const int* F, int n, const int* incptr, const int* inc_fc, const int* nbr,
                                 const int* rowptr, int* col, int* diagpos, int2* inc, int* err, cudaStream_t st);
 cudaError_t launch_sell_width(const int* rowptr, int n, int* width32, cudaStream_t st);
-cudaError_t launch_sell_c16(const int* sell_ptr, const int* sell_col, int n, short* c16, unsigned char* ok,
+cudaError_t launch_sell_c16(const int* sell_ptr, const int* sell_col, int n, short* c16, int* nfar,
                             cudaStream_t st);
 cudaError_t launch_sell_fill(const int* rowptr, const int* col, int n, const int* sell_ptr, int* sell_col,
                              cudaStream_t st);

@@ -248,12 +248,12 @@ __global__ void __launch_bounds__(256) sell_fill_kernel(const int* __restrict__ 
   for (int j = 0; j < w; ++j) sell_col[base + 32 * j] = j < len ? col[r0 + j] : pad;
 }
 
-// One warp per slice: if every stored column of the slice lies within +-32767 of the slice's
-// first row, store the offsets as 16-bit values and flag the slice (a grid's neighbours are
-// within +-(nx + 1) rows; an icosphere's subdivision order can put them anywhere).
+// One warp per slice: the slice's columns as 16-bit offsets from its first row; nfar counts the
+// slices with a column farther than +-32767 (a grid's neighbours are within +-(nx + 1) rows; an
+// icosphere's subdivision order can put them anywhere), in which case the offsets are not used.
 __global__ void __launch_bounds__(256) sell_c16_kernel(const int* __restrict__ sell_ptr,
                                                        const int* __restrict__ sell_col, int n,
-                                                       short* __restrict__ c16, unsigned char* __restrict__ ok) {
+                                                       short* __restrict__ c16, int* __restrict__ nfar) {
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int nsl = (n + 31) / 32;
   const int sl = (int)(t >> 5), lane = (int)(t & 31);
@@ -264,11 +264,9 @@ __global__ void __launch_bounds__(256) sell_c16_kernel(const int* __restrict__ s
   for (int j = 0; j < w; ++j) {
     const int d = sell_col[b0 + 32 * j + lane] - base;
     fits = fits && d >= -32767 && d <= 32767;
+    c16[b0 + 32 * j + lane] = (short)(fits ? d : 0);
   }
-  const bool all = __all_sync(0xffffffffu, fits);
-  if (all)
-    for (int j = 0; j < w; ++j) c16[b0 + 32 * j + lane] = (short)(sell_col[b0 + 32 * j + lane] - base);
-  if (lane == 0) ok[sl] = all ? 1 : 0;
+  if (!__all_sync(0xffffffffu, fits) && lane == 0) atomicAdd(nfar, 1);
 }
 
 inline int blocks_for(long work) { return (int)((work + 255) / 256); }
@@ -303,9 +301,9 @@ cudaError_t launch_sell_width(const int* rowptr, int n, int* width32, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_sell_c16(const int* sell_ptr, const int* sell_col, int n, short* c16, unsigned char* ok,
+cudaError_t launch_sell_c16(const int* sell_ptr, const int* sell_col, int n, short* c16, int* nfar,
                             cudaStream_t st) {
-  sell_c16_kernel<<<blocks_for((long)((n + 31) / 32) * 32), 256, 0, st>>>(sell_ptr, sell_col, n, c16, ok);
+  sell_c16_kernel<<<blocks_for((long)((n + 31) / 32) * 32), 256, 0, st>>>(sell_ptr, sell_col, n, c16, nfar);
   return cudaGetLastError();
 }
 
