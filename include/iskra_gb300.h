@@ -216,6 +216,29 @@ ig_status ig_solve_end(ig_mesh* mesh, int k, double* out_dev, ig_solve_info* inf
 ig_status ig_vjp(ig_mesh* mesh, const double* V_dev, const double* B_dev, int b_is_V, const double* U_dev, int k,
                  double* gV_dev, double* gB_dev, double* gt_dev);
 
+/* ---- mass gradient and the inverse-fairing loop (§7.1) --------------------------------------- */
+
+/* gV_dev [n][3] = d( sum_i M_i(V) w_i )/dV for positions V_dev [n][3] and per-vertex weights
+ * w_dev [n] (the lumped mass M_i = sum of area/3 over the faces at vertex i). This is the
+ * part of a loss that depends on V through the mass directly, e.g. the M-norm loss
+ * 1/2 ||T - U||_M^2 of §7.1 (Eq. for the inverse-fairing objective) with w = |T - U|^2 / 2.
+ * Needs only ig_mesh_upload. Asynchronous. Errors: IG_ERR_INVALID_ARG (NULL pointer). */
+ig_status ig_mass_vjp(ig_mesh* mesh, const double* V_dev, const double* w_dev, double* gV_dev);
+
+/* One step of the inverse-fairing optimisation of §7.1, every part on the device:
+ *   assemble A = M(V) + t L(V); U = A^-1 M V (the fairing of V);
+ *   loss = 1/2 sum_i M_i |T_i - U_i|^2 (the M-norm objective against targets T_dev [n][3]);
+ *   g = dloss/dV by the adjoint rule (Eq. 3; with B = V) plus the direct mass term;
+ *   Sobolev H^1 preconditioning with the same operator, g~ = A^-1 g; V <- V - eta g~.
+ * V_dev [n][3] is updated in place. precision as for ig_assemble. loss_host (may be NULL)
+ * receives the loss at the positions the step started from (synchronises). info3 (may be NULL)
+ * is an array of 3 ig_solve_info for the forward, adjoint and preconditioning solves
+ * (synchronises). Workspace (13 n doubles) is allocated on the mesh at the first call.
+ * Errors: IG_ERR_INVALID_ARG (NULL pointer, eta < 0 or not finite, bad t or precision),
+ * the errors of ig_assemble and ig_solve, IG_ERR_OOM, IG_ERR_CUDA. */
+ig_status ig_fairing_step(ig_mesh* mesh, double* V_dev, const double* T_dev, double t, double eta, int precision,
+                          const ig_solve_opts* opts, double* loss_host, ig_solve_info* info3);
+
 /* ---- allocation-free solve ----------------------------------------------------------------- */
 
 /* Largest number of rows ig_solve_csr_noalloc accepts. */

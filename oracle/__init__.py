@@ -60,6 +60,7 @@ def lib():
             L.orc_dense_cholesky_solve.argtypes = [i64, vp, vp, vp, i32, vp, vp]
             L.orc_pcg_solve.argtypes = [i64, vp, vp, vp, i32, vp, vp, dbl, i32, vp, vp]
             L.orc_vjp.argtypes = [i64, vp, i64, vp, dbl, i32, vp, vp, vp, i32, vp, vp, vp]
+            L.orc_mass_vjp.argtypes = [i64, vp, i64, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -195,6 +196,42 @@ def forward_adjoint(V, F, B, t, T, b_is_V, tol=1e-14, method="auto"):
     gV, gB, gt = vjp(V, F, t, U, Lam, B, b_is_V)
     return dict(U=U, Lam=Lam, gV=gV, gB=gB, gt=gt, loss=0.5 * float(np.sum(G * G)), rowptr=rowptr, col=col,
                 Aval=Aval, Lval=Lval, M=M, R=R, G=G)
+
+
+def mass_vjp(V, F, w):
+    """d(sum_i M_i(V) w_i)/dV [n][3] (see orc_mass_vjp)."""
+    V, F, w = _f64(V), _i32(F), _f64(w)
+    gV = np.empty((V.shape[0], 3))
+    st = lib().orc_mass_vjp(V.shape[0], _p(V), F.shape[0], _p(F), _p(w), _p(gV))
+    if st:
+        raise OracleError(st, "mass_vjp")
+    return gV
+
+
+def mnorm_objective(V, F, T, t, tol=1e-14, method="auto"):
+    """The inverse-fairing objective of §7.1 at V: U = g(V) = (M + tL)^-1 M V and
+    loss = 1/2 ||T - U||_M^2 = 1/2 sum_i M_i |T_i - U_i|^2, with its gradient by the adjoint rule
+    (Eq. 3, B = V) plus the direct dependence through M. Returns a dict with U, loss, gV, G, Lam,
+    w and the operator."""
+    rowptr, col, Aval, Lval, M = operator(V, F, t)
+    V = _f64(V)
+    U = solve(rowptr, col, Aval, M[:, None] * V, tol=tol, method=method)
+    D = U - _f64(T)
+    G = M[:, None] * D                      # dl/dU
+    w = 0.5 * np.sum(D * D, axis=1)         # l = sum_i M_i w_i
+    Lam = solve(rowptr, col, Aval, G, tol=tol, method=method)
+    gV, _, _ = vjp(V, F, t, U, Lam, None, True)
+    gV = gV + mass_vjp(V, F, w)
+    return dict(U=U, loss=float(np.sum(M * w)), gV=gV, G=G, Lam=Lam, w=w, rowptr=rowptr, col=col, Aval=Aval, M=M)
+
+
+def fairing_step(V, F, T, t, eta, tol=1e-14, method="auto"):
+    """One Sobolev-preconditioned gradient step of the inverse-fairing problem (§7.1): the
+    gradient of mnorm_objective smoothed with the same operator, g~ = (M + tL)^-1 g, then
+    V - eta g~. Returns (new V, loss at V)."""
+    r = mnorm_objective(V, F, T, t, tol=tol, method=method)
+    gs = solve(r["rowptr"], r["col"], r["Aval"], r["gV"], tol=tol, method=method)
+    return _f64(V) - eta * gs, r["loss"]
 
 
 def num_threads():

@@ -391,5 +391,33 @@ int orc_vjp(int64_t n, const double* V, int64_t m, const int32_t* F, double t, i
   return ORC_OK;
 }
 
+/* Gradient of the mass term sum_i M_i(v) w_i (M_i = sum over the faces at i of area/3) with
+ * respect to the positions: for each face, ((1/3) sum_{v in f} w_v) times grad area_f, with
+ * grad_{p_i} area = 1/2 n x (p_k - p_j) for CCW (i, j, k). This is how the M-norm objective
+ * 1/2 ||t - g(v)||_M^2 of the inverse-fairing problem (§7.1) depends on v through M, with
+ * w = |t - g(v)|^2 / 2. gV is [n][3] (overwritten). */
+int orc_mass_vjp(int64_t n, const double* V, int64_t m, const int32_t* F, const double* w, double* gV) {
+  for (int64_t i = 0; i < 3 * n; ++i) gV[i] = 0.0;
+  for (int64_t f = 0; f < m; ++f) {
+    int64_t vid[3] = {F[3 * f], F[3 * f + 1], F[3 * f + 2]};
+    const double* P[3] = {V + 3 * vid[0], V + 3 * vid[1], V + 3 * vid[2]};
+    double e1[3], e2[3], x[3], nrm[3];
+    sub3(P[1], P[0], e1);
+    sub3(P[2], P[0], e2);
+    cross3(e1, e2, x);
+    double s = sqrt(dot3(x, x));
+    if (!(s > 0.0)) return ORC_ERR_DEGENERATE;
+    for (int d = 0; d < 3; ++d) nrm[d] = x[d] / s;
+    double wf = (w[vid[0]] + w[vid[1]] + w[vid[2]]) / 3.0;
+    for (int a = 0; a < 3; ++a) {
+      double opp[3], g[3];
+      sub3(P[(a + 2) % 3], P[(a + 1) % 3], opp);
+      cross3(nrm, opp, g);
+      for (int d = 0; d < 3; ++d) gV[vid[a] * 3 + d] += wf * 0.5 * g[d];
+    }
+  }
+  return ORC_OK;
+}
+
 /* Number of threads this oracle uses (it is single-threaded). */
 int orc_num_threads(void) { return 1; }

@@ -134,6 +134,24 @@ class Mesh:
         self.ctx.check(self.ctx.lib.ig_operator(self.h, _ptr(A), _ptr(M)))
         return A, M
 
+    def mass(self):
+        """The lumped mass M [n] of the assembled operator."""
+        M = torch.empty(self.n, dtype=torch.float64, device=self.ctx.device)
+        self.ctx.sync_stream()
+        self.ctx.check(self.ctx.lib.ig_operator(self.h, None, _ptr(M)))
+        return M
+
+    def mass_vjp(self, V: torch.Tensor, w: torch.Tensor):
+        """d(sum_i M_i(V) w_i)/dV [n][3] for per-vertex weights w [n] (ig_mass_vjp)."""
+        V = self._dev(V, 3, "V")
+        w = w.to(device=self.ctx.device, dtype=torch.float64).contiguous().reshape(-1)
+        if w.numel() != self.n:
+            raise ValueError(f"w must have {self.n} entries")
+        gV = torch.empty((self.n, 3), dtype=torch.float64, device=self.ctx.device)
+        self.ctx.sync_stream()
+        self.ctx.check(self.ctx.lib.ig_mass_vjp(self.h, _ptr(V), _ptr(w), _ptr(gV)))
+        return gV
+
     def pattern(self):
         rowptr = torch.empty(self.n + 1, dtype=torch.int32, device=self.ctx.device)
         col = torch.empty(self.nnz, dtype=torch.int32, device=self.ctx.device)
@@ -210,6 +228,63 @@ class SmoothSolve(torch.autograd.Function):
 def smooth(mesh: Mesh, V: torch.Tensor, B: Optional[torch.Tensor], t, precision: str = "fp64", opts=None):
     """Differentiable implicit smoothing step: solve (M(V) + t L(V)) U = M(V) B (B = V if None)."""
     return SmoothSolve.apply(V, B, t, mesh, precision, opts)
+
+
+class MassFn(torch.autograd.Function):
+    """The lumped mass M(V) [n] (area/3 per incident face), differentiable in V."""
+
+    @staticmethod
+    def forward(ctx, V, mesh: Mesh):
+        t = mesh.t if mesh.t is not None else 0.0
+        prec = mesh.precision if mesh.precision is not None else "fp64"
+        if mesh._token != (V.data_ptr(), V._version, t, prec):
+            mesh.assemble(V, t, prec)
+        ctx.mesh = mesh
+        ctx.save_for_backward(V)
+        return mesh.mass()
+
+    @staticmethod
+    def backward(ctx, gM):
+        (V,) = ctx.saved_tensors
+        return ctx.mesh.mass_vjp(V, gM.to(torch.float64).contiguous()), None
+
+
+def mass(mesh: Mesh, V: torch.Tensor):
+    """Differentiable lumped mass M(V); with smooth() it forms the M-norm loss of §7.1:
+    0.5 * (mass(mesh, V)[:, None] * (smooth(mesh, V, None, t) - T) ** 2).sum()."""
+    return MassFn.apply(V, mesh)
+
+
+class InverseFairing:
+    """The inverse-fairing optimisation of §7.1, one device-side step per call (ig_fairing_step):
+    g(V) = (M + tL)^-1 M V, loss = 1/2 ||T - g(V)||_M^2, and the Sobolev-preconditioned step
+    V <- V - eta (M + tL)^-1 dloss/dV with the same operator."""
+
+    def __init__(self, mesh: Mesh, T: torch.Tensor, t: float, eta: float, precision: str = "fp64", opts=None):
+        self.mesh = mesh
+        self.T = mesh._dev(T, 3, "T")
+        self.t, self.eta, self.precision = float(t), float(eta), precision
+        self.opts = opts if opts is not None else make_opts()
+
+    def step(self, V: torch.Tensor, want_loss: bool = True, info: bool = False):
+        """Update V [n][3] (float64, on the device) in place; returns the loss at the starting V
+        (None unless want_loss), and with info the three solves' info dicts."""
+        mesh = self.mesh
+        if V.dtype != torch.float64 or not V.is_contiguous() or V.device != mesh.ctx.device:
+            raise ValueError("V must be a contiguous float64 tensor on the mesh's device")
+        loss = ctypes.c_double(0.0)
+        infos = (N.SolveInfo * 3)() if info else None
+        mesh.ctx.sync_stream()
+        st = mesh.ctx.lib.ig_fairing_step(mesh.h, _ptr(V), _ptr(self.T), self.t, self.eta, _PREC[self.precision],
+                                          ctypes.byref(self.opts), ctypes.byref(loss) if want_loss else None,
+                                          infos)
+        mesh.ctx.check(st)
+        mesh.t, mesh.precision = self.t, self.precision
+        mesh._token = None  # V changed after the assembly
+        out = loss.value if want_loss else None
+        if info:
+            return out, [i.as_dict() for i in infos]
+        return out
 
 
 def _ptr_array(tensors):

@@ -676,6 +676,81 @@ ig_status ig_vjp(ig_mesh* mesh, const double* V_dev, const double* B_dev, int b_
   return IG_OK;
 }
 
+ig_status ig_mass_vjp(ig_mesh* mesh, const double* V_dev, const double* w_dev, double* gV_dev) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (!V_dev || !w_dev || !gV_dev) return bad_arg(ctx, "V, w and gV must be non-NULL");
+  DeviceGuard guard(ctx->device);
+  CallDev call{};
+  call.V = V_dev;
+  call.gV = gV_dev;
+  call.wm = w_dev;
+  call.mass_only = 1;
+  IG_CK(ctx, group_set_calls(mesh->group, &call, ctx->stream), "upload");
+  IG_CK(ctx, launch_vjp(mesh->group, 1, ctx->stream), "mass vjp");
+  return IG_OK;
+}
+
+ig_status ig_fairing_step(ig_mesh* mesh, double* V_dev, const double* T_dev, double t, double eta, int precision,
+                          const ig_solve_opts* opts, double* loss_host, ig_solve_info* info3) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (!V_dev || !T_dev) return bad_arg(ctx, "V and T must be non-NULL");
+  if (!(eta >= 0.0) || !(eta < 1e300)) return bad_arg(ctx, "eta must be finite and >= 0");
+  const ig_solve_opts o = resolve_opts(opts);
+  ig_status cs = check_opts(ctx, o);
+  if (cs != IG_OK) return cs;
+  DeviceGuard guard(ctx->device);
+  const size_t n = (size_t)mesh->n;
+  if (!mesh->fair) IG_CK(ctx, mesh_alloc(mesh, &mesh->fair, 13 * n + 1), "alloc");
+  double* U = mesh->fair;
+  double* G = U + 3 * n;
+  double* graw = G + 3 * n;
+  double* gs = graw + 3 * n;
+  double* w = gs + 3 * n;
+  double* loss = w + n;
+  ig_status st = ig_assemble(mesh, V_dev, t, precision);
+  if (st != IG_OK) return st;
+  const int mixed = mesh->assembled == 2;
+  auto io = std::make_unique<IoTable>();
+  auto solve = [&](const double* in, double* out, int rhs_mass, int slot) -> ig_status {
+    io->in[0] = in;
+    io->out[0] = out;
+    IG_CK(ctx, group_solve(mesh->group, 3, mixed, *io, rhs_mass, o, ctx->stream), "solve");
+    if (info3) {
+      IG_CK(ctx, group_true_residual(mesh->group, 3, *io, rhs_mass, ctx->stream), "residual");
+      ig_status s2 = collect_info(mesh, 3, &info3[slot]);
+      if (s2 != IG_OK && s2 != IG_ERR_NOT_CONVERGED) return s2;
+    }
+    return IG_OK;
+  };
+  // forward: U = A^-1 M V
+  if ((st = solve(V_dev, U, 1, 0)) != IG_OK) return st;
+  // M-norm loss, its adjoint right-hand side G = M (U - T) and mass weights w = |U - T|^2 / 2
+  IG_CK(ctx, launch_mnorm(mesh->group, U, T_dev, G, w, loss, ctx->stream), "loss");
+  // adjoint: Lambda = A^-1 G, then dl/dV with B = V and the mass term of the loss
+  if ((st = solve(G, mesh->md.lam, 0, 1)) != IG_OK) return st;
+  CallDev call{};
+  call.V = V_dev;
+  call.B = V_dev;
+  call.U = U;
+  call.gV = graw;
+  call.t = mesh->t;
+  call.b_is_V = 1;
+  call.bstride = 3;
+  call.wm = w;
+  IG_CK(ctx, group_set_calls(mesh->group, &call, ctx->stream), "upload");
+  IG_CK(ctx, launch_vjp(mesh->group, 3, ctx->stream), "vjp");
+  // Sobolev H^1 step with the same operator, then V <- V - eta g~
+  if ((st = solve(graw, gs, 0, 2)) != IG_OK) return st;
+  IG_CK(ctx, launch_step(V_dev, gs, eta, (long)(3 * n), ctx->num_sms, ctx->stream), "step");
+  if (loss_host) {
+    IG_CK(ctx, cudaMemcpyAsync(loss_host, loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "loss");
+    IG_CK(ctx, cudaStreamSynchronize(ctx->stream), "sync");
+  }
+  return IG_OK;
+}
+
 ig_status ig_profile_enable(int enable) {
   ProfState& P = prof_state();
   std::lock_guard<std::mutex> lk(P.mu);

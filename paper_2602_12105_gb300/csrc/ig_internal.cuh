@@ -224,6 +224,8 @@ struct CallDev {
   double t;          // time step of the assembled operator
   int b_is_V;
   int bstride;       // columns of B (3 when b_is_V)
+  const double* wm;  // null, or per-vertex weights w [n]: gV also gets d(sum_i M_i(V) w_i)/dV
+  int mass_only;     // 1: gV is that mass term alone (no solve terms; U, B, Lambda unused)
 };
 
 // A cached solver launch for one (k, precision): a CUDA graph whose WHILE node runs the
@@ -297,6 +299,7 @@ struct ig_mesh {
   ig::MeshDev md{};         // host copy of the device pointers
   ig::Group group;          // this mesh alone
   std::vector<void*> allocs;
+  double* fair = nullptr;   // inverse-fairing workspace: U, G, g, g~ [n][3], w [n], loss (on first use)
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -327,5 +330,9 @@ cudaError_t launch_operator_csr(const MeshDev& md, double* Acsr, cudaStream_t st
 
 // ig_vjp.cu
 cudaError_t launch_vjp(Group& g, int k, cudaStream_t st);
+// ig_fairing.cu
+cudaError_t launch_mnorm(Group& g, const double* U, const double* T, double* G, double* w, double* loss,
+                         cudaStream_t st);
+cudaError_t launch_step(double* V, const double* g, double eta, long count, int num_sms, cudaStream_t st);
 
 }  // namespace ig

@@ -14,6 +14,10 @@
 //                    + (w_a / 2 - P / s^2) (N x d_c) / s.
 // (The CPU oracle reaches the same numbers through the per-corner cotangent gradients.)
 //
+// A loss may also depend on V through the mass directly (the M-norm loss of the inverse-fairing
+// problem, §7.1): with per-vertex weights w, d(sum_i M_i w_i)/dV adds w_v / 3 per vertex of the
+// face to w_a (M_i = sum over the faces at i of area / 3), and mass_only computes that term alone.
+//
 // K6a (face-parallel) writes the three per-corner gradients of each face to gface [m][9] and a
 // per-tile partial of dl/dt; K6b (vertex-parallel) gathers gface over the vertex's incidence
 // list in face order (atomic-free, deterministic) and adds M Lambda where B is V.
@@ -72,31 +76,35 @@ __global__ void __launch_bounds__(256) vjp_face_kernel(const MeshDev* __restrict
       const int a = (c + 1) % 3, b = (c + 2) % 3;
       dot[c] = dd[a][0] * dd[b][0] + dd[a][1] * dd[b][1] + dd[a][2] * dd[b][2];
     }
-    // per-vertex <Lambda_v, B_v - U_v> and the per-corner <dLambda, dU>
-    double L[3][K], Uv[3][K];
+    // per-vertex <Lambda_v, B_v - U_v> and the per-corner <dLambda, dU>; with mass weights w,
+    // d(sum_i M_i w_i)/dV adds sum_f ((1/3) sum_{v in f} w_v) grad area_f, i.e. w_v to the sum
     double wa = 0.0;
+    double omega[3] = {0.0, 0.0, 0.0};
+    if (!cl.mass_only) {
+      double L[3][K], Uv[3][K];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+      for (int c = 0; c < 3; ++c) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        L[c][k] = lam[(long)vid[c] * K + k];
-        Uv[c][k] = U[(long)vid[c] * K + k];
-        wa = fma(L[c][k], Bsrc[(long)vid[c] * bstride + k] - Uv[c][k], wa);
+        for (int k = 0; k < K; ++k) {
+          L[c][k] = lam[(long)vid[c] * K + k];
+          Uv[c][k] = U[(long)vid[c] * K + k];
+          wa = fma(L[c][k], Bsrc[(long)vid[c] * bstride + k] - Uv[c][k], wa);
+        }
+      }
+      const double mt2 = -0.5 * tval;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int a = (c + 1) % 3, b = (c + 2) % 3;
+        double lu = 0.0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) lu = fma(L[a][k] - L[b][k], Uv[a][k] - Uv[b][k], lu);
+        omega[c] = mt2 * lu;
+        // dl/dt = -<Lambda, L U> = -sum_c (cot_c / 2) lu_c = sum_c (dot_c / s / 2) lu_c
+        if (gt) gt_part = fma(0.5 * dot[c] * inv_s, lu, gt_part);
       }
     }
+    if (cl.wm) wa += (__ldg(cl.wm + vid[0]) + __ldg(cl.wm + vid[1])) + __ldg(cl.wm + vid[2]);
     wa *= (1.0 / 3.0);
-    double omega[3];
-    const double mt2 = -0.5 * tval;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int a = (c + 1) % 3, b = (c + 2) % 3;
-      double lu = 0.0;
-#pragma unroll
-      for (int k = 0; k < K; ++k) lu = fma(L[a][k] - L[b][k], Uv[a][k] - Uv[b][k], lu);
-      omega[c] = mt2 * lu;
-      // dl/dt = -<Lambda, L U> = -sum_c (cot_c / 2) lu_c = sum_c (dot_c / s / 2) lu_c
-      if (gt) gt_part = fma(0.5 * dot[c] * inv_s, lu, gt_part);
-    }
     const double Pv = -(omega[0] * dot[0] + omega[1] * dot[1] + omega[2] * dot[2]);
     const double coef = (0.5 * wa - Pv * inv_s * inv_s) * inv_s;
     double g[9];
