@@ -52,7 +52,7 @@ def parse():
                     help="skip the other workloads (mixed grid, largest mesh, 256-mesh batch, serving)")
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="requests in the bounded sample of the serving stream")
-    ap.add_argument("--variants", default="mixed,largest,batch,serve",
+    ap.add_argument("--variants", default="mixed,largest,batch,fairing,serve",
                     help="comma list of the extra workloads to run")
     return ap.parse_args()
 
@@ -608,6 +608,43 @@ def variant_batch(api, _native, dev, tol, steps):
             "profile_one_step_host_launch": {"fp64": prof64, "mixed": prof32}}
 
 
+def variant_fairing(api, _native, dev, steps, level=7):
+    """The inverse-fairing loop of §7.1 (ig_fairing_step: forward solve, M-norm objective,
+    adjoint gradient with the mass term, Sobolev-preconditioned step; three solves per step) on an
+    icosphere with radial noise, V starting at the targets, in FP64 and mixed precision."""
+    import torch
+    from paper_2602_12105_gb300 import meshgen as mg
+    Vc, F = mg.icosphere(level)
+    T = mg.radial_perturb(Vc, 0.02, np.random.default_rng(35))
+    t, eta = 2e-3, 1.0
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": f"ico{level} ({T.shape[0]} vertices, {F.shape[0]} faces), radial N(0, 0.02), t = {t:g}, "
+                       f"eta = {eta:g}, solves to 1e-10; one step = assemble + 3 solves + VJP + update",
+           "unit": "steps/s", "steps": steps}
+    for prec in ("fp64", "mixed"):
+        mesh = api.Mesh(torch.from_numpy(F).to(dev), T.shape[0])
+        Td = torch.from_numpy(T).to(dev)
+        fair = api.InverseFairing(mesh, Td, t, eta, precision=prec)
+        V = Td.clone()
+        loss0, infos = fair.step(V, info=True)
+        for _ in range(2):
+            fair.step(V, want_loss=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fair.step(V, want_loss=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = float(e0.elapsed_time(e1)) / steps
+        loss_end = fair.step(V)
+        out[prec] = {"value": round(1000.0 / ms, 3), "ms_per_step": round(ms, 4),
+                     "iterations_first_step": [i["iterations"] for i in infos],
+                     "loss_first": loss0, f"loss_after_{steps + 4}_steps": loss_end}
+        mesh.close()
+    return out
+
+
 def serving_requests(count, seed=7):
     """A bounded sample of the serving stream: request sizes log-uniform in [1e3, 2e6] vertices,
     half icospheres (levels 4..8), half square grids whose side is snapped to one of 32
@@ -689,6 +726,8 @@ def run_variants(args, p, U64, gV64, dev):
         out["grid4096x2048_mixed"] = variant_largest(api, _native, dev, args.tol, 10, clocks_guess)
     if "batch" in want:
         out["batch256_icospheres"] = variant_batch(api, _native, dev, args.tol, 6)
+    if "fairing" in want:
+        out["inverse_fairing_ico7"] = variant_fairing(api, _native, dev, 20)
     if "serve" in want and args.serve_requests > 0:
         out["serving"] = variant_serving(dev, args.tol, args.serve_requests)
     out["clocks"] = sampler.stop()

@@ -496,6 +496,28 @@ __device__ __forceinline__ void block_exscan3(int a, int b, int c, int& ea, int&
   __syncthreads();
 }
 
+// Start table of one grid: entry g = (list position j, local tile, mesh, tile count) of the chunk
+// [g·chunk, (g+1)·chunk) of the listed tiles, or a zero count past them. off[0..ns] are the tile
+// offsets of the listed meshes (off[ns] = total).
+__device__ __forceinline__ void fill_starts(int4* st, int grid, int chunk, int total, const int* off,
+                                            const int* mesh, int ns) {
+  for (int g = threadIdx.x; g < grid; g += kBlock) {
+    const long x = (long)g * chunk;
+    if (x >= total || ns == 0) {
+      st[g] = make_int4(0, 0, -1, 0);
+      continue;
+    }
+    int lo = 0, hi = ns - 1;  // the largest j with off[j] <= x
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= x) lo = mid;
+      else hi = mid - 1;
+    }
+    const int cnt = total - x < chunk ? (int)(total - x) : chunk;
+    st[g] = make_int4(lo, (int)(x - off[lo]), mesh[lo], cnt);
+  }
+}
+
 // Build one list (run by every thread of one CTA, after every other CTA of the launch is done
 // with it): the meshes that are not done and satisfy sel(s). Big meshes go to `big`; the others to
 // `mesh` with their tile offsets (FP64 tiling in off64 when given, mixed tiling in off32) and the
@@ -545,28 +567,10 @@ __device__ __forceinline__ void build_list(const MeshDev* __restrict__ mds, int 
     off32[ns] = tot32;
   }
   __syncthreads();  // the offsets above are visible to the whole CTA
-  // the thread of listed mesh j writes the start of every CTA whose chunk begins in its tiles
-  for (int j = threadIdx.x; j < ns; j += kBlock) {
-    const int mi = mesh[j];
-    if (st64) {
-      const int a = off64[j], z = off64[j + 1];
-      for (int g = (a + ch64 - 1) / ch64; g < g64 && g * ch64 < z; ++g) {
-        const int cnt = tot64 - g * ch64 < ch64 ? tot64 - g * ch64 : ch64;
-        st64[g] = make_int4(j, g * ch64 - a, mi, cnt);
-      }
-    }
-    const int a = off32[j], z = off32[j + 1];
-    for (int g = (a + ch32 - 1) / ch32; g < g32 && g * ch32 < z; ++g) {
-      const int cnt = tot32 - g * ch32 < ch32 ? tot32 - g * ch32 : ch32;
-      st32[g] = make_int4(j, g * ch32 - a, mi, cnt);
-    }
-  }
-  // CTAs past the listed tiles get none
-  if (st64)
-    for (int g = threadIdx.x; g < g64; g += kBlock)
-      if ((long)g * ch64 >= tot64) st64[g] = make_int4(0, 0, -1, 0);
-  for (int g = threadIdx.x; g < g32; g += kBlock)
-    if ((long)g * ch32 >= tot32) st32[g] = make_int4(0, 0, -1, 0);
+  // each CTA's start: the listed mesh whose tiles contain the chunk's first tile (binary search
+  // over the offsets, one CTA entry per thread)
+  if (st64) fill_starts(st64, g64, ch64, tot64, off64, mesh, ns);
+  fill_starts(st32, g32, ch32, tot32, off32, mesh, ns);
 }
 
 struct SelAll {
