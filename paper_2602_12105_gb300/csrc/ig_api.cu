@@ -410,8 +410,29 @@ ig_status ig_mesh_upload(ig_ctx* ctx, const int32_t* F_dev, int64_t m, int64_t n
   UP_CK(launch_sell_width(rowptr, ni, width32, st), "sell width");
   UP_CK(exclusive_scan_int(width32, sell_ptr, nsl, totals, scratch, scan_ints, st), "scan");
   int nnz_sell = 0;
+  std::vector<int> widths((size_t)nsl);
   UP_CK(cudaMemcpyAsync(&nnz_sell, totals, sizeof(int), cudaMemcpyDeviceToHost, st), "read totals");
+  UP_CK(cudaMemcpyAsync(widths.data(), width32, sizeof(int) * (size_t)nsl, cudaMemcpyDeviceToHost, st),
+        "read widths");
   UP_CK(cudaStreamSynchronize(st), "sell width");
+  // When padding every slice to the widest one costs at most 1/64 more entries (a grid: only the
+  // slices of its first and last row of vertices are narrower), all slices get that width and
+  // the SpMV computes a slice's offset instead of loading it.
+  int sell_w = 0;
+  {
+    long wmax = 0;
+    for (int w : widths) wmax = w > wmax ? w : wmax;
+    const long padded = wmax * (long)nsl;
+    if (nsl > 0 && padded <= (long)nnz_sell + (long)nnz_sell / 64 && padded < (long)INT32_MAX) {
+      std::vector<int> ptr((size_t)nsl + 1);
+      for (long s2 = 0; s2 <= nsl; ++s2) ptr[(size_t)s2] = (int)(s2 * wmax);
+      UP_CK(cudaMemcpyAsync(sell_ptr, ptr.data(), sizeof(int) * ((size_t)nsl + 1), cudaMemcpyHostToDevice, st),
+            "sell ptr");
+      UP_CK(cudaStreamSynchronize(st), "sell ptr");
+      nnz_sell = (int)padded;
+      sell_w = (int)(wmax / 32);
+    }
+  }
   UP_CK(mesh_alloc(M, &sell_col, (size_t)nnz_sell), "alloc sell");
   UP_CK(launch_sell_fill(rowptr, col, ni, sell_ptr, sell_col, st), "sell fill");
 
@@ -439,6 +460,7 @@ ig_status ig_mesh_upload(ig_ctx* ctx, const int32_t* F_dev, int64_t m, int64_t n
   choose_tiles(ctx->solver_slots, md.tile_rows, md.ntiles);
   choose_tiles(ctx->solver_slots32, md.tile_rows32, md.ntiles32);
   md.nnz_sell = nnz_sell;
+  md.sell_w = sell_w;
   md.sell_ptr = sell_ptr;
   md.sell_col = sell_col;
   md.F = F;
@@ -685,9 +707,8 @@ ig_status ig_mass_vjp(ig_mesh* mesh, const double* V_dev, const double* w_dev, d
   call.V = V_dev;
   call.gV = gV_dev;
   call.wm = w_dev;
-  call.mass_only = 1;
   IG_CK(ctx, group_set_calls(mesh->group, &call, ctx->stream), "upload");
-  IG_CK(ctx, launch_vjp(mesh->group, 1, ctx->stream), "mass vjp");
+  IG_CK(ctx, launch_vjp(mesh->group, 1, ctx->stream, 2), "mass vjp");
   return IG_OK;
 }
 
@@ -740,7 +761,7 @@ ig_status ig_fairing_step(ig_mesh* mesh, double* V_dev, const double* T_dev, dou
   call.bstride = 3;
   call.wm = w;
   IG_CK(ctx, group_set_calls(mesh->group, &call, ctx->stream), "upload");
-  IG_CK(ctx, launch_vjp(mesh->group, 3, ctx->stream), "vjp");
+  IG_CK(ctx, launch_vjp(mesh->group, 3, ctx->stream, 1), "vjp");
   // Sobolev H^1 step with the same operator, then V <- V - eta g~
   if ((st = solve(graw, gs, 0, 2)) != IG_OK) return st;
   IG_CK(ctx, launch_step(V_dev, gs, eta, (long)(3 * n), ctx->num_sms, ctx->stream), "step");

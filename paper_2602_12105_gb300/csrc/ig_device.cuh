@@ -177,8 +177,14 @@ __device__ __forceinline__ void row_product(const MeshDev& md, const TA* __restr
   for (int c = 0; c < K; ++c) acc[c] = TX(0);
   if (md.sell_ptr) {
     const int sl = (int)(row >> 5);
-    const int b0 = __ldg(md.sell_ptr + sl), b1 = __ldg(md.sell_ptr + sl + 1);
-    const int w = (b1 - b0) >> 5;
+    int b0, w;
+    if (md.sell_w) {  // slices of one width: the offset is computed, not loaded
+      w = md.sell_w;
+      b0 = sl * 32 * w;
+    } else {
+      b0 = __ldg(md.sell_ptr + sl);
+      w = (__ldg(md.sell_ptr + sl + 1) - b0) >> 5;
+    }
     const int base = b0 + (int)(row & 31);
     const int* __restrict__ sc = md.sell_col;
     if constexpr (sizeof(TX) == 4) {

@@ -88,6 +88,7 @@ struct MeshDev {
   int tile_rows;           // rows per FP64 solver tile (<= kTileRows, a multiple of 32), chosen at upload
   int ntiles32, tile_rows32;  // the same for the mixed-precision kernels (their own occupancy)
   int nnz_sell;            // stored entries of the sliced layout (0: A is plain CSR on rowptr/col)
+  int sell_w;              // every slice has this many entries per row (0: widths differ)
   const int* sell_ptr;     // [ceil(n/32)+1] slice offsets, or null for plain CSR
   const int* sell_col;     // [nnz_sell]
   // mixed precision: the columns as 16-bit offsets from each slice's first row, kept when every
@@ -224,8 +225,8 @@ struct CallDev {
   double t;          // time step of the assembled operator
   int b_is_V;
   int bstride;       // columns of B (3 when b_is_V)
-  const double* wm;  // null, or per-vertex weights w [n]: gV also gets d(sum_i M_i(V) w_i)/dV
-  int mass_only;     // 1: gV is that mass term alone (no solve terms; U, B, Lambda unused)
+  const double* wm;  // per-vertex weights w [n] of the mass term d(sum_i M_i(V) w_i)/dV (VJP
+                     // modes 1 and 2; see launch_vjp)
 };
 
 // A cached solver launch for one (k, precision): a CUDA graph whose WHILE node runs the
@@ -329,7 +330,8 @@ cudaError_t launch_operator_csr(const MeshDev& md, double* Acsr, cudaStream_t st
 // ig_pcg.cu: see Group above
 
 // ig_vjp.cu
-cudaError_t launch_vjp(Group& g, int k, cudaStream_t st);
+// mode 0: solve terms; 1: solve terms and the mass weights of the calls; 2: mass weights alone
+cudaError_t launch_vjp(Group& g, int k, cudaStream_t st, int mode = 0);
 // ig_fairing.cu
 cudaError_t launch_mnorm(Group& g, const double* U, const double* T, double* G, double* w, double* loss,
                          cudaStream_t st);

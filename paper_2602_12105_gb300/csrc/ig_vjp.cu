@@ -16,7 +16,8 @@
 //
 // A loss may also depend on V through the mass directly (the M-norm loss of the inverse-fairing
 // problem, §7.1): with per-vertex weights w, d(sum_i M_i w_i)/dV adds w_v / 3 per vertex of the
-// face to w_a (M_i = sum over the faces at i of area / 3), and mass_only computes that term alone.
+// face to w_a (M_i = sum over the faces at i of area / 3); the kernel's MODE selects the solve
+// terms alone (0), both (1) or the mass term alone (2, no U, B or Lambda read).
 //
 // K6a (face-parallel) writes the three per-corner gradients of each face to gface [m][9] and a
 // per-tile partial of dl/dt; K6b (vertex-parallel) gathers gface over the vertex's incidence
@@ -29,7 +30,8 @@ namespace {
 
 constexpr int kFaceTile = 256;
 
-template <int K>
+// MODE 0: the solve terms; 1: the solve terms and the mass weights; 2: the mass weights alone.
+template <int K, int MODE>
 __global__ void __launch_bounds__(256) vjp_face_kernel(const MeshDev* __restrict__ mds,
                                                        const CallDev* __restrict__ calls,
                                                        const int2* __restrict__ ftiles) {
@@ -80,7 +82,7 @@ __global__ void __launch_bounds__(256) vjp_face_kernel(const MeshDev* __restrict
     // d(sum_i M_i w_i)/dV adds sum_f ((1/3) sum_{v in f} w_v) grad area_f, i.e. w_v to the sum
     double wa = 0.0;
     double omega[3] = {0.0, 0.0, 0.0};
-    if (!cl.mass_only) {
+    if constexpr (MODE != 2) {
       double L[3][K], Uv[3][K];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(256) vjp_face_kernel(const MeshDev* __restrict
         if (gt) gt_part = fma(0.5 * dot[c] * inv_s, lu, gt_part);
       }
     }
-    if (cl.wm) wa += (__ldg(cl.wm + vid[0]) + __ldg(cl.wm + vid[1])) + __ldg(cl.wm + vid[2]);
+    if constexpr (MODE != 0) wa += (__ldg(cl.wm + vid[0]) + __ldg(cl.wm + vid[1])) + __ldg(cl.wm + vid[2]);
     wa *= (1.0 / 3.0);
     const double Pv = -(omega[0] * dot[0] + omega[1] * dot[1] + omega[2] * dot[2]);
     const double coef = (0.5 * wa - Pv * inv_s * inv_s) * inv_s;
@@ -193,10 +195,12 @@ __global__ void __launch_bounds__(256) vjp_gather_kernel(const MeshDev* __restri
 }
 
 template <int K>
-cudaError_t vjp_k(Group& g, cudaStream_t st) {
+cudaError_t vjp_k(Group& g, int mode, cudaStream_t st) {
   {
     IG_PROF("vjp_face", st);
-    vjp_face_kernel<K><<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
+    if (mode == 0) vjp_face_kernel<K, 0><<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
+    else if (mode == 1) vjp_face_kernel<K, 1><<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
+    else vjp_face_kernel<K, 2><<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -209,12 +213,13 @@ cudaError_t vjp_k(Group& g, cudaStream_t st) {
 
 }  // namespace
 
-cudaError_t launch_vjp(Group& g, int k, cudaStream_t st) {
+cudaError_t launch_vjp(Group& g, int k, cudaStream_t st, int mode) {
+  if (mode == 2) return vjp_k<1>(g, 2, st);
   switch (k) {
-    case 1: return vjp_k<1>(g, st);
-    case 2: return vjp_k<2>(g, st);
-    case 3: return vjp_k<3>(g, st);
-    case 4: return vjp_k<4>(g, st);
+    case 1: return vjp_k<1>(g, mode, st);
+    case 2: return vjp_k<2>(g, mode, st);
+    case 3: return vjp_k<3>(g, mode, st);
+    case 4: return vjp_k<4>(g, mode, st);
     default: return cudaErrorInvalidValue;
   }
 }
