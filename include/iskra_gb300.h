@@ -221,7 +221,7 @@ ig_status ig_vjp(ig_mesh* mesh, const double* V_dev, const double* B_dev, int b_
 /* gV_dev [n][3] = d( sum_i M_i(V) w_i )/dV for positions V_dev [n][3] and per-vertex weights
  * w_dev [n] (the lumped mass M_i = sum of area/3 over the faces at vertex i). This is the
  * part of a loss that depends on V through the mass directly, e.g. the M-norm loss
- * 1/2 ||T - U||_M^2 of §7.1 (Eq. for the inverse-fairing objective) with w = |T - U|^2 / 2.
+ * 1/2 ||T - U||_M^2 of the inverse-fairing objective of §7.1, with w = |T - U|^2 / 2.
  * Needs only ig_mesh_upload. Asynchronous. Errors: IG_ERR_INVALID_ARG (NULL pointer). */
 ig_status ig_mass_vjp(ig_mesh* mesh, const double* V_dev, const double* w_dev, double* gV_dev);
 
