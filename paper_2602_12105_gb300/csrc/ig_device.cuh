@@ -73,54 +73,6 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
   __syncthreads();
 }
 
-// Mixed precision: sum float per-thread partials over the CTA. Each warp adds its 32 lanes in FP32
-// with shuffles (the FP32 pipe is fast); the 8 warp sums are added in FP64. Thread 0 receives the
-// totals in v64. sh holds NV*8 doubles.
-template <int NV>
-__device__ __forceinline__ void block_sum_f32(const float (&v)[NV], double (&v64)[NV], double* sh) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    float a = v[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) sh[i * 8 + warp] = (double)a;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      double a = lane < kBlock / 32 ? sh[i * 8 + lane] : 0.0;
-#pragma unroll
-      for (int o = 4; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      v64[i] = a;
-    }
-  }
-  __syncthreads();
-}
-
-// Publish a tile's partials (already CTA-summed in thread 0's v) and return true in the last CTA
-// of the mesh, whose thread 0 then holds the mesh totals (tile order, deterministic).
-template <int NV>
-__device__ __forceinline__ bool publish_tiles(double (&v)[NV], double* part, int tile, int ntiles,
-                                              unsigned int* cnt, double* sh) {
-  __shared__ int s_last2;
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) part[tile * kPartStride + i] = v[i];
-    __threadfence();
-    const unsigned prev = atomicAdd(cnt, 1u);
-    s_last2 = (prev == (unsigned)ntiles - 1u);
-  }
-  __syncthreads();
-  if (!s_last2) return false;
-  __threadfence();
-  gather_partials<NV>(part, ntiles, v);
-  block_sum<NV>(v, sh);
-  if (threadIdx.x == 0) *cnt = 0u;
-  return true;
-}
-
 // Block-sum v, publish the tile's partials, and return true in the last CTA of the mesh, whose
 // thread 0 then holds the mesh totals (partials added in tile order, so the result does not
 // depend on which CTA finished last).
