@@ -417,6 +417,7 @@ def kernel_roofline(prof, n, m, nnz, k, precision, clocks, workload, idx32=4):
         roofline = {"bound": "hbm", "achieved": round(d["gbs"], 1), "peak": hbm_peak, "unit": "GB/s",
                     "frac": round(d["hbm_frac"], 4), "traffic": measured_traffic(dom, workload),
                     "kernel": dom, "peak_source": f"{peak_kind} (hbm_gbs copy bandwidth)",
+                    "frac_of_nominal_7900_gbs": round(d["gbs"] / 7900.0, 4),
                     "algorithmic_bytes_per_launch": int(d["bytes"])}
     table = {kname: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in kv.items()
                      if kk not in ("alu_peak", "bytes")} for kname, kv in rl_all.items()}
