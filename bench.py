@@ -162,29 +162,32 @@ def peaks():
 
 
 def algorithmic(kernel, n, m, nnz, k, prec, idx32=4):
-    """(flops, bytes) one launch of `kernel` must do / move (vectors [n][k], p rows padded to kp).
-    FP64 path: the update kernel also writes z = D^-1 r (over q), which the p-update reads instead
-    of D^-1 and r. Mixed path (pcg32_*): 4-byte values and vectors, p-update reads D^-1 and r, and
-    the SpMV reads idx32-byte column indices (2 where every slice of 32 rows keeps its columns as
-    16-bit offsets, as on the grid workloads)."""
-    sv = 8 if prec == "fp64" else 4   # value and vector element size
+    """(flops, bytes) one launch of `kernel` must do / move (vectors [k][n], p and z rows padded to
+    kp). FP64 path (pcg_*): two kernels per iteration. The SpMV gathers z = D^-1 r, forms
+    p = z + beta p and q = A z + beta q (the recurrence q = A p) and the sum p.q; the update writes
+    x, r and z. Mixed path (pcg32_*): 4-byte values and vectors, three kernels per iteration (SpMV
+    q = A p, update, p-update reading D^-1 and r), and the SpMV reads idx32-byte column indices
+    (2 where every slice of 32 rows keeps its columns as 16-bit offsets, as on the grid
+    workloads)."""
     kp = 4 if k == 3 else k
-    z_in_q = True
-    si = 4
     if kernel.startswith("pcg32_"):
-        sv = 4
-        si = idx32
-        z_in_q = False
-        kernel = "pcg_" + kernel[len("pcg32_"):]
+        sv, si = 4, idx32
+        kernel = kernel[len("pcg32_"):]
+        if kernel == "spmv":
+            return (float(2 * k * nnz + 2 * k * n),
+                    float(nnz * (sv + si) + 4 * (n + 1) + sv * kp * n + sv * k * n))
+        if kernel == "update":
+            return float(11 * k * n), float(sv * (n + 3 * k * n + kp * n) + 2 * sv * k * n)
+        if kernel == "pupdate":
+            return float(3 * k * n), float(sv * (n + k * n + kp * n) + sv * kp * n)
+        return None, None
+    sv = 8
     if kernel == "pcg_spmv":
-        flops = 2 * k * nnz + 2 * k * n
-        byts = nnz * (sv + si) + 4 * (n + 1) + sv * kp * n + sv * k * n
+        flops = 2 * k * nnz + 6 * k * n
+        byts = nnz * (sv + 4) + 4 * (n + 1) + sv * kp * n + 2 * sv * kp * n + 2 * sv * k * n
     elif kernel == "pcg_update":
-        flops = 10 * k * n + k * n
-        byts = sv * (n + 3 * k * n + kp * n) + 2 * sv * k * n + (sv * k * n if z_in_q else 0)
-    elif kernel == "pcg_pupdate":
-        flops = (2 if z_in_q else 3) * k * n
-        byts = (sv * (k * n + kp * n) if z_in_q else sv * (n + k * n + kp * n)) + sv * kp * n
+        flops = 9 * k * n
+        byts = sv * (n + kp * n + 3 * k * n) + sv * (2 * k * n + kp * n)
     elif kernel == "assemble_face":
         flops = 60 * m
         byts = 12 * m + 24 * n + 32 * m
@@ -370,13 +373,13 @@ def run_ours(args, rank, world, local_rank):
 def gpu_launches(prof, steps, its_f, its_a, launch):
     """Kernel launches of the timed region, counted from the profile pass (one host-launched
     step, every launch bracketed by events): the kernels outside the solver loops as they were
-    counted, the loop bodies as 3 kernels per iteration of the two solves (the device-side
+    counted, the loop bodies as 2 kernels per iteration of the two FP64 solves (the device-side
     loop runs exactly the iterations the solves report)."""
     if not prof:
-        return int(steps * (2 + (2 + 3 * its_f) + (2 + 3 * its_a) + 2))
-    loop = {"pcg_spmv", "pcg_update", "pcg_pupdate"}
+        return int(steps * (2 + (2 + 2 * its_f) + (2 + 2 * its_a) + 2))
+    loop = {"pcg_spmv", "pcg_update"}
     outside = sum(c for name, (c, _) in prof.items() if name not in loop)
-    per_step = outside / 3.0 + 3 * (its_f + its_a) if launch == "graph" else \
+    per_step = outside / 3.0 + 2 * (its_f + its_a) if launch == "graph" else \
         sum(c for c, _ in prof.values()) / 3.0
     return int(round(steps * per_step))
 

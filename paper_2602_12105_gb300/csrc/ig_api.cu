@@ -482,6 +482,7 @@ ig_status ig_mesh_upload(ig_ctx* ctx, const int32_t* F_dev, int64_t m, int64_t n
   UP_CK(mesh_alloc(M, &md.r, nv), "alloc");
   UP_CK(mesh_alloc(M, &md.p, nv), "alloc");
   UP_CK(mesh_alloc(M, &md.q, nv), "alloc");
+  UP_CK(mesh_alloc(M, &md.z, nv), "alloc");
   md.rhs = md.q;  // the FP64 q vector is unused in mixed precision, where it keeps the rhs
   UP_CK(mesh_alloc(M, &md.lam, nv), "alloc");
   UP_CK(mesh_alloc(M, &md.gface, 9 * (size_t)m), "alloc");
@@ -489,6 +490,8 @@ ig_status ig_mesh_upload(ig_ctx* ctx, const int32_t* F_dev, int64_t m, int64_t n
   UP_CK(mesh_alloc(M, &md.s, 1), "alloc");
   UP_CK(cudaMemsetAsync(md.s, 0, sizeof(SolveScal), st), "memset");
   UP_CK(cudaMemsetAsync(md.p, 0, sizeof(double) * nv, st), "memset");
+  UP_CK(cudaMemsetAsync(md.q, 0, sizeof(double) * nv, st), "memset");
+  UP_CK(cudaMemsetAsync(md.z, 0, sizeof(double) * nv, st), "memset");
   UP_CK(group_init(M->group, &md, 1, ctx->solver_slots, ctx->solver_slots32, st), "group");
   UP_CK(cudaStreamSynchronize(st), "upload");
 #undef UP_CK

@@ -112,6 +112,21 @@ __device__ __forceinline__ void load_row(const double* __restrict__ p, long row,
   }
 }
 
+// Row store into a padded [n][KP] vector (16-byte stores where the row allows).
+template <int K>
+__device__ __forceinline__ void store_row(double* __restrict__ p, long row, const double (&v)[K]) {
+  if constexpr (K == 3 || K == 4) {
+    double2* q = reinterpret_cast<double2*>(p + row * KP<K>::v);
+    q[0] = make_double2(v[0], v[1]);
+    if constexpr (K == 4) q[1] = make_double2(v[2], v[3]);
+    else p[row * 4 + 2] = v[2];
+  } else if constexpr (K == 2) {
+    reinterpret_cast<double2*>(p + row * 2)[0] = make_double2(v[0], v[1]);
+  } else {
+    p[row] = v[0];
+  }
+}
+
 template <int K>
 __device__ __forceinline__ void load_row32(const float* __restrict__ p, long row, float (&v)[K]);
 

@@ -109,11 +109,12 @@ struct MeshDev {
   double* M;
   double* Dinv;
   float* Dinv32;
-  // FP64 solver vectors
+  // FP64 solver vectors: x, r, q [k][n]; p and z = D^-1 r [n][KP] (rows padded for the gathers)
   double* x;
   double* r;
   double* p;
   double* q;
+  double* z;
   // mixed-precision inner vectors
   float* x32;
   float* r32;

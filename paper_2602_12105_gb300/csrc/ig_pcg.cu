@@ -2,12 +2,13 @@
 // solved together (the matrix is read once per iteration for all columns), on a group of one or
 // more meshes (the forward solve of §7.1 and the adjoint solve of §5.2 use the same operator).
 //
-// One iteration is three kernels over tiles of kTileRows rows (a tile belongs to one mesh):
-//   spmv   : q = A p for the tile's rows, partial p.q  -> last tile of the mesh: alpha = rz / pq
-//   update : x += alpha p, r -= alpha q, partial r.z and r.r with z = D^-1 r recomputed
+// One iteration is two kernels over tiles of up to kTileRows rows (a tile belongs to one mesh):
+//   spmv   : p = z + beta p, q = A p = A z + beta q (the product carried by its recurrence, so
+//            that the direction update needs no pass of its own), partial p.q
+//            -> last tile of the mesh: alpha = rz / pq
+//   update : x += alpha p, r -= alpha q, z = D^-1 r, partial r.z and r.r
 //            -> last tile of the mesh: convergence test, beta = rz_new / rz
 //            -> last CTA of the launch: loop control (all meshes done or the cap reached)
-//   pupdate: p = D^-1 r + beta p
 // Reductions are deterministic: every CTA writes its partial sums, the last CTA of a mesh (found
 // with a counter) adds the partials in tile order. No atomics touch floating-point data, so a mesh
 // gives the same bits alone and inside a batch.
@@ -97,7 +98,7 @@ __device__ __noinline__ void finish_update(SolveScal* s, int k, const double* ac
 }
 
 // ------------------------------------------------------------------------------- init
-// rhs = M * in (rhs_mass) or in; x = 0; r = rhs; p = z = D^-1 r; per mesh: rz, ||rhs||^2.
+// rhs = M * in (rhs_mass) or in; x = 0; r = rhs; z = D^-1 r; p = q = 0; per mesh: rz, ||rhs||^2.
 template <int K>
 __global__ void __launch_bounds__(kBlock) init_kernel(const MeshDev* __restrict__ mds, const int2* __restrict__ tiles,
                                                       IoTable io, int rhs_mass, LoopCtl* ctl, double tol,
@@ -132,7 +133,9 @@ __global__ void __launch_bounds__(kBlock) init_kernel(const MeshDev* __restrict_
         const double z = dinv * b;
         md.x[c * nn + row] = 0.0;
         md.r[c * nn + row] = b;
-        md.p[row * KP<K>::v + c] = z;
+        md.z[row * KP<K>::v + c] = z;
+        md.p[row * KP<K>::v + c] = 0.0;  // with beta = 0 the first SpMV sets p = z, q = A z
+        md.q[c * nn + row] = 0.0;
         acc[c] = fma(b, z, acc[c]);
         acc[K + c] = fma(b, b, acc[K + c]);
       }
@@ -143,14 +146,20 @@ __global__ void __launch_bounds__(kBlock) init_kernel(const MeshDev* __restrict_
 }
 
 // ------------------------------------------------------------------------------- spmv
-// q = A p and the tile's sums p.q, over the rows of one tile (t0..t1).
+// The search direction and its product with A in one pass, for the rows of one tile (t0..t1):
+// p = z + beta p and q = A p = A z + beta q (z = D^-1 r from the update kernel; A z gathers z),
+// and the tile's sums p.q. Carrying q = A p by this recurrence removes the separate p-update
+// pass of the textbook iteration (its p = z + beta p happens here), so an iteration is two
+// kernels. beta = 0 at the start of a solve (p = q = 0 there), so the first pass is q = A z.
 template <int K>
-__device__ __forceinline__ void spmv_tile(const MeshDev& md, int tile, double* red, double* out) {
+__device__ __forceinline__ void spmv_tile(const MeshDev& md, int tile, const ScalSnap& sn, double* red,
+                                          double* out) {
   const long nn = md.n;
   const long t0 = (long)tile * md.tile_rows;
   const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
   const double* __restrict__ A = md.A;
-  const double* __restrict__ p = md.p;
+  const double* __restrict__ z = md.z;
+  double* __restrict__ p = md.p;
   double* __restrict__ q = md.q;
   double pq[K];
 #pragma unroll
@@ -159,14 +168,21 @@ __device__ __forceinline__ void spmv_tile(const MeshDev& md, int tile, double* r
   for (int rr = 0; rr < kRowsPerThread; ++rr) {
     const long row = t0 + rr * kBlock + threadIdx.x;
     if (row < t1) {
-      double acc[K];
-      row_product<K>(md, A, row, GatherP64<K>{p}, acc);
-      double pi[K];
+      double w[K];
+      row_product<K>(md, A, row, GatherP64<K>{z}, w);
+      double zi[K], pi[K], qi[K];
+      load_row<K>(z, row, zi);
       load_row<K>(p, row, pi);
 #pragma unroll
+      for (int c = 0; c < K; ++c) qi[c] = q[c * nn + row];
+#pragma unroll
       for (int c = 0; c < K; ++c) {
-        q[c * nn + row] = acc[c];
-        pq[c] = fma(pi[c], acc[c], pq[c]);
+        const double b = sn.beta[c];
+        const double pn = fma(b, pi[c], zi[c]);
+        const double qn = fma(b, qi[c], w[c]);
+        p[row * KP<K>::v + c] = pn;
+        q[c * nn + row] = qn;
+        pq[c] = fma(pn, qn, pq[c]);
       }
     }
   }
@@ -178,14 +194,14 @@ __global__ void __launch_bounds__(kBlock, 4) spmv_kernel(const MeshDev* __restri
   __shared__ TileCtx tc;
   tile_loop<K>(
       mds, L, 0, 0, tc, [](const ScalSnap& x) { return !x.done; },
-      [&](const MeshDev& md, int tile, double* red, double* out) { spmv_tile<K>(md, tile, red, out); },
+      [&](const MeshDev& md, int tile, double* red, double* out) { spmv_tile<K>(md, tile, tc.sn, red, out); },
       [](const MeshDev& md, const double* v) { finish_spmv(md.s, K, v); });
 }
 
 // ------------------------------------------------------------------------------- update
-// x += alpha p, r -= alpha q, z = D^-1 r (written over q, which the next SpMV rewrites) and the
-// tile's sums r.z, r.r; a row's loads are issued before its stores. (FP64 arithmetic bounds this
-// kernel, so rows are not batched further.)
+// x += alpha p, r -= alpha q, z = D^-1 r (rows padded like p, for the next SpMV's gathers) and the
+// tile's sums r.z, r.r; a row's loads are issued before its stores. Rows are taken one at a time:
+// FP64 arithmetic bounds this kernel, and unrolling the row loop only spills at 64 registers.
 template <int K>
 __device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const ScalSnap& sn, double* red,
                                             double* out) {
@@ -197,10 +213,11 @@ __device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const S
   for (int i = 0; i < 2 * K; ++i) acc[i] = 0.0;
   const double* __restrict__ Dinv = md.Dinv;
   const double* __restrict__ p = md.p;
-  double* __restrict__ q = md.q;
+  const double* __restrict__ q = md.q;
+  double* __restrict__ zv = md.z;
   double* __restrict__ x = md.x;
   double* __restrict__ r = md.r;
-#pragma unroll
+#pragma unroll 1
   for (int rr = 0; rr < kRowsPerThread; ++rr) {
     const int row = t0 + rr * kBlock + threadIdx.x;
     if (row < t1) {
@@ -213,17 +230,18 @@ __device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const S
         qs[c] = q[(long)c * nn + row];
         rs[c] = r[(long)c * nn + row];
       }
+      double zo[K];
 #pragma unroll
       for (int c = 0; c < K; ++c) {
         const double a = sn.alpha[c];
         const double rn = fma(-a, qs[c], rs[c]);
-        const double z = d * rn;
+        zo[c] = d * rn;
         x[(long)c * nn + row] = fma(a, pi[c], xs[c]);
         r[(long)c * nn + row] = rn;
-        q[(long)c * nn + row] = z;  // q is dead until the next SpMV: it carries z to pupdate
-        acc[c] = fma(rn, z, acc[c]);
+        acc[c] = fma(rn, zo[c], acc[c]);
         acc[K + c] = fma(rn, rn, acc[K + c]);
       }
+      store_row<K>(zv, row, zo);
     }
   }
   tile_reduce<2 * K>(acc, red, out);
@@ -238,44 +256,6 @@ __global__ void __launch_bounds__(kBlock, 4) update_kernel(const MeshDev* __rest
       [&](const MeshDev& md, int tile, double* red, double* out) { update_tile<K>(md, tile, tc.sn, red, out); },
       [](const MeshDev& md, const double* v) { finish_update(md.s, K, v); });
   loop_control(mds, ctl, handle, use_graph);
-}
-
-// ------------------------------------------------------------------------------- pupdate
-// p = z + beta p with z = D^-1 r from the update kernel (kept in q); all of a thread's loads are
-// issued before its stores.
-template <int K>
-__global__ void __launch_bounds__(kBlock, 4) pupdate_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L) {
-  __shared__ TileCtx tc;
-  tile_loop_plain(mds, L, 0, tc, [](const ScalSnap& x) { return !x.done; },
-                  [&](const MeshDev& md, int tile) {
-                    const long nn = md.n;
-                    const long t0 = (long)tile * md.tile_rows;
-                    const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
-                    const double* __restrict__ z = md.q;
-                    double* __restrict__ p = md.p;
-                    constexpr int RB = kRowsPerThread;
-#pragma unroll
-                    for (int r0 = 0; r0 < kRowsPerThread; r0 += RB) {
-                      double pi[RB][K], zs[RB][K];
-#pragma unroll
-                      for (int u = 0; u < RB; ++u) {
-                        const long row = t0 + (r0 + u) * kBlock + threadIdx.x;
-                        if (row < t1) {
-                          load_row<K>(p, row, pi[u]);
-#pragma unroll
-                          for (int c = 0; c < K; ++c) zs[u][c] = z[c * nn + row];
-                        }
-                      }
-#pragma unroll
-                      for (int u = 0; u < RB; ++u) {
-                        const long row = t0 + (r0 + u) * kBlock + threadIdx.x;
-                        if (row < t1) {
-#pragma unroll
-                          for (int c = 0; c < K; ++c) p[row * KP<K>::v + c] = fma(tc.sn.beta[c], pi[u][c], zs[u][c]);
-                        }
-                      }
-                    }
-                  });
 }
 
 // ------------------------------------------------------------------------------- true residual
@@ -339,7 +319,6 @@ cudaError_t build_plan(Group& g, SolvePlan& pl) {
   if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
   spmv_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.list64);
   update_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.list64, handle, 1);
-  pupdate_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.list64);
   cudaError_t le = cudaGetLastError();
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(cs, &captured);
@@ -376,10 +355,6 @@ cudaError_t host_loop_k(Group& g, int max_it, int poll, cudaStream_t st) {
     {
       IG_PROF("pcg_update", st);
       update_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.ctl, g.list64, cudaGraphConditionalHandle{}, 0);
-    }
-    {
-      IG_PROF("pcg_pupdate", st);
-      pupdate_kernel<K><<<g.grid64, kBlock, 0, st>>>(g.mds, g.ctl, g.list64);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -510,12 +485,10 @@ cudaError_t group_end(Group& g, int k, const IoTable& io, cudaStream_t st) {
 
 
 int solver_blocks_per_sm() {
-  int a = 0, b = 0, c = 0;
+  int a = 0, b = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, spmv_kernel<3>, kBlock, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, update_kernel<3>, kBlock, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, pupdate_kernel<3>, kBlock, 0);
-  int m = a < b ? a : b;
-  m = m < c ? m : c;
+  const int m = a < b ? a : b;
   return m > 0 ? m : 1;
 }
 
@@ -685,7 +658,8 @@ constexpr size_t kNaX = align256(kNaDinv + sizeof(double) * kNoAllocMaxRows);
 constexpr size_t kNaR = align256(kNaX + kNaVec);
 constexpr size_t kNaP = align256(kNaR + kNaVec);
 constexpr size_t kNaQ = align256(kNaP + kNaVec);
-constexpr size_t kNaList = align256(kNaQ + kNaVec);   // active lists of the one mesh: 8 ints
+constexpr size_t kNaZ = align256(kNaQ + kNaVec);
+constexpr size_t kNaList = align256(kNaZ + kNaVec);   // active lists of the one mesh: 8 ints
 constexpr size_t kNaStart = align256(kNaList + sizeof(int) * 8);
 constexpr size_t kNoAllocBytes = align256(kNaStart + sizeof(int4) * (kNoAllocMaxTiles + 1));
 
@@ -767,6 +741,7 @@ extern "C" ig_status ig_solve_csr_noalloc(const int32_t* rowptr_dev, const int32
   md.r = reinterpret_cast<double*>(base + kNaR);
   md.p = reinterpret_cast<double*>(base + kNaP);
   md.q = reinterpret_cast<double*>(base + kNaQ);
+  md.z = reinterpret_cast<double*>(base + kNaZ);
   md.part = reinterpret_cast<double*>(base + kNaPart);
   md.s = reinterpret_cast<SolveScal*>(base + kNaScal);
   md.err = reinterpret_cast<int*>(base + kNaErr);
