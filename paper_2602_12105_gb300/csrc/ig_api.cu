@@ -442,10 +442,10 @@ ig_status ig_mesh_upload(ig_ctx* ctx, const int32_t* F_dev, int64_t m, int64_t n
   md.n = ni;
   md.m = mi;
   md.nnz = nnz;
-  // Solver tiles (256..1024 rows, whole warps): a mesh that fills the GPU gets a tile count that
-  // is a whole multiple of the resident CTA slots S of the solver kernels, so every launch ends in
-  // full waves; a smaller mesh gets tiles of 256 rows so that it still spreads over the SMs. The
-  // choice depends on n and the device only, never on a batch.
+  // Solver tiles (whole warps, at least kBlock rows): the choice depends on n and the device only,
+  // never on a batch.
+  // Mixed precision: 256..1024 rows; a mesh that fills the GPU gets a tile count that is a whole
+  // multiple of the resident CTA slots S of the solver kernels, so every launch ends in full waves.
   auto choose_tiles = [ni](long S, int& tile_rows, int& ntiles) {
     if (S < 1) S = 1;
     long waves = ((long)ni + S * kTileRows - 1) / (S * kTileRows);
@@ -457,7 +457,32 @@ ig_status ig_mesh_upload(ig_ctx* ctx, const int32_t* F_dev, int64_t m, int64_t n
     tile_rows = (int)rows;
     ntiles = (int)(((long)ni + rows - 1) / rows);
   };
-  choose_tiles(ctx->solver_slots, md.tile_rows, md.ntiles);
+  // FP64: a CTA takes a tile in passes of kBlock rows (one row per thread), and its warps meet at
+  // the tile's reduction, so a last pass that is only partly filled leaves most warps waiting.
+  // For w waves of tiles (rows = n / (S w), at most kTileRows64) a CTA makes w * ceil(rows /
+  // kBlock) passes; the tiling takes the w with the fewest passes, counting each tile's
+  // reduction as a quarter pass. 1,048,576 rows on 608 slots: one wave of 1728-row tiles
+  // (7 passes) where two waves of 864-row tiles took 2 x 4.
+  auto choose_tiles64 = [ni](long S, int& tile_rows, int& ntiles) {
+    if (S < 1) S = 1;
+    long w0 = ((long)ni + S * kTileRows64 - 1) / (S * kTileRows64);
+    if (w0 < 1) w0 = 1;
+    long best_rows = kBlock, best_cost = -1;
+    for (long w = w0; w < w0 + 64; ++w) {
+      long r = ((long)ni + S * w - 1) / (S * w);
+      r = (r + 31) / 32 * 32;
+      if (r < kBlock) r = kBlock;
+      const long cost = 4 * w * ((r + kBlock - 1) / kBlock) + w;  // in quarter passes
+      if (best_cost < 0 || cost < best_cost) {
+        best_cost = cost;
+        best_rows = r;
+      }
+      if (r == kBlock) break;  // more waves only add passes
+    }
+    tile_rows = (int)best_rows;
+    ntiles = (int)(((long)ni + best_rows - 1) / best_rows);
+  };
+  choose_tiles64(ctx->solver_slots, md.tile_rows, md.ntiles);
   choose_tiles(ctx->solver_slots32, md.tile_rows32, md.ntiles32);
   md.nnz_sell = nnz_sell;
   md.sell_w = sell_w;

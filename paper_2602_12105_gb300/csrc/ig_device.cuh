@@ -765,13 +765,9 @@ __global__ void __launch_bounds__(kBlock) finalize_kernel(const MeshDev* __restr
   const long t0 = (long)tl.y * md.tile_rows;
   const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
   double* __restrict__ out = io.out[tl.x];
+  for (long row = t0 + threadIdx.x; row < t1; row += kBlock) {
 #pragma unroll
-  for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const long row = t0 + rr * kBlock + threadIdx.x;
-    if (row < t1) {
-#pragma unroll
-      for (int c = 0; c < K; ++c) out[row * K + c] = md.x[c * nn + row];
-    }
+    for (int c = 0; c < K; ++c) out[row * K + c] = md.x[c * nn + row];
   }
 }
 

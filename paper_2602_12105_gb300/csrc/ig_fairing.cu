@@ -28,21 +28,17 @@ __global__ void __launch_bounds__(kBlock) mnorm_kernel(const MeshDev* __restrict
   const long t0 = (long)tl.y * md.tile_rows;
   const long t1 = t0 + md.tile_rows < nn ? t0 + md.tile_rows : nn;
   double acc[1] = {0.0};
+  for (long row = t0 + threadIdx.x; row < t1; row += kBlock) {
+    const double m = md.M[row];
+    double e = 0.0;
 #pragma unroll
-  for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const long row = t0 + rr * kBlock + threadIdx.x;
-    if (row < t1) {
-      const double m = md.M[row];
-      double e = 0.0;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double d = U[3 * row + c] - T[3 * row + c];
-        G[3 * row + c] = m * d;
-        e = fma(d, d, e);
-      }
-      w[row] = 0.5 * e;
-      acc[0] = fma(m, 0.5 * e, acc[0]);
+    for (int c = 0; c < 3; ++c) {
+      const double d = U[3 * row + c] - T[3 * row + c];
+      G[3 * row + c] = m * d;
+      e = fma(d, d, e);
     }
+    w[row] = 0.5 * e;
+    acc[0] = fma(m, 0.5 * e, acc[0]);
   }
   if (reduce_tiles<1>(acc, md.part, tl.y, md.ntiles, &md.s->cnt[2], sh) && threadIdx.x == 0) *loss = acc[0];
 }

@@ -32,8 +32,10 @@
 namespace ig {
 
 constexpr int kBlock = 256;          // threads per CTA of every row- or face-parallel kernel
-constexpr int kRowsPerThread = 4;    // rows per thread in the solver kernels
+constexpr int kRowsPerThread = 4;    // rows per thread in the mixed-precision solver kernels
 constexpr int kTileRows = kBlock * kRowsPerThread;
+constexpr int kMaxPasses64 = 8;      // FP64 solver tiles: at most 8 passes of kBlock rows
+constexpr int kTileRows64 = kBlock * kMaxPasses64;
 constexpr int kMaxK = 4;
 constexpr int kPartStride = 8;       // doubles per tile in the partial-sum arrays
 
@@ -85,7 +87,7 @@ enum : int {
 // that a batch of meshes is a list of these).
 struct MeshDev {
   int n, m, nnz, ntiles;   // ntiles = ceil(n / tile_rows)
-  int tile_rows;           // rows per FP64 solver tile (<= kTileRows, a multiple of 32), chosen at upload
+  int tile_rows;           // rows per FP64 solver tile (<= kTileRows64, a multiple of 32), chosen at upload
   int ntiles32, tile_rows32;  // the same for the mixed-precision kernels (their own occupancy)
   int nnz_sell;            // stored entries of the sliced layout (0: A is plain CSR on rowptr/col)
   int sell_w;              // every slice has this many entries per row (0: widths differ)

@@ -18,7 +18,7 @@
 // polls nor synchronises per iteration. Every loop is bounded by a hard cap.
 //
 // FP64 instructions are the scarce resource of this GPU (2 FP64 FMA per clock per SM). Each thread
-// handles kRowsPerThread rows so the block reductions, which cost FP64 adds, are amortised.
+// handles several rows of a tile so the block reductions, which cost FP64 adds, are amortised.
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -121,24 +121,20 @@ __global__ void __launch_bounds__(kBlock) init_kernel(const MeshDev* __restrict_
   double acc[2 * K];
 #pragma unroll
   for (int i = 0; i < 2 * K; ++i) acc[i] = 0.0;
+  for (long row = t0 + threadIdx.x; row < t1; row += kBlock) {
+    const double dinv = md.Dinv[row];
+    const double mass = rhs_mass ? md.M[row] : 1.0;
 #pragma unroll
-  for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const long row = t0 + rr * kBlock + threadIdx.x;
-    if (row < t1) {
-      const double dinv = md.Dinv[row];
-      const double mass = rhs_mass ? md.M[row] : 1.0;
-#pragma unroll
-      for (int c = 0; c < K; ++c) {
-        const double b = rhs_mass ? mass * src[row * K + c] : src[row * K + c];
-        const double z = dinv * b;
-        md.x[c * nn + row] = 0.0;
-        md.r[c * nn + row] = b;
-        md.z[row * KP<K>::v + c] = z;
-        md.p[row * KP<K>::v + c] = 0.0;  // with beta = 0 the first SpMV sets p = z, q = A z
-        md.q[c * nn + row] = 0.0;
-        acc[c] = fma(b, z, acc[c]);
-        acc[K + c] = fma(b, b, acc[K + c]);
-      }
+    for (int c = 0; c < K; ++c) {
+      const double b = rhs_mass ? mass * src[row * K + c] : src[row * K + c];
+      const double z = dinv * b;
+      md.x[c * nn + row] = 0.0;
+      md.r[c * nn + row] = b;
+      md.z[row * KP<K>::v + c] = z;
+      md.p[row * KP<K>::v + c] = 0.0;  // with beta = 0 the first SpMV sets p = z, q = A z
+      md.q[c * nn + row] = 0.0;
+      acc[c] = fma(b, z, acc[c]);
+      acc[K + c] = fma(b, b, acc[K + c]);
     }
   }
   if (reduce_tiles<2 * K>(acc, md.part, tl.y, md.ntiles, &md.s->cnt[2], sh) && threadIdx.x == 0)
@@ -164,26 +160,22 @@ __device__ __forceinline__ void spmv_tile(const MeshDev& md, int tile, const Sca
   double pq[K];
 #pragma unroll
   for (int c = 0; c < K; ++c) pq[c] = 0.0;
+  for (long row = t0 + threadIdx.x; row < t1; row += kBlock) {
+    double w[K];
+    row_product<K>(md, A, row, GatherP64<K>{z}, w);
+    double zi[K], pi[K], qi[K];
+    load_row<K>(z, row, zi);
+    load_row<K>(p, row, pi);
 #pragma unroll
-  for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const long row = t0 + rr * kBlock + threadIdx.x;
-    if (row < t1) {
-      double w[K];
-      row_product<K>(md, A, row, GatherP64<K>{z}, w);
-      double zi[K], pi[K], qi[K];
-      load_row<K>(z, row, zi);
-      load_row<K>(p, row, pi);
+    for (int c = 0; c < K; ++c) qi[c] = q[c * nn + row];
 #pragma unroll
-      for (int c = 0; c < K; ++c) qi[c] = q[c * nn + row];
-#pragma unroll
-      for (int c = 0; c < K; ++c) {
-        const double b = sn.beta[c];
-        const double pn = fma(b, pi[c], zi[c]);
-        const double qn = fma(b, qi[c], w[c]);
-        p[row * KP<K>::v + c] = pn;
-        q[c * nn + row] = qn;
-        pq[c] = fma(pn, qn, pq[c]);
-      }
+    for (int c = 0; c < K; ++c) {
+      const double b = sn.beta[c];
+      const double pn = fma(b, pi[c], zi[c]);
+      const double qn = fma(b, qi[c], w[c]);
+      p[row * KP<K>::v + c] = pn;
+      q[c * nn + row] = qn;
+      pq[c] = fma(pn, qn, pq[c]);
     }
   }
   tile_reduce<K>(pq, red, out);
@@ -218,31 +210,28 @@ __device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const S
   double* __restrict__ x = md.x;
   double* __restrict__ r = md.r;
 #pragma unroll 1
-  for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const int row = t0 + rr * kBlock + threadIdx.x;
-    if (row < t1) {
-      double pi[K], xs[K], qs[K], rs[K];
-      const double d = Dinv[row];
-      load_row<K>(p, row, pi);
+  for (int row = t0 + threadIdx.x; row < t1; row += kBlock) {
+    double pi[K], xs[K], qs[K], rs[K];
+    const double d = Dinv[row];
+    load_row<K>(p, row, pi);
 #pragma unroll
-      for (int c = 0; c < K; ++c) {
-        xs[c] = x[(long)c * nn + row];
-        qs[c] = q[(long)c * nn + row];
-        rs[c] = r[(long)c * nn + row];
-      }
-      double zo[K];
-#pragma unroll
-      for (int c = 0; c < K; ++c) {
-        const double a = sn.alpha[c];
-        const double rn = fma(-a, qs[c], rs[c]);
-        zo[c] = d * rn;
-        x[(long)c * nn + row] = fma(a, pi[c], xs[c]);
-        r[(long)c * nn + row] = rn;
-        acc[c] = fma(rn, zo[c], acc[c]);
-        acc[K + c] = fma(rn, rn, acc[K + c]);
-      }
-      store_row<K>(zv, row, zo);
+    for (int c = 0; c < K; ++c) {
+      xs[c] = x[(long)c * nn + row];
+      qs[c] = q[(long)c * nn + row];
+      rs[c] = r[(long)c * nn + row];
     }
+    double zo[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const double a = sn.alpha[c];
+      const double rn = fma(-a, qs[c], rs[c]);
+      zo[c] = d * rn;
+      x[(long)c * nn + row] = fma(a, pi[c], xs[c]);
+      r[(long)c * nn + row] = rn;
+      acc[c] = fma(rn, zo[c], acc[c]);
+      acc[K + c] = fma(rn, rn, acc[K + c]);
+    }
+    store_row<K>(zv, row, zo);
   }
   tile_reduce<2 * K>(acc, red, out);
 }
@@ -274,19 +263,15 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(const MeshDev* __restr
   double acc[K];
 #pragma unroll
   for (int c = 0; c < K; ++c) acc[c] = 0.0;
+  for (long row = t0 + threadIdx.x; row < t1; row += kBlock) {
+    double ax[K];
+    row_product<K>(md, md.A, row, GatherAoS64<K>{xs}, ax);
+    const double mass = rhs_mass ? md.M[row] : 1.0;
 #pragma unroll
-  for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const long row = t0 + rr * kBlock + threadIdx.x;
-    if (row < t1) {
-      double ax[K];
-      row_product<K>(md, md.A, row, GatherAoS64<K>{xs}, ax);
-      const double mass = rhs_mass ? md.M[row] : 1.0;
-#pragma unroll
-      for (int c = 0; c < K; ++c) {
-        const double b = rhs_mass ? mass * src[row * K + c] : src[row * K + c];
-        const double res = b - ax[c];
-        acc[c] = fma(res, res, acc[c]);
-      }
+    for (int c = 0; c < K; ++c) {
+      const double b = rhs_mass ? mass * src[row * K + c] : src[row * K + c];
+      const double res = b - ax[c];
+      acc[c] = fma(res, res, acc[c]);
     }
   }
   if (reduce_tiles<K>(acc, md.part, tl.y, md.ntiles, &md.s->cnt[2], sh) && threadIdx.x == 0) {

@@ -16,7 +16,7 @@ def rel2(a, b):
 
 
 def case(name, seed=0, k=3):
-    """Small cases that the oracle solves in seconds. Several span more than one 1024-row tile
+    """Small cases that the oracle solves in seconds. Several span more than one 256-row tile
     with a ragged last tile (grid61x53: 3233 rows; ico5: 10242 rows)."""
     rng = np.random.default_rng(seed)
     if name == "tetra":

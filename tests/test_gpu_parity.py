@@ -2,7 +2,7 @@
 
 Tolerances (FP64 path): pattern bit-exact; A and M within 1e-12 of max|.|; U, Lambda-driven
 gradients gV, gB and dl/dt within 1e-10 relative 2-norm when both sides solve to 1e-13 or
-tighter. Sizes span several 1024-row tiles with a ragged last tile.
+tighter. Sizes span several 256-row tiles with a ragged last tile.
 """
 import numpy as np
 import pytest
