@@ -398,7 +398,7 @@ __device__ __forceinline__ void load_mesh(const MeshDev* __restrict__ mds, int i
 // (G = gridDim.x). A tile's sums go to the mesh's part[tile]; each CTA counts the tiles it did
 // per run of consecutive tiles of one mesh and adds that count to the mesh's counter with one
 // atomic. The CTA whose addition completes the mesh adds the partials in tile order
-// (deterministic, independent of G and of any batch) and calls finish(md, totals) on thread 0.
+// (deterministic, independent of G and of any batch) and calls finish(md, totals) on warp 0.
 template <int NV, typename Finish>
 __device__ __forceinline__ void flush_tiles(TileCtx& tc, int tiling, unsigned run, int cnt_idx,
                                             const Finish& finish) {
@@ -418,8 +418,8 @@ __device__ __forceinline__ void flush_tiles(TileCtx& tc, int tiling, unsigned ru
     gather_partials<NV>(tc.md.part, ntiles, v);
     tile_reduce<NV>(v, tc.red[0], tc.tot);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      *cnt = 0u;
+    if (threadIdx.x < 32) {
+      if (threadIdx.x == 0) *cnt = 0u;
       finish(tc.md, tc.tot);
     }
   }
@@ -740,18 +740,25 @@ __device__ __forceinline__ void load_row32(const float* __restrict__ p, long row
   }
 }
 
-// alpha_c = rz_c / (p_c . q_c) for active columns.
+// alpha_c = rz_c / (p_c . q_c) for active columns. The finish steps run on the 32 lanes of warp 0
+// of the CTA that completes a mesh: lane c handles column c (its divisions and square roots
+// run side by side instead of one after another on one thread), lane 0 the mesh's own fields.
 __device__ __noinline__ void finish_spmv(SolveScal* s, int k, const double* pq) {
-  for (int c = 0; c < k; ++c) {
+  const int c = threadIdx.x & 31;
+  int bad = 0;
+  if (c < k) {
     if (s->active[c] == 0) {
       s->alpha[c] = 0.0;
     } else if (!positive_finite(pq[c])) {
       s->alpha[c] = 0.0;
-      s->status = IG_ERR_NONFINITE;
-      s->done = 1;
+      bad = 1;
     } else {
       s->alpha[c] = s->rz[c] / pq[c];
     }
+  }
+  if (__any_sync(0xffffffffu, bad) && c == 0) {
+    s->status = IG_ERR_NONFINITE;
+    s->done = 1;
   }
 }
 

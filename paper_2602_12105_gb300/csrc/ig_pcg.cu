@@ -63,37 +63,42 @@ __device__ __noinline__ void finish_init(SolveScal* s, int k, const double* acc,
   s->done = (bad != 0 || nact == 0) ? 1 : 0;
 }
 
-// Convergence test per column (recursive residual), beta_c = rz_new / rz, iteration count.
+// Convergence test per column (recursive residual), beta_c = rz_new / rz, iteration count. Runs on
+// warp 0 of the CTA that completes the mesh: lane c takes column c, lane 0 the mesh's fields.
 __device__ __noinline__ void finish_update(SolveScal* s, int k, const double* acc) {
-  int nact = 0, bad = 0;
-  for (int c = 0; c < k; ++c) {
-    if (s->active[c] == 0) continue;
+  const int c = threadIdx.x & 31;
+  int act = 0, bad = 0;
+  if (c < k && s->active[c] != 0) {
     const double rzn = acc[c], rr = acc[k + c];
     if (!is_finite(rzn) || !is_finite(rr)) {
       bad = 1;
-      continue;
-    }
-    const double rel = sqrt(rr / s->bnorm2[c]);
-    s->relres[c] = rel;
-    if (rel <= s->tol) {
-      s->active[c] = 0;
-      s->beta[c] = 0.0;
     } else {
-      s->beta[c] = rzn / s->rz[c];
-      s->rz[c] = rzn;
-      nact += 1;
+      const double rel = sqrt(rr / s->bnorm2[c]);
+      s->relres[c] = rel;
+      if (rel <= s->tol) {
+        s->active[c] = 0;
+        s->beta[c] = 0.0;
+      } else {
+        s->beta[c] = rzn / s->rz[c];
+        s->rz[c] = rzn;
+        act = 1;
+      }
     }
   }
-  const int it = s->iter + 1;
-  s->iter = it;
-  if (bad) {
-    s->status = IG_ERR_NONFINITE;
-    s->done = 1;
-  } else if (nact == 0) {
-    s->done = 1;
-  } else if (it >= s->max_iter) {
-    s->status = IG_ERR_NOT_CONVERGED;
-    s->done = 1;
+  const int nact = __popc(__ballot_sync(0xffffffffu, act));
+  const int anybad = __any_sync(0xffffffffu, bad);
+  if (c == 0) {
+    const int it = s->iter + 1;
+    s->iter = it;
+    if (anybad) {
+      s->status = IG_ERR_NONFINITE;
+      s->done = 1;
+    } else if (nact == 0) {
+      s->done = 1;
+    } else if (it >= s->max_iter) {
+      s->status = IG_ERR_NOT_CONVERGED;
+      s->done = 1;
+    }
   }
 }
 

@@ -63,84 +63,100 @@ __device__ __noinline__ void finish_init_mixed(SolveScal* s, int k, const double
   s->done = (bad || nact == 0) ? 1 : 0;
 }
 
+// The finish steps below run on the 32 lanes of warp 0 of the CTA that completes a mesh: lane c
+// handles column c, lane 0 the mesh's own fields (written after the warp's votes).
+
 // After r64 = rhs - A64 x64: FP64 convergence test per column, the scale of the next inner
 // right-hand side, and the refinement cap.
 __device__ __noinline__ void finish_residual(SolveScal* s, int k, const double* res2) {
-  int nact = 0, bad = 0;
-  s->refine = s->refine + 1;
-  for (int c = 0; c < k; ++c) {
-    if (s->active64[c] == 0) continue;
+  const int c = threadIdx.x & 31;
+  const int refine = s->refine + 1;
+  int act = 0, bad = 0;
+  if (c < k && s->active64[c] != 0) {
     if (!is_finite(res2[c])) {
       bad = 1;
-      continue;
-    }
-    const double rel = sqrt(res2[c] / s->rhs2[c]);
-    s->relres[c] = rel;
-    if (rel <= s->tol || !positive_finite(res2[c])) {
-      s->active64[c] = 0;
     } else {
-      s->scale[c] = sqrt(res2[c]);
-      nact += 1;
+      const double rel = sqrt(res2[c] / s->rhs2[c]);
+      s->relres[c] = rel;
+      if (rel <= s->tol || !positive_finite(res2[c])) {
+        s->active64[c] = 0;
+      } else {
+        s->scale[c] = sqrt(res2[c]);
+        act = 1;
+      }
     }
   }
-  if (bad) {
-    s->status = IG_ERR_NONFINITE;
-    s->done = 1;
-  } else if (nact == 0) {
-    s->done = 1;
-  } else if (s->refine >= s->max_refine || s->iter >= s->max_iter) {
-    s->status = IG_ERR_NOT_CONVERGED;
-    s->done = 1;
-  } else {
-    s->phase = kPhaseRestart;
+  const int nact = __popc(__ballot_sync(0xffffffffu, act));
+  const int anybad = __any_sync(0xffffffffu, bad);
+  if (c == 0) {
+    s->refine = refine;
+    if (anybad) {
+      s->status = IG_ERR_NONFINITE;
+      s->done = 1;
+    } else if (nact == 0) {
+      s->done = 1;
+    } else if (refine >= s->max_refine || s->iter >= s->max_iter) {
+      s->status = IG_ERR_NOT_CONVERGED;
+      s->done = 1;
+    } else {
+      s->phase = kPhaseRestart;
+    }
   }
 }
 
 // After forming r32 = r64 / scale: start a new inner solve.
 __device__ __noinline__ void finish_restart(SolveScal* s, int k, const double* acc) {
-  int nact = 0;
-  for (int c = 0; c < k; ++c) {
-    const int act = (s->active64[c] && positive_finite(acc[k + c])) ? 1 : 0;
+  const int c = threadIdx.x & 31;
+  int act = 0;
+  if (c < k) {
+    act = (s->active64[c] && positive_finite(acc[k + c])) ? 1 : 0;
     s->active[c] = act;
     s->rz[c] = acc[c];
     s->bnorm2[c] = acc[k + c];
     s->alpha[c] = 0.0;
     s->beta[c] = 0.0;
     s->relres_inner[c] = act ? 1.0 : 0.0;
-    nact += act;
   }
-  s->inner_iter = 0;
-  s->phase = nact ? kPhaseInner : kPhaseApply;
+  const int nact = __popc(__ballot_sync(0xffffffffu, act));
+  if (c == 0) {
+    s->inner_iter = 0;
+    s->phase = nact ? kPhaseInner : kPhaseApply;
+  }
 }
 
 // Inner FP32 iteration: inner convergence test, beta, switch to Apply when the inner solve is done.
 __device__ __noinline__ void finish_update_mixed(SolveScal* s, int k, const double* acc) {
-  int nact = 0, bad = 0;
-  for (int c = 0; c < k; ++c) {
-    if (s->active[c] == 0) continue;
+  const int c = threadIdx.x & 31;
+  int act = 0, bad = 0;
+  if (c < k && s->active[c] != 0) {
     const double rzn = acc[c], rr = acc[k + c];
     if (!is_finite(rzn) || !is_finite(rr)) {
       bad = 1;
-      continue;
-    }
-    const double rel = sqrt(rr / s->bnorm2[c]);
-    s->relres_inner[c] = rel;
-    if (rel <= s->inner_tol || !positive_finite(rzn)) {
-      s->active[c] = 0;
-      s->beta[c] = 0.0;
     } else {
-      s->beta[c] = rzn / s->rz[c];
-      s->rz[c] = rzn;
-      nact += 1;
+      const double rel = sqrt(rr / s->bnorm2[c]);
+      s->relres_inner[c] = rel;
+      if (rel <= s->inner_tol || !positive_finite(rzn)) {
+        s->active[c] = 0;
+        s->beta[c] = 0.0;
+      } else {
+        s->beta[c] = rzn / s->rz[c];
+        s->rz[c] = rzn;
+        act = 1;
+      }
     }
   }
-  s->iter = s->iter + 1;
-  s->inner_iter = s->inner_iter + 1;
-  if (bad) {
-    s->status = IG_ERR_NONFINITE;
-    s->done = 1;
-  } else if (nact == 0 || s->inner_iter >= s->inner_cap || s->iter >= s->max_iter) {
-    s->phase = kPhaseApply;
+  const int nact = __popc(__ballot_sync(0xffffffffu, act));
+  const int anybad = __any_sync(0xffffffffu, bad);
+  if (c == 0) {
+    const int it = s->iter + 1, inner = s->inner_iter + 1;
+    s->iter = it;
+    s->inner_iter = inner;
+    if (anybad) {
+      s->status = IG_ERR_NONFINITE;
+      s->done = 1;
+    } else if (nact == 0 || inner >= s->inner_cap || it >= s->max_iter) {
+      s->phase = kPhaseApply;
+    }
   }
 }
 
@@ -345,7 +361,10 @@ __global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* 
         tile_reduce<2 * K>(acc, red, out);
       },
       [](const MeshDev& md, const double* v) {
-        if (md.s->phase == kPhaseInner) finish_update_mixed(md.s, K, v);
+        // every lane reads the phase before the warp's finish step changes it
+        const int phase = md.s->phase;
+        __syncwarp();
+        if (phase == kPhaseInner) finish_update_mixed(md.s, K, v);
         else finish_restart(md.s, K, v);
       });
   loop_control(mds, ctl, handle, use_graph);
