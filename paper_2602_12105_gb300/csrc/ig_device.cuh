@@ -28,21 +28,21 @@ __device__ __noinline__ void gather_partials_impl(const double* __restrict__ par
   double v[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) v[i] = 0.0;
-  int t = threadIdx.x;
-  for (; t + 3 * kBlock < ntiles; t += 4 * kBlock) {
+  for (int t = threadIdx.x; t < ntiles; t += 4 * kBlock) {
+    // four tiles' loads in flight together; a tile past the end reads as +0, which leaves the
+    // sum unchanged
     double b[4][NV];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 4; ++u) {
+      const int tu = t + u * kBlock;
 #pragma unroll
-      for (int i = 0; i < NV; ++i) b[u][i] = __ldcg(part + (t + u * kBlock) * kPartStride + i);
+      for (int i = 0; i < NV; ++i) b[u][i] = tu < ntiles ? __ldcg(part + tu * kPartStride + i) : 0.0;
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int i = 0; i < NV; ++i) v[i] += b[u][i];
   }
-  for (; t < ntiles; t += kBlock)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] += __ldcg(part + t * kPartStride + i);
 #pragma unroll
   for (int i = 0; i < NV; ++i) out[i] = v[i];
 }
@@ -370,6 +370,7 @@ struct TileCtx {
   ScalSnap sn;
   double red[2][8 * kWarps];  // tile sums, double-buffered
   double tot[8];              // mesh totals in the CTA that completes a mesh
+  SolveScal cur;              // the mesh's scalars as the CTA that completes it found them
   int last;
 };
 
@@ -398,7 +399,8 @@ __device__ __forceinline__ void load_mesh(const MeshDev* __restrict__ mds, int i
 // (G = gridDim.x). A tile's sums go to the mesh's part[tile]; each CTA counts the tiles it did
 // per run of consecutive tiles of one mesh and adds that count to the mesh's counter with one
 // atomic. The CTA whose addition completes the mesh adds the partials in tile order
-// (deterministic, independent of G and of any batch) and calls finish(md, totals) on warp 0.
+// (deterministic, independent of G and of any batch) and calls finish(md, scalars, totals) on
+// warp 0, with a shared-memory copy of the mesh's scalars to read (writes go to md.s).
 template <int NV, typename Finish>
 __device__ __forceinline__ void flush_tiles(TileCtx& tc, int tiling, unsigned run, int cnt_idx,
                                             const Finish& finish) {
@@ -414,13 +416,19 @@ __device__ __forceinline__ void flush_tiles(TileCtx& tc, int tiling, unsigned ru
   __syncthreads();
   if (tc.last) {
     __threadfence();
+    // the mesh's scalars are read into shared memory while the partials are gathered, so that
+    // the finish step does not wait on one global load after another
+    static_assert(sizeof(SolveScal) % 4 == 0 && sizeof(SolveScal) / 4 <= kBlock, "SolveScal copy");
+    if (threadIdx.x < (int)(sizeof(SolveScal) / 4))
+      reinterpret_cast<unsigned*>(&tc.cur)[threadIdx.x] =
+          __ldcg(reinterpret_cast<const unsigned*>(tc.md.s) + threadIdx.x);
     double v[NV];
     gather_partials<NV>(tc.md.part, ntiles, v);
     tile_reduce<NV>(v, tc.red[0], tc.tot);
     __syncthreads();
     if (threadIdx.x < 32) {
       if (threadIdx.x == 0) *cnt = 0u;
-      finish(tc.md, tc.tot);
+      finish(tc.md, tc.cur, tc.tot);
     }
   }
   __syncthreads();
@@ -743,17 +751,18 @@ __device__ __forceinline__ void load_row32(const float* __restrict__ p, long row
 // alpha_c = rz_c / (p_c . q_c) for active columns. The finish steps run on the 32 lanes of warp 0
 // of the CTA that completes a mesh: lane c handles column c (its divisions and square roots
 // run side by side instead of one after another on one thread), lane 0 the mesh's own fields.
-__device__ __noinline__ void finish_spmv(SolveScal* s, int k, const double* pq) {
+// They read the scalars from cur (a copy in shared memory) and write them to s.
+__device__ __noinline__ void finish_spmv(SolveScal* s, const SolveScal& cur, int k, const double* pq) {
   const int c = threadIdx.x & 31;
   int bad = 0;
   if (c < k) {
-    if (s->active[c] == 0) {
+    if (cur.active[c] == 0) {
       s->alpha[c] = 0.0;
     } else if (!positive_finite(pq[c])) {
       s->alpha[c] = 0.0;
       bad = 1;
     } else {
-      s->alpha[c] = s->rz[c] / pq[c];
+      s->alpha[c] = cur.rz[c] / pq[c];
     }
   }
   if (__any_sync(0xffffffffu, bad) && c == 0) {

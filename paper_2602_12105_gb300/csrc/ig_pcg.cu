@@ -65,21 +65,22 @@ __device__ __noinline__ void finish_init(SolveScal* s, int k, const double* acc,
 
 // Convergence test per column (recursive residual), beta_c = rz_new / rz, iteration count. Runs on
 // warp 0 of the CTA that completes the mesh: lane c takes column c, lane 0 the mesh's fields.
-__device__ __noinline__ void finish_update(SolveScal* s, int k, const double* acc) {
+__device__ __noinline__ void finish_update(SolveScal* s, const SolveScal& cur, int k, const double* acc) {
   const int c = threadIdx.x & 31;
   int act = 0, bad = 0;
-  if (c < k && s->active[c] != 0) {
+  if (c < k && cur.active[c] != 0) {
     const double rzn = acc[c], rr = acc[k + c];
     if (!is_finite(rzn) || !is_finite(rr)) {
       bad = 1;
     } else {
-      const double rel = sqrt(rr / s->bnorm2[c]);
+      const double rel = sqrt(rr / cur.bnorm2[c]);
+      const double bta = rzn / cur.rz[c];  // computed alongside rel, kept only if not converged
       s->relres[c] = rel;
-      if (rel <= s->tol) {
+      if (rel <= cur.tol) {
         s->active[c] = 0;
         s->beta[c] = 0.0;
       } else {
-        s->beta[c] = rzn / s->rz[c];
+        s->beta[c] = bta;
         s->rz[c] = rzn;
         act = 1;
       }
@@ -88,14 +89,14 @@ __device__ __noinline__ void finish_update(SolveScal* s, int k, const double* ac
   const int nact = __popc(__ballot_sync(0xffffffffu, act));
   const int anybad = __any_sync(0xffffffffu, bad);
   if (c == 0) {
-    const int it = s->iter + 1;
+    const int it = cur.iter + 1;
     s->iter = it;
     if (anybad) {
       s->status = IG_ERR_NONFINITE;
       s->done = 1;
     } else if (nact == 0) {
       s->done = 1;
-    } else if (it >= s->max_iter) {
+    } else if (it >= cur.max_iter) {
       s->status = IG_ERR_NOT_CONVERGED;
       s->done = 1;
     }
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(kBlock, 4) spmv_kernel(const MeshDev* __restri
   tile_loop<K>(
       mds, L, 0, 0, tc, [](const ScalSnap& x) { return !x.done; },
       [&](const MeshDev& md, int tile, double* red, double* out) { spmv_tile<K>(md, tile, tc.sn, red, out); },
-      [](const MeshDev& md, const double* v) { finish_spmv(md.s, K, v); });
+      [](const MeshDev& md, const SolveScal& cur, const double* v) { finish_spmv(md.s, cur, K, v); });
 }
 
 // ------------------------------------------------------------------------------- update
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kBlock, 4) update_kernel(const MeshDev* __rest
   tile_loop<2 * K>(
       mds, L, 0, 1, tc, [](const ScalSnap& x) { return !x.done; },
       [&](const MeshDev& md, int tile, double* red, double* out) { update_tile<K>(md, tile, tc.sn, red, out); },
-      [](const MeshDev& md, const double* v) { finish_update(md.s, K, v); });
+      [](const MeshDev& md, const SolveScal& cur, const double* v) { finish_update(md.s, cur, K, v); });
   loop_control(mds, ctl, handle, use_graph);
 }
 

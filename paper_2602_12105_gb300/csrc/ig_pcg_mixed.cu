@@ -64,21 +64,22 @@ __device__ __noinline__ void finish_init_mixed(SolveScal* s, int k, const double
 }
 
 // The finish steps below run on the 32 lanes of warp 0 of the CTA that completes a mesh: lane c
-// handles column c, lane 0 the mesh's own fields (written after the warp's votes).
+// handles column c, lane 0 the mesh's own fields (written after the warp's votes). They read the
+// scalars from cur, a shared-memory copy, and write them to s.
 
 // After r64 = rhs - A64 x64: FP64 convergence test per column, the scale of the next inner
 // right-hand side, and the refinement cap.
-__device__ __noinline__ void finish_residual(SolveScal* s, int k, const double* res2) {
+__device__ __noinline__ void finish_residual(SolveScal* s, const SolveScal& cur, int k, const double* res2) {
   const int c = threadIdx.x & 31;
-  const int refine = s->refine + 1;
+  const int refine = cur.refine + 1;
   int act = 0, bad = 0;
-  if (c < k && s->active64[c] != 0) {
+  if (c < k && cur.active64[c] != 0) {
     if (!is_finite(res2[c])) {
       bad = 1;
     } else {
-      const double rel = sqrt(res2[c] / s->rhs2[c]);
+      const double rel = sqrt(res2[c] / cur.rhs2[c]);
       s->relres[c] = rel;
-      if (rel <= s->tol || !positive_finite(res2[c])) {
+      if (rel <= cur.tol || !positive_finite(res2[c])) {
         s->active64[c] = 0;
       } else {
         s->scale[c] = sqrt(res2[c]);
@@ -95,7 +96,7 @@ __device__ __noinline__ void finish_residual(SolveScal* s, int k, const double* 
       s->done = 1;
     } else if (nact == 0) {
       s->done = 1;
-    } else if (refine >= s->max_refine || s->iter >= s->max_iter) {
+    } else if (refine >= cur.max_refine || cur.iter >= cur.max_iter) {
       s->status = IG_ERR_NOT_CONVERGED;
       s->done = 1;
     } else {
@@ -105,11 +106,11 @@ __device__ __noinline__ void finish_residual(SolveScal* s, int k, const double* 
 }
 
 // After forming r32 = r64 / scale: start a new inner solve.
-__device__ __noinline__ void finish_restart(SolveScal* s, int k, const double* acc) {
+__device__ __noinline__ void finish_restart(SolveScal* s, const SolveScal& cur, int k, const double* acc) {
   const int c = threadIdx.x & 31;
   int act = 0;
   if (c < k) {
-    act = (s->active64[c] && positive_finite(acc[k + c])) ? 1 : 0;
+    act = (cur.active64[c] && positive_finite(acc[k + c])) ? 1 : 0;
     s->active[c] = act;
     s->rz[c] = acc[c];
     s->bnorm2[c] = acc[k + c];
@@ -125,21 +126,22 @@ __device__ __noinline__ void finish_restart(SolveScal* s, int k, const double* a
 }
 
 // Inner FP32 iteration: inner convergence test, beta, switch to Apply when the inner solve is done.
-__device__ __noinline__ void finish_update_mixed(SolveScal* s, int k, const double* acc) {
+__device__ __noinline__ void finish_update_mixed(SolveScal* s, const SolveScal& cur, int k, const double* acc) {
   const int c = threadIdx.x & 31;
   int act = 0, bad = 0;
-  if (c < k && s->active[c] != 0) {
+  if (c < k && cur.active[c] != 0) {
     const double rzn = acc[c], rr = acc[k + c];
     if (!is_finite(rzn) || !is_finite(rr)) {
       bad = 1;
     } else {
-      const double rel = sqrt(rr / s->bnorm2[c]);
+      const double rel = sqrt(rr / cur.bnorm2[c]);
+      const double bta = rzn / cur.rz[c];  // computed alongside rel, kept only if not converged
       s->relres_inner[c] = rel;
-      if (rel <= s->inner_tol || !positive_finite(rzn)) {
+      if (rel <= cur.inner_tol || !positive_finite(rzn)) {
         s->active[c] = 0;
         s->beta[c] = 0.0;
       } else {
-        s->beta[c] = rzn / s->rz[c];
+        s->beta[c] = bta;
         s->rz[c] = rzn;
         act = 1;
       }
@@ -148,13 +150,13 @@ __device__ __noinline__ void finish_update_mixed(SolveScal* s, int k, const doub
   const int nact = __popc(__ballot_sync(0xffffffffu, act));
   const int anybad = __any_sync(0xffffffffu, bad);
   if (c == 0) {
-    const int it = s->iter + 1, inner = s->inner_iter + 1;
+    const int it = cur.iter + 1, inner = cur.inner_iter + 1;
     s->iter = it;
     s->inner_iter = inner;
     if (anybad) {
       s->status = IG_ERR_NONFINITE;
       s->done = 1;
-    } else if (nact == 0 || inner >= s->inner_cap || it >= s->max_iter) {
+    } else if (nact == 0 || inner >= cur.inner_cap || it >= cur.max_iter) {
       s->phase = kPhaseApply;
     }
   }
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(kBlock, 4) spmv_mixed_kernel(const MeshDev* __
         }
         tile_reduce<K>(pq, red, out);
       },
-      [](const MeshDev& md, const double* v) { finish_spmv(md.s, K, v); });
+      [](const MeshDev& md, const SolveScal& cur, const double* v) { finish_spmv(md.s, cur, K, v); });
 }
 
 // Apply phase: r64 = rhs - A64 x64 in FP64 and its squared norms (the refinement residual).
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__(kBlock) resid_mixed_kernel(const MeshDev* __re
         }
         tile_reduce<K>(acc, red, out);
       },
-      [](const MeshDev& md, const double* v) { finish_residual(md.s, K, v); });
+      [](const MeshDev& md, const SolveScal& cur, const double* v) { finish_residual(md.s, cur, K, v); });
 }
 
 // Inner phase: x32 += alpha p32, r32 -= alpha q32 and the tile's sums r.z, r.r; all loads of a
@@ -360,12 +362,9 @@ __global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* 
         }
         tile_reduce<2 * K>(acc, red, out);
       },
-      [](const MeshDev& md, const double* v) {
-        // every lane reads the phase before the warp's finish step changes it
-        const int phase = md.s->phase;
-        __syncwarp();
-        if (phase == kPhaseInner) finish_update_mixed(md.s, K, v);
-        else finish_restart(md.s, K, v);
+      [](const MeshDev& md, const SolveScal& cur, const double* v) {
+        if (cur.phase == kPhaseInner) finish_update_mixed(md.s, cur, K, v);
+        else finish_restart(md.s, cur, K, v);
       });
   loop_control(mds, ctl, handle, use_graph);
 }
