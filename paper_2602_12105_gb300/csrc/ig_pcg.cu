@@ -190,8 +190,10 @@ __device__ __forceinline__ void spmv_tile(const MeshDev& md, int tile, const Sca
 template <int K>
 __global__ void __launch_bounds__(kBlock, 4) spmv_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L) {
   __shared__ TileCtx tc;
+  __shared__ int s_stop;  // the loop has stopped: a launch after that (second half of a graph pass) does nothing
+  if (threadIdx.x == 0) s_stop = __ldcg(&ctl->all_done);
   tile_loop<K>(
-      mds, L, 0, 0, tc, [](const ScalSnap& x) { return !x.done; },
+      mds, L, 0, 0, tc, [&](const ScalSnap& x) { return !x.done && !s_stop; },
       [&](const MeshDev& md, int tile, double* red, double* out) { spmv_tile<K>(md, tile, tc.sn, red, out); },
       [](const MeshDev& md, const SolveScal& cur, const double* v) { finish_spmv(md.s, cur, K, v); });
 }
@@ -242,15 +244,45 @@ __device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const S
   tile_reduce<2 * K>(acc, red, out);
 }
 
+// Loop control of a group of one mesh, on lane 0 of the CTA that completes the mesh, right after
+// its finish step: the loop stops when the mesh is done or the cap is reached. A launch in which
+// the mesh takes no part is stopped by its CTA 0 at entry, so every launch either completes the
+// mesh (and counts towards the cap) or stops the loop. (A group of several meshes needs every CTA
+// of the launch to have finished, for the list rebuilds: loop_control.)
+__device__ __noinline__ void single_loop_control(const SolveScal* s, LoopCtl* ctl, cudaGraphConditionalHandle handle,
+                                                 int use_graph) {
+  const int it = __ldcg(&ctl->iter) + 1;
+  ctl->iter = it;
+  if (s->done || it >= __ldcg(&ctl->cap)) {  // done: this thread's own write in the finish step
+    ctl->all_done = 1;
+    if (use_graph) cudaGraphSetConditional(handle, 0u);
+  }
+}
+
 template <int K>
 __global__ void __launch_bounds__(kBlock, 4) update_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L,
     cudaGraphConditionalHandle handle, int use_graph) {
   __shared__ TileCtx tc;
+  __shared__ int s_single, s_stop;
+  if (threadIdx.x == 0) {
+    s_single = (__ldcg(&ctl->nmesh) == 1);
+    s_stop = __ldcg(&ctl->all_done);
+    // a group of one mesh whose mesh takes no part in this launch (done, or the loop stopped):
+    // no CTA completes it, so the loop is stopped here
+    if (s_single && blockIdx.x == 0 && (s_stop || __ldcg(&mds[0].s->done))) {
+      ctl->all_done = 1;
+      if (use_graph) cudaGraphSetConditional(handle, 0u);
+    }
+  }
+  __syncthreads();
   tile_loop<2 * K>(
-      mds, L, 0, 1, tc, [](const ScalSnap& x) { return !x.done; },
+      mds, L, 0, 1, tc, [&](const ScalSnap& x) { return !x.done && !s_stop; },
       [&](const MeshDev& md, int tile, double* red, double* out) { update_tile<K>(md, tile, tc.sn, red, out); },
-      [](const MeshDev& md, const SolveScal& cur, const double* v) { finish_update(md.s, cur, K, v); });
-  loop_control(mds, ctl, handle, use_graph);
+      [&](const MeshDev& md, const SolveScal& cur, const double* v) {
+        finish_update(md.s, cur, K, v);
+        if (s_single && threadIdx.x == 0) single_loop_control(md.s, ctl, handle, use_graph);
+      });
+  if (!s_single) loop_control(mds, ctl, handle, use_graph);
 }
 
 // ------------------------------------------------------------------------------- true residual
@@ -308,8 +340,13 @@ cudaError_t build_plan(Group& g, SolvePlan& pl) {
   cudaStream_t cs = g.capture_stream;
   e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
-  spmv_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.list64);
-  update_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.list64, handle, 1);
+  // Two iterations per pass of the WHILE body: its re-evaluation costs more than a kernel
+  // boundary. When the first iteration ends the loop, the second pair of launches finds every
+  // mesh done and returns at once.
+  for (int u = 0; u < 2; ++u) {
+    spmv_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.list64);
+    update_kernel<K><<<g.grid64, kBlock, 0, cs>>>(g.mds, g.ctl, g.list64, handle, 1);
+  }
   cudaError_t le = cudaGetLastError();
   cudaGraph_t captured = nullptr;
   e = cudaStreamEndCapture(cs, &captured);
