@@ -373,13 +373,15 @@ def run_ours(args, rank, world, local_rank):
 def gpu_launches(prof, steps, its_f, its_a, launch):
     """Kernel launches of the timed region, counted from the profile pass (one host-launched
     step, every launch bracketed by events): the kernels outside the solver loops as they were
-    counted, the loop bodies as 2 kernels per iteration of the two FP64 solves (the device-side
-    loop runs exactly the iterations the solves report)."""
+    counted, the loop bodies as 2 kernels per iteration of the two FP64 solves, in passes of two
+    iterations (a solve with an odd count ends with one pass whose second half does no work)."""
+    def in_graph(its):  # the graph's body holds two iterations (four launches) per pass
+        return 4 * ((its + 1) // 2)
     if not prof:
-        return int(steps * (2 + (2 + 2 * its_f) + (2 + 2 * its_a) + 2))
+        return int(steps * (2 + (2 + in_graph(its_f)) + (2 + in_graph(its_a)) + 2))
     loop = {"pcg_spmv", "pcg_update"}
     outside = sum(c for name, (c, _) in prof.items() if name not in loop)
-    per_step = outside / 3.0 + 2 * (its_f + its_a) if launch == "graph" else \
+    per_step = outside / 3.0 + in_graph(its_f) + in_graph(its_a) if launch == "graph" else \
         sum(c for c, _ in prof.values()) / 3.0
     return int(round(steps * per_step))
 
