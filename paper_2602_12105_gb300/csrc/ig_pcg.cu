@@ -2,7 +2,7 @@
 // solved together (the matrix is read once per iteration for all columns), on a group of one or
 // more meshes (the forward solve of §7.1 and the adjoint solve of §5.2 use the same operator).
 //
-// One iteration is two kernels over tiles of up to kTileRows rows (a tile belongs to one mesh):
+// One iteration is two kernels over tiles of up to kTileRows64 rows (a tile belongs to one mesh):
 //   spmv   : p = z + beta p, q = A p = A z + beta q (the product carried by its recurrence, so
 //            that the direction update needs no pass of its own), partial p.q
 //            -> last tile of the mesh: alpha = rz / pq

@@ -79,3 +79,50 @@ def test_budget_admission_and_rejection(mods):
     done = srv.run([reqs[0]], realtime=False)
     from paper_2602_12105_gb300 import _native as N
     assert done[0].status == N.IG_ERR_OOM and srv.stats["rejected"] == 1
+
+
+@pytest.mark.parametrize("nmesh", [1, 2])
+def test_round_budget_is_never_exceeded(mods, nmesh):
+    """ig_batch_iterate advances each running solve by at most max_iters iterations per call, also
+    when the device loop runs two iterations per graph pass and the budget is odd: a solve of I
+    iterations needs at least ceil(I / 3) rounds of 3 (exactly that many when it runs alone), and
+    its result is the same as the one-call solve."""
+    import ctypes
+    api, meshgen, _ = mods
+    from paper_2602_12105_gb300 import _native as N
+    from paper_2602_12105_gb300.api import _ptr
+    ctx = api.default_context()
+    rng = np.random.default_rng(11 + nmesh)
+    probs = [meshgen.config_grid(36 + 9 * i, 28, seed=20 + i, t=2e-3) for i in range(nmesh)]
+    meshes = [api.Mesh(torch.from_numpy(p.F).to("cuda:0"), p.n) for p in probs]
+    Bs = [torch.from_numpy(rng.uniform(-1, 1, (p.n, 3))).to("cuda:0") for p in probs]
+    opts = api.make_opts(rel_tol=1e-10)
+    for m, p, B in zip(meshes, probs, Bs):
+        m.assemble(torch.from_numpy(np.ascontiguousarray(p.V)).to("cuda:0"), p.t, "fp64")
+        ctx.check(ctx.lib.ig_solve_begin(m.h, _ptr(B), 3, 1, ctypes.byref(opts)))
+    batch = api.Batch(meshes)
+    finished_at = [None] * nmesh
+    for rnd in range(1, 2000):
+        flags = (ctypes.c_int * nmesh)()
+        torch.cuda.synchronize()
+        ctx.check(ctx.lib.ig_batch_iterate(batch.h, 3, 3, flags))
+        for i in range(nmesh):
+            if flags[i] and finished_at[i] is None:
+                finished_at[i] = rnd
+        if all(f is not None for f in finished_at):
+            break
+    assert all(f is not None for f in finished_at)
+    for i, (m, p) in enumerate(zip(meshes, probs)):
+        U = torch.empty((p.n, 3), dtype=torch.float64, device="cuda:0")
+        info = N.SolveInfo()
+        st = ctx.lib.ig_solve_end(m.h, 3, _ptr(U), ctypes.byref(info))
+        assert st == N.IG_OK
+        iters = info.iterations
+        need = -(-iters // 3)
+        assert finished_at[i] >= need, (i, iters, finished_at[i])
+        if nmesh == 1:
+            assert finished_at[i] == need, (iters, finished_at[i])
+        U1, info1 = m.solve(Bs[i], opts=opts, info=True)
+        assert info1["iterations"] == iters
+        assert torch.equal(U, U1)
+    batch.close()
