@@ -234,5 +234,44 @@ def fairing_step(V, F, T, t, eta, tol=1e-14, method="auto"):
     return _f64(V) - eta * gs, r["loss"]
 
 
+def canonical_sign(U):
+    """Flip each column so that its first entry (in vertex order) whose magnitude is within a
+    relative 1e-6 of the column's largest magnitude is positive: the canonical sign that the
+    orthonormalization Q of Eq. eigiter (§5) chooses, in the reading taken here. (Eigenvectors of
+    symmetric meshes reach their largest magnitude at several vertices, with either sign, so the
+    first such vertex is taken rather than the largest entry itself.)"""
+    U = _f64(U).copy()
+    A = np.abs(U)
+    big = A >= (1.0 - 1e-6) * A.max(axis=0)[None, :]
+    j = np.argmax(big, axis=0)
+    s = np.where(U[j, np.arange(U.shape[1])] < 0.0, -1.0, 1.0)
+    return U * s[None, :]
+
+
+def m_orthonormalize(Y, M):
+    """Q of Eq. eigiter: an M-orthonormal basis of the columns of Y in Gram-Schmidt order, Y = Q R
+    with R upper triangular (the transposed Cholesky factor of the Gram matrix Y^T M Y), followed
+    by the canonical sign of each column."""
+    Y = _f64(Y)
+    G = Y.T @ (M[:, None] * Y)
+    R = np.linalg.cholesky(G).T
+    Q = np.linalg.solve(R.T, Y.T).T
+    return canonical_sign(Q)
+
+
+def subspace_iteration(V, F, t, U0, iters, tol=1e-14, method="auto"):
+    """Shift-invert subspace iteration of Eq. eigiter (§5) for the eigenpairs of L u = lambda M u
+    with the shift sigma = -1/t: (L - sigma M)^-1 M = t (M + t L)^-1 M, so each step solves
+    (M + t L) Y = M U with the smoothing operator of §7.1 and takes U = Q(Y). The constant t drops
+    out in Q. Returns (U, lam) with lam_c = u_c^T L u_c (u_c M-normalized)."""
+    rowptr, col, Aval, Lval, M = operator(V, F, t)
+    U = _f64(U0)
+    for _ in range(int(iters)):
+        Y = solve(rowptr, col, Aval, M[:, None] * U, tol=tol, method=method)
+        U = m_orthonormalize(Y, M)
+    LU = spmv(rowptr, col, Lval, U)
+    return U, np.sum(U * LU, axis=0)
+
+
 def num_threads():
     return 1
