@@ -52,7 +52,7 @@ def parse():
                     help="skip the other workloads (mixed grid, largest mesh, 256-mesh batch, serving)")
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="requests in the bounded sample of the serving stream")
-    ap.add_argument("--variants", default="mixed,largest,batch,fairing,serve",
+    ap.add_argument("--variants", default="mixed,largest,batch,fairing,eigs,serve",
                     help="comma list of the extra workloads to run")
     return ap.parse_args()
 
@@ -651,6 +651,37 @@ def variant_fairing(api, _native, dev, steps, level=7):
     return out
 
 
+def variant_eigs(api, dev, steps, level=7):
+    """The lowest four eigenpairs of L u = lambda M u on a slightly perturbed unit icosphere by the
+    shift-invert subspace iteration of Eq. eigiter (§5, ig_eigs): each step is a 4-column
+    smoothing solve (M + tL) Y = M U to 1e-10 and the M-orthonormalization of Y. The smooth unit
+    sphere's lowest eigenvalues are 0 and 2 (three times), then 6, so with t = 0.5 a step
+    contracts the error by about (1 + 2t) / (1 + 6t) = 1/2."""
+    import torch
+    from paper_2602_12105_gb300 import meshgen as mg
+    Vc, F = mg.icosphere(level)
+    V = mg.radial_perturb(Vc, 0.002, np.random.default_rng(41))
+    t = 0.5
+    mesh = api.Mesh(torch.from_numpy(F).to(dev), V.shape[0])
+    mesh.assemble(torch.from_numpy(V).to(dev), t)
+    U0 = torch.from_numpy(np.random.default_rng(42).uniform(-1, 1, (V.shape[0], 4))).to(dev)
+    opts = api.make_opts(rel_tol=1e-10)
+    mesh.eigs(U0, 2, opts=opts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    U, lam, info = mesh.eigs(U0, steps, opts=opts, info=True)
+    dt = time.perf_counter() - t0
+    M = mesh.mass()
+    G = U.T @ (M[:, None] * U)
+    orth = float((G - torch.eye(4, dtype=G.dtype, device=G.device)).abs().max())
+    mesh.close()
+    return {"workload": f"ico{level} ({V.shape[0]} vertices), radial N(0, 0.002), t = {t:g}, k = 4, "
+                        f"{steps} subspace steps, each a 4-column solve to 1e-10 and an M-orthonormalization",
+            "unit": "subspace steps/s", "value": round(steps / dt, 3), "ms_per_step": round(1000.0 * dt / steps, 4),
+            "pcg_iterations_last_step": info["iterations"], "eigenvalues": [float(x) for x in lam],
+            "max_abs_UtMU_minus_I": orth}
+
+
 def serving_requests(count, seed=7):
     """A bounded sample of the serving stream: request sizes log-uniform in [1e3, 2e6] vertices,
     half icospheres (levels 4..8), half square grids whose side is snapped to one of 32
@@ -734,6 +765,8 @@ def run_variants(args, p, U64, gV64, dev):
         out["batch256_icospheres"] = variant_batch(api, _native, dev, args.tol, 6)
     if "fairing" in want:
         out["inverse_fairing_ico7"] = variant_fairing(api, _native, dev, 20)
+    if "eigs" in want:
+        out["eigs_ico7"] = variant_eigs(api, dev, 40)
     if "serve" in want and args.serve_requests > 0:
         out["serving"] = variant_serving(dev, args.tol, args.serve_requests)
     out["clocks"] = sampler.stop()

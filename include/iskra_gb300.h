@@ -239,6 +239,31 @@ ig_status ig_mass_vjp(ig_mesh* mesh, const double* V_dev, const double* w_dev, d
 ig_status ig_fairing_step(ig_mesh* mesh, double* V_dev, const double* T_dev, double t, double eta, int precision,
                           const ig_solve_opts* opts, double* loss_host, ig_solve_info* info3);
 
+/* ---- Laplacian eigenvectors by shift-invert subspace iteration (Eq. eigiter of §5) ------------ */
+
+/* The lowest k eigenpairs of the pencil L u = lambda M u of the assembled mesh, by the
+ * fixed-point iteration U <- Q((L - sigma M)^-1 M U) of Eq. eigiter (§5) with the shift
+ * sigma = -1/t of the assembled operator: (L - sigma M)^-1 M = t (M + t L)^-1 M, so each of the
+ * `iters` steps is the smoothing solve (M + tL) Y = M U (k columns together, to opts->rel_tol, in
+ * the assembled precision) followed by Q: the M-orthonormal basis of Y's columns in Gram-Schmidt
+ * order (Y = Q R, R upper triangular from the Cholesky factor of Y^T M Y). A larger t separates
+ * the lowest eigenvalues more per step: the error of column c shrinks by about
+ * (1 + t lambda_c) / (1 + t lambda_{c+1}) per step.
+ * After the last step every column gets a canonical sign: its first entry, in vertex order, whose
+ * magnitude is within a relative 1e-6 of the column's largest magnitude is made positive.
+ * U_dev: [n][k] row-major device buffer: the start basis on entry (linearly independent
+ * columns, e.g. random), the M-orthonormal result on return. k in 1..4, iters >= 1.
+ * lambda_host (may be NULL): k doubles, lambda_c = u_c^T L u_c, computed from the FP64 operator as
+ * (u_c^T A u_c - u_c^T M u_c) / t. info (may be NULL): status and iteration count of the last
+ * solve. Either synchronises the stream; without both the call is asynchronous.
+ * Workspace (4 n + 16 ceil(n / 256) doubles and a few bytes) is allocated on the mesh at the
+ * first call. Errors: IG_ERR_STATE (not assembled), IG_ERR_INVALID_ARG (NULL U_dev, k or iters
+ * out of range), IG_ERR_NONFINITE (a Gram matrix was not positive definite: the start columns
+ * were dependent or not finite; reported when lambda_host or info is given), the errors of
+ * ig_solve, IG_ERR_OOM, IG_ERR_CUDA. The gradient through this fixed point is not provided. */
+ig_status ig_eigs(ig_mesh* mesh, int k, int iters, double* U_dev, double* lambda_host, const ig_solve_opts* opts,
+                  ig_solve_info* info);
+
 /* ---- allocation-free solve ----------------------------------------------------------------- */
 
 /* Largest number of rows ig_solve_csr_noalloc accepts. */

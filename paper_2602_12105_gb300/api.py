@@ -174,6 +174,24 @@ class Mesh:
         self.ctx.check(st)
         return U
 
+    def eigs(self, U0: torch.Tensor, iters: int, opts=None, info: bool = False):
+        """The lowest k = U0.shape[1] (<= 4) eigenpairs of L u = lambda M u by the shift-invert
+        subspace iteration of Eq. eigiter (§5), starting from U0 [n][k] (linearly independent
+        columns), with the shift -1/t of the assembled operator (see ig_eigs). Returns (U, lam)
+        with M-orthonormal, canonically signed columns; with info=True also the last solve's
+        info."""
+        U = self._dev(U0, None, "U0").clone()
+        k = U.shape[1]
+        lam = (ctypes.c_double * k)()
+        inf = N.SolveInfo() if info else None
+        self.ctx.sync_stream()
+        st = self.ctx.lib.ig_eigs(self.h, k, int(iters), _ptr(U), lam,
+                                  ctypes.byref(opts) if opts is not None else None,
+                                  ctypes.byref(inf) if inf is not None else None)
+        self.ctx.check(st)
+        lam_t = torch.tensor(list(lam), dtype=torch.float64)
+        return (U, lam_t, inf.as_dict()) if info else (U, lam_t)
+
     def adjoint(self, V, B, b_is_V, U, G, want_gB=False, want_gt=False, opts=None, info: bool = False):
         V = self._dev(V, 3, "V")
         G = self._dev(G, None, "G")

@@ -800,6 +800,49 @@ ig_status ig_fairing_step(ig_mesh* mesh, double* V_dev, const double* T_dev, dou
   return IG_OK;
 }
 
+ig_status ig_eigs(ig_mesh* mesh, int k, int iters, double* U_dev, double* lambda_host, const ig_solve_opts* opts,
+                  ig_solve_info* info) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (!mesh->assembled) {
+    set_error(ctx, "eigs before assemble");
+    return IG_ERR_STATE;
+  }
+  if (!U_dev) return bad_arg(ctx, "U must be non-NULL");
+  if (k < 1 || k > kMaxK) return bad_arg(ctx, "k must be in [1, 4]");
+  if (iters < 1) return bad_arg(ctx, "iters must be >= 1");
+  if (!(mesh->t > 0.0)) return bad_arg(ctx, "the shift -1/t needs an assembled t > 0");
+  const ig_solve_opts o = resolve_opts(opts);
+  ig_status cs = check_opts(ctx, o);
+  if (cs != IG_OK) return cs;
+  DeviceGuard guard(ctx->device);
+  const long n = (long)mesh->n;
+  if (!mesh->eig) IG_CK(ctx, mesh_alloc(mesh, &mesh->eig, eig_workspace_doubles(n)), "alloc");
+  double* Y = mesh->eig;
+  IG_CK(ctx, eig_reset(mesh->eig, n, ctx->stream), "eigs");
+  auto io = std::make_unique<IoTable>();
+  io->in[0] = U_dev;
+  io->out[0] = Y;
+  for (int it = 0; it < iters; ++it) {
+    // Y = (M + tL)^-1 M U, then U = Q(Y)
+    IG_CK(ctx, group_solve(mesh->group, k, mesh->assembled == 2, *io, 1, o, ctx->stream), "eigs solve");
+    IG_CK(ctx, eig_step(k, mesh->eig, mesh->md.M, n, U_dev, ctx->stream), "eigs");
+  }
+  IG_CK(ctx, eig_finish(k, mesh->group.mds, mesh->t, mesh->eig, n, U_dev, ctx->stream), "eigs");
+  if (!lambda_host && !info) return IG_OK;
+  int fail = 0;
+  IG_CK(ctx, eig_read(mesh->eig, n, k, lambda_host, &fail, ctx->stream), "eigs");
+  if (info) {
+    ig_status s = collect_info(mesh, k, info);  // the last solve's status and iterations
+    if (s != IG_OK) return s;
+  }
+  if (fail) {
+    set_error(ctx, "eigs: a Gram matrix was not positive definite (dependent or non-finite columns)");
+    return IG_ERR_NONFINITE;
+  }
+  return IG_OK;
+}
+
 ig_status ig_profile_enable(int enable) {
   ProfState& P = prof_state();
   std::lock_guard<std::mutex> lk(P.mu);

@@ -1,0 +1,408 @@
+// ig_eigs.cu -- shift-invert subspace iteration for the lowest eigenpairs of the pencil (L, M):
+// the forward half of the eigenvector fixed point of Eq. eigiter (§5),
+//   f(A, B, U) = Q((A - sigma B)^-1 B U) - U = 0,
+// here with A = L, B = M and the shift sigma = -1/t of the assembled smoothing operator, so that
+// (L - sigma M)^-1 M = t (M + t L)^-1 M: a step is the smoothing solve (M + tL) Y = M U (done by
+// the PCG path, k columns together) followed by Q. The constant t drops out in Q.
+//
+// Q (per step): the Gram matrix G = Y^T M Y (k x k, tile partials added in tile order), its
+// Cholesky factor G = R^T R (R upper triangular, on one thread of the CTA that completes the sum)
+// and U = Y R^-1: the M-orthonormal basis of Y's columns in Gram-Schmidt order.
+// After the last step: the canonical sign of each column (its first entry, in vertex order,
+// within a relative 1e-6 of the column's largest magnitude is made positive; column signs of the
+// intermediate iterates do not change the final basis) and lambda_c = u_c^T L u_c, computed as
+// (u_c^T A u_c - u_c^T M u_c) / t with the FP64 operator A = M + tL.
+//
+// Every reduction is over tiles of kBlock rows; the CTA that completes it (a counter) adds the
+// tile partials in tile order, so results do not depend on scheduling.
+#include <climits>
+
+#include "ig_device.cuh"
+
+namespace ig {
+
+namespace {
+
+constexpr int kEigStride = 16;        // doubles per tile partial
+constexpr double kSignBand = 1e-6;    // relative band below the largest magnitude for the sign rule
+
+// Small results: R^-1 (k x k, row-major), column maxima, signs, eigenvalues, status word.
+struct EigSmall {
+  double rinv[kMaxK * kMaxK];
+  double colmax[kMaxK];
+  double sign[kMaxK];
+  double lambda[kMaxK];
+  int sign_row[kMaxK];
+  int fail;        // 1 once a Gram matrix was not numerically positive definite (dependent or non-finite columns)
+  unsigned cnt;    // last-CTA counter, reset by the CTA that completes each reduction
+};
+
+// Publish this CTA's partials (thread 0 holds them in v) and return true in the CTA that completes
+// the reduction; every thread of that CTA then sees the partials of all tiles.
+__device__ __forceinline__ bool eig_publish(EigSmall* sm, int ntile) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&sm->cnt, 1u);
+    s_last = (prev == (unsigned)ntile - 1u);
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+// Sum of the NV partials over all tiles in tile order: thread j adds tiles j, j + kBlock, ...,
+// then the CTA adds the threads' sums in thread order. Thread 0 receives the totals.
+template <int NV>
+__device__ __forceinline__ void eig_gather_sum(const double* __restrict__ part, int ntile, double (&v)[NV],
+                                               double* sh) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = 0.0;
+  for (int b = threadIdx.x; b < ntile; b += kBlock)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += __ldcg(part + (long)b * kEigStride + i);
+  block_sum<NV>(v, sh);
+}
+
+// Maximum (MIN = false) or minimum (MIN = true) of part[b * kEigStride + off + c] over the tiles,
+// for c < K; thread 0 receives the results (max and min are exact, so the order is free).
+template <int K, bool MIN>
+__device__ __forceinline__ void eig_gather_ext(const double* __restrict__ part, int ntile, int off, double (&v)[K]) {
+  __shared__ double sw[K][kBlock / 32];
+#pragma unroll
+  for (int c = 0; c < K; ++c) v[c] = MIN ? 1e300 : 0.0;
+  for (int b = threadIdx.x; b < ntile; b += kBlock)
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const double x = __ldcg(part + (long)b * kEigStride + off + c);
+      v[c] = MIN ? fmin(v[c], x) : fmax(v[c], x);
+    }
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double x = __shfl_xor_sync(0xffffffffu, v[c], o);
+      v[c] = MIN ? fmin(v[c], x) : fmax(v[c], x);
+    }
+    if ((threadIdx.x & 31) == 0) sw[c][threadIdx.x >> 5] = v[c];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      double m = sw[c][0];
+      for (int w = 1; w < kBlock / 32; ++w) m = MIN ? fmin(m, sw[c][w]) : fmax(m, sw[c][w]);
+      v[c] = m;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// G = Y^T M Y, then R^-1 of its Cholesky factor.
+template <int K>
+__global__ void __launch_bounds__(kBlock) eig_gram_kernel(const double* __restrict__ Y, const double* __restrict__ M,
+                                                          long n, double* __restrict__ part, EigSmall* sm) {
+  constexpr int NG = K * (K + 1) / 2;
+  __shared__ double sh[NG * kBlock];
+  const int ntile = (int)((n + kBlock - 1) / kBlock);
+  const long row = (long)blockIdx.x * kBlock + threadIdx.x;
+  double acc[NG];
+#pragma unroll
+  for (int i = 0; i < NG; ++i) acc[i] = 0.0;
+  if (row < n) {
+    double y[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) y[c] = Y[row * K + c];
+    const double m = M[row];
+    int i = 0;
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+      for (int b = a; b < K; ++b) acc[i++] = m * y[a] * y[b];
+  }
+  block_sum<NG>(acc, sh);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < NG; ++i) part[(long)blockIdx.x * kEigStride + i] = acc[i];
+  if (!eig_publish(sm, ntile)) return;
+  double g[NG];
+  eig_gather_sum<NG>(part, ntile, g, sh);
+  if (threadIdx.x != 0) return;
+  // Cholesky G = R^T R (R upper triangular), then R^-1 by back substitution
+  double G[K][K], R[K][K], Ri[K][K];
+  int i = 0;
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+#pragma unroll
+    for (int b = a; b < K; ++b) {
+      G[a][b] = g[i];
+      G[b][a] = g[i];
+      ++i;
+    }
+  int bad = 0;
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+#pragma unroll
+    for (int b = 0; b < K; ++b) {
+      R[a][b] = 0.0;
+      Ri[a][b] = 0.0;
+    }
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+    double d = G[a][a];
+#pragma unroll
+    for (int p = 0; p < a; ++p) d -= R[p][a] * R[p][a];
+    // a pivot within rounding of zero relative to the column's own norm: the column depends on
+    // the ones before it (exactly dependent columns leave a pivot of about 1e-16 G_aa)
+    if (!(d > 1e-14 * G[a][a]) || !(d < 1e300)) {
+      bad = 1;
+      d = 1.0;
+    }
+    R[a][a] = sqrt(d);
+#pragma unroll
+    for (int b = a + 1; b < K; ++b) {
+      double e = G[a][b];
+#pragma unroll
+      for (int p = 0; p < a; ++p) e -= R[p][a] * R[p][b];
+      R[a][b] = e / R[a][a];
+    }
+  }
+  // R^-1, column by column: R Ri[:, c] = e_c
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+#pragma unroll
+    for (int a = K - 1; a >= 0; --a) {
+      double e = (a == c) ? 1.0 : 0.0;
+#pragma unroll
+      for (int p = a + 1; p < K; ++p) e -= R[a][p] * Ri[p][c];
+      Ri[a][c] = e / R[a][a];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+#pragma unroll
+    for (int c = 0; c < K; ++c) sm->rinv[a * K + c] = Ri[a][c];
+  if (bad) sm->fail = 1;
+  sm->cnt = 0u;
+}
+
+// U = Y R^-1 (row by row).
+template <int K>
+__global__ void __launch_bounds__(kBlock) eig_transform_kernel(const double* __restrict__ Y, double* __restrict__ U,
+                                                               long n, const EigSmall* __restrict__ sm) {
+  __shared__ double ri[K * K];
+  if (threadIdx.x < K * K) ri[threadIdx.x] = sm->rinv[threadIdx.x];
+  __syncthreads();
+  const long row = (long)blockIdx.x * kBlock + threadIdx.x;
+  if (row >= n) return;
+  double y[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) y[c] = Y[row * K + c];
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    double u = 0.0;
+#pragma unroll
+    for (int a = 0; a <= c; ++a) u = fma(y[a], ri[a * K + c], u);
+    U[row * K + c] = u;
+  }
+}
+
+// Column maxima of |U| (exact, order-free) and the Rayleigh quotients: u^T A u and u^T M u per
+// column, summed in tile order; the completing CTA writes colmax and lambda.
+template <int K>
+__global__ void __launch_bounds__(kBlock) eig_stats_kernel(const MeshDev* __restrict__ mds, const double* __restrict__ U,
+                                                           double t, double* __restrict__ part, EigSmall* sm) {
+  __shared__ double sh[2 * K * kBlock];
+  __shared__ double smax[K][kBlock / 32];
+  const MeshDev& md = mds[0];
+  const long n = md.n;
+  const int ntile = (int)((n + kBlock - 1) / kBlock);
+  const long row = (long)blockIdx.x * kBlock + threadIdx.x;
+  double acc[2 * K];
+  double mx[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    acc[c] = 0.0;
+    acc[K + c] = 0.0;
+    mx[c] = 0.0;
+  }
+  if (row < n) {
+    double au[K], u[K];
+    row_product<K>(md, md.A, row, GatherAoS64<K>{U}, au);
+    const double m = md.M[row];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      u[c] = U[row * K + c];
+      acc[c] = u[c] * au[c];
+      acc[K + c] = m * u[c] * u[c];
+      mx[c] = fabs(u[c]);
+    }
+  }
+  // CTA maximum per column (warp shuffles, then the warps in order; max is exact)
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx[c] = fmax(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
+    if ((threadIdx.x & 31) == 0) smax[c][threadIdx.x >> 5] = mx[c];
+  }
+  block_sum<2 * K>(acc, sh);  // its barriers also publish smax
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      double m = smax[c][0];
+      for (int w = 1; w < kBlock / 32; ++w) m = fmax(m, smax[c][w]);
+      part[(long)blockIdx.x * kEigStride + 2 * K + c] = m;
+    }
+#pragma unroll
+    for (int i = 0; i < 2 * K; ++i) part[(long)blockIdx.x * kEigStride + i] = acc[i];
+  }
+  if (!eig_publish(sm, ntile)) return;
+  double tot[2 * K];
+  eig_gather_sum<2 * K>(part, ntile, tot, sh);
+  double cm[K];
+  eig_gather_ext<K, false>(part, ntile, 2 * K, cm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      sm->colmax[c] = cm[c];
+      sm->lambda[c] = (tot[c] - tot[K + c]) / t;
+    }
+    sm->cnt = 0u;
+  }
+}
+
+// The first row (in vertex order) of each column whose magnitude is within the band below the
+// column maximum; its sign is the column's canonical sign.
+template <int K>
+__global__ void __launch_bounds__(kBlock) eig_sign_kernel(const double* __restrict__ U, long n,
+                                                          double* __restrict__ part, EigSmall* sm) {
+  __shared__ int smin[K][kBlock / 32];
+  const int ntile = (int)((n + kBlock - 1) / kBlock);
+  const long row = (long)blockIdx.x * kBlock + threadIdx.x;
+  int first[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    first[c] = INT_MAX;
+    if (row < n) {
+      const double thr = (1.0 - kSignBand) * __ldcg(&sm->colmax[c]);
+      if (fabs(U[row * K + c]) >= thr) first[c] = (int)row;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) first[c] = min(first[c], __shfl_xor_sync(0xffffffffu, first[c], o));
+    if ((threadIdx.x & 31) == 0) smin[c][threadIdx.x >> 5] = first[c];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      int m = smin[c][0];
+      for (int w = 1; w < kBlock / 32; ++w) m = min(m, smin[c][w]);
+      part[(long)blockIdx.x * kEigStride + c] = (double)m;
+    }
+  }
+  if (!eig_publish(sm, ntile)) return;
+  double fr[K];
+  eig_gather_ext<K, true>(part, ntile, 0, fr);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const long r = fr[c] < (double)n ? (long)fr[c] : 0;
+      sm->sign_row[c] = (int)r;
+      sm->sign[c] = U[r * K + c] < 0.0 ? -1.0 : 1.0;
+    }
+    sm->cnt = 0u;
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) eig_flip_kernel(double* __restrict__ U, long n, const EigSmall* __restrict__ sm) {
+  const long row = (long)blockIdx.x * kBlock + threadIdx.x;
+  if (row >= n) return;
+#pragma unroll
+  for (int c = 0; c < K; ++c) U[row * K + c] *= sm->sign[c];
+}
+
+}  // namespace
+
+size_t eig_workspace_doubles(long n) {
+  const long ntile = (n + kBlock - 1) / kBlock;
+  return (size_t)(kMaxK * n + kEigStride * ntile) + (sizeof(EigSmall) + 7) / 8 + 1;
+}
+
+// Workspace: Y [n][k], tile partials [ntile][kEigStride], EigSmall (zeroed by eig_reset).
+static EigSmall* eig_small(double* ws, long n) {
+  const long ntile = (n + kBlock - 1) / kBlock;
+  return reinterpret_cast<EigSmall*>(ws + kMaxK * n + kEigStride * ntile);
+}
+
+cudaError_t eig_reset(double* ws, long n, cudaStream_t st) {
+  return cudaMemsetAsync(eig_small(ws, n), 0, sizeof(EigSmall), st);
+}
+
+template <int K>
+static cudaError_t eig_step_k(double* ws, const double* M, long n, double* U, cudaStream_t st) {
+  const long ntile = (n + kBlock - 1) / kBlock;
+  double* Y = ws;
+  double* part = ws + kMaxK * n;
+  EigSmall* sm = eig_small(ws, n);
+  {
+    IG_PROF("eig_gram", st);
+    eig_gram_kernel<K><<<(unsigned)ntile, kBlock, 0, st>>>(Y, M, n, part, sm);
+  }
+  {
+    IG_PROF("eig_transform", st);
+    eig_transform_kernel<K><<<(unsigned)ntile, kBlock, 0, st>>>(Y, U, n, sm);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t eig_step(int k, double* ws, const double* M, long n, double* U, cudaStream_t st) {
+  switch (k) {
+    case 1: return eig_step_k<1>(ws, M, n, U, st);
+    case 2: return eig_step_k<2>(ws, M, n, U, st);
+    case 3: return eig_step_k<3>(ws, M, n, U, st);
+    case 4: return eig_step_k<4>(ws, M, n, U, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int K>
+static cudaError_t eig_finish_k(const MeshDev* mds, double t, double* ws, long n, double* U, cudaStream_t st) {
+  const long ntile = (n + kBlock - 1) / kBlock;
+  double* part = ws + kMaxK * n;
+  EigSmall* sm = eig_small(ws, n);
+  {
+    IG_PROF("eig_stats", st);
+    eig_stats_kernel<K><<<(unsigned)ntile, kBlock, 0, st>>>(mds, U, t, part, sm);
+  }
+  {
+    IG_PROF("eig_sign", st);
+    eig_sign_kernel<K><<<(unsigned)ntile, kBlock, 0, st>>>(U, n, part, sm);
+  }
+  {
+    IG_PROF("eig_flip", st);
+    eig_flip_kernel<K><<<(unsigned)ntile, kBlock, 0, st>>>(U, n, sm);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t eig_finish(int k, const MeshDev* mds, double t, double* ws, long n, double* U, cudaStream_t st) {
+  switch (k) {
+    case 1: return eig_finish_k<1>(mds, t, ws, n, U, st);
+    case 2: return eig_finish_k<2>(mds, t, ws, n, U, st);
+    case 3: return eig_finish_k<3>(mds, t, ws, n, U, st);
+    case 4: return eig_finish_k<4>(mds, t, ws, n, U, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t eig_read(double* ws, long n, int k, double* lambda_host, int* fail_host, cudaStream_t st) {
+  EigSmall* sm = eig_small(ws, n);
+  cudaError_t e = cudaSuccess;
+  if (lambda_host) e = cudaMemcpyAsync(lambda_host, sm->lambda, sizeof(double) * k, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && fail_host) e = cudaMemcpyAsync(fail_host, &sm->fail, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+}  // namespace ig

@@ -304,6 +304,7 @@ struct ig_mesh {
   ig::Group group;          // this mesh alone
   std::vector<void*> allocs;
   double* fair = nullptr;   // inverse-fairing workspace: U, G, g, g~ [n][3], w [n], loss (on first use)
+  double* eig = nullptr;    // eigen-iteration workspace (eig_workspace_doubles, on first use)
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -331,6 +332,15 @@ cudaError_t launch_assemble(Group& g, int mixed, cudaStream_t st);
 cudaError_t launch_operator_csr(const MeshDev& md, double* Acsr, cudaStream_t st);
 
 // ig_pcg.cu: see Group above
+
+// ig_eigs.cu: shift-invert subspace iteration (workspace of eig_workspace_doubles(n) doubles)
+size_t eig_workspace_doubles(long n);
+cudaError_t eig_reset(double* ws, long n, cudaStream_t st);
+// Q of one step: Y (the workspace's first [n][k]) -> U = Y R^-1
+cudaError_t eig_step(int k, double* ws, const double* M, long n, double* U, cudaStream_t st);
+// canonical signs of U's columns and the eigenvalues (u^T A u - u^T M u) / t
+cudaError_t eig_finish(int k, const MeshDev* mds, double t, double* ws, long n, double* U, cudaStream_t st);
+cudaError_t eig_read(double* ws, long n, int k, double* lambda_host, int* fail_host, cudaStream_t st);
 
 // ig_vjp.cu
 // mode 0: solve terms; 1: solve terms and the mass weights of the calls; 2: mass weights alone
