@@ -338,6 +338,8 @@ def run_ours(args, rank, world, local_rank):
     its_f, its_a = finfo["iterations"], ainfo["iterations"]
     rl_all, roofline = kernel_roofline(prof, p.n, p.m, mesh.nnz, k, precision, clocks, args.workload,
                                        idx32=2 if args.workload.startswith("grid") else 4)
+    step_roof = step_hbm(prof, 3, total_ms / args.steps, p.n, p.m, mesh.nnz, k, precision,
+                         idx32=2 if args.workload.startswith("grid") else 4) if prof else None
 
     # the CPU oracle on the same workload (bounded sample)
     cpu = None
@@ -360,6 +362,7 @@ def run_ours(args, rank, world, local_rank):
                        "p99": round(float(np.percentile(step_ms, 99)), 4)},
         "clocks": clocks,
         "roofline": roofline,
+        "step_roofline": step_roof,
         "kernels": rl_all,
         "gpu_launches": gpu_launches(prof, args.steps, its_f, its_a, args.launch),
         "e2e": e2e,
@@ -427,6 +430,28 @@ def kernel_roofline(prof, n, m, nnz, k, precision, clocks, workload, idx32=4):
     table = {kname: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in kv.items()
                      if kk not in ("alu_peak", "bytes")} for kname, kv in rl_all.items()}
     return table, roofline
+
+
+def step_hbm(prof, nsteps, ms_per_step, n, m, nnz, k, precision, idx32=4):
+    """The whole step against the HBM roofline: the algorithmic bytes of every profiled kernel
+    that has a byte model (the solver loop, assembly and the VJP; the small init, finalize,
+    gather and residual kernels are left out, so the figure is a lower bound), per step, divided
+    by the step time of the timed region."""
+    hbm_peak, peak_kind = peaks()
+    total, counted = 0.0, []
+    for name, (cnt, _) in prof.items():
+        is64 = name.startswith(("assemble", "vjp")) or (name.startswith("pcg_") and precision == "fp64")
+        _, by = algorithmic(name, n, m, nnz, k, "fp64" if is64 else "fp32", idx32)
+        if by is None or cnt == 0:
+            continue
+        total += by * cnt / nsteps
+        counted.append(name)
+    if total == 0.0 or ms_per_step <= 0:
+        return None
+    gbs = total / (ms_per_step / 1000.0) / 1e9
+    return {"bytes_per_step": int(total), "achieved_gbs": round(gbs, 1), "peak": hbm_peak,
+            "peak_source": f"{peak_kind} (hbm_gbs copy bandwidth)", "frac": round(gbs / hbm_peak, 4),
+            "kernels_counted": sorted(counted)}
 
 
 # ------------------------------------------------------------------------------- other workloads
@@ -497,7 +522,10 @@ def variant_mixed_grid(api, _native, dev, p, tol, steps, fp64_U, fp64_gV, clocks
            "true_rel_residual": {"forward": max(r["finfo"]["true_rel_residual"]),
                                  "adjoint": max(r["ainfo"]["true_rel_residual"])},
            "rel_err_vs_fp64_gpu": {"U": _rel(r["U"], fp64_U), "gV": _rel(r["gV"], fp64_gV)},
-           "roofline": roof, "kernels": table}
+           "roofline": roof,
+           "step_roofline": step_hbm(r["prof"], 1, r["ms_per_step"], p.n, p.m, r["mesh"].nnz, p.B.shape[1], "mixed",
+                                     idx32=2),
+           "kernels": table}
     r["mesh"].close()
     return out
 
@@ -520,7 +548,10 @@ def variant_largest(api, _native, dev, tol, steps, clocks):
            "true_rel_residual": {"forward": max(r["finfo"]["true_rel_residual"]),
                                  "adjoint": max(r["ainfo"]["true_rel_residual"])},
            "rel_err_vs_fp64_gpu": {"U": _rel(r["U"], r64["U"]), "gV": _rel(r["gV"], r64["gV"])},
-           "resident_mb": round(mesh.device_bytes / 1e6, 1), "roofline": roof, "kernels": table}
+           "resident_mb": round(mesh.device_bytes / 1e6, 1), "roofline": roof,
+           "step_roofline": step_hbm(r["prof"], 1, r["ms_per_step"], p.n, p.m, mesh.nnz, p.B.shape[1], "mixed",
+                                     idx32=2),
+           "kernels": table}
     mesh.close()
     return out
 
