@@ -273,5 +273,43 @@ def subspace_iteration(V, F, t, U0, iters, tol=1e-14, method="auto"):
     return U, np.sum(U * LU, axis=0)
 
 
+def _phi(C):
+    """Upper triangle with half the diagonal: the map X = Phi(R^-T dG R^-1) with X + X^T =
+    R^-T dG R^-1 that gives dR R^-1 for the Cholesky factor (and is its own adjoint)."""
+    return np.triu(C) - 0.5 * np.diag(np.diag(C))
+
+
+def eigs_vjp(V, F, t, U, gU, iters, tol=1e-14, method="auto"):
+    """Gradient of a loss l(U*) with respect to the positions V through the fixed point of
+    Eq. eigiter (§5), U* = f(U*) = Q(S U*) with S = (M + tL)^-1 M (the factor t of the shift
+    drops out in Q), by the implicit-function rule for fixed points: w = gU + J^T w with
+    J = df/dU at U*, solved here by its Neumann series (iters terms; it converges at the forward
+    iteration's own rate when the k lowest eigenvalues are distinct), then dl/dV = (df/dV)^T w.
+    The Q step's adjoint is that of the Cholesky factor of Y^T M Y. U: the converged basis
+    [n][k] (canonical signs); gU = dl/dU [n][k]. Returns gV [n][3]."""
+    rowptr, col, Aval, Lval, M = operator(V, F, t)
+    U, gU = _f64(U), _f64(gU)
+    Y = solve(rowptr, col, Aval, M[:, None] * U, tol=tol, method=method)
+    R = np.linalg.cholesky(Y.T @ (M[:, None] * Y)).T
+    Ri = np.linalg.inv(R)
+    Qraw = Y @ Ri
+    s = np.where(np.sum(M[:, None] * Qraw * U, axis=0) < 0.0, -1.0, 1.0)
+
+    def ybar(w):
+        Qb = w * s[None, :]
+        P = Ri @ _phi(Qraw.T @ Qb) @ Ri.T
+        return Qb @ Ri.T - (M[:, None] * Y) @ (P + P.T), P
+
+    w = gU
+    for _ in range(int(iters)):
+        Yb, _ = ybar(w)
+        w = gU + M[:, None] * solve(rowptr, col, Aval, Yb, tol=tol, method=method)
+    Yb, P = ybar(w)
+    Lam = solve(rowptr, col, Aval, Yb, tol=tol, method=method)
+    gV, _, _ = vjp(V, F, t, Y, Lam, U, False)
+    wts = -np.einsum("ic,cd,id->i", Y, P, Y)
+    return gV + mass_vjp(V, F, wts)
+
+
 def num_threads():
     return 1

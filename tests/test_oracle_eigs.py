@@ -68,3 +68,45 @@ def test_constant_mode_orthonormality_and_fixed_point():
     # a converged U is (to rounding) a fixed point of the step
     U2, _ = oracle.subspace_iteration(V, F, 0.5, U, 1)
     assert np.abs(U2[:, 0] - U[:, 0]).max() <= 1e-12
+
+
+def _bumpy_grid():
+    from paper_2602_12105_gb300 import meshgen as mg
+    p = mg.config_grid(10, 7, seed=0, t=1.0)
+    V = p.V.copy()
+    V[:, 2] = 0.05 * np.random.default_rng(5).standard_normal(V.shape[0])
+    return V, p.F
+
+
+def test_eigs_vjp_matches_central_differences():
+    """d(sum c * U*)/dV through the converged eigenvectors, against central differences of
+    fully converged subspace iterations (step 1e-6) at sampled coordinates."""
+    V, F = _bumpy_grid()
+    n, k = V.shape[0], 3
+    U0 = np.random.default_rng(1).uniform(-1, 1, (n, k))
+    c = np.random.default_rng(2).standard_normal((n, k))
+
+    def converged(Vx):
+        return oracle.subspace_iteration(Vx, F, 1.0, U0, 150)[0]
+
+    U = converged(V)
+    g = oracle.eigs_vjp(V, F, 1.0, U, c, 150)
+    eps = 1e-6
+    for i, d in [(0, 2), (13, 0), (25, 2), (40, 1), (66, 2), (69, 0)]:
+        Vp, Vm = V.copy(), V.copy()
+        Vp[i, d] += eps
+        Vm[i, d] -= eps
+        fd = (np.sum(c * converged(Vp)) - np.sum(c * converged(Vm))) / (2 * eps)
+        assert abs(fd - g[i, d]) <= 1e-6 * max(1.0, abs(fd)), (i, d, fd, g[i, d])
+
+
+def test_eigs_vjp_does_not_depend_on_the_shift():
+    """The converged eigenvectors do not depend on t, so neither may their gradient, although
+    every step of the adjoint uses the shifted operator."""
+    V, F = _bumpy_grid()
+    n, k = V.shape[0], 3
+    U = oracle.subspace_iteration(V, F, 1.0, np.random.default_rng(1).uniform(-1, 1, (n, k)), 150)[0]
+    c = np.random.default_rng(3).standard_normal((n, k))
+    g1 = oracle.eigs_vjp(V, F, 1.0, U, c, 150)
+    g2 = oracle.eigs_vjp(V, F, 0.3, U, c, 400)
+    assert np.abs(g1 - g2).max() <= 1e-9 * np.abs(g1).max()
