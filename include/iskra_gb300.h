@@ -256,13 +256,31 @@ ig_status ig_fairing_step(ig_mesh* mesh, double* V_dev, const double* T_dev, dou
  * lambda_host (may be NULL): k doubles, lambda_c = u_c^T L u_c, computed from the FP64 operator as
  * (u_c^T A u_c - u_c^T M u_c) / t. info (may be NULL): status and iteration count of the last
  * solve. Either synchronises the stream; without both the call is asynchronous.
- * Workspace (4 n + 16 ceil(n / 256) doubles and a few bytes) is allocated on the mesh at the
- * first call. Errors: IG_ERR_STATE (not assembled), IG_ERR_INVALID_ARG (NULL U_dev, k or iters
+ * Workspace (17 n + 16 ceil(n / 256) doubles and a few bytes, shared with ig_eigs_vjp) is
+ * allocated on the mesh at the first call. Errors: IG_ERR_STATE (not assembled), IG_ERR_INVALID_ARG (NULL U_dev, k or iters
  * out of range), IG_ERR_NONFINITE (a Gram matrix was not positive definite: the start columns
  * were dependent or not finite; reported when lambda_host or info is given), the errors of
- * ig_solve, IG_ERR_OOM, IG_ERR_CUDA. The gradient through this fixed point is not provided. */
+ * ig_solve, IG_ERR_OOM, IG_ERR_CUDA. The gradient through this fixed point: ig_eigs_vjp. */
 ig_status ig_eigs(ig_mesh* mesh, int k, int iters, double* U_dev, double* lambda_host, const ig_solve_opts* opts,
                   ig_solve_info* info);
+
+/* Gradient of a loss l(U*) with respect to the positions through the fixed point of ig_eigs,
+ * U* = Q((M + tL)^-1 M U*) (Eq. eigiter, §5), by the implicit-function rule for fixed points:
+ * w = gU + J^T w with J = dQ((M + tL)^-1 M U)/dU at U*, solved by `iters` terms of its Neumann
+ * series (each one k-column solve with the assembled operator; the series contracts at the rate
+ * of the forward iteration, so about as many terms as forward steps are needed, and it converges
+ * only when the k lowest eigenvalues are distinct), then dl/dV = (df/dV)^T w: the adjoint-solve
+ * term <Lambda, d(M U*)/dV - dA/dV Y> (Y = (M + tL)^-1 M U*, Lambda = (M + tL)^-1 Ybar) and the
+ * mass term of the orthonormalization's Gram matrix Y^T M Y. The converged eigenvectors do not
+ * depend on t, nor does this gradient.
+ * V_dev [n][3]: the positions the mesh was assembled at. U_dev [n][k]: the result of ig_eigs.
+ * gU_dev [n][k]: dl/dU*. gV_dev [n][3]: the result. k in 1..4, iters >= 1.
+ * Synchronises. Uses ig_eigs's workspace and the mesh's adjoint buffer.
+ * Errors: IG_ERR_STATE (not assembled), IG_ERR_INVALID_ARG (NULL pointer, k or iters out of range),
+ * IG_ERR_NONFINITE (the Gram matrix of (M + tL)^-1 M U* is not positive definite), the errors of
+ * ig_solve, IG_ERR_OOM, IG_ERR_CUDA. */
+ig_status ig_eigs_vjp(ig_mesh* mesh, const double* V_dev, int k, int iters, const double* U_dev, const double* gU_dev,
+                      double* gV_dev, const ig_solve_opts* opts);
 
 /* ---- allocation-free solve ----------------------------------------------------------------- */
 

@@ -192,6 +192,18 @@ class Mesh:
         lam_t = torch.tensor(list(lam), dtype=torch.float64)
         return (U, lam_t, inf.as_dict()) if info else (U, lam_t)
 
+    def eigs_vjp(self, V: torch.Tensor, U: torch.Tensor, gU: torch.Tensor, iters: int, opts=None):
+        """dl/dV [n][3] through the eigenvector fixed point of eigs (see ig_eigs_vjp), for the
+        result U of eigs at the assembled positions V and the cotangent gU = dl/dU."""
+        V = self._dev(V, 3, "V")
+        U = self._dev(U, None, "U")
+        gU = self._dev(gU, U.shape[1], "gU")
+        gV = torch.empty((self.n, 3), dtype=torch.float64, device=self.ctx.device)
+        self.ctx.sync_stream()
+        self.ctx.check(self.ctx.lib.ig_eigs_vjp(self.h, _ptr(V), U.shape[1], int(iters), _ptr(U), _ptr(gU), _ptr(gV),
+                                                ctypes.byref(opts) if opts is not None else None))
+        return gV
+
     def adjoint(self, V, B, b_is_V, U, G, want_gB=False, want_gt=False, opts=None, info: bool = False):
         V = self._dev(V, 3, "V")
         G = self._dev(G, None, "G")
@@ -246,6 +258,37 @@ class SmoothSolve(torch.autograd.Function):
 def smooth(mesh: Mesh, V: torch.Tensor, B: Optional[torch.Tensor], t, precision: str = "fp64", opts=None):
     """Differentiable implicit smoothing step: solve (M(V) + t L(V)) U = M(V) B (B = V if None)."""
     return SmoothSolve.apply(V, B, t, mesh, precision, opts)
+
+
+class EigsFn(torch.autograd.Function):
+    """The lowest k eigenvectors U of L(V) u = lambda M(V) u by the shift-invert subspace
+    iteration of Eq. eigiter (§5; shift -1/t), differentiable in V through the fixed point
+    (ig_eigs_vjp). The eigenvalues are returned alongside, without a gradient."""
+
+    @staticmethod
+    def forward(ctx, V, mesh: Mesh, t, U0, iters, adj_iters, opts):
+        mesh.assemble(V, float(t), "fp64")
+        U, lam = mesh.eigs(U0, iters, opts=opts)
+        ctx.mesh, ctx.t, ctx.adj_iters, ctx.opts = mesh, float(t), adj_iters, opts
+        ctx.save_for_backward(V, U)
+        ctx.mark_non_differentiable(lam)
+        return U, lam
+
+    @staticmethod
+    def backward(ctx, gU, glam):
+        mesh: Mesh = ctx.mesh
+        V, U = ctx.saved_tensors
+        if mesh._token != (V.data_ptr(), V._version, ctx.t, "fp64"):
+            mesh.assemble(V, ctx.t, "fp64")
+        gV = mesh.eigs_vjp(V, U, gU.to(torch.float64).contiguous(), ctx.adj_iters, opts=ctx.opts)
+        return gV, None, None, None, None, None, None
+
+
+def eigs(mesh: Mesh, V: torch.Tensor, t: float, U0: torch.Tensor, iters: int, adj_iters: Optional[int] = None,
+         opts=None):
+    """Differentiable lowest eigenvectors of the pencil (L(V), M(V)) (see EigsFn); adj_iters
+    defaults to iters. Returns (U, lam)."""
+    return EigsFn.apply(V, mesh, t, U0, iters, adj_iters if adj_iters is not None else iters, opts)
 
 
 class MassFn(torch.autograd.Function):

@@ -843,6 +843,66 @@ ig_status ig_eigs(ig_mesh* mesh, int k, int iters, double* U_dev, double* lambda
   return IG_OK;
 }
 
+ig_status ig_eigs_vjp(ig_mesh* mesh, const double* V_dev, int k, int iters, const double* U_dev, const double* gU_dev,
+                      double* gV_dev, const ig_solve_opts* opts) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (!mesh->assembled) {
+    set_error(ctx, "eigs_vjp before assemble");
+    return IG_ERR_STATE;
+  }
+  if (!V_dev || !U_dev || !gU_dev || !gV_dev) return bad_arg(ctx, "V, U, gU and gV must be non-NULL");
+  if (k < 1 || k > kMaxK) return bad_arg(ctx, "k must be in [1, 4]");
+  if (iters < 1) return bad_arg(ctx, "iters must be >= 1");
+  const ig_solve_opts o = resolve_opts(opts);
+  ig_status cs = check_opts(ctx, o);
+  if (cs != IG_OK) return cs;
+  DeviceGuard guard(ctx->device);
+  const long n = (long)mesh->n;
+  if (!mesh->eig) IG_CK(ctx, mesh_alloc(mesh, &mesh->eig, eig_workspace_doubles(n)), "alloc");
+  const EigBuffers eb = eig_buffers(mesh->eig, n);
+  const int mixed = mesh->assembled == 2;
+  IG_CK(ctx, eig_reset(mesh->eig, n, ctx->stream), "eigs_vjp");
+  auto io = std::make_unique<IoTable>();
+  auto solve = [&](const double* in, double* out, int rhs_mass) -> cudaError_t {
+    io->in[0] = in;
+    io->out[0] = out;
+    return group_solve(mesh->group, k, mixed, *io, rhs_mass, o, ctx->stream);
+  };
+  // Y = (M + tL)^-1 M U*; R^-1 of Y^T M Y and the signs that map Y R^-1 onto U*; W = gU
+  IG_CK(ctx, solve(U_dev, eb.Y, 1), "eigs_vjp solve");
+  IG_CK(ctx, eig_vjp_prepare(k, mesh->eig, mesh->md.M, n, U_dev, gU_dev, ctx->stream), "eigs_vjp");
+  // Neumann series of W = gU + J^T W, J^T W = M (M + tL)^-1 Ybar(W)
+  for (int it = 0; it < iters; ++it) {
+    IG_CK(ctx, eig_vjp_ybar(k, mesh->eig, mesh->md.M, n, ctx->stream), "eigs_vjp");
+    IG_CK(ctx, solve(eb.Yb, eb.X, 0), "eigs_vjp solve");
+    IG_CK(ctx, eig_vjp_next(k, mesh->eig, mesh->md.M, n, gU_dev, ctx->stream), "eigs_vjp");
+  }
+  // dl/dV = <Lambda, d(M U*)/dV - dA/dV Y> with Lambda = (M + tL)^-1 Ybar(W), plus the mass term
+  // of the Gram matrix (weights -Y P Y^T)
+  IG_CK(ctx, eig_vjp_ybar(k, mesh->eig, mesh->md.M, n, ctx->stream), "eigs_vjp");
+  IG_CK(ctx, solve(eb.Yb, mesh->md.lam, 0), "eigs_vjp solve");
+  IG_CK(ctx, eig_vjp_massw(k, mesh->eig, n, ctx->stream), "eigs_vjp");
+  CallDev call{};
+  call.V = V_dev;
+  call.B = U_dev;
+  call.U = eb.Y;
+  call.gV = gV_dev;
+  call.t = mesh->t;
+  call.b_is_V = 0;
+  call.bstride = k;
+  call.wm = eb.wm;
+  IG_CK(ctx, group_set_calls(mesh->group, &call, ctx->stream), "upload");
+  IG_CK(ctx, launch_vjp(mesh->group, k, ctx->stream, 1), "vjp");
+  int fail = 0;
+  IG_CK(ctx, eig_read(mesh->eig, n, k, nullptr, &fail, ctx->stream), "eigs_vjp");
+  if (fail) {
+    set_error(ctx, "eigs_vjp: the Gram matrix of (M + tL)^-1 M U was not positive definite");
+    return IG_ERR_NONFINITE;
+  }
+  return IG_OK;
+}
+
 ig_status ig_profile_enable(int enable) {
   ProfState& P = prof_state();
   std::lock_guard<std::mutex> lk(P.mu);

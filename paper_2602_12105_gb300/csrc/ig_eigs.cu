@@ -13,6 +13,14 @@
 // intermediate iterates do not change the final basis) and lambda_c = u_c^T L u_c, computed as
 // (u_c^T A u_c - u_c^T M u_c) / t with the FP64 operator A = M + tL.
 //
+// The gradient through the fixed point (eig_vjp_*): with S = (M + tL)^-1 M (t drops out in Q)
+// and U* = Q(S U*), the implicit-function rule gives w = gU + J^T w (J = df/dU at U*), solved by
+// its Neumann series, then dl/dV = (df/dV)^T w. For Y = S U*, Y = Qraw R (Qraw = U* diag(s), s the
+// canonical signs) and a cotangent w on U*: Qb = w diag(s), P = R^-1 Phi(Qraw^T Qb) R^-T (Phi: upper
+// triangle, half diagonal), Ybar = Qb R^-T - M Y (P + P^T); then J^T w = M (M + tL)^-1 Ybar, and
+// dl/dV = <Lambda, d(M U*)/dV - dA/dV Y> with Lambda = (M + tL)^-1 Ybar, plus the Gram matrix's mass
+// term d(sum_i M_i w_i)/dV with w_i = -Y_i P Y_i^T.
+//
 // Every reduction is over tiles of kBlock rows; the CTA that completes it (a counter) adds the
 // tile partials in tile order, so results do not depend on scheduling.
 #include <climits>
@@ -29,6 +37,7 @@ constexpr double kSignBand = 1e-6;    // relative band below the largest magnitu
 // Small results: R^-1 (k x k, row-major), column maxima, signs, eigenvalues, status word.
 struct EigSmall {
   double rinv[kMaxK * kMaxK];
+  double p[kMaxK * kMaxK];   // P of the gradient step (row-major)
   double colmax[kMaxK];
   double sign[kMaxK];
   double lambda[kMaxK];
@@ -322,29 +331,218 @@ __global__ void __launch_bounds__(kBlock) eig_flip_kernel(double* __restrict__ U
   for (int c = 0; c < K; ++c) U[row * K + c] *= sm->sign[c];
 }
 
+// ---------------------------------------------------------------------------------------------
+// Gradient through the fixed point.
+
+// s_c = sign(sum_i M_i (Y R^-1)_ic U_ic): the canonical signs that turn Qraw = Y R^-1 into U*.
+template <int K>
+__global__ void __launch_bounds__(kBlock) eig_align_kernel(const double* __restrict__ Y, const double* __restrict__ U,
+                                                           const double* __restrict__ M, long n,
+                                                           double* __restrict__ part, EigSmall* sm) {
+  __shared__ double sh[K * kBlock];
+  __shared__ double ri[K * K];
+  if (threadIdx.x < K * K) ri[threadIdx.x] = sm->rinv[threadIdx.x];
+  __syncthreads();
+  const int ntile = (int)((n + kBlock - 1) / kBlock);
+  const long row = (long)blockIdx.x * kBlock + threadIdx.x;
+  double acc[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) acc[c] = 0.0;
+  if (row < n) {
+    double y[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) y[c] = Y[row * K + c];
+    const double m = M[row];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      double q = 0.0;
+#pragma unroll
+      for (int a = 0; a <= c; ++a) q = fma(y[a], ri[a * K + c], q);
+      acc[c] = m * q * U[row * K + c];
+    }
+  }
+  block_sum<K>(acc, sh);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int c = 0; c < K; ++c) part[(long)blockIdx.x * kEigStride + c] = acc[c];
+  if (!eig_publish(sm, ntile)) return;
+  double tot[K];
+  eig_gather_sum<K>(part, ntile, tot, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < K; ++c) sm->sign[c] = tot[c] < 0.0 ? -1.0 : 1.0;
+    sm->cnt = 0u;
+  }
+}
+
+// C0 = Qraw^T Qb (Qb = w diag(s)), then P = R^-1 Phi(C0) R^-T on the completing CTA.
+template <int K>
+__global__ void __launch_bounds__(kBlock) eig_qtq_kernel(const double* __restrict__ Y, const double* __restrict__ W,
+                                                         long n, double* __restrict__ part, EigSmall* sm) {
+  __shared__ double sh[K * K * kBlock];
+  __shared__ double ri[K * K];
+  __shared__ double sg[K];
+  if (threadIdx.x < K * K) ri[threadIdx.x] = sm->rinv[threadIdx.x];
+  if (threadIdx.x < K) sg[threadIdx.x] = sm->sign[threadIdx.x];
+  __syncthreads();
+  const int ntile = (int)((n + kBlock - 1) / kBlock);
+  const long row = (long)blockIdx.x * kBlock + threadIdx.x;
+  double acc[K * K];
+#pragma unroll
+  for (int i = 0; i < K * K; ++i) acc[i] = 0.0;
+  if (row < n) {
+    double y[K], q[K], b[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) y[c] = Y[row * K + c];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a <= c; ++a) v = fma(y[a], ri[a * K + c], v);
+      q[c] = v;
+      b[c] = W[row * K + c] * sg[c];
+    }
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+      for (int c = 0; c < K; ++c) acc[a * K + c] = q[a] * b[c];
+  }
+  block_sum<K * K>(acc, sh);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < K * K; ++i) part[(long)blockIdx.x * kEigStride + i] = acc[i];
+  if (!eig_publish(sm, ntile)) return;
+  double c0[K * K];
+  eig_gather_sum<K * K>(part, ntile, c0, sh);
+  if (threadIdx.x != 0) return;
+  double C[K][K], T[K][K];
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+#pragma unroll
+    for (int c = 0; c < K; ++c) C[a][c] = a < c ? c0[a * K + c] : (a == c ? 0.5 * c0[a * K + c] : 0.0);
+  // T = R^-1 C, then P = T R^-T
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      double v = 0.0;
+#pragma unroll
+      for (int e = 0; e < K; ++e) v = fma(ri[a * K + e], C[e][c], v);
+      T[a][c] = v;
+    }
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      double v = 0.0;
+#pragma unroll
+      for (int e = 0; e < K; ++e) v = fma(T[a][e], ri[c * K + e], v);
+      sm->p[a * K + c] = v;
+    }
+  sm->cnt = 0u;
+}
+
+// Ybar = Qb R^-T - M Y (P + P^T), row by row.
+template <int K>
+__global__ void __launch_bounds__(kBlock) eig_ybar_kernel(const double* __restrict__ Y, const double* __restrict__ W,
+                                                          const double* __restrict__ M, long n,
+                                                          double* __restrict__ Yb, const EigSmall* __restrict__ sm) {
+  __shared__ double ri[K * K];
+  __shared__ double ps[K * K];  // P + P^T
+  __shared__ double sg[K];
+  if (threadIdx.x < K * K) {
+    const int a = threadIdx.x / K, c = threadIdx.x % K;
+    ri[threadIdx.x] = sm->rinv[threadIdx.x];
+    ps[threadIdx.x] = sm->p[a * K + c] + sm->p[c * K + a];
+  }
+  if (threadIdx.x < K) sg[threadIdx.x] = sm->sign[threadIdx.x];
+  __syncthreads();
+  const long row = (long)blockIdx.x * kBlock + threadIdx.x;
+  if (row >= n) return;
+  double y[K], b[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    y[c] = Y[row * K + c];
+    b[c] = W[row * K + c] * sg[c];
+  }
+  const double m = M[row];
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    double v = 0.0, u = 0.0;
+#pragma unroll
+    for (int a = c; a < K; ++a) v = fma(b[a], ri[c * K + a], v);  // (Qb R^-T)_c = sum_a Qb_a Rinv[c][a]
+#pragma unroll
+    for (int a = 0; a < K; ++a) u = fma(y[a], ps[a * K + c], u);
+    Yb[row * K + c] = fma(-m, u, v);
+  }
+}
+
+// W = gU + M X (the next Neumann term).
+template <int K>
+__global__ void __launch_bounds__(kBlock) eig_wnext_kernel(const double* __restrict__ gU, const double* __restrict__ X,
+                                                           const double* __restrict__ M, long n, double* __restrict__ W) {
+  const long row = (long)blockIdx.x * kBlock + threadIdx.x;
+  if (row >= n) return;
+  const double m = M[row];
+#pragma unroll
+  for (int c = 0; c < K; ++c) W[row * K + c] = fma(m, X[row * K + c], gU[row * K + c]);
+}
+
+// Mass weights of the Gram matrix's term: w_i = -Y_i P Y_i^T.
+template <int K>
+__global__ void __launch_bounds__(kBlock) eig_massw_kernel(const double* __restrict__ Y, long n,
+                                                           double* __restrict__ wm, const EigSmall* __restrict__ sm) {
+  __shared__ double ps[K * K];
+  if (threadIdx.x < K * K) ps[threadIdx.x] = sm->p[threadIdx.x];
+  __syncthreads();
+  const long row = (long)blockIdx.x * kBlock + threadIdx.x;
+  if (row >= n) return;
+  double y[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) y[c] = Y[row * K + c];
+  double v = 0.0;
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+#pragma unroll
+    for (int c = 0; c < K; ++c) v = fma(y[a] * ps[a * K + c], y[c], v);
+  wm[row] = -v;
+}
+
 }  // namespace
+
+// Workspace layout (doubles): Y, Ybar, X, W [n][4] each; mass weights [n]; tile partials
+// [ntile][kEigStride]; EigSmall.
+struct EigLayout {
+  double *Y, *Yb, *X, *W, *wm, *part;
+  EigSmall* sm;
+  EigLayout(double* ws, long n) {
+    const long ntile = (n + kBlock - 1) / kBlock;
+    Y = ws;
+    Yb = Y + kMaxK * n;
+    X = Yb + kMaxK * n;
+    W = X + kMaxK * n;
+    wm = W + kMaxK * n;
+    part = wm + n;
+    sm = reinterpret_cast<EigSmall*>(part + kEigStride * ntile);
+  }
+};
 
 size_t eig_workspace_doubles(long n) {
   const long ntile = (n + kBlock - 1) / kBlock;
-  return (size_t)(kMaxK * n + kEigStride * ntile) + (sizeof(EigSmall) + 7) / 8 + 1;
-}
-
-// Workspace: Y [n][k], tile partials [ntile][kEigStride], EigSmall (zeroed by eig_reset).
-static EigSmall* eig_small(double* ws, long n) {
-  const long ntile = (n + kBlock - 1) / kBlock;
-  return reinterpret_cast<EigSmall*>(ws + kMaxK * n + kEigStride * ntile);
+  return (size_t)(4 * kMaxK * n + n + kEigStride * ntile) + (sizeof(EigSmall) + 7) / 8 + 1;
 }
 
 cudaError_t eig_reset(double* ws, long n, cudaStream_t st) {
-  return cudaMemsetAsync(eig_small(ws, n), 0, sizeof(EigSmall), st);
+  return cudaMemsetAsync(EigLayout(ws, n).sm, 0, sizeof(EigSmall), st);
 }
 
 template <int K>
 static cudaError_t eig_step_k(double* ws, const double* M, long n, double* U, cudaStream_t st) {
   const long ntile = (n + kBlock - 1) / kBlock;
-  double* Y = ws;
-  double* part = ws + kMaxK * n;
-  EigSmall* sm = eig_small(ws, n);
+  const EigLayout L(ws, n);
+  double* Y = L.Y;
+  double* part = L.part;
+  EigSmall* sm = L.sm;
   {
     IG_PROF("eig_gram", st);
     eig_gram_kernel<K><<<(unsigned)ntile, kBlock, 0, st>>>(Y, M, n, part, sm);
@@ -369,8 +567,9 @@ cudaError_t eig_step(int k, double* ws, const double* M, long n, double* U, cuda
 template <int K>
 static cudaError_t eig_finish_k(const MeshDev* mds, double t, double* ws, long n, double* U, cudaStream_t st) {
   const long ntile = (n + kBlock - 1) / kBlock;
-  double* part = ws + kMaxK * n;
-  EigSmall* sm = eig_small(ws, n);
+  const EigLayout L(ws, n);
+  double* part = L.part;
+  EigSmall* sm = L.sm;
   {
     IG_PROF("eig_stats", st);
     eig_stats_kernel<K><<<(unsigned)ntile, kBlock, 0, st>>>(mds, U, t, part, sm);
@@ -397,12 +596,110 @@ cudaError_t eig_finish(int k, const MeshDev* mds, double t, double* ws, long n, 
 }
 
 cudaError_t eig_read(double* ws, long n, int k, double* lambda_host, int* fail_host, cudaStream_t st) {
-  EigSmall* sm = eig_small(ws, n);
+  EigSmall* sm = EigLayout(ws, n).sm;
   cudaError_t e = cudaSuccess;
   if (lambda_host) e = cudaMemcpyAsync(lambda_host, sm->lambda, sizeof(double) * k, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && fail_host) e = cudaMemcpyAsync(fail_host, &sm->fail, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e;
+}
+
+// Gradient step helpers (see the header comment). Y: the workspace's Y = (M + tL)^-1 M U*.
+template <int K>
+static cudaError_t eig_vjp_prepare_k(double* ws, const double* M, long n, const double* U, const double* gU,
+                                     cudaStream_t st) {
+  const long ntile = (n + kBlock - 1) / kBlock;
+  const EigLayout L(ws, n);
+  {
+    IG_PROF("eig_gram", st);
+    eig_gram_kernel<K><<<(unsigned)ntile, kBlock, 0, st>>>(L.Y, M, n, L.part, L.sm);
+  }
+  {
+    IG_PROF("eig_align", st);
+    eig_align_kernel<K><<<(unsigned)ntile, kBlock, 0, st>>>(L.Y, U, M, n, L.part, L.sm);
+  }
+  cudaError_t e = cudaMemcpyAsync(L.W, gU, sizeof(double) * K * n, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t eig_vjp_ybar_k(double* ws, const double* M, long n, cudaStream_t st) {
+  const long ntile = (n + kBlock - 1) / kBlock;
+  const EigLayout L(ws, n);
+  {
+    IG_PROF("eig_qtq", st);
+    eig_qtq_kernel<K><<<(unsigned)ntile, kBlock, 0, st>>>(L.Y, L.W, n, L.part, L.sm);
+  }
+  {
+    IG_PROF("eig_ybar", st);
+    eig_ybar_kernel<K><<<(unsigned)ntile, kBlock, 0, st>>>(L.Y, L.W, M, n, L.Yb, L.sm);
+  }
+  return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t eig_vjp_next_k(double* ws, const double* M, long n, const double* gU, cudaStream_t st) {
+  const long ntile = (n + kBlock - 1) / kBlock;
+  const EigLayout L(ws, n);
+  IG_PROF("eig_wnext", st);
+  eig_wnext_kernel<K><<<(unsigned)ntile, kBlock, 0, st>>>(gU, L.X, M, n, L.W);
+  return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t eig_vjp_massw_k(double* ws, long n, cudaStream_t st) {
+  const long ntile = (n + kBlock - 1) / kBlock;
+  const EigLayout L(ws, n);
+  IG_PROF("eig_massw", st);
+  eig_massw_kernel<K><<<(unsigned)ntile, kBlock, 0, st>>>(L.Y, n, L.wm, L.sm);
+  return cudaGetLastError();
+}
+
+cudaError_t eig_vjp_prepare(int k, double* ws, const double* M, long n, const double* U, const double* gU,
+                            cudaStream_t st) {
+  switch (k) {
+    case 1: return eig_vjp_prepare_k<1>(ws, M, n, U, gU, st);
+    case 2: return eig_vjp_prepare_k<2>(ws, M, n, U, gU, st);
+    case 3: return eig_vjp_prepare_k<3>(ws, M, n, U, gU, st);
+    case 4: return eig_vjp_prepare_k<4>(ws, M, n, U, gU, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t eig_vjp_ybar(int k, double* ws, const double* M, long n, cudaStream_t st) {
+  switch (k) {
+    case 1: return eig_vjp_ybar_k<1>(ws, M, n, st);
+    case 2: return eig_vjp_ybar_k<2>(ws, M, n, st);
+    case 3: return eig_vjp_ybar_k<3>(ws, M, n, st);
+    case 4: return eig_vjp_ybar_k<4>(ws, M, n, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t eig_vjp_next(int k, double* ws, const double* M, long n, const double* gU, cudaStream_t st) {
+  switch (k) {
+    case 1: return eig_vjp_next_k<1>(ws, M, n, gU, st);
+    case 2: return eig_vjp_next_k<2>(ws, M, n, gU, st);
+    case 3: return eig_vjp_next_k<3>(ws, M, n, gU, st);
+    case 4: return eig_vjp_next_k<4>(ws, M, n, gU, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t eig_vjp_massw(int k, double* ws, long n, cudaStream_t st) {
+  switch (k) {
+    case 1: return eig_vjp_massw_k<1>(ws, n, st);
+    case 2: return eig_vjp_massw_k<2>(ws, n, st);
+    case 3: return eig_vjp_massw_k<3>(ws, n, st);
+    case 4: return eig_vjp_massw_k<4>(ws, n, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+EigBuffers eig_buffers(double* ws, long n) {
+  const EigLayout L(ws, n);
+  return EigBuffers{L.Y, L.Yb, L.X, L.W, L.wm};
 }
 
 }  // namespace ig

@@ -341,6 +341,16 @@ cudaError_t eig_step(int k, double* ws, const double* M, long n, double* U, cuda
 // canonical signs of U's columns and the eigenvalues (u^T A u - u^T M u) / t
 cudaError_t eig_finish(int k, const MeshDev* mds, double t, double* ws, long n, double* U, cudaStream_t st);
 cudaError_t eig_read(double* ws, long n, int k, double* lambda_host, int* fail_host, cudaStream_t st);
+// gradient through the fixed point: Y (= (M + tL)^-1 M U*) must be in the workspace first
+struct EigBuffers {
+  double *Y, *Yb, *X, *W, *wm;  // Y, Ybar, the solve of Ybar, the Neumann iterate W, mass weights
+};
+EigBuffers eig_buffers(double* ws, long n);
+cudaError_t eig_vjp_prepare(int k, double* ws, const double* M, long n, const double* U, const double* gU,
+                            cudaStream_t st);                      // R^-1, signs, W = gU
+cudaError_t eig_vjp_ybar(int k, double* ws, const double* M, long n, cudaStream_t st);  // P, Ybar from W
+cudaError_t eig_vjp_next(int k, double* ws, const double* M, long n, const double* gU, cudaStream_t st);  // W = gU + M X
+cudaError_t eig_vjp_massw(int k, double* ws, long n, cudaStream_t st);  // wm = -Y P Y^T per row
 
 // ig_vjp.cu
 // mode 0: solve terms; 1: solve terms and the mass weights of the calls; 2: mass weights alone

@@ -116,3 +116,53 @@ def test_eigs_errors(api):
     # the mesh still solves afterwards
     U, lam = mesh.eigs(_t(np.random.default_rng(1).uniform(-1, 1, (n, 2))), 5)
     assert np.isfinite(U.cpu().numpy()).all()
+
+
+def _bumpy_grid(nx=10, ny=7, seed=5):
+    V, F = _flat_grid(nx, ny)
+    V[:, 2] = 0.05 * np.random.default_rng(seed).standard_normal(V.shape[0])
+    return V, F
+
+
+@pytest.mark.parametrize("nx,ny,k,t", [(10, 7, 3, 1.0), (63, 50, 4, 0.5)])
+def test_eigs_vjp_matches_oracle(api, nx, ny, k, t):
+    """dl/dV through the fixed point, with the same converged U and cotangent on both sides
+    (3500 rows in the second case: 14 tiles, the oracle solving by PCG)."""
+    V, F = _bumpy_grid(nx, ny)
+    n = V.shape[0]
+    U0 = np.random.default_rng(1).uniform(-1, 1, (n, k))
+    iters = 150 if n < 1000 else 60
+    U, _ = oracle.subspace_iteration(V, F, t, U0, iters)
+    c = np.random.default_rng(2).standard_normal((n, k))
+    ref = oracle.eigs_vjp(V, F, t, U, c, iters)
+    mesh = api.Mesh(_t(F, torch.int32), n)
+    mesh.assemble(_t(V), t)
+    g = mesh.eigs_vjp(_t(V), _t(U), _t(c), iters, opts=api.make_opts(rel_tol=1e-13)).cpu().numpy()
+    assert np.abs(g - ref).max() <= 1e-8 * np.abs(ref).max(), (np.abs(g - ref).max(), np.abs(ref).max())
+
+
+def test_eigs_autograd_matches_central_differences(api):
+    """Through the autograd wrapper: d(sum c * U)/dV against central differences of the
+    converged GPU eigenvectors (step 1e-5: each solve stops at 1e-13, so smaller steps would
+    see that rounding) at sampled coordinates."""
+    V, F = _bumpy_grid()
+    n, k = V.shape[0], 3
+    U0 = _t(np.random.default_rng(1).uniform(-1, 1, (n, k)))
+    c = _t(np.random.default_rng(2).standard_normal((n, k)))
+    mesh = api.Mesh(_t(F, torch.int32), n)
+    opts = api.make_opts(rel_tol=1e-13)
+    Vt = _t(V).requires_grad_(True)
+    U, lam = api.eigs(mesh, Vt, 1.0, U0, 150, opts=opts)
+    (U * c).sum().backward()
+    g = Vt.grad.cpu().numpy()
+    eps = 1e-5
+    for i, d in [(0, 2), (13, 0), (25, 2), (66, 2)]:
+        vals = []
+        for sgn in (1.0, -1.0):
+            Vp = V.copy()
+            Vp[i, d] += sgn * eps
+            mesh.assemble(_t(Vp), 1.0)
+            Up, _ = mesh.eigs(U0, 150, opts=opts)
+            vals.append(float((Up * c).sum()))
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        assert abs(fd - g[i, d]) <= 1e-6 * max(1.0, abs(fd)), (i, d, fd, g[i, d])
