@@ -311,5 +311,58 @@ def eigs_vjp(V, F, t, U, gU, iters, tol=1e-14, method="auto"):
     return gV + mass_vjp(V, F, wts)
 
 
+def hat_gradients(V, F):
+    """Per face, the gradients of its three piecewise-linear hat functions, [m][3][3] (corner,
+    coordinate), and the face areas [m]: grad phi_c = n x e_c / (2 area) with e_c the edge
+    opposite corner c taken counter-clockwise (e_0 = p_2 - p_1, ...) and n the unit normal."""
+    V, F = _f64(V), _i32(F)
+    P = V[F]                                   # [m][3][3]
+    e = np.stack([P[:, 2] - P[:, 1], P[:, 0] - P[:, 2], P[:, 1] - P[:, 0]], axis=1)
+    N = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])
+    twice = np.linalg.norm(N, axis=1)
+    nhat = N / twice[:, None]
+    grads = np.cross(nhat[:, None, :], e) / twice[:, None, None]
+    return grads, 0.5 * twice
+
+
+def face_gradient(V, F, u):
+    """G u: the gradient of the piecewise-linear function u [n] on every face, [m][3]."""
+    grads, _ = hat_gradients(V, F)
+    return np.einsum("fcd,fc->fd", grads, _f64(u)[_i32(F)])
+
+
+def divergence(V, F, Y):
+    """D Y = G^T A_F Y: per vertex, the sum over its faces of area * <grad phi, Y_f> for per-face
+    vectors Y [m][3]. (With this D the cotangent Laplacian is L = D G.)"""
+    grads, area = hat_gradients(V, F)
+    contrib = area[:, None] * np.einsum("fcd,fd->fc", grads, _f64(Y))
+    out = np.zeros(_f64(V).shape[0])
+    np.add.at(out, _i32(F).ravel(), contrib.ravel())
+    return out
+
+
+def rgd_u_step(V, F, sources, y, z, rho, beta, tol=1e-14):
+    """The u-step of the ADMM scheme for regularized geodesic distances (§ geodesics, formulation
+    eq. edelstein): b = m - D y + rho D z with m the lumped vertex areas, then L u = b / (beta + rho)
+    on the vertices that are not sources, u = 0 on the sources (the constraint u_s = 0). Dense
+    Cholesky of the reduced Laplacian for small meshes, else Jacobi-PCG to tol."""
+    V, F = _f64(V), _i32(F)
+    n = V.shape[0]
+    rowptr, col, Lval = laplacian(V, F)
+    m = mass(V, F)
+    b = (m - divergence(V, F, y) + rho * divergence(V, F, z)) / (beta + rho)
+    src = np.zeros(n, dtype=bool)
+    src[np.asarray(sources, dtype=np.int64)] = True
+    # the reduced system as a CSR matrix on all vertices: identity rows and columns at the sources
+    Aval = Lval.copy()
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    Aval[src[rows] | src[col]] = 0.0
+    Aval[(rows == col) & src[rows]] = 1.0
+    rhs = np.where(src, 0.0, b)
+    u = solve(rowptr, col, Aval, rhs[:, None], tol=tol)[:, 0]
+    u[src] = 0.0
+    return u
+
+
 def num_threads():
     return 1
