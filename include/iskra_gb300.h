@@ -282,6 +282,27 @@ ig_status ig_eigs(ig_mesh* mesh, int k, int iters, double* U_dev, double* lambda
 ig_status ig_eigs_vjp(ig_mesh* mesh, const double* V_dev, int k, int iters, const double* U_dev, const double* gU_dev,
                       double* gV_dev, const ig_solve_opts* opts);
 
+/* ---- regularized geodesic distances: the ADMM u-step --------------------------------------- */
+
+/* The u-step of the ADMM scheme for regularized geodesic distances (the geodesics application,
+ * formulation eq. edelstein: minimise -m^T u + beta/2 u^T L u subject to |(G u)_f| <= 1 and
+ * u_s = 0 on the sources): with per-face iterates y_dev and z_dev [m][3] (the dual variable and
+ * z = G u),
+ *   b = m - D y + rho D z,   L u = b / (beta + rho) on the non-source vertices,   u = 0 on the sources,
+ * with m the lumped vertex areas, G the face gradient of piecewise-linear functions, D = G^T A_F its
+ * area-weighted adjoint (L = D G is the cotangent Laplacian). The solve is the Jacobi-PCG of
+ * ig_solve on the Laplacian whose source rows and columns are the identity, in FP64, to
+ * opts->rel_tol. V_dev [n][3]: positions. sources_host: nsrc >= 1 vertex indices in host memory
+ * (every connected part of the mesh needs one, or the system is singular and the solve reports
+ * IG_ERR_NOT_CONVERGED). u_dev [n]: the result. rho, beta >= 0, rho + beta > 0.
+ * The call assembles the mesh at V (t = 1) and then rewrites its operator, so the mesh must be
+ * assembled again before any other solve. info as for ig_solve (synchronises).
+ * Errors: IG_ERR_INVALID_ARG (NULL pointer, no source, a source out of range, bad rho or beta),
+ * the errors of ig_assemble and ig_solve, IG_ERR_OOM, IG_ERR_CUDA. */
+ig_status ig_rgd_u_step(ig_mesh* mesh, const double* V_dev, const int32_t* sources_host, int nsrc, const double* y_dev,
+                        const double* z_dev, double rho, double beta, double* u_dev, const ig_solve_opts* opts,
+                        ig_solve_info* info);
+
 /* ---- allocation-free solve ----------------------------------------------------------------- */
 
 /* Largest number of rows ig_solve_csr_noalloc accepts. */

@@ -92,6 +92,7 @@ SIGNATURES = {
     "ig_fairing_step": (_i32, [_vp, _vp, _vp, _dbl, _dbl, _i32, _P(SolveOpts), _P(_dbl), _P(SolveInfo)]),
     "ig_eigs": (_i32, [_vp, _i32, _i32, _vp, _P(_dbl), _P(SolveOpts), _P(SolveInfo)]),
     "ig_eigs_vjp": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _P(SolveOpts)]),
+    "ig_rgd_u_step": (_i32, [_vp, _vp, _P(_i32), _i32, _vp, _vp, _dbl, _dbl, _vp, _P(SolveOpts), _P(SolveInfo)]),
     "ig_solve_csr_noalloc": (_i32, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, _i32, _vp, _vp, _P(SolveOpts),
                                      _P(SolveInfo)]),
     "ig_profile_enable": (_i32, [_i32]),

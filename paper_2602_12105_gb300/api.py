@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 from typing import Optional
 
+import numpy as np
 import torch
 
 from . import _native as N
@@ -191,6 +192,32 @@ class Mesh:
         self.ctx.check(st)
         lam_t = torch.tensor(list(lam), dtype=torch.float64)
         return (U, lam_t, inf.as_dict()) if info else (U, lam_t)
+
+    def rgd_u_step(self, V: torch.Tensor, sources, y: torch.Tensor, z: torch.Tensor, rho: float, beta: float,
+                   opts=None, info: bool = False):
+        """The u-step of the regularized-geodesic ADMM (see ig_rgd_u_step): u [n] with
+        L u = (m - D y + rho D z) / (beta + rho) off the sources and u = 0 on them, for per-face
+        y and z [m][3]. Leaves the mesh to be assembled again before other solves."""
+        V = self._dev(V, 3, "V")
+        y, z = (x.to(self.ctx.device, torch.float64).contiguous() for x in (y, z))
+        if y.shape != (self.m, 3) or z.shape != (self.m, 3):
+            raise ValueError(f"y and z must be [{self.m}][3]")
+        src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).ravel())
+        u = torch.empty(self.n, dtype=torch.float64, device=self.ctx.device)
+        inf = N.SolveInfo() if info else None
+        self.ctx.sync_stream()
+        st = self.ctx.lib.ig_rgd_u_step(self.h, _ptr(V), src.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                        int(src.size), _ptr(y), _ptr(z), float(rho), float(beta), _ptr(u),
+                                        ctypes.byref(opts) if opts is not None else None,
+                                        ctypes.byref(inf) if inf is not None else None)
+        self._token = None
+        self.t = None
+        if info:
+            if st not in (N.IG_OK, N.IG_ERR_NOT_CONVERGED):
+                self.ctx.check(st)
+            return u, inf.as_dict()
+        self.ctx.check(st)
+        return u
 
     def eigs_vjp(self, V: torch.Tensor, U: torch.Tensor, gU: torch.Tensor, iters: int, opts=None):
         """dl/dV [n][3] through the eigenvector fixed point of eigs (see ig_eigs_vjp), for the

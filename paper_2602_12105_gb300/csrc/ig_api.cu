@@ -903,6 +903,48 @@ ig_status ig_eigs_vjp(ig_mesh* mesh, const double* V_dev, int k, int iters, cons
   return IG_OK;
 }
 
+ig_status ig_rgd_u_step(ig_mesh* mesh, const double* V_dev, const int32_t* sources_host, int nsrc, const double* y_dev,
+                        const double* z_dev, double rho, double beta, double* u_dev, const ig_solve_opts* opts,
+                        ig_solve_info* info) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (!V_dev || !sources_host || !y_dev || !z_dev || !u_dev) return bad_arg(ctx, "V, sources, y, z and u must be non-NULL");
+  if (nsrc < 1) return bad_arg(ctx, "at least one source is needed (u_s = 0 fixes the constant)");
+  if (!(rho >= 0.0) || !(beta >= 0.0) || !(rho + beta > 0.0) || !(rho + beta < 1e300))
+    return bad_arg(ctx, "rho and beta must be finite, >= 0, and not both 0");
+  const long n = (long)mesh->n;
+  std::vector<int> mask((size_t)n, 0);
+  for (int i = 0; i < nsrc; ++i) {
+    if (sources_host[i] < 0 || sources_host[i] >= n) return bad_arg(ctx, "a source index is out of range");
+    mask[(size_t)sources_host[i]] = 1;
+  }
+  const ig_solve_opts o = resolve_opts(opts);
+  ig_status cs = check_opts(ctx, o);
+  if (cs != IG_OK) return cs;
+  DeviceGuard guard(ctx->device);
+  if (!mesh->rgd) IG_CK(ctx, mesh_alloc(mesh, &mesh->rgd, 2 * (size_t)n), "alloc");
+  double* b = mesh->rgd;
+  int* src = reinterpret_cast<int*>(mesh->rgd + n);
+  IG_CK(ctx, cudaMemcpyAsync(src, mask.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream), "sources");
+  // A = M + L (t = 1), then the Laplacian with the sources' rows and columns replaced by the identity
+  ig_status st = ig_assemble(mesh, V_dev, 1.0, IG_PRECISION_FP64);
+  if (st != IG_OK) return st;
+  IG_CK(ctx, launch_rgd_operator(mesh->group.mds, (int)n, src, ctx->stream), "u-step operator");
+  IG_CK(ctx, launch_rgd_rhs(mesh->group.mds, (int)n, V_dev, y_dev, z_dev, rho, beta, src, b, ctx->stream),
+        "u-step rhs");
+  auto io = std::make_unique<IoTable>();
+  io->in[0] = b;
+  io->out[0] = u_dev;
+  st = IG_OK;
+  cudaError_t e = group_solve(mesh->group, 1, 0, *io, 0, o, ctx->stream);
+  if (e == cudaSuccess && info) e = group_true_residual(mesh->group, 1, *io, 0, ctx->stream);
+  if (e == cudaSuccess && info) st = collect_info(mesh, 1, info);
+  // the values are no longer the smoothing operator
+  mesh->assembled = 0;
+  IG_CK(ctx, e, "u-step solve");
+  return st;
+}
+
 ig_status ig_profile_enable(int enable) {
   ProfState& P = prof_state();
   std::lock_guard<std::mutex> lk(P.mu);

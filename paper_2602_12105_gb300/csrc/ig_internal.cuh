@@ -305,6 +305,7 @@ struct ig_mesh {
   std::vector<void*> allocs;
   double* fair = nullptr;   // inverse-fairing workspace: U, G, g, g~ [n][3], w [n], loss (on first use)
   double* eig = nullptr;    // eigen-iteration workspace (eig_workspace_doubles, on first use)
+  double* rgd = nullptr;    // geodesic u-step workspace: right-hand side [n], source mask [n] ints
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -351,6 +352,11 @@ cudaError_t eig_vjp_prepare(int k, double* ws, const double* M, long n, const do
 cudaError_t eig_vjp_ybar(int k, double* ws, const double* M, long n, cudaStream_t st);  // P, Ybar from W
 cudaError_t eig_vjp_next(int k, double* ws, const double* M, long n, const double* gU, cudaStream_t st);  // W = gU + M X
 cudaError_t eig_vjp_massw(int k, double* ws, long n, cudaStream_t st);  // wm = -Y P Y^T per row
+
+// ig_rgd.cu: the u-step of the regularized-geodesic ADMM (mds: a group of one mesh)
+cudaError_t launch_rgd_operator(const MeshDev* mds, int n, const int* src, cudaStream_t st);
+cudaError_t launch_rgd_rhs(const MeshDev* mds, int n, const double* V, const double* y, const double* z, double rho,
+                           double beta, const int* src, double* b, cudaStream_t st);
 
 // ig_vjp.cu
 // mode 0: solve terms; 1: solve terms and the mass weights of the calls; 2: mass weights alone
