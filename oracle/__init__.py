@@ -364,5 +364,64 @@ def rgd_u_step(V, F, sources, y, z, rho, beta, tol=1e-14):
     return u
 
 
+def divergence_vjp(V, F, lam, W):
+    """d(lam^T D W)/dV [n][3] for per-vertex lam [n] and per-face vectors W [m][3] held fixed.
+    Per face, sum_c lam_c area <grad phi_c, W_f> = n . (E x W_f) / 2 with E = sum_c lam_c e_c
+    (e_c the edge opposite corner c) and n the unit normal; differentiated through E (linear in
+    the positions) and through n (dn = (I - n n^T) dN / |N|, N = (p1 - p0) x (p2 - p0))."""
+    V, F, lam, W = _f64(V), _i32(F), _f64(lam), _f64(W)
+    P = V[F]
+    lf = lam[F]                                             # [m][3]
+    e = np.stack([P[:, 2] - P[:, 1], P[:, 0] - P[:, 2], P[:, 1] - P[:, 0]], axis=1)
+    E = np.einsum("fc,fcd->fd", lf, e)
+    a, b = P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]
+    N = np.cross(a, b)
+    nN = np.linalg.norm(N, axis=1)
+    nh = N / nN[:, None]
+    g = np.zeros((F.shape[0], 3, 3))
+    # through E: dE = sum_c (lam_{c+1} - lam_{c+2}) dp_c, and n . (dE x W) = dE . (W x n)
+    wxn = np.cross(W, nh)
+    for c in range(3):
+        g[:, c] += 0.5 * (lf[:, (c + 1) % 3] - lf[:, (c + 2) % 3])[:, None] * wxn
+    # through n: v = (I - n n^T)(E x W) / |N|, and v . dN = da . (b x v) + db . (v x a)
+    ExW = np.cross(E, W)
+    v = (ExW - np.sum(ExW * nh, axis=1)[:, None] * nh) / nN[:, None]
+    ga, gb = np.cross(b, v), np.cross(v, a)
+    g[:, 1] += 0.5 * ga
+    g[:, 2] += 0.5 * gb
+    g[:, 0] -= 0.5 * (ga + gb)
+    out = np.zeros_like(V)
+    np.add.at(out, F.ravel(), g.reshape(-1, 3))
+    return out
+
+
+def rgd_u_step_vjp(V, F, sources, y, z, rho, beta, gu, tol=1e-14):
+    """Gradients of l(u) through the u-step (rgd_u_step) for gu = dl/du [n]: with
+    lam = L_D^-1 gu (L_D the source-constrained Laplacian, lam = 0 on the sources),
+      dl/dy_f = -area_f grad(lam)_f / (beta + rho),   dl/dz_f = rho area_f grad(lam)_f / (beta + rho),
+      dl/dV = [<lam, dm> + <lam, dD (rho z - y)>] / (beta + rho) - <lam, dL u>.
+    Returns (gV [n][3], gy [m][3], gz [m][3])."""
+    V, F = _f64(V), _i32(F)
+    n = V.shape[0]
+    u = rgd_u_step(V, F, sources, y, z, rho, beta, tol=tol)
+    rowptr, col, Lval = laplacian(V, F)
+    src = np.zeros(n, dtype=bool)
+    src[np.asarray(sources, dtype=np.int64)] = True
+    Aval = Lval.copy()
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    Aval[src[rows] | src[col]] = 0.0
+    Aval[(rows == col) & src[rows]] = 1.0
+    lam = solve(rowptr, col, Aval, np.where(src, 0.0, _f64(gu))[:, None], tol=tol)[:, 0]
+    lam[src] = 0.0
+    s = 1.0 / (beta + rho)
+    grads, area = hat_gradients(V, F)
+    agl = area[:, None] * np.einsum("fcd,fc->fd", grads, lam[F])   # area * grad(lam) per face
+    gy, gz = -s * agl, rho * s * agl
+    # <lam, dm> / (beta + rho) - <lam, dL u>: the smoothing VJP with t = 1 (A = M + L), B = u + s, U = u
+    gV, _, _ = vjp(V, F, 1.0, u[:, None], lam[:, None], (u + s)[:, None], False)
+    gV = gV + s * divergence_vjp(V, F, lam, rho * _f64(z) - _f64(y))
+    return gV, gy, gz
+
+
 def num_threads():
     return 1

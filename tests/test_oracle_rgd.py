@@ -57,3 +57,35 @@ def test_u_step_is_the_reduced_sparse_solve():
     ref[free] = spl.spsolve(L[free][:, free].tocsc(), b[free])
     assert np.all(u[src] == 0.0)
     assert np.abs(u - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_u_step_gradients_match_central_differences():
+    """d(gu . u)/d(V, y, z) through the u-step against central differences (step 1e-6), and the
+    positional gradient is translation invariant (sum over vertices is 0)."""
+    from paper_2602_12105_gb300 import meshgen as mg
+    V, F = mg.icosphere(1)
+    V = mg.radial_perturb(V, 0.05, np.random.default_rng(0))
+    n, m = V.shape[0], F.shape[0]
+    rng = np.random.default_rng(1)
+    y, z, gu = rng.standard_normal((m, 3)), rng.standard_normal((m, 3)), rng.standard_normal(n)
+    src, rho, beta = [0, 5], 2.0, 0.5
+    gV, gy, gz = oracle.rgd_u_step_vjp(V, F, src, y, z, rho, beta, gu)
+
+    def loss(Vx, yx, zx):
+        return float(gu @ oracle.rgd_u_step(Vx, F, src, yx, zx, rho, beta))
+
+    eps = 1e-6
+    for i, d in [(1, 0), (7, 2), (20, 1), (41, 2)]:
+        Vp, Vm = V.copy(), V.copy()
+        Vp[i, d] += eps
+        Vm[i, d] -= eps
+        fd = (loss(Vp, y, z) - loss(Vm, y, z)) / (2 * eps)
+        assert abs(fd - gV[i, d]) <= 1e-7 * max(1.0, abs(fd)), (i, d, fd, gV[i, d])
+    for j, d in [(3, 1), (50, 0)]:
+        for which, g in (("y", gy), ("z", gz)):
+            p_, m_ = (y.copy(), y.copy()) if which == "y" else (z.copy(), z.copy())
+            p_[j, d] += eps
+            m_[j, d] -= eps
+            fd = ((loss(V, p_, z) - loss(V, m_, z)) if which == "y" else (loss(V, y, p_) - loss(V, y, m_))) / (2 * eps)
+            assert abs(fd - g[j, d]) <= 1e-7 * max(1.0, abs(fd)), (which, j, d, fd, g[j, d])
+    assert np.abs(gV.sum(axis=0)).max() <= 1e-10 * np.abs(gV).max()
