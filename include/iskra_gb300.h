@@ -303,6 +303,20 @@ ig_status ig_rgd_u_step(ig_mesh* mesh, const double* V_dev, const int32_t* sourc
                         const double* z_dev, double rho, double beta, double* u_dev, const ig_solve_opts* opts,
                         ig_solve_info* info);
 
+/* Gradients of a loss l(u) through the u-step of ig_rgd_u_step, for its result u_dev [n] and
+ * gu_dev = dl/du [n], with the same V, sources, y, z, rho and beta: with lam = L_D^-1 gu (the same
+ * source-constrained Laplacian; lam = 0 on the sources) and s = 1 / (beta + rho),
+ *   gy_dev [m][3] = dl/dy = -s area_f grad(lam)_f,   gz_dev [m][3] = dl/dz = rho s area_f grad(lam)_f,
+ *   gV_dev [n][3] = dl/dV = s <lam, dm/dV> - <lam, dL/dV u> + s <lam, dD/dV (rho z - y)>.
+ * gy_dev and gz_dev may be NULL. Asynchronous. Like ig_rgd_u_step it assembles the mesh at V and
+ * rewrites the operator, and it uses the mesh's adjoint buffer.
+ * Errors: as ig_rgd_u_step (a solve that does not converge is not reported; use ig_rgd_u_step's
+ * info on the same inputs). */
+ig_status ig_rgd_u_step_vjp(ig_mesh* mesh, const double* V_dev, const int32_t* sources_host, int nsrc,
+                            const double* y_dev, const double* z_dev, double rho, double beta, const double* u_dev,
+                            const double* gu_dev, double* gV_dev, double* gy_dev, double* gz_dev,
+                            const ig_solve_opts* opts);
+
 /* ---- allocation-free solve ----------------------------------------------------------------- */
 
 /* Largest number of rows ig_solve_csr_noalloc accepts. */

@@ -219,6 +219,26 @@ class Mesh:
         self.ctx.check(st)
         return u
 
+    def rgd_u_step_vjp(self, V: torch.Tensor, sources, y: torch.Tensor, z: torch.Tensor, rho: float, beta: float,
+                       u: torch.Tensor, gu: torch.Tensor, opts=None):
+        """Gradients (gV [n][3], gy [m][3], gz [m][3]) of a loss through the u-step, for its result
+        u and the cotangent gu = dl/du (see ig_rgd_u_step_vjp)."""
+        V = self._dev(V, 3, "V")
+        y, z, u, gu = (x.to(self.ctx.device, torch.float64).contiguous() for x in (y, z, u, gu))
+        src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).ravel())
+        gV = torch.empty((self.n, 3), dtype=torch.float64, device=self.ctx.device)
+        gy = torch.empty((self.m, 3), dtype=torch.float64, device=self.ctx.device)
+        gz = torch.empty((self.m, 3), dtype=torch.float64, device=self.ctx.device)
+        self.ctx.sync_stream()
+        st = self.ctx.lib.ig_rgd_u_step_vjp(self.h, _ptr(V), src.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                            int(src.size), _ptr(y), _ptr(z), float(rho), float(beta), _ptr(u),
+                                            _ptr(gu), _ptr(gV), _ptr(gy), _ptr(gz),
+                                            ctypes.byref(opts) if opts is not None else None)
+        self._token = None
+        self.t = None
+        self.ctx.check(st)
+        return gV, gy, gz
+
     def eigs_vjp(self, V: torch.Tensor, U: torch.Tensor, gU: torch.Tensor, iters: int, opts=None):
         """dl/dV [n][3] through the eigenvector fixed point of eigs (see ig_eigs_vjp), for the
         result U of eigs at the assembled positions V and the cotangent gU = dl/dU."""
@@ -316,6 +336,31 @@ def eigs(mesh: Mesh, V: torch.Tensor, t: float, U0: torch.Tensor, iters: int, ad
     """Differentiable lowest eigenvectors of the pencil (L(V), M(V)) (see EigsFn); adj_iters
     defaults to iters. Returns (U, lam)."""
     return EigsFn.apply(V, mesh, t, U0, iters, adj_iters if adj_iters is not None else iters, opts)
+
+
+class RgdUStep(torch.autograd.Function):
+    """The u-step of the regularized-geodesic ADMM (ig_rgd_u_step), differentiable in V, y and z
+    (ig_rgd_u_step_vjp)."""
+
+    @staticmethod
+    def forward(ctx, V, y, z, mesh: Mesh, sources, rho, beta, opts):
+        u = mesh.rgd_u_step(V, sources, y, z, rho, beta, opts=opts)
+        ctx.mesh, ctx.sources, ctx.rho, ctx.beta, ctx.opts = mesh, sources, float(rho), float(beta), opts
+        ctx.save_for_backward(V, y, z, u)
+        return u
+
+    @staticmethod
+    def backward(ctx, gu):
+        V, y, z, u = ctx.saved_tensors
+        gV, gy, gz = ctx.mesh.rgd_u_step_vjp(V, ctx.sources, y, z, ctx.rho, ctx.beta, u,
+                                             gu.to(torch.float64).contiguous(), opts=ctx.opts)
+        return gV, gy, gz, None, None, None, None, None
+
+
+def rgd_u_step(mesh: Mesh, V: torch.Tensor, y: torch.Tensor, z: torch.Tensor, sources, rho: float, beta: float,
+               opts=None):
+    """Differentiable u-step of the regularized-geodesic ADMM (see RgdUStep)."""
+    return RgdUStep.apply(V, y, z, mesh, sources, rho, beta, opts)
 
 
 class MassFn(torch.autograd.Function):

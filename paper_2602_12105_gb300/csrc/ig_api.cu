@@ -903,12 +903,11 @@ ig_status ig_eigs_vjp(ig_mesh* mesh, const double* V_dev, int k, int iters, cons
   return IG_OK;
 }
 
-ig_status ig_rgd_u_step(ig_mesh* mesh, const double* V_dev, const int32_t* sources_host, int nsrc, const double* y_dev,
-                        const double* z_dev, double rho, double beta, double* u_dev, const ig_solve_opts* opts,
-                        ig_solve_info* info) {
-  if (!mesh) return IG_ERR_INVALID_ARG;
+// Shared set-up of the geodesic u-step and its gradient: argument checks, the source mask, the
+// assembly at V with t = 1 and its rewrite into the source-constrained Laplacian.
+static ig_status rgd_prepare(ig_mesh* mesh, const double* V_dev, const int32_t* sources_host, int nsrc, double rho,
+                             double beta, int** src_out) {
   ig_ctx* ctx = mesh->ctx;
-  if (!V_dev || !sources_host || !y_dev || !z_dev || !u_dev) return bad_arg(ctx, "V, sources, y, z and u must be non-NULL");
   if (nsrc < 1) return bad_arg(ctx, "at least one source is needed (u_s = 0 fixes the constant)");
   if (!(rho >= 0.0) || !(beta >= 0.0) || !(rho + beta > 0.0) || !(rho + beta < 1e300))
     return bad_arg(ctx, "rho and beta must be finite, >= 0, and not both 0");
@@ -918,24 +917,38 @@ ig_status ig_rgd_u_step(ig_mesh* mesh, const double* V_dev, const int32_t* sourc
     if (sources_host[i] < 0 || sources_host[i] >= n) return bad_arg(ctx, "a source index is out of range");
     mask[(size_t)sources_host[i]] = 1;
   }
+  if (!mesh->rgd) IG_CK(ctx, mesh_alloc(mesh, &mesh->rgd, 2 * (size_t)n), "alloc");
+  int* src = reinterpret_cast<int*>(mesh->rgd + n);
+  IG_CK(ctx, cudaMemcpyAsync(src, mask.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream), "sources");
+  // the copy reads mask before this function returns
+  IG_CK(ctx, cudaStreamSynchronize(ctx->stream), "sources");
+  ig_status st = ig_assemble(mesh, V_dev, 1.0, IG_PRECISION_FP64);
+  if (st != IG_OK) return st;
+  IG_CK(ctx, launch_rgd_operator(mesh->group.mds, (int)n, src, ctx->stream), "u-step operator");
+  *src_out = src;
+  return IG_OK;
+}
+
+ig_status ig_rgd_u_step(ig_mesh* mesh, const double* V_dev, const int32_t* sources_host, int nsrc, const double* y_dev,
+                        const double* z_dev, double rho, double beta, double* u_dev, const ig_solve_opts* opts,
+                        ig_solve_info* info) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (!V_dev || !sources_host || !y_dev || !z_dev || !u_dev) return bad_arg(ctx, "V, sources, y, z and u must be non-NULL");
   const ig_solve_opts o = resolve_opts(opts);
   ig_status cs = check_opts(ctx, o);
   if (cs != IG_OK) return cs;
   DeviceGuard guard(ctx->device);
-  if (!mesh->rgd) IG_CK(ctx, mesh_alloc(mesh, &mesh->rgd, 2 * (size_t)n), "alloc");
-  double* b = mesh->rgd;
-  int* src = reinterpret_cast<int*>(mesh->rgd + n);
-  IG_CK(ctx, cudaMemcpyAsync(src, mask.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream), "sources");
-  // A = M + L (t = 1), then the Laplacian with the sources' rows and columns replaced by the identity
-  ig_status st = ig_assemble(mesh, V_dev, 1.0, IG_PRECISION_FP64);
+  const long n = (long)mesh->n;
+  int* src = nullptr;
+  ig_status st = rgd_prepare(mesh, V_dev, sources_host, nsrc, rho, beta, &src);
   if (st != IG_OK) return st;
-  IG_CK(ctx, launch_rgd_operator(mesh->group.mds, (int)n, src, ctx->stream), "u-step operator");
+  double* b = mesh->rgd;
   IG_CK(ctx, launch_rgd_rhs(mesh->group.mds, (int)n, V_dev, y_dev, z_dev, rho, beta, src, b, ctx->stream),
         "u-step rhs");
   auto io = std::make_unique<IoTable>();
   io->in[0] = b;
   io->out[0] = u_dev;
-  st = IG_OK;
   cudaError_t e = group_solve(mesh->group, 1, 0, *io, 0, o, ctx->stream);
   if (e == cudaSuccess && info) e = group_true_residual(mesh->group, 1, *io, 0, ctx->stream);
   if (e == cudaSuccess && info) st = collect_info(mesh, 1, info);
@@ -943,6 +956,53 @@ ig_status ig_rgd_u_step(ig_mesh* mesh, const double* V_dev, const int32_t* sourc
   mesh->assembled = 0;
   IG_CK(ctx, e, "u-step solve");
   return st;
+}
+
+ig_status ig_rgd_u_step_vjp(ig_mesh* mesh, const double* V_dev, const int32_t* sources_host, int nsrc,
+                            const double* y_dev, const double* z_dev, double rho, double beta, const double* u_dev,
+                            const double* gu_dev, double* gV_dev, double* gy_dev, double* gz_dev,
+                            const ig_solve_opts* opts) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (!V_dev || !sources_host || !y_dev || !z_dev || !u_dev || !gu_dev || !gV_dev)
+    return bad_arg(ctx, "V, sources, y, z, u, gu and gV must be non-NULL");
+  const ig_solve_opts o = resolve_opts(opts);
+  ig_status cs = check_opts(ctx, o);
+  if (cs != IG_OK) return cs;
+  DeviceGuard guard(ctx->device);
+  const long n = (long)mesh->n;
+  int* src = nullptr;
+  ig_status st = rgd_prepare(mesh, V_dev, sources_host, nsrc, rho, beta, &src);
+  if (st != IG_OK) return st;
+  double* b = mesh->rgd;
+  const double s = 1.0 / (beta + rho);
+  // lam = L_D^-1 gu (zero on the sources), into the mesh's adjoint buffer
+  IG_CK(ctx, launch_rgd_vec(gu_dev, src, (int)n, 0, 0.0, b, ctx->stream), "u-step adjoint rhs");
+  auto io = std::make_unique<IoTable>();
+  io->in[0] = b;
+  io->out[0] = mesh->md.lam;
+  cudaError_t e = group_solve(mesh->group, 1, 0, *io, 0, o, ctx->stream);
+  if (e == cudaSuccess) e = launch_rgd_vec(u_dev, src, (int)n, 1, s, b, ctx->stream);  // B = u + s
+  if (e == cudaSuccess) {
+    // s <lam, dm> - <lam, dL u>: the smoothing step's VJP with t = 1, B = u + s, U = u
+    CallDev call{};
+    call.V = V_dev;
+    call.B = b;
+    call.U = u_dev;
+    call.gV = gV_dev;
+    call.t = 1.0;
+    call.b_is_V = 0;
+    call.bstride = 1;
+    e = group_set_calls(mesh->group, &call, ctx->stream);
+  }
+  if (e == cudaSuccess) e = launch_vjp(mesh->group, 1, ctx->stream, 0);
+  // s <lam, dD (rho z - y)>, and dl/dy, dl/dz
+  if (e == cudaSuccess)
+    e = launch_rgd_dD(mesh->group.mds, (int)n, (int)mesh->m, V_dev, y_dev, z_dev, rho, beta, gV_dev, gy_dev, gz_dev,
+                      ctx->stream);
+  mesh->assembled = 0;
+  IG_CK(ctx, e, "u-step gradient");
+  return IG_OK;
 }
 
 ig_status ig_profile_enable(int enable) {

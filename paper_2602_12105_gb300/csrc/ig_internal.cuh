@@ -357,6 +357,11 @@ cudaError_t eig_vjp_massw(int k, double* ws, long n, cudaStream_t st);  // wm = 
 cudaError_t launch_rgd_operator(const MeshDev* mds, int n, const int* src, cudaStream_t st);
 cudaError_t launch_rgd_rhs(const MeshDev* mds, int n, const double* V, const double* y, const double* z, double rho,
                            double beta, const int* src, double* b, cudaStream_t st);
+// out = x with zeros on the sources (add_s = 0), or x + s (add_s = 1)
+cudaError_t launch_rgd_vec(const double* x, const int* src, int n, int add_s, double s, double* out, cudaStream_t st);
+// the divergence term of dl/dV (added to gV) and dl/dy, dl/dz (may be null), with lam in md.lam
+cudaError_t launch_rgd_dD(const MeshDev* mds, int n, int m, const double* V, const double* y, const double* z,
+                          double rho, double beta, double* gV, double* gy, double* gz, cudaStream_t st);
 
 // ig_vjp.cu
 // mode 0: solve terms; 1: solve terms and the mass weights of the calls; 2: mass weights alone

@@ -10,8 +10,15 @@
 // values in place into the Laplacian with the sources' rows and columns replaced by the identity
 // (so the sources decouple and stay 0), with the new Jacobi diagonal. The right-hand side:
 //   (D w)_i = sum over the faces f at i of area_f <grad phi_i, w_f> = sum_f <N_f x e_i, w_f> / (2 |N_f|)
-// (N_f the face's unnormal normal, e_i the edge opposite i), gathered over the vertex's incidence
+// (N_f the face's unnormalized normal, e_i the edge opposite i), gathered over the vertex's incidence
 // list in face order (atomic-free). The solve is the PCG path of the smoothing step.
+//
+// Gradients (for gu = dl/du): lam = L_D^-1 gu (L_D the constrained operator, lam = 0 on sources),
+//   dl/dy_f = -s area_f grad(lam)_f,  dl/dz_f = rho s area_f grad(lam)_f   (s = 1 / (beta + rho)),
+//   dl/dV = s <lam, dm> - <lam, dL u> + s <lam, dD (rho z - y)>.
+// The first two terms are the smoothing step's VJP with t = 1 (A = M + L), B = u + s and U = u;
+// the last: per face, sum_c lam_c area <grad phi_c, W> = n . (E x W) / 2 with E = sum_c lam_c e_c,
+// differentiated through E (linear in the positions) and the unit normal n.
 #include "ig_device.cuh"
 
 namespace ig {
@@ -91,6 +98,95 @@ __global__ void __launch_bounds__(kBlock) rgd_rhs_kernel(const MeshDev* __restri
   b[v] = (md.M[v] - div) * scale;
 }
 
+// gu with zeros on the sources (the adjoint right-hand side), or u + s (the VJP's B) when add_s.
+__global__ void __launch_bounds__(kBlock) rgd_vec_kernel(const double* __restrict__ x, const int* __restrict__ src,
+                                                         int n, int add_s, double s, double* __restrict__ out) {
+  const int v = blockIdx.x * kBlock + threadIdx.x;
+  if (v >= n) return;
+  out[v] = add_s ? x[v] + s : (src[v] != 0 ? 0.0 : x[v]);
+}
+
+// Per face: the derivative of s * n . (E x W) / 2 (W = rho z - y) with respect to the corners,
+// into gface [m][9]; and area grad(lam) = n x E / 2 for dl/dy and dl/dz.
+__global__ void __launch_bounds__(kBlock) rgd_dface_kernel(const MeshDev* __restrict__ mds,
+                                                           const double* __restrict__ V, const double* __restrict__ y,
+                                                           const double* __restrict__ z, double rho, double s,
+                                                           double* __restrict__ gy, double* __restrict__ gz) {
+  const MeshDev& md = mds[0];
+  const int f = blockIdx.x * kBlock + threadIdx.x;
+  if (f >= md.m) return;
+  double p[3][3], l[3];
+  for (int c = 0; c < 3; ++c) {
+    const int vid = md.F[3 * f + c];
+    l[c] = md.lam[vid];
+    for (int d = 0; d < 3; ++d) p[c][d] = V[3 * (long)vid + d];
+  }
+  double a[3], b[3], N[3], E[3], W[3];
+  for (int d = 0; d < 3; ++d) {
+    a[d] = p[1][d] - p[0][d];
+    b[d] = p[2][d] - p[0][d];
+    // E = sum_c lam_c e_c, e_c = p_{c+2} - p_{c+1}
+    E[d] = l[0] * (p[2][d] - p[1][d]) + l[1] * (p[0][d] - p[2][d]) + l[2] * (p[1][d] - p[0][d]);
+    W[d] = rho * z[3 * (long)f + d] - y[3 * (long)f + d];
+  }
+  N[0] = a[1] * b[2] - a[2] * b[1];
+  N[1] = a[2] * b[0] - a[0] * b[2];
+  N[2] = a[0] * b[1] - a[1] * b[0];
+  const double nN = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+  double n[3], wxn[3], exw[3], v[3], ga[3], gb[3];
+  for (int d = 0; d < 3; ++d) n[d] = N[d] / nN;
+  wxn[0] = W[1] * n[2] - W[2] * n[1];
+  wxn[1] = W[2] * n[0] - W[0] * n[2];
+  wxn[2] = W[0] * n[1] - W[1] * n[0];
+  exw[0] = E[1] * W[2] - E[2] * W[1];
+  exw[1] = E[2] * W[0] - E[0] * W[2];
+  exw[2] = E[0] * W[1] - E[1] * W[0];
+  const double en = exw[0] * n[0] + exw[1] * n[1] + exw[2] * n[2];
+  for (int d = 0; d < 3; ++d) v[d] = (exw[d] - en * n[d]) / nN;
+  ga[0] = b[1] * v[2] - b[2] * v[1];
+  ga[1] = b[2] * v[0] - b[0] * v[2];
+  ga[2] = b[0] * v[1] - b[1] * v[0];
+  gb[0] = v[1] * a[2] - v[2] * a[1];
+  gb[1] = v[2] * a[0] - v[0] * a[2];
+  gb[2] = v[0] * a[1] - v[1] * a[0];
+  double* out = md.gface + 9 * (long)f;
+  for (int c = 0; c < 3; ++c) {
+    const double dl = l[(c + 1) % 3] - l[(c + 2) % 3];
+    for (int d = 0; d < 3; ++d) {
+      double g = dl * wxn[d];
+      if (c == 1) g += ga[d];
+      else if (c == 2) g += gb[d];
+      else g -= ga[d] + gb[d];
+      out[3 * c + d] = 0.5 * s * g;
+    }
+  }
+  if (gy || gz) {
+    double ag[3];  // area grad(lam) = n x E / 2
+    ag[0] = 0.5 * (n[1] * E[2] - n[2] * E[1]);
+    ag[1] = 0.5 * (n[2] * E[0] - n[0] * E[2]);
+    ag[2] = 0.5 * (n[0] * E[1] - n[1] * E[0]);
+    for (int d = 0; d < 3; ++d) {
+      if (gy) gy[3 * (long)f + d] = -s * ag[d];
+      if (gz) gz[3 * (long)f + d] = rho * s * ag[d];
+    }
+  }
+}
+
+// gV[v] += sum over the faces at v (incidence order) of their corner's entry of gface.
+__global__ void __launch_bounds__(kBlock) rgd_dgather_kernel(const MeshDev* __restrict__ mds, double* __restrict__ gV) {
+  const MeshDev& md = mds[0];
+  const int v = blockIdx.x * kBlock + threadIdx.x;
+  if (v >= md.n) return;
+  double g[3] = {0.0, 0.0, 0.0};
+  const int e0 = md.incptr[v], e1 = md.incptr[v + 1];
+  for (int e = e0; e < e1; ++e) {
+    const int2 ic = md.inc[e];
+    const int f = ic.x >> 2, c = ic.x & 3;
+    for (int d = 0; d < 3; ++d) g[d] += md.gface[9 * (long)f + 3 * c + d];
+  }
+  for (int d = 0; d < 3; ++d) gV[3 * (long)v + d] += g[d];
+}
+
 }  // namespace
 
 cudaError_t launch_rgd_operator(const MeshDev* mds, int n, const int* src, cudaStream_t st) {
@@ -103,6 +199,26 @@ cudaError_t launch_rgd_rhs(const MeshDev* mds, int n, const double* V, const dou
                            double beta, const int* src, double* b, cudaStream_t st) {
   IG_PROF("rgd_rhs", st);
   rgd_rhs_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(mds, V, y, z, rho, 1.0 / (beta + rho), src, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rgd_vec(const double* x, const int* src, int n, int add_s, double s, double* out, cudaStream_t st) {
+  rgd_vec_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(x, src, n, add_s, s, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rgd_dD(const MeshDev* mds, int n, int m, const double* V, const double* y, const double* z,
+                          double rho, double beta, double* gV, double* gy, double* gz, cudaStream_t st) {
+  {
+    IG_PROF("rgd_dface", st);
+    rgd_dface_kernel<<<(m + kBlock - 1) / kBlock, kBlock, 0, st>>>(mds, V, y, z, rho, 1.0 / (beta + rho), gy, gz);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  {
+    IG_PROF("rgd_dgather", st);
+    rgd_dgather_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(mds, gV);
+  }
   return cudaGetLastError();
 }
 

@@ -83,3 +83,51 @@ def test_u_step_errors(api):
         with pytest.raises(N.IgError) as e:
             mesh.rgd_u_step(_t(V), bad_src, y, z, rho, beta)
         assert e.value.status == N.IG_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name", ["ico2", "grid70x50"])
+def test_u_step_gradients_match_oracle(api, name):
+    V, F, src = _case(name)
+    n, m = V.shape[0], F.shape[0]
+    rng = np.random.default_rng(8)
+    y, z, gu = rng.standard_normal((m, 3)), rng.standard_normal((m, 3)), rng.standard_normal(n)
+    rho, beta = 2.0, 0.5
+    rgV, rgy, rgz = oracle.rgd_u_step_vjp(V, F, src, y, z, rho, beta, gu)
+    mesh = api.Mesh(_t(F, torch.int32), n)
+    opts = api.make_opts(rel_tol=1e-13)
+    u = mesh.rgd_u_step(_t(V), src, _t(y), _t(z), rho, beta, opts=opts)
+    gV, gy, gz = mesh.rgd_u_step_vjp(_t(V), src, _t(y), _t(z), rho, beta, u, _t(gu), opts=opts)
+    for got, ref in ((gV, rgV), (gy, rgy), (gz, rgz)):
+        got = got.cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max(), (np.abs(got - ref).max(), np.abs(ref).max())
+
+
+def test_u_step_autograd_matches_central_differences(api):
+    """Through the autograd wrapper: d(gu . u)/dV and d/dy at sampled entries against central
+    differences of GPU u-steps (step 1e-5; each solve stops at 1e-13)."""
+    V, F, src = _case("ico2")
+    n, m = V.shape[0], F.shape[0]
+    rng = np.random.default_rng(9)
+    y, z, gu = _t(rng.standard_normal((m, 3))), _t(rng.standard_normal((m, 3))), _t(rng.standard_normal(n))
+    mesh = api.Mesh(_t(F, torch.int32), n)
+    opts = api.make_opts(rel_tol=1e-13)
+    Vt = _t(V).requires_grad_(True)
+    yt = y.clone().requires_grad_(True)
+    (api.rgd_u_step(mesh, Vt, yt, z, src, 2.0, 0.5, opts=opts) * gu).sum().backward()
+    eps = 1e-5
+
+    def loss(Vx, yx):
+        return float((mesh.rgd_u_step(Vx, src, yx, z, 2.0, 0.5, opts=opts) * gu).sum())
+
+    for i, d in [(1, 0), (9, 2), (77, 1)]:
+        Vp, Vm = _t(V), _t(V)
+        Vp[i, d] += eps
+        Vm[i, d] -= eps
+        fd = (loss(Vp, y) - loss(Vm, y)) / (2 * eps)
+        assert abs(fd - float(Vt.grad[i, d])) <= 1e-6 * max(1.0, abs(fd)), (i, d, fd, float(Vt.grad[i, d]))
+    for j, d in [(5, 1), (200, 2)]:
+        yp, ym = y.clone(), y.clone()
+        yp[j, d] += eps
+        ym[j, d] -= eps
+        fd = (loss(_t(V), yp) - loss(_t(V), ym)) / (2 * eps)
+        assert abs(fd - float(yt.grad[j, d])) <= 1e-6 * max(1.0, abs(fd)), (j, d, fd, float(yt.grad[j, d]))
