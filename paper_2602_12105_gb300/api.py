@@ -219,6 +219,28 @@ class Mesh:
         self.ctx.check(st)
         return u
 
+    def rgd_admm(self, V: torch.Tensor, sources, rho: float, beta: float, beta_k: float, iters: int,
+                 y: Optional[torch.Tensor] = None, z: Optional[torch.Tensor] = None, opts=None):
+        """`iters` rounds of the regularized-geodesic ADMM (see ig_rgd_admm) from y and z (zeros
+        when not given). Returns (u [n], y [m][3], z [m][3], primal residual of the last round)."""
+        V = self._dev(V, 3, "V")
+        dev = self.ctx.device
+        y = torch.zeros((self.m, 3), dtype=torch.float64, device=dev) if y is None else \
+            y.to(dev, torch.float64).contiguous().clone()
+        z = torch.zeros((self.m, 3), dtype=torch.float64, device=dev) if z is None else \
+            z.to(dev, torch.float64).contiguous().clone()
+        src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).ravel())
+        u = torch.empty(self.n, dtype=torch.float64, device=dev)
+        primal = ctypes.c_double(0.0)
+        self.ctx.sync_stream()
+        st = self.ctx.lib.ig_rgd_admm(self.h, _ptr(V), src.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(src.size),
+                                      float(rho), float(beta), float(beta_k), int(iters), _ptr(u), _ptr(y), _ptr(z),
+                                      ctypes.byref(primal), ctypes.byref(opts) if opts is not None else None)
+        self._token = None
+        self.t = None
+        self.ctx.check(st)
+        return u, y, z, primal.value
+
     def rgd_u_step_vjp(self, V: torch.Tensor, sources, y: torch.Tensor, z: torch.Tensor, rho: float, beta: float,
                        u: torch.Tensor, gu: torch.Tensor, opts=None):
         """Gradients (gV [n][3], gy [m][3], gz [m][3]) of a loss through the u-step, for its result

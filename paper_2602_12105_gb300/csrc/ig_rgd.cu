@@ -19,6 +19,11 @@
 // The first two terms are the smoothing step's VJP with t = 1 (A = M + L), B = u + s and U = u;
 // the last: per face, sum_c lam_c area <grad phi_c, W> = n . (E x W) / 2 with E = sum_c lam_c e_c,
 // differentiated through E (linear in the positions) and the unit normal n.
+//
+// The ADMM rounds around the u-step (rgd_zy_kernel, per face): g = G u = N x (sum_c u_c e_c) / |N|^2,
+// z = P(y / rho + g) with P the projection onto the unit ball, y += rho (beta_k g + (1 - beta_k)
+// z_old - z); the primal residual max_f |g - z| is kept as a maximum over faces (exact, so free of
+// the order of the faces).
 #include "ig_device.cuh"
 
 namespace ig {
@@ -187,6 +192,52 @@ __global__ void __launch_bounds__(kBlock) rgd_dgather_kernel(const MeshDev* __re
   for (int d = 0; d < 3; ++d) gV[3 * (long)v + d] += g[d];
 }
 
+// One z-step and dual step per face; primal (when not null) receives max_f |g - z| by atomicMax on
+// the bits of a non-negative double (ordered like the values).
+__global__ void __launch_bounds__(kBlock) rgd_zy_kernel(const MeshDev* __restrict__ mds, const double* __restrict__ V,
+                                                        const double* __restrict__ u, double* __restrict__ y,
+                                                        double* __restrict__ z, double rho, double beta_k,
+                                                        unsigned long long* primal) {
+  const MeshDev& md = mds[0];
+  const int f = blockIdx.x * kBlock + threadIdx.x;
+  if (f >= md.m) return;
+  double p[3][3], uc[3];
+  for (int c = 0; c < 3; ++c) {
+    const int vid = md.F[3 * f + c];
+    uc[c] = u[vid];
+    for (int d = 0; d < 3; ++d) p[c][d] = V[3 * (long)vid + d];
+  }
+  double a[3], b[3], E[3], N[3], g[3];
+  for (int d = 0; d < 3; ++d) {
+    a[d] = p[1][d] - p[0][d];
+    b[d] = p[2][d] - p[0][d];
+    E[d] = uc[0] * (p[2][d] - p[1][d]) + uc[1] * (p[0][d] - p[2][d]) + uc[2] * (p[1][d] - p[0][d]);
+  }
+  N[0] = a[1] * b[2] - a[2] * b[1];
+  N[1] = a[2] * b[0] - a[0] * b[2];
+  N[2] = a[0] * b[1] - a[1] * b[0];
+  const double inv = 1.0 / (N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+  g[0] = (N[1] * E[2] - N[2] * E[1]) * inv;
+  g[1] = (N[2] * E[0] - N[0] * E[2]) * inv;
+  g[2] = (N[0] * E[1] - N[1] * E[0]) * inv;
+  double yo[3], zo[3], zn[3];
+  for (int d = 0; d < 3; ++d) {
+    yo[d] = y[3 * (long)f + d];
+    zo[d] = z[3 * (long)f + d];
+    zn[d] = yo[d] / rho + g[d];
+  }
+  const double nz = sqrt(zn[0] * zn[0] + zn[1] * zn[1] + zn[2] * zn[2]);
+  const double den = nz >= 1.0 ? nz : 1.0;
+  double r2 = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    zn[d] = zn[d] / den;
+    y[3 * (long)f + d] = yo[d] + rho * (beta_k * g[d] + (1.0 - beta_k) * zo[d] - zn[d]);
+    z[3 * (long)f + d] = zn[d];
+    r2 = fma(g[d] - zn[d], g[d] - zn[d], r2);
+  }
+  if (primal) atomicMax(primal, (unsigned long long)__double_as_longlong(sqrt(r2)));
+}
+
 }  // namespace
 
 cudaError_t launch_rgd_operator(const MeshDev* mds, int n, const int* src, cudaStream_t st) {
@@ -219,6 +270,13 @@ cudaError_t launch_rgd_dD(const MeshDev* mds, int n, int m, const double* V, con
     IG_PROF("rgd_dgather", st);
     rgd_dgather_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(mds, gV);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rgd_zy(const MeshDev* mds, int m, const double* V, const double* u, double* y, double* z, double rho,
+                          double beta_k, unsigned long long* primal, cudaStream_t st) {
+  IG_PROF("rgd_zy", st);
+  rgd_zy_kernel<<<(m + kBlock - 1) / kBlock, kBlock, 0, st>>>(mds, V, u, y, z, rho, beta_k, primal);
   return cudaGetLastError();
 }
 

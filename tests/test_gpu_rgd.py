@@ -131,3 +131,19 @@ def test_u_step_autograd_matches_central_differences(api):
         ym[j, d] -= eps
         fd = (loss(_t(V), yp) - loss(_t(V), ym)) / (2 * eps)
         assert abs(fd - float(yt.grad[j, d])) <= 1e-6 * max(1.0, abs(fd)), (j, d, fd, float(yt.grad[j, d]))
+
+
+@pytest.mark.parametrize("name,iters", [("ico2", 30), ("grid70x50", 8)])
+def test_admm_rounds_match_oracle(api, name, iters):
+    """Rounds of the ADMM (u-step, projection z-step, over-relaxed dual step) from zero iterates,
+    against the oracle's rounds: u, y and z within 1e-8 of their largest entries."""
+    V, F, src = _case(name)
+    n = V.shape[0]
+    rho, beta, beta_k = 5.0, 0.1, 1.5
+    ru, ry, rz, rprimal = oracle.rgd_admm(V, F, src, rho, beta, beta_k, iters)
+    mesh = api.Mesh(_t(F, torch.int32), n)
+    u, y, z, primal = mesh.rgd_admm(_t(V), src, rho, beta, beta_k, iters, opts=api.make_opts(rel_tol=1e-13))
+    for got, ref in ((u, ru), (y, ry), (z, rz)):
+        got = got.cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max(), (np.abs(got - ref).max(), np.abs(ref).max())
+    assert abs(primal - rprimal) <= 1e-8 * max(1.0, rprimal)
