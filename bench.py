@@ -52,7 +52,7 @@ def parse():
                     help="skip the other workloads (mixed grid, largest mesh, 256-mesh batch, serving)")
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="requests in the bounded sample of the serving stream")
-    ap.add_argument("--variants", default="mixed,largest,batch,fairing,eigs,serve",
+    ap.add_argument("--variants", default="mixed,largest,batch,fairing,eigs,rgd,serve",
                     help="comma list of the extra workloads to run")
     return ap.parse_args()
 
@@ -713,6 +713,34 @@ def variant_eigs(api, dev, steps, level=7):
             "max_abs_UtMU_minus_I": orth}
 
 
+def variant_rgd(api, dev, rounds, side=257):
+    """Regularized geodesic distances by the ADMM of formulation eq. edelstein (ig_rgd_admm) on a
+    flat square grid with the source at a corner and beta = 0, where the answer is the Euclidean
+    distance: rounds/s, the primal residual of the last round and the largest error against the
+    Euclidean distance (relative to the largest distance)."""
+    import torch
+    from paper_2602_12105_gb300 import meshgen as mg
+    p = mg.config_grid(side, side, seed=0, t=1.0)
+    V = p.V.copy()
+    V[:, 2] = 0.0
+    mesh = api.Mesh(torch.from_numpy(p.F).to(dev), p.n)
+    Vd = torch.from_numpy(V).to(dev)
+    opts = api.make_opts(rel_tol=1e-10)
+    mesh.rgd_admm(Vd, [0], 10.0, 0.0, 1.0, 2, opts=opts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    u, y, z, primal = mesh.rgd_admm(Vd, [0], 10.0, 0.0, 1.0, rounds, opts=opts)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    d = np.linalg.norm(V - V[0], axis=1)
+    err = float(np.abs(u.cpu().numpy() - d).max() / d.max())
+    mesh.close()
+    return {"workload": f"flat {side} x {side} grid ({p.n} vertices), source at a corner, beta = 0, rho = 10, "
+                        f"beta_k = 1, {rounds} ADMM rounds, each a constrained Laplacian solve to 1e-10",
+            "unit": "ADMM rounds/s", "value": round(rounds / dt, 3), "ms_per_round": round(1000.0 * dt / rounds, 3),
+            "primal_residual_last_round": primal, "max_rel_err_vs_euclidean_distance": err}
+
+
 def serving_requests(count, seed=7):
     """A bounded sample of the serving stream: request sizes log-uniform in [1e3, 2e6] vertices,
     half icospheres (levels 4..8), half square grids whose side is snapped to one of 32
@@ -798,6 +826,8 @@ def run_variants(args, p, U64, gV64, dev):
         out["inverse_fairing_ico7"] = variant_fairing(api, _native, dev, 20)
     if "eigs" in want:
         out["eigs_ico7"] = variant_eigs(api, dev, 40)
+    if "rgd" in want:
+        out["rgd_grid257"] = variant_rgd(api, dev, 100)
     if "serve" in want and args.serve_requests > 0:
         out["serving"] = variant_serving(dev, args.tol, args.serve_requests)
     out["clocks"] = sampler.stop()
