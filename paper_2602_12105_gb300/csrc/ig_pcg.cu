@@ -274,15 +274,18 @@ __global__ void __launch_bounds__(kBlock, 4) update_kernel(const MeshDev* __rest
       if (use_graph) cudaGraphSetConditional(handle, 0u);
     }
   }
+  if (threadIdx.x == 0) tc.last = 0;
   __syncthreads();
   tile_loop<2 * K>(
       mds, L, 0, 1, tc, [&](const ScalSnap& x) { return !x.done && !s_stop; },
       [&](const MeshDev& md, int tile, double* red, double* out) { update_tile<K>(md, tile, tc.sn, red, out); },
-      [&](const MeshDev& md, const SolveScal& cur, const double* v) {
-        finish_update(md.s, cur, K, v);
-        if (s_single && threadIdx.x == 0) single_loop_control(md.s, ctl, handle, use_graph);
-      });
-  if (!s_single) loop_control(mds, ctl, handle, use_graph);
+      [](const MeshDev& md, const SolveScal& cur, const double* v) { finish_update(md.s, cur, K, v); });
+  if (!s_single) {
+    loop_control(mds, ctl, handle, use_graph);
+  } else if (tc.last && threadIdx.x == 0) {
+    // the CTA that completed the mesh (its finish step is done: flush_tiles ends in a barrier)
+    single_loop_control(tc.md.s, ctl, handle, use_graph);
+  }
 }
 
 // ------------------------------------------------------------------------------- true residual
