@@ -823,9 +823,23 @@ ig_status ig_eigs(ig_mesh* mesh, int k, int iters, double* U_dev, double* lambda
   auto io = std::make_unique<IoTable>();
   io->in[0] = U_dev;
   io->out[0] = Y;
+  const EigBuffers eb = eig_buffers(mesh->eig, n);
+  auto io_warm = std::make_unique<IoTable>();
+  io_warm->in[0] = eb.Yb;
+  io_warm->out[0] = eb.X;
   for (int it = 0; it < iters; ++it) {
-    // Y = (M + tL)^-1 M U, then U = Q(Y)
-    IG_CK(ctx, group_solve(mesh->group, k, mesh->assembled == 2, *io, 1, o, ctx->stream), "eigs solve");
+    // Y = (M + tL)^-1 M U, then U = Q(Y). After the first step the solve starts from
+    // Y0 = U diag(R_cc) and finds the correction to the same accuracy relative to |M U|.
+    if (it == 0) {
+      IG_CK(ctx, group_solve(mesh->group, k, mesh->assembled == 2, *io, 1, o, ctx->stream), "eigs solve");
+    } else {
+      double ratio = 1.0;
+      IG_CK(ctx, eig_warm(k, mesh->group.mds, mesh->eig, n, U_dev, &ratio, ctx->stream), "eigs");
+      ig_solve_opts ow = o;
+      ow.rel_tol = std::min(0.5, o.rel_tol * ratio);
+      IG_CK(ctx, group_solve(mesh->group, k, mesh->assembled == 2, *io_warm, 0, ow, ctx->stream), "eigs solve");
+      IG_CK(ctx, eig_addx(k, mesh->eig, n, ctx->stream), "eigs");
+    }
     IG_CK(ctx, eig_step(k, mesh->eig, mesh->md.M, n, U_dev, ctx->stream), "eigs");
   }
   IG_CK(ctx, eig_finish(k, mesh->group.mds, mesh->t, mesh->eig, n, U_dev, ctx->stream), "eigs");

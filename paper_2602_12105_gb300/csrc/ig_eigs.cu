@@ -41,6 +41,8 @@ struct EigSmall {
   double colmax[kMaxK];
   double sign[kMaxK];
   double lambda[kMaxK];
+  double rdiag[kMaxK];     // diagonal of R of the last step: about 1 / (1 + t lambda_c) near convergence
+  double tol_ratio;        // min_c |M U_c| / |M U_c - A Y0_c| of the warm start
   int sign_row[kMaxK];
   int fail;        // 1 once a Gram matrix was not numerically positive definite (dependent or non-finite columns)
   unsigned cnt;    // last-CTA counter, reset by the CTA that completes each reduction
@@ -191,8 +193,70 @@ __global__ void __launch_bounds__(kBlock) eig_gram_kernel(const double* __restri
   for (int a = 0; a < K; ++a)
 #pragma unroll
     for (int c = 0; c < K; ++c) sm->rinv[a * K + c] = Ri[a][c];
+#pragma unroll
+  for (int a = 0; a < K; ++a) sm->rdiag[a] = R[a][a];
   if (bad) sm->fail = 1;
   sm->cnt = 0u;
+}
+
+// Warm start of the next solve (A Y = M U): Y0 = U diag(rdiag), which A maps to about M U once U
+// holds eigenvectors (A u = (1 + t lambda) M u); the solve then finds the correction from
+// rhs = M U - A Y0, to a tolerance relative to |M U| rather than to |rhs| (tol_ratio).
+template <int K>
+__global__ void __launch_bounds__(kBlock) eig_warm_kernel(const MeshDev* __restrict__ mds,
+                                                          const double* __restrict__ U, double* __restrict__ Y0,
+                                                          double* __restrict__ rhs, double* __restrict__ part,
+                                                          EigSmall* sm) {
+  __shared__ double sh[2 * K * kBlock];
+  __shared__ double rd[K];
+  if (threadIdx.x < K) rd[threadIdx.x] = sm->rdiag[threadIdx.x];
+  __syncthreads();
+  const MeshDev& md = mds[0];
+  const long n = md.n;
+  const int ntile = (int)((n + kBlock - 1) / kBlock);
+  const long row = (long)blockIdx.x * kBlock + threadIdx.x;
+  double acc[2 * K];
+#pragma unroll
+  for (int i = 0; i < 2 * K; ++i) acc[i] = 0.0;
+  if (row < n) {
+    double au[K];
+    row_product<K>(md, md.A, row, GatherAoS64<K>{U}, au);
+    const double m = md.M[row];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const double u = U[row * K + c];
+      const double mu = m * u;
+      const double res = fma(-rd[c], au[c], mu);
+      Y0[row * K + c] = rd[c] * u;
+      rhs[row * K + c] = res;
+      acc[c] = mu * mu;
+      acc[K + c] = res * res;
+    }
+  }
+  block_sum<2 * K>(acc, sh);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < 2 * K; ++i) part[(long)blockIdx.x * kEigStride + i] = acc[i];
+  if (!eig_publish(sm, ntile)) return;
+  double tot[2 * K];
+  eig_gather_sum<2 * K>(part, ntile, tot, sh);
+  if (threadIdx.x == 0) {
+    double ratio = 1e300;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const double rr = tot[K + c] > 0.0 ? sqrt(tot[c] / tot[K + c]) : 1e300;
+      ratio = rr < ratio ? rr : ratio;
+    }
+    sm->tol_ratio = ratio;
+    sm->cnt = 0u;
+  }
+}
+
+// Y += X (the solved correction), row by row.
+template <int K>
+__global__ void __launch_bounds__(kBlock) eig_addx_kernel(double* __restrict__ Y, const double* __restrict__ X, long n) {
+  const long i = (long)blockIdx.x * kBlock + threadIdx.x;
+  if (i < n * K) Y[i] += X[i];
 }
 
 // U = Y R^-1 (row by row).
@@ -695,6 +759,45 @@ cudaError_t eig_vjp_massw(int k, double* ws, long n, cudaStream_t st) {
     case 4: return eig_vjp_massw_k<4>(ws, n, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <int K>
+static cudaError_t eig_warm_k(const MeshDev* mds, double* ws, long n, const double* U, cudaStream_t st) {
+  const long ntile = (n + kBlock - 1) / kBlock;
+  const EigLayout L(ws, n);
+  IG_PROF("eig_warm", st);
+  eig_warm_kernel<K><<<(unsigned)ntile, kBlock, 0, st>>>(mds, U, L.Y, L.Yb, L.part, L.sm);
+  return cudaGetLastError();
+}
+
+cudaError_t eig_warm(int k, const MeshDev* mds, double* ws, long n, const double* U, double* tol_ratio_host,
+                     cudaStream_t st) {
+  cudaError_t e;
+  switch (k) {
+    case 1: e = eig_warm_k<1>(mds, ws, n, U, st); break;
+    case 2: e = eig_warm_k<2>(mds, ws, n, U, st); break;
+    case 3: e = eig_warm_k<3>(mds, ws, n, U, st); break;
+    case 4: e = eig_warm_k<4>(mds, ws, n, U, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(tol_ratio_host, &EigLayout(ws, n).sm->tol_ratio, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
+}
+
+cudaError_t eig_addx(int k, double* ws, long n, cudaStream_t st) {
+  const EigLayout L(ws, n);
+  const long count = (long)k * n;
+  IG_PROF("eig_addx", st);
+  switch (k) {
+    case 1: eig_addx_kernel<1><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(L.Y, L.X, n); break;
+    case 2: eig_addx_kernel<2><<<(unsigned)((count + kBlock - 1) / kBlock), kBlock, 0, st>>>(L.Y, L.X, n); break;
+    case 3: eig_addx_kernel<3><<<(unsigned)((count + kBlock - 1) / kBlock), kBlock, 0, st>>>(L.Y, L.X, n); break;
+    case 4: eig_addx_kernel<4><<<(unsigned)((count + kBlock - 1) / kBlock), kBlock, 0, st>>>(L.Y, L.X, n); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 EigBuffers eig_buffers(double* ws, long n) {

@@ -342,6 +342,12 @@ cudaError_t eig_step(int k, double* ws, const double* M, long n, double* U, cuda
 // canonical signs of U's columns and the eigenvalues (u^T A u - u^T M u) / t
 cudaError_t eig_finish(int k, const MeshDev* mds, double t, double* ws, long n, double* U, cudaStream_t st);
 cudaError_t eig_read(double* ws, long n, int k, double* lambda_host, int* fail_host, cudaStream_t st);
+// warm start of a step after the first: Y = U diag(R_cc of the last step), Ybar = M U - A Y, and
+// (synchronising) min_c |M U_c| / |Ybar_c| into *tol_ratio_host; then, after solving A X = Ybar,
+// eig_addx: Y += X
+cudaError_t eig_warm(int k, const MeshDev* mds, double* ws, long n, const double* U, double* tol_ratio_host,
+                     cudaStream_t st);
+cudaError_t eig_addx(int k, double* ws, long n, cudaStream_t st);
 // gradient through the fixed point: Y (= (M + tL)^-1 M U*) must be in the workspace first
 struct EigBuffers {
   double *Y, *Yb, *X, *W, *wm;  // Y, Ybar, the solve of Ybar, the Neumann iterate W, mass weights
