@@ -317,21 +317,28 @@ ig_status ig_rgd_u_step_vjp(ig_mesh* mesh, const double* V_dev, const int32_t* s
                             const double* gu_dev, double* gV_dev, double* gy_dev, double* gz_dev,
                             const ig_solve_opts* opts);
 
-/* `iters` rounds of the ADMM scheme for regularized geodesic distances (formulation eq. edelstein
- * and its listing), every part on the device: the u-step of ig_rgd_u_step; the z-step
+/* Rounds of the ADMM scheme for regularized geodesic distances (formulation eq. edelstein and its
+ * listing), every part on the device: the u-step of ig_rgd_u_step; the z-step
  * z_f = P(y_f / rho + (G u)_f), P the projection onto the unit ball; the dual step
  * y_f += rho (beta_k (G u)_f + (1 - beta_k) z_f,old - z_f). With beta = 0 and enough rounds u
  * approaches the geodesic distance from the sources (under the constraint |G u| <= 1).
+ * Residuals of a round: primal = max_f |(G u)_f - z_f|, dual = rho max_i |(D (z - z_old))_i| / m_i
+ * over the non-source vertices. With tol > 0 the rounds stop once both are <= tol; with adapt_rho
+ * rho is doubled after a round whose primal exceeds 10 x its dual, halved in the opposite case
+ * (residual balancing; y is the unscaled dual, so it needs no rescaling). Either setting reads the
+ * residuals after every round (one synchronisation per round); with neither, exactly max_rounds
+ * rounds run without synchronising.
  * y_dev and z_dev [m][3]: the start (e.g. zeros) on entry, the last iterates on return. u_dev [n]:
- * the last u. primal_host (may be NULL; synchronises): max_f |(G u)_f - z_f| of the last round.
- * rho > 0, beta >= 0, beta_k in [0, 2] (over-relaxation), iters >= 1. The operator is built once
- * (as in ig_rgd_u_step) and each round is one Laplacian solve to opts->rel_tol; the mesh must be
- * assembled again before other solves. Solver statuses of the rounds are not reported (call
- * ig_rgd_u_step with info on the final y and z to check the last solve).
- * Errors: as ig_rgd_u_step, and IG_ERR_INVALID_ARG for iters, rho or beta_k out of range. */
+ * the last u. stats_host (may be NULL; synchronises): 4 doubles, the rounds run, the primal and
+ * dual residuals of the last round, and the final rho. rho > 0, beta >= 0, beta_k in [0, 2]
+ * (over-relaxation), max_rounds >= 1, tol >= 0. The operator is built once (as in ig_rgd_u_step)
+ * and each round is one Laplacian solve to opts->rel_tol; the mesh must be assembled again before
+ * other solves. Solver statuses of the rounds are not reported (call ig_rgd_u_step with info on
+ * the final y and z to check the last solve).
+ * Errors: as ig_rgd_u_step, and IG_ERR_INVALID_ARG for max_rounds, rho, beta_k or tol out of range. */
 ig_status ig_rgd_admm(ig_mesh* mesh, const double* V_dev, const int32_t* sources_host, int nsrc, double rho, double beta,
-                      double beta_k, int iters, double* u_dev, double* y_dev, double* z_dev, double* primal_host,
-                      const ig_solve_opts* opts);
+                      double beta_k, int max_rounds, double tol, int adapt_rho, double* u_dev, double* y_dev,
+                      double* z_dev, double* stats_host, const ig_solve_opts* opts);
 
 /* ---- allocation-free solve ----------------------------------------------------------------- */
 

@@ -423,26 +423,41 @@ def rgd_u_step_vjp(V, F, sources, y, z, rho, beta, gu, tol=1e-14):
     return gV, gy, gz
 
 
-def rgd_admm(V, F, sources, rho, beta, beta_k, iters, y=None, z=None, tol=1e-14):
+def rgd_admm(V, F, sources, rho, beta, beta_k, iters, y=None, z=None, tol=0.0, adapt_rho=False, solve_tol=1e-14):
     """The ADMM scheme for regularized geodesic distances (formulation eq. edelstein and its
-    listing), `iters` rounds of: the u-step (rgd_u_step); the z-step z = P(y / rho + G u), P the
-    projection of each face's vector onto the unit ball; the dual step
-    y += rho (beta_k G u + (1 - beta_k) z_old - z). y and z start at 0 unless given.
-    Returns (u, y, z, primal) with primal = max_f |(G u)_f - z_f| of the last round."""
+    listing), up to `iters` rounds of: the u-step (rgd_u_step); the z-step z = P(y / rho + G u), P
+    the projection of each face's vector onto the unit ball; the dual step
+    y += rho (beta_k G u + (1 - beta_k) z_old - z). Residuals of a round: primal = max_f |G u - z|,
+    dual = rho max_i |(D (z - z_old))_i| / m_i over the non-source vertices. With tol > 0 the
+    rounds stop once both are <= tol; with adapt_rho, rho doubles when primal > 10 dual and halves
+    when dual > 10 primal (residual balancing). y and z start at 0 unless given.
+    Returns (u, y, z, stats) with stats = (rounds, primal, dual, rho)."""
     V, F = _f64(V), _i32(F)
     m = F.shape[0]
     y = np.zeros((m, 3)) if y is None else _f64(y).copy()
     z = np.zeros((m, 3)) if z is None else _f64(z).copy()
-    u, primal = None, 0.0
-    for _ in range(int(iters)):
-        u = rgd_u_step(V, F, sources, y, z, rho, beta, tol=tol)
+    M = mass(V, F)
+    free = np.ones(V.shape[0], dtype=bool)
+    free[np.asarray(sources, dtype=np.int64)] = False
+    u, primal, dual, rounds = None, 0.0, 0.0, 0
+    for it in range(int(iters)):
+        u = rgd_u_step(V, F, sources, y, z, rho, beta, tol=solve_tol)
         g = face_gradient(V, F, u)
         zn = y / rho + g
         zn = zn / np.maximum(np.linalg.norm(zn, axis=1), 1.0)[:, None]
         y = y + rho * (beta_k * g + (1.0 - beta_k) * z - zn)
+        primal = float(np.linalg.norm(g - zn, axis=1).max())
+        dual = float((rho * np.abs(divergence(V, F, zn - z)) / M)[free].max())
         z = zn
-        primal = float(np.linalg.norm(g - z, axis=1).max())
-    return u, y, z, primal
+        rounds = it + 1
+        if tol > 0.0 and primal <= tol and dual <= tol:
+            break
+        if adapt_rho:
+            if primal > 10.0 * dual:
+                rho *= 2.0
+            elif dual > 10.0 * primal:
+                rho *= 0.5
+    return u, y, z, (rounds, primal, dual, rho)
 
 
 def num_threads():

@@ -219,10 +219,13 @@ class Mesh:
         self.ctx.check(st)
         return u
 
-    def rgd_admm(self, V: torch.Tensor, sources, rho: float, beta: float, beta_k: float, iters: int,
-                 y: Optional[torch.Tensor] = None, z: Optional[torch.Tensor] = None, opts=None):
-        """`iters` rounds of the regularized-geodesic ADMM (see ig_rgd_admm) from y and z (zeros
-        when not given). Returns (u [n], y [m][3], z [m][3], primal residual of the last round)."""
+    def rgd_admm(self, V: torch.Tensor, sources, rho: float, beta: float, beta_k: float, max_rounds: int,
+                 tol: float = 0.0, adapt_rho: bool = False, y: Optional[torch.Tensor] = None,
+                 z: Optional[torch.Tensor] = None, opts=None):
+        """Rounds of the regularized-geodesic ADMM (see ig_rgd_admm) from y and z (zeros when not
+        given), at most max_rounds, stopping early at tol when tol > 0, with residual balancing of
+        rho when adapt_rho. Returns (u [n], y [m][3], z [m][3], stats) with stats a dict of the
+        rounds run, the last primal and dual residuals and the final rho."""
         V = self._dev(V, 3, "V")
         dev = self.ctx.device
         y = torch.zeros((self.m, 3), dtype=torch.float64, device=dev) if y is None else \
@@ -231,15 +234,16 @@ class Mesh:
             z.to(dev, torch.float64).contiguous().clone()
         src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).ravel())
         u = torch.empty(self.n, dtype=torch.float64, device=dev)
-        primal = ctypes.c_double(0.0)
+        stats = (ctypes.c_double * 4)()
         self.ctx.sync_stream()
         st = self.ctx.lib.ig_rgd_admm(self.h, _ptr(V), src.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(src.size),
-                                      float(rho), float(beta), float(beta_k), int(iters), _ptr(u), _ptr(y), _ptr(z),
-                                      ctypes.byref(primal), ctypes.byref(opts) if opts is not None else None)
+                                      float(rho), float(beta), float(beta_k), int(max_rounds), float(tol),
+                                      int(bool(adapt_rho)), _ptr(u), _ptr(y), _ptr(z), stats,
+                                      ctypes.byref(opts) if opts is not None else None)
         self._token = None
         self.t = None
         self.ctx.check(st)
-        return u, y, z, primal.value
+        return u, y, z, {"rounds": int(stats[0]), "primal": stats[1], "dual": stats[2], "rho": stats[3]}
 
     def rgd_u_step_vjp(self, V: torch.Tensor, sources, y: torch.Tensor, z: torch.Tensor, rho: float, beta: float,
                        u: torch.Tensor, gu: torch.Tensor, opts=None):

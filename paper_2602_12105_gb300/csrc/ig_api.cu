@@ -931,7 +931,7 @@ static ig_status rgd_prepare(ig_mesh* mesh, const double* V_dev, const int32_t* 
     if (sources_host[i] < 0 || sources_host[i] >= n) return bad_arg(ctx, "a source index is out of range");
     mask[(size_t)sources_host[i]] = 1;
   }
-  if (!mesh->rgd) IG_CK(ctx, mesh_alloc(mesh, &mesh->rgd, 2 * (size_t)n + 8), "alloc");
+  if (!mesh->rgd) IG_CK(ctx, mesh_alloc(mesh, &mesh->rgd, 2 * (size_t)n + 8 + 3 * (size_t)mesh->m), "alloc");
   int* src = reinterpret_cast<int*>(mesh->rgd + n);
   IG_CK(ctx, cudaMemcpyAsync(src, mask.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream), "sources");
   // the copy reads mask before this function returns
@@ -1020,43 +1020,73 @@ ig_status ig_rgd_u_step_vjp(ig_mesh* mesh, const double* V_dev, const int32_t* s
 }
 
 ig_status ig_rgd_admm(ig_mesh* mesh, const double* V_dev, const int32_t* sources_host, int nsrc, double rho, double beta,
-                      double beta_k, int iters, double* u_dev, double* y_dev, double* z_dev, double* primal_host,
-                      const ig_solve_opts* opts) {
+                      double beta_k, int max_rounds, double tol, int adapt_rho, double* u_dev, double* y_dev,
+                      double* z_dev, double* stats_host, const ig_solve_opts* opts) {
   if (!mesh) return IG_ERR_INVALID_ARG;
   ig_ctx* ctx = mesh->ctx;
   if (!V_dev || !sources_host || !u_dev || !y_dev || !z_dev) return bad_arg(ctx, "V, sources, u, y and z must be non-NULL");
-  if (iters < 1) return bad_arg(ctx, "iters must be >= 1");
-  if (!(rho > 0.0) || !(beta_k >= 0.0) || !(beta_k <= 2.0)) return bad_arg(ctx, "rho must be > 0, beta_k in [0, 2]");
+  if (max_rounds < 1) return bad_arg(ctx, "max_rounds must be >= 1");
+  if (!(rho > 0.0) || !(rho < 1e300) || !(beta_k >= 0.0) || !(beta_k <= 2.0))
+    return bad_arg(ctx, "rho must be > 0 and finite, beta_k in [0, 2]");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return bad_arg(ctx, "tol must be finite and >= 0");
   const ig_solve_opts o = resolve_opts(opts);
   ig_status cs = check_opts(ctx, o);
   if (cs != IG_OK) return cs;
   DeviceGuard guard(ctx->device);
-  const long n = (long)mesh->n;
+  const long n = (long)mesh->n, m = (long)mesh->m;
   int* src = nullptr;
   ig_status st = rgd_prepare(mesh, V_dev, sources_host, nsrc, rho, beta, &src);
   if (st != IG_OK) return st;
   double* b = mesh->rgd;
-  unsigned long long* primal = reinterpret_cast<unsigned long long*>(mesh->rgd + 2 * n);
+  unsigned long long* res = reinterpret_cast<unsigned long long*>(mesh->rgd + 2 * n);  // primal, dual
+  double* zold = mesh->rgd + 2 * n + 8;
   auto io = std::make_unique<IoTable>();
   io->in[0] = b;
   io->out[0] = u_dev;
+  const bool watch = tol > 0.0 || adapt_rho != 0;  // residuals needed after every round
+  double primal = 0.0, dual = 0.0;
+  int rounds = 0;
   cudaError_t e = cudaSuccess;
-  for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+  for (int it = 0; it < max_rounds && e == cudaSuccess; ++it) {
     e = launch_rgd_rhs(mesh->group.mds, (int)n, V_dev, y_dev, z_dev, rho, beta, src, b, ctx->stream);
     if (e == cudaSuccess) e = group_solve(mesh->group, 1, 0, *io, 0, o, ctx->stream);
-    const bool last = it == iters - 1;
-    if (e == cudaSuccess && last) e = cudaMemsetAsync(primal, 0, sizeof(unsigned long long), ctx->stream);
+    const bool need = watch || it == max_rounds - 1;
+    if (e == cudaSuccess && need) e = cudaMemcpyAsync(zold, z_dev, sizeof(double) * 3 * m, cudaMemcpyDeviceToDevice,
+                                                      ctx->stream);
+    if (e == cudaSuccess && need) e = cudaMemsetAsync(res, 0, 2 * sizeof(unsigned long long), ctx->stream);
     if (e == cudaSuccess)
-      e = launch_rgd_zy(mesh->group.mds, (int)mesh->m, V_dev, u_dev, y_dev, z_dev, rho, beta_k, last ? primal : nullptr,
+      e = launch_rgd_zy(mesh->group.mds, (int)m, V_dev, u_dev, y_dev, z_dev, rho, beta_k, need ? res : nullptr,
                         ctx->stream);
+    if (e == cudaSuccess && need) e = launch_rgd_dual(mesh->group.mds, (int)n, V_dev, z_dev, zold, src, rho, res + 1,
+                                                      ctx->stream);
+    rounds = it + 1;
+    if (e != cudaSuccess || !watch) continue;
+    unsigned long long bits[2] = {0, 0};
+    e = cudaMemcpyAsync(bits, res, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    std::memcpy(&primal, &bits[0], sizeof(double));
+    std::memcpy(&dual, &bits[1], sizeof(double));
+    if (tol > 0.0 && primal <= tol && dual <= tol) break;
+    // residual balancing: keep the primal and dual residuals within a factor of 10 of each other
+    if (adapt_rho) {
+      if (primal > 10.0 * dual) rho *= 2.0;
+      else if (dual > 10.0 * primal) rho *= 0.5;
+    }
   }
   mesh->assembled = 0;
   IG_CK(ctx, e, "admm");
-  if (primal_host) {
-    unsigned long long bits = 0;
-    IG_CK(ctx, cudaMemcpyAsync(&bits, primal, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream), "admm");
-    IG_CK(ctx, cudaStreamSynchronize(ctx->stream), "admm");
-    std::memcpy(primal_host, &bits, sizeof(double));
+  if (stats_host) {
+    if (!watch) {
+      unsigned long long bits[2] = {0, 0};
+      IG_CK(ctx, cudaMemcpyAsync(bits, res, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream), "admm");
+      IG_CK(ctx, cudaStreamSynchronize(ctx->stream), "admm");
+      std::memcpy(&primal, &bits[0], sizeof(double));
+      std::memcpy(&dual, &bits[1], sizeof(double));
+    }
+    stats_host[0] = rounds;
+    stats_host[1] = primal;
+    stats_host[2] = dual;
+    stats_host[3] = rho;
   }
   return IG_OK;
 }

@@ -305,7 +305,8 @@ struct ig_mesh {
   std::vector<void*> allocs;
   double* fair = nullptr;   // inverse-fairing workspace: U, G, g, g~ [n][3], w [n], loss (on first use)
   double* eig = nullptr;    // eigen-iteration workspace (eig_workspace_doubles, on first use)
-  double* rgd = nullptr;    // geodesic workspace: right-hand side [n], source mask [n] ints, scalars [8]
+  double* rgd = nullptr;    // geodesic workspace: right-hand side [n], source mask [n] ints, scalars [8],
+                            // previous z [m][3]
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -368,6 +369,9 @@ cudaError_t launch_rgd_vec(const double* x, const int* src, int n, int add_s, do
 // one ADMM z-step and dual step per face (primal: max_f |G u - z| as double bits, may be null)
 cudaError_t launch_rgd_zy(const MeshDev* mds, int m, const double* V, const double* u, double* y, double* z, double rho,
                           double beta_k, unsigned long long* primal, cudaStream_t st);
+// dual residual rho max_i |(D (z - zold))_i| / m_i over non-source vertices, as double bits
+cudaError_t launch_rgd_dual(const MeshDev* mds, int n, const double* V, const double* z, const double* zold,
+                            const int* src, double rho, unsigned long long* dual, cudaStream_t st);
 // the divergence term of dl/dV (added to gV) and dl/dy, dl/dz (may be null), with lam in md.lam
 cudaError_t launch_rgd_dD(const MeshDev* mds, int n, int m, const double* V, const double* y, const double* z,
                           double rho, double beta, double* gV, double* gy, double* gz, cudaStream_t st);

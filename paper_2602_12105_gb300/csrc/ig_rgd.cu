@@ -238,6 +238,46 @@ __global__ void __launch_bounds__(kBlock) rgd_zy_kernel(const MeshDev* __restric
   if (primal) atomicMax(primal, (unsigned long long)__double_as_longlong(sqrt(r2)));
 }
 
+// Dual residual of a round: rho max over the non-source vertices of |(D (z - z_old))_i| / m_i
+// (area-normalised, in the units of the primal residual), by atomicMax on double bits.
+__global__ void __launch_bounds__(kBlock) rgd_dual_kernel(const MeshDev* __restrict__ mds,
+                                                          const double* __restrict__ V, const double* __restrict__ z,
+                                                          const double* __restrict__ zold, const int* __restrict__ src,
+                                                          double rho, unsigned long long* dual) {
+  const MeshDev& md = mds[0];
+  const int v = blockIdx.x * kBlock + threadIdx.x;
+  if (v >= md.n || src[v] != 0) return;
+  double div = 0.0;
+  const int e0 = md.incptr[v], e1 = md.incptr[v + 1];
+  for (int e = e0; e < e1; ++e) {
+    const int2 ic = md.inc[e];
+    const int f = ic.x >> 2, c = ic.x & 3;
+    double p[3][3];
+    for (int a = 0; a < 3; ++a) {
+      const int vid = md.F[3 * f + a];
+      for (int d = 0; d < 3; ++d) p[a][d] = V[3 * (long)vid + d];
+    }
+    double e1v[3], e2v[3], ec[3], N[3];
+    for (int d = 0; d < 3; ++d) {
+      e1v[d] = p[1][d] - p[0][d];
+      e2v[d] = p[2][d] - p[0][d];
+      ec[d] = p[(c + 2) % 3][d] - p[(c + 1) % 3][d];
+    }
+    N[0] = e1v[1] * e2v[2] - e1v[2] * e2v[1];
+    N[1] = e1v[2] * e2v[0] - e1v[0] * e2v[2];
+    N[2] = e1v[0] * e2v[1] - e1v[1] * e2v[0];
+    const double inv2 = 0.5 / sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    const double g0 = (N[1] * ec[2] - N[2] * ec[1]) * inv2;
+    const double g1 = (N[2] * ec[0] - N[0] * ec[2]) * inv2;
+    const double g2 = (N[0] * ec[1] - N[1] * ec[0]) * inv2;
+    div = fma(g0, z[3 * (long)f + 0] - zold[3 * (long)f + 0], div);
+    div = fma(g1, z[3 * (long)f + 1] - zold[3 * (long)f + 1], div);
+    div = fma(g2, z[3 * (long)f + 2] - zold[3 * (long)f + 2], div);
+  }
+  const double r = rho * fabs(div) / md.M[v];
+  atomicMax(dual, (unsigned long long)__double_as_longlong(r));
+}
+
 }  // namespace
 
 cudaError_t launch_rgd_operator(const MeshDev* mds, int n, const int* src, cudaStream_t st) {
@@ -277,6 +317,13 @@ cudaError_t launch_rgd_zy(const MeshDev* mds, int m, const double* V, const doub
                           double beta_k, unsigned long long* primal, cudaStream_t st) {
   IG_PROF("rgd_zy", st);
   rgd_zy_kernel<<<(m + kBlock - 1) / kBlock, kBlock, 0, st>>>(mds, V, u, y, z, rho, beta_k, primal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rgd_dual(const MeshDev* mds, int n, const double* V, const double* z, const double* zold,
+                            const int* src, double rho, unsigned long long* dual, cudaStream_t st) {
+  IG_PROF("rgd_dual", st);
+  rgd_dual_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(mds, V, z, zold, src, rho, dual);
   return cudaGetLastError();
 }
 

@@ -140,10 +140,28 @@ def test_admm_rounds_match_oracle(api, name, iters):
     V, F, src = _case(name)
     n = V.shape[0]
     rho, beta, beta_k = 5.0, 0.1, 1.5
-    ru, ry, rz, rprimal = oracle.rgd_admm(V, F, src, rho, beta, beta_k, iters)
+    ru, ry, rz, rst = oracle.rgd_admm(V, F, src, rho, beta, beta_k, iters)
     mesh = api.Mesh(_t(F, torch.int32), n)
-    u, y, z, primal = mesh.rgd_admm(_t(V), src, rho, beta, beta_k, iters, opts=api.make_opts(rel_tol=1e-13))
+    u, y, z, st = mesh.rgd_admm(_t(V), src, rho, beta, beta_k, iters, opts=api.make_opts(rel_tol=1e-13))
     for got, ref in ((u, ru), (y, ry), (z, rz)):
         got = got.cpu().numpy()
         assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max(), (np.abs(got - ref).max(), np.abs(ref).max())
-    assert abs(primal - rprimal) <= 1e-8 * max(1.0, rprimal)
+    assert st["rounds"] == iters
+    assert abs(st["primal"] - rst[1]) <= 1e-8 * max(1.0, rst[1])
+    assert abs(st["dual"] - rst[2]) <= 1e-8 * max(1.0, rst[2])
+
+
+def test_admm_stopping_and_rho_balancing_match_oracle(api):
+    """With a tolerance and residual balancing, the GPU takes the same decisions as the oracle:
+    the same number of rounds and the same final rho, and the same iterates."""
+    from paper_2602_12105_gb300 import meshgen as mg
+    p = mg.config_grid(17, 17, seed=0, t=1.0)
+    V = p.V.copy()
+    V[:, 2] = 0.0
+    ru, ry, rz, rst = oracle.rgd_admm(V, p.F, [0], 1.0, 0.0, 1.0, 2000, tol=1e-3, adapt_rho=True)
+    mesh = api.Mesh(_t(p.F, torch.int32), p.n)
+    u, y, z, st = mesh.rgd_admm(_t(V), [0], 1.0, 0.0, 1.0, 2000, tol=1e-3, adapt_rho=True,
+                                opts=api.make_opts(rel_tol=1e-13))
+    assert st["rounds"] == rst[0] and st["rho"] == rst[3], (st, rst)
+    assert st["primal"] <= 1e-3 and st["dual"] <= 1e-3
+    assert np.abs(u.cpu().numpy() - ru).max() <= 1e-7 * np.abs(ru).max()

@@ -100,9 +100,24 @@ def test_admm_approaches_the_euclidean_distance_on_a_flat_square():
     p = mg.config_grid(17, 17, seed=0, t=1.0)
     V = p.V.copy()
     V[:, 2] = 0.0
-    u, y, z, primal = oracle.rgd_admm(V, p.F, [0], rho=10.0, beta=0.0, beta_k=1.0, iters=300)
+    u, y, z, stats = oracle.rgd_admm(V, p.F, [0], rho=10.0, beta=0.0, beta_k=1.0, iters=300)
     d = np.linalg.norm(V - V[0], axis=1)
     assert u[0] == 0.0
     assert np.abs(u - d).max() <= 0.03 * d.max()
     assert np.linalg.norm(oracle.face_gradient(V, p.F, u), axis=1).max() <= 1.005
-    assert primal <= 5e-3
+    assert stats[0] == 300 and stats[1] <= 5e-3
+
+
+def test_admm_stops_on_its_residuals_with_rho_balancing():
+    """With a tolerance the rounds stop as soon as both residuals meet it, and residual balancing
+    changes rho only by factors of 2; the result still approaches the distance."""
+    from paper_2602_12105_gb300 import meshgen as mg
+    p = mg.config_grid(17, 17, seed=0, t=1.0)
+    V = p.V.copy()
+    V[:, 2] = 0.0
+    u, y, z, (rounds, primal, dual, rho) = oracle.rgd_admm(V, p.F, [0], rho=1.0, beta=0.0, beta_k=1.0, iters=2000,
+                                                          tol=1e-3, adapt_rho=True)
+    assert rounds < 2000 and primal <= 1e-3 and dual <= 1e-3
+    assert np.log2(rho) == round(np.log2(rho))
+    d = np.linalg.norm(V - V[0], axis=1)
+    assert np.abs(u - d).max() <= 0.04 * d.max()
