@@ -460,5 +460,102 @@ def rgd_admm(V, F, sources, rho, beta, beta_k, iters, y=None, z=None, tol=0.0, a
     return u, y, z, (rounds, primal, dual, rho)
 
 
+
+def face_gradient_vjp(V, F, u, W):
+    """d(sum_f <W_f, (G u)_f>)/dV [n][3] for per-vertex u [n] and per-face vectors W [m][3] held
+    fixed. Per face, G u = N x E / |N|^2 with N = (p1 - p0) x (p2 - p0) and E = sum_c u_c e_c (e_c
+    the edge opposite corner c), so <W, G u> = N . (E x W) / |N|^2; differentiated through E
+    (linear in the positions) and through N (both in the numerator and in |N|^2)."""
+    V, F, u, W = _f64(V), _i32(F), _f64(u), _f64(W)
+    P = V[F]
+    uf = u[F]
+    e = np.stack([P[:, 2] - P[:, 1], P[:, 0] - P[:, 2], P[:, 1] - P[:, 0]], axis=1)
+    E = np.einsum("fc,fcd->fd", uf, e)
+    a, b = P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]
+    N = np.cross(a, b)
+    nn = np.sum(N * N, axis=1)
+    g = np.zeros((F.shape[0], 3, 3))
+    # through E: N . (dE x W) = dE . (W x N), dE = sum_c (u_{c+1} - u_{c+2}) dp_c
+    wxn = np.cross(W, N) / nn[:, None]
+    for c in range(3):
+        g[:, c] += (uf[:, (c + 1) % 3] - uf[:, (c + 2) % 3])[:, None] * wxn
+    # through N: d(N . X / |N|^2) = v . dN with v = X / |N|^2 - 2 (N . X) N / |N|^4, X = E x W;
+    # v . dN = da . (b x v) + db . (v x a)
+    X = np.cross(E, W)
+    sval = np.sum(N * X, axis=1) / nn
+    v = X / nn[:, None] - 2.0 * (sval / nn)[:, None] * N
+    ga, gb = np.cross(b, v), np.cross(v, a)
+    g[:, 1] += ga
+    g[:, 2] += gb
+    g[:, 0] -= ga + gb
+    out = np.zeros_like(V)
+    np.add.at(out, F.ravel(), g.reshape(-1, 3))
+    return out
+
+
+def rgd_round(V, F, sources, y, z, rho, beta, beta_k, tol=1e-14):
+    """One round T(y, z) of the geodesic ADMM (its listing, fixed rho): u = rgd_u_step(y, z),
+    g = G u, z_new = P(y / rho + g), y_new = y + rho (beta_k g + (1 - beta_k) z - z_new).
+    Returns (y_new, z_new, u)."""
+    y, z = _f64(y), _f64(z)
+    u = rgd_u_step(V, F, sources, y, z, rho, beta, tol=tol)
+    g = face_gradient(V, F, u)
+    a = y / rho + g
+    zn = a / np.maximum(np.linalg.norm(a, axis=1), 1.0)[:, None]
+    yn = y + rho * (beta_k * g + (1.0 - beta_k) * z - zn)
+    return yn, zn, u
+
+
+def rgd_round_vjp(V, F, sources, y, z, rho, beta, beta_k, wy, wz, tol=1e-14):
+    """Vector-Jacobian product of one round (rgd_round) for cotangents wy, wz [m][3] of y_new and
+    z_new, by the chain rule through its three steps:
+      y_new: y gets wy, g gets rho beta_k wy, z gets rho (1 - beta_k) wy, z_new gets -rho wy;
+      z_new = P(a), a = y / rho + g: abar = dP(a)^T (wz - rho wy), with dP = I inside the unit ball
+        (|a| <= 1) and (I - ahat ahat^T) / |a| outside; y gets abar / rho, g gets abar;
+      g = G u: u gets G^T gbar, V gets the derivative of <gbar, G u> at fixed u;
+      u = rgd_u_step(y, z): rgd_u_step_vjp.
+    Returns (gV [n][3], gy [m][3], gz [m][3])."""
+    V, F, y, z, wy, wz = _f64(V), _i32(F), _f64(y), _f64(z), _f64(wy), _f64(wz)
+    u = rgd_u_step(V, F, sources, y, z, rho, beta, tol=tol)
+    grads, _ = hat_gradients(V, F)
+    g = np.einsum("fcd,fc->fd", grads, u[F])
+    a = y / rho + g
+    na = np.linalg.norm(a, axis=1)
+    zb = wz - rho * wy
+    ah = a / na[:, None]
+    outside = na > 1.0
+    abar = np.where(outside[:, None], (zb - np.sum(ah * zb, axis=1)[:, None] * ah) / na[:, None], zb)
+    gy = wy + abar / rho
+    gz = rho * (1.0 - beta_k) * wy
+    gbar = rho * beta_k * wy + abar
+    gu = np.zeros(V.shape[0])
+    np.add.at(gu, F.ravel(), np.einsum("fcd,fd->fc", grads, gbar).ravel())
+    gV = face_gradient_vjp(V, F, u, gbar)
+    gVu, gyu, gzu = rgd_u_step_vjp(V, F, sources, y, z, rho, beta, gu, tol=tol)
+    return gV + gVu, gy + gyu, gz + gzu
+
+
+def rgd_admm_vjp(V, F, sources, y, z, rho, beta, beta_k, gu, tol=1e-14):
+    """dl/dV for l(u*) with u* = rgd_u_step(y*, z*) at a fixed point (y*, z*) = T(y*, z*) of the
+    ADMM round (the fixed-point implicit layer of the framework section on implicit
+    differentiation, applied to the geodesics application): with (gV0, gy0, gz0) the u-step's VJP
+    of gu, solve w = (gy0, gz0) + J^T w (J = dT/d(y, z)), then dl/dV = gV0 + (dT/dV)^T w. J^T is
+    formed column by column from rgd_round_vjp and the system is solved densely, so this is for
+    small meshes. Returns (gV [n][3], w_y [m][3], w_z [m][3])."""
+    V, F, y, z = _f64(V), _i32(F), _f64(y), _f64(z)
+    m = F.shape[0]
+    gV0, gy0, gz0 = rgd_u_step_vjp(V, F, sources, y, z, rho, beta, gu, tol=tol)
+    JT = np.zeros((6 * m, 6 * m))
+    for j in range(6 * m):
+        e = np.zeros(6 * m)
+        e[j] = 1.0
+        _, cy, cz = rgd_round_vjp(V, F, sources, y, z, rho, beta, beta_k, e[:3 * m].reshape(m, 3),
+                                  e[3 * m:].reshape(m, 3), tol=tol)
+        JT[:, j] = np.concatenate([cy.ravel(), cz.ravel()])
+    w = np.linalg.solve(np.eye(6 * m) - JT, np.concatenate([gy0.ravel(), gz0.ravel()]))
+    wy, wz = w[:3 * m].reshape(m, 3), w[3 * m:].reshape(m, 3)
+    gVw, _, _ = rgd_round_vjp(V, F, sources, y, z, rho, beta, beta_k, wy, wz, tol=tol)
+    return gV0 + gVw, wy, wz
+
 def num_threads():
     return 1

@@ -121,3 +121,95 @@ def test_admm_stops_on_its_residuals_with_rho_balancing():
     assert np.log2(rho) == round(np.log2(rho))
     d = np.linalg.norm(V - V[0], axis=1)
     assert np.abs(u - d).max() <= 0.04 * d.max()
+
+
+def _bumpy_grid(nx, ny, seed=0, amp=0.05):
+    from paper_2602_12105_gb300 import meshgen as mg
+    p = mg.config_grid(nx, ny, seed=seed, t=1.0)
+    V = p.V.copy()
+    V[:, 2] = amp * np.random.default_rng(seed + 7).standard_normal(p.n)
+    return V, p.F
+
+
+def test_round_vjp_matches_central_differences():
+    """The VJP of one ADMM round against central differences of the round in y, z and V, at
+    iterates where some faces are projected onto the unit ball and others are not."""
+    V, F = _bumpy_grid(6, 5, seed=1)
+    m = F.shape[0]
+    rng = np.random.default_rng(3)
+    rho, beta, bk = 1.7, 0.3, 1.4
+    y = 1.5 * rng.standard_normal((m, 3))
+    z = 0.4 * rng.standard_normal((m, 3))
+    wy, wz = rng.standard_normal((m, 3)), rng.standard_normal((m, 3))
+    yn, zn, u = oracle.rgd_round(V, F, [0, 7], y, z, rho, beta, bk)
+    a = np.linalg.norm(y / rho + oracle.face_gradient(V, F, u), axis=1)
+    assert (a > 1.0).sum() >= 5 and (a < 1.0).sum() >= 5
+    gV, gy, gz = oracle.rgd_round_vjp(V, F, [0, 7], y, z, rho, beta, bk, wy, wz)
+
+    def ell(V_, y_, z_):
+        yn_, zn_, _ = oracle.rgd_round(V_, F, [0, 7], y_, z_, rho, beta, bk)
+        return np.sum(wy * yn_) + np.sum(wz * zn_)
+
+    eps = 1e-6
+    for _ in range(2):
+        dV, dy, dz = rng.standard_normal(V.shape), rng.standard_normal(y.shape), rng.standard_normal(z.shape)
+        for want, fd in ((np.sum(gV * dV), ell(V + eps * dV, y, z) - ell(V - eps * dV, y, z)),
+                         (np.sum(gy * dy), ell(V, y + eps * dy, z) - ell(V, y - eps * dy, z)),
+                         (np.sum(gz * dz), ell(V, y, z + eps * dz) - ell(V, y, z - eps * dz))):
+            assert abs(fd / (2 * eps) - want) <= 1e-6 * max(1.0, abs(want)), (fd / (2 * eps), want)
+
+
+def test_face_gradient_vjp_matches_central_differences():
+    V, F = _bumpy_grid(5, 4, seed=2)
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal(V.shape[0])
+    W = rng.standard_normal((F.shape[0], 3))
+    g = oracle.face_gradient_vjp(V, F, u, W)
+    dV = rng.standard_normal(V.shape)
+    eps = 1e-6
+    fd = (np.sum(W * oracle.face_gradient(V + eps * dV, F, u)) - np.sum(W * oracle.face_gradient(V - eps * dV, F, u)))
+    assert abs(fd / (2 * eps) - np.sum(g * dV)) <= 1e-7 * max(1.0, abs(np.sum(g * dV)))
+
+
+def _converged(V, F, rho, beta, bk, y=None, z=None):
+    u, y, z, st = oracle.rgd_admm(V, F, [0], rho, beta, bk, 20000, y=y, z=z, tol=1e-13)
+    assert st[0] < 20000, st
+    return u, y, z
+
+
+def test_admm_vjp_matches_central_differences_of_the_converged_distance():
+    """The fixed-point VJP of the ADMM against central differences of <c, u*(V)> with u* the
+    distance the rounds converge to (tol 1e-13 on both residuals)."""
+    V, F = _bumpy_grid(6, 5, seed=0)
+    rho, beta, bk = 2.0, 0.5, 1.0
+    u, y, z = _converged(V, F, rho, beta, bk)
+    rng = np.random.default_rng(11)
+    c = rng.standard_normal(V.shape[0])
+    gV, wy, wz = oracle.rgd_admm_vjp(V, F, [0], y, z, rho, beta, bk, c)
+    dV = rng.standard_normal(V.shape)
+    dV[:, 2] *= 0.2
+    eps = 1e-5
+    up = _converged(V + eps * dV, F, rho, beta, bk, y, z)[0]
+    um = _converged(V - eps * dV, F, rho, beta, bk, y, z)[0]
+    fd = np.sum(c * (up - um)) / (2 * eps)
+    want = np.sum(gV * dV)
+    assert abs(fd - want) <= 1e-5 * max(1.0, abs(want)), (fd, want)
+    # a planted mistake: the u-step's own gradient alone (no fixed-point solve) is far off
+    gV0, _, _ = oracle.rgd_u_step_vjp(V, F, [0], y, z, rho, beta, c)
+    assert abs(np.sum(gV0 * dV) - fd) > 1e-2 * abs(fd)
+
+
+def test_admm_vjp_does_not_depend_on_rho_and_is_translation_invariant():
+    """u* solves the regularized problem (formulation eq. edelstein), which has no rho: the
+    fixed points reached with two penalties give the same u* and the same dl/dV. And u* does not
+    change when the mesh is translated, so the rows of dl/dV sum to zero."""
+    V, F = _bumpy_grid(5, 5, seed=4)
+    beta, bk = 0.5, 1.0
+    c = np.random.default_rng(2).standard_normal(V.shape[0])
+    u1, y1, z1 = _converged(V, F, 2.0, beta, bk)
+    u2, y2, z2 = _converged(V, F, 5.0, beta, bk)
+    assert np.abs(u1 - u2).max() <= 1e-10
+    g1 = oracle.rgd_admm_vjp(V, F, [0], y1, z1, 2.0, beta, bk, c)[0]
+    g2 = oracle.rgd_admm_vjp(V, F, [0], y2, z2, 5.0, beta, bk, c)[0]
+    assert np.abs(g1 - g2).max() <= 1e-8 * np.abs(g1).max()
+    assert np.abs(g1.sum(axis=0)).max() <= 1e-10 * np.abs(g1).max()
