@@ -340,6 +340,30 @@ ig_status ig_rgd_admm(ig_mesh* mesh, const double* V_dev, const int32_t* sources
                       double beta_k, int max_rounds, double tol, int adapt_rho, double* u_dev, double* y_dev,
                       double* z_dev, double* stats_host, const ig_solve_opts* opts);
 
+/* Gradient through the converged ADMM (the framework's fixed-point implicit layer, section on
+ * implicit differentiation, applied to the geodesics application): for l(u*) with u* the u-step
+ * at a fixed point (y*, z*) = T(y*, z*) of one round T of ig_rgd_admm (fixed rho), and
+ * gu_dev [n] = dl/du*, it writes
+ *   gV_dev [n][3] = dl/dV = gV0 + (dT/dV)^T w,   where (I - J^T) w = (gy0, gz0),
+ * J = dT/d(y, z) and (gV0, gy0, gz0) is the u-step's VJP of gu (ig_rgd_u_step_vjp). The adjoint
+ * system is solved by restarted GMRES (restart vectors of 6 m doubles each, 1 <= restart <= 100;
+ * at most max_iter Arnoldi steps; stop when the residual estimate is <= tol |(gy0, gz0)|), and
+ * each product with J^T is the round's backward pass: per face through the projection and the dual
+ * step, G^T, and one constrained Laplacian solve to opts->rel_tol.
+ * y_dev, z_dev [m][3]: the fixed point, e.g. the iterates ig_rgd_admm returned with its final rho
+ * (y is the unscaled dual, so (y*, z*) is a fixed point of T for every rho). w_dev [2][m][3] (may
+ * be NULL): receives w = (w_y, w_z). stats_host (may be NULL): 3 doubles, the Arnoldi steps
+ * taken, the final relative residual estimate and 1 if it met tol, else 0. Synchronises; the
+ * GMRES basis ((restart + 1) x 6 m doubles) is allocated for the call. Like ig_rgd_u_step it
+ * assembles the mesh at V, rewrites the operator and uses the mesh's adjoint buffer.
+ * Errors: as ig_rgd_admm; IG_ERR_INVALID_ARG for restart or max_iter out of range;
+ * IG_ERR_NOT_CONVERGED when GMRES stops at max_iter above tol (gV is still written from its best
+ * iterate); IG_ERR_NONFINITE for a non-finite residual. */
+ig_status ig_rgd_admm_vjp(ig_mesh* mesh, const double* V_dev, const int32_t* sources_host, int nsrc, double rho,
+                          double beta, double beta_k, const double* y_dev, const double* z_dev, const double* gu_dev,
+                          int restart, int max_iter, double tol, double* gV_dev, double* w_dev, double* stats_host,
+                          const ig_solve_opts* opts);
+
 /* ---- allocation-free solve ----------------------------------------------------------------- */
 
 /* Largest number of rows ig_solve_csr_noalloc accepts. */

@@ -97,6 +97,8 @@ SIGNATURES = {
                                  _P(SolveOpts)]),
     "ig_rgd_admm": (_i32, [_vp, _vp, _P(_i32), _i32, _dbl, _dbl, _dbl, _i32, _dbl, _i32, _vp, _vp, _vp, _P(_dbl),
                            _P(SolveOpts)]),
+    "ig_rgd_admm_vjp": (_i32, [_vp, _vp, _P(_i32), _i32, _dbl, _dbl, _dbl, _vp, _vp, _vp, _i32, _i32, _dbl, _vp, _vp,
+                               _P(_dbl), _P(SolveOpts)]),
     "ig_solve_csr_noalloc": (_i32, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, _i32, _vp, _vp, _P(SolveOpts),
                                      _P(SolveInfo)]),
     "ig_profile_enable": (_i32, [_i32]),

@@ -8,6 +8,7 @@ solves (M + tL) U = M B (§7.1) and the backward solves the adjoint system with 
 from __future__ import annotations
 
 import ctypes
+import warnings
 from typing import Optional
 
 import numpy as np
@@ -265,6 +266,37 @@ class Mesh:
         self.ctx.check(st)
         return gV, gy, gz
 
+    def rgd_admm_vjp(self, V: torch.Tensor, sources, y: torch.Tensor, z: torch.Tensor, rho: float, beta: float,
+                     beta_k: float, gu: torch.Tensor, restart: int = 30, max_iter: int = 300, tol: float = 1e-10,
+                     strict: bool = False, return_w: bool = False, opts=None):
+        """dl/dV [n][3] through the converged ADMM (see ig_rgd_admm_vjp), for its fixed point (y, z)
+        and the cotangent gu = dl/du*. The adjoint system is solved by restarted GMRES; when it stops
+        at max_iter above tol this warns (raises with strict=True) and returns the best iterate's
+        gradient. Returns (gV, stats) with stats a dict of the Arnoldi steps, the final relative
+        residual and whether tol was met, and w = (w_y, w_z) [2][m][3] as well with return_w."""
+        V = self._dev(V, 3, "V")
+        dev = self.ctx.device
+        y, z, gu = (x.to(dev, torch.float64).contiguous() for x in (y, z, gu))
+        src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).ravel())
+        gV = torch.empty((self.n, 3), dtype=torch.float64, device=dev)
+        w = torch.empty((2, self.m, 3), dtype=torch.float64, device=dev) if return_w else None
+        stats = (ctypes.c_double * 3)()
+        self.ctx.sync_stream()
+        st = self.ctx.lib.ig_rgd_admm_vjp(self.h, _ptr(V), src.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                          int(src.size), float(rho), float(beta), float(beta_k), _ptr(y), _ptr(z),
+                                          _ptr(gu), int(restart), int(max_iter), float(tol), _ptr(gV),
+                                          _ptr(w) if w is not None else None, stats,
+                                          ctypes.byref(opts) if opts is not None else None)
+        self._token = None
+        self.t = None
+        info = {"iterations": int(stats[0]), "rel_resid": stats[1], "converged": bool(stats[2])}
+        if st == N.IG_ERR_NOT_CONVERGED and not strict:
+            warnings.warn(f"rgd_admm_vjp: GMRES stopped at max_iter with relative residual {stats[1]:.3e}",
+                          RuntimeWarning)
+        else:
+            self.ctx.check(st)
+        return (gV, info, w) if return_w else (gV, info)
+
     def eigs_vjp(self, V: torch.Tensor, U: torch.Tensor, gU: torch.Tensor, iters: int, opts=None):
         """dl/dV [n][3] through the eigenvector fixed point of eigs (see ig_eigs_vjp), for the
         result U of eigs at the assembled positions V and the cotangent gU = dl/dU."""
@@ -387,6 +419,34 @@ def rgd_u_step(mesh: Mesh, V: torch.Tensor, y: torch.Tensor, z: torch.Tensor, so
                opts=None):
     """Differentiable u-step of the regularized-geodesic ADMM (see RgdUStep)."""
     return RgdUStep.apply(V, y, z, mesh, sources, rho, beta, opts)
+
+
+class RgdAdmm(torch.autograd.Function):
+    """Regularized geodesic distance u* from the ADMM run to its tolerance (ig_rgd_admm, y and z from
+    zeros), differentiable in V through the fixed point of the rounds (ig_rgd_admm_vjp)."""
+
+    @staticmethod
+    def forward(ctx, V, mesh: Mesh, sources, rho, beta, beta_k, max_rounds, tol, adapt_rho, gmres, opts):
+        u, y, z, st = mesh.rgd_admm(V, sources, rho, beta, beta_k, max_rounds, tol=tol, adapt_rho=adapt_rho,
+                                    opts=opts)
+        ctx.mesh, ctx.sources, ctx.beta, ctx.beta_k, ctx.opts = mesh, sources, float(beta), float(beta_k), opts
+        ctx.rho, ctx.gmres, ctx.stats = st["rho"], dict(gmres or {}), st
+        ctx.save_for_backward(V, y, z)
+        return u
+
+    @staticmethod
+    def backward(ctx, gu):
+        V, y, z = ctx.saved_tensors
+        gV, _ = ctx.mesh.rgd_admm_vjp(V, ctx.sources, y, z, ctx.rho, ctx.beta, ctx.beta_k,
+                                      gu.to(torch.float64).contiguous(), opts=ctx.opts, **ctx.gmres)
+        return gV, None, None, None, None, None, None, None, None, None, None
+
+
+def rgd_distance(mesh: Mesh, V: torch.Tensor, sources, rho: float, beta: float, beta_k: float = 1.0,
+                 max_rounds: int = 2000, tol: float = 1e-6, adapt_rho: bool = False, gmres=None, opts=None):
+    """Differentiable regularized geodesic distance (see RgdAdmm); gmres: keyword arguments of
+    Mesh.rgd_admm_vjp (restart, max_iter, tol, strict)."""
+    return RgdAdmm.apply(V, mesh, sources, rho, beta, beta_k, max_rounds, tol, adapt_rho, gmres, opts)
 
 
 class MassFn(torch.autograd.Function):

@@ -1091,6 +1091,105 @@ ig_status ig_rgd_admm(ig_mesh* mesh, const double* V_dev, const int32_t* sources
   return IG_OK;
 }
 
+ig_status ig_rgd_admm_vjp(ig_mesh* mesh, const double* V_dev, const int32_t* sources_host, int nsrc, double rho,
+                          double beta, double beta_k, const double* y_dev, const double* z_dev, const double* gu_dev,
+                          int restart, int max_iter, double tol, double* gV_dev, double* w_dev, double* stats_host,
+                          const ig_solve_opts* opts) {
+  if (!mesh) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (!V_dev || !sources_host || !y_dev || !z_dev || !gu_dev || !gV_dev)
+    return bad_arg(ctx, "V, sources, y, z, gu and gV must be non-NULL");
+  if (!(rho > 0.0) || !(rho < 1e300) || !(beta_k >= 0.0) || !(beta_k <= 2.0))
+    return bad_arg(ctx, "rho must be > 0 and finite, beta_k in [0, 2]");
+  if (restart < 1 || restart > 100) return bad_arg(ctx, "restart must be in [1, 100]");
+  if (max_iter < 1) return bad_arg(ctx, "max_iter must be >= 1");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return bad_arg(ctx, "tol must be finite and >= 0");
+  const ig_solve_opts o = resolve_opts(opts);
+  ig_status cs = check_opts(ctx, o);
+  if (cs != IG_OK) return cs;
+  DeviceGuard guard(ctx->device);
+  const long n = (long)mesh->n, m = (long)mesh->m;
+  int* src = nullptr;
+  ig_status st = rgd_prepare(mesh, V_dev, sources_host, nsrc, rho, beta, &src);
+  if (st != IG_OK) return st;
+  double* b = mesh->rgd;
+  const double s = 1.0 / (beta + rho);
+  // workspace: u* [n], gbar [m][3], the right-hand side and (unless the caller takes it) w, [6m] each
+  double* ws = nullptr;
+  const size_t count = (size_t)n + 3 * (size_t)m + 6 * (size_t)m + (w_dev ? 0 : 6 * (size_t)m);
+  IG_CK(ctx, cudaMalloc(&ws, sizeof(double) * count), "alloc");
+  std::unique_ptr<double, void (*)(double*)> hold(ws, [](double* p) { cudaFree(p); });
+  double* u = ws;
+  double* gbar = u + n;
+  double* rhs = gbar + 3 * m;
+  double* w = w_dev ? w_dev : rhs + 6 * m;
+  const MeshDev* mds = mesh->group.mds;
+  auto io = std::make_unique<IoTable>();
+  io->in[0] = b;
+  auto solve_into = [&](double* out) -> cudaError_t {
+    io->out[0] = out;
+    return group_solve(mesh->group, 1, 0, *io, 0, o, ctx->stream);
+  };
+  // u* = the u-step at (y*, z*)
+  cudaError_t e = launch_rgd_rhs(mds, (int)n, V_dev, y_dev, z_dev, rho, beta, src, b, ctx->stream);
+  if (e == cudaSuccess) e = solve_into(u);
+  // right-hand side (gy0, gz0): the u-step's VJP of gu, lam = L_D^-1 gu
+  if (e == cudaSuccess) e = launch_rgd_vec(gu_dev, src, (int)n, 0, 0.0, b, ctx->stream);
+  if (e == cudaSuccess) e = solve_into(mesh->md.lam);
+  if (e == cudaSuccess) e = cudaMemsetAsync(rhs, 0, sizeof(double) * 6 * m, ctx->stream);
+  if (e == cudaSuccess) e = launch_rgd_lamgrad(mds, (int)m, V_dev, -s, rho * s, rhs, ctx->stream);
+  IG_CK(ctx, e, "admm adjoint set-up");
+  // (I - J^T) v: the round's backward pass, with J^T's u-step part through one constrained solve
+  auto apply = [&](const double* in, double* out) -> cudaError_t {
+    cudaError_t e2 = launch_rgd_rvjp_face(mds, (int)m, V_dev, u, y_dev, in, rho, beta_k, gbar, out, ctx->stream);
+    if (e2 == cudaSuccess) e2 = launch_rgd_gT(mds, (int)n, V_dev, gbar, nullptr, src, b, ctx->stream);
+    if (e2 == cudaSuccess) e2 = solve_into(mesh->md.lam);
+    if (e2 == cudaSuccess) e2 = launch_rgd_lamgrad(mds, (int)m, V_dev, s, -rho * s, out, ctx->stream);
+    return e2;
+  };
+  GmresResult gr{};
+  e = gmres_solve(apply, rhs, w, 6 * m, restart, max_iter, tol, ctx->stream, &gr);
+  IG_CK(ctx, e, "admm adjoint GMRES");
+  // dl/dV = the u-step's VJP of gu + G^T gbar(w), plus d<gbar(w), G u*>/dV
+  e = launch_rgd_rvjp_face(mds, (int)m, V_dev, u, y_dev, w, rho, beta_k, gbar, nullptr, ctx->stream);
+  if (e == cudaSuccess) e = launch_rgd_gT(mds, (int)n, V_dev, gbar, gu_dev, src, b, ctx->stream);
+  if (e == cudaSuccess) e = solve_into(mesh->md.lam);
+  if (e == cudaSuccess) e = launch_rgd_vec(u, src, (int)n, 1, s, b, ctx->stream);  // B = u + s
+  if (e == cudaSuccess) {
+    CallDev call{};
+    call.V = V_dev;
+    call.B = b;
+    call.U = u;
+    call.gV = gV_dev;
+    call.t = 1.0;
+    call.b_is_V = 0;
+    call.bstride = 1;
+    e = group_set_calls(mesh->group, &call, ctx->stream);
+  }
+  if (e == cudaSuccess) e = launch_vjp(mesh->group, 1, ctx->stream, 0);
+  if (e == cudaSuccess)
+    e = launch_rgd_dD(mds, (int)n, (int)m, V_dev, y_dev, z_dev, rho, beta, gV_dev, nullptr, nullptr, ctx->stream);
+  if (e == cudaSuccess) e = launch_rgd_dG(mds, (int)n, (int)m, V_dev, u, gbar, gV_dev, ctx->stream);
+  // the workspace is freed on return
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  mesh->assembled = 0;
+  IG_CK(ctx, e, "admm adjoint gradient");
+  if (stats_host) {
+    stats_host[0] = gr.iterations;
+    stats_host[1] = gr.rel_resid;
+    stats_host[2] = gr.converged;
+  }
+  if (!std::isfinite(gr.rel_resid)) {
+    set_error(ctx, "admm adjoint: GMRES produced a non-finite residual");
+    return IG_ERR_NONFINITE;
+  }
+  if (!gr.converged) {
+    set_error(ctx, "admm adjoint: GMRES reached max_iter above tol (the best iterate is used)");
+    return IG_ERR_NOT_CONVERGED;
+  }
+  return IG_OK;
+}
+
 ig_status ig_profile_enable(int enable) {
   ProfState& P = prof_state();
   std::lock_guard<std::mutex> lk(P.mu);

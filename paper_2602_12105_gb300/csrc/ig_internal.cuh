@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -375,6 +376,30 @@ cudaError_t launch_rgd_dual(const MeshDev* mds, int n, const double* V, const do
 // the divergence term of dl/dV (added to gV) and dl/dy, dl/dz (may be null), with lam in md.lam
 cudaError_t launch_rgd_dD(const MeshDev* mds, int n, int m, const double* V, const double* y, const double* z,
                           double rho, double beta, double* gV, double* gy, double* gz, cudaStream_t st);
+// the fixed-point adjoint of the rounds: per face abar, gbar and (when out is given) the face parts of
+// (I - J^T) w, for w and out laid out [wy (m x 3) | wz (m x 3)]
+cudaError_t launch_rgd_rvjp_face(const MeshDev* mds, int m, const double* V, const double* u, const double* y,
+                                 const double* w, double rho, double beta_k, double* gbar, double* out,
+                                 cudaStream_t st);
+// ubar = G^T gbar (+ add when given), 0 on the sources
+cudaError_t launch_rgd_gT(const MeshDev* mds, int n, const double* V, const double* gbar, const double* add,
+                          const int* src, double* ubar, cudaStream_t st);
+// out_y += cy area grad(lam), out_z += cz area grad(lam), with lam in md.lam
+cudaError_t launch_rgd_lamgrad(const MeshDev* mds, int m, const double* V, double cy, double cz, double* out,
+                               cudaStream_t st);
+// gV += d<W, G u>/dV at fixed u and W (through md.gface)
+cudaError_t launch_rgd_dG(const MeshDev* mds, int n, int m, const double* V, const double* u, const double* W,
+                          double* gV, cudaStream_t st);
+
+// ig_gmres.cu: restarted GMRES on device vectors (deterministic reductions), for the fixed-point
+// adjoint; apply(in, out) computes out = A in on the stream
+struct GmresResult {
+  int iterations;    // Arnoldi steps taken (one product with A each, plus one per restart)
+  double rel_resid;  // the final residual estimate relative to |rhs|
+  int converged;
+};
+cudaError_t gmres_solve(const std::function<cudaError_t(const double*, double*)>& apply, const double* rhs, double* x,
+                        long N, int restart, int max_iter, double rel_tol, cudaStream_t st, GmresResult* res);
 
 // ig_vjp.cu
 // mode 0: solve terms; 1: solve terms and the mass weights of the calls; 2: mass weights alone

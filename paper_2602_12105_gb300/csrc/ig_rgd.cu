@@ -24,6 +24,19 @@
 // z = P(y / rho + g) with P the projection onto the unit ball, y += rho (beta_k g + (1 - beta_k)
 // z_old - z); the primal residual max_f |g - z| is kept as a maximum over faces (exact, so free of
 // the order of the faces).
+//
+// The fixed-point adjoint of the rounds (the implicit layer of the framework's fixed-point
+// interface, for the geodesics application): at a fixed point x* = (y*, z*) = T(x*) of one round
+// T, dl/dV = gV0 + (dT/dV)^T w with (I - J^T) w = (gy0, gz0), J = dT/dx and (gV0, gy0, gz0) the
+// u-step's VJP of gu. A product J^T w (w = (wy, wz)) follows the round's three steps backwards:
+//   rgd_rvjp_face: abar = dP(a)^T (wz - rho wy) with a = y / rho + G u (dP = I inside the unit ball,
+//     (I - ahat ahat^T) / |a| outside), gbar = rho beta_k wy + abar (the cotangent of G u), and the
+//     face parts of (I - J^T) w: -abar / rho for y, wz - rho (1 - beta_k) wy for z;
+//   rgd_gT: ubar = G^T gbar (0 on the sources), then lam = L_D^-1 ubar;
+//   rgd_lamgrad: the u-step's part, area grad(lam) times -s for y and rho s for z (taken with the
+//     opposite sign inside I - J^T).
+// (dT/dV)^T w is the same chain with ubar += gu: the u-step's VJP of the sum, plus rgd_gdface, the
+// derivative of <gbar, G u> at fixed u (G u = N x E / |N|^2 per face, through E and N).
 #include "ig_device.cuh"
 
 namespace ig {
@@ -278,6 +291,190 @@ __global__ void __launch_bounds__(kBlock) rgd_dual_kernel(const MeshDev* __restr
   atomicMax(dual, (unsigned long long)__double_as_longlong(r));
 }
 
+// Per face, the round's backward step through the z- and y-updates (see the file header): gbar =
+// rho beta_k wy + abar, and, when out is given, out_y = -abar / rho, out_z = wz - rho (1 - beta_k) wy.
+// w and out hold [wy (m x 3) | wz (m x 3)].
+__global__ void __launch_bounds__(kBlock) rgd_rvjp_face_kernel(const MeshDev* __restrict__ mds,
+                                                               const double* __restrict__ V,
+                                                               const double* __restrict__ u,
+                                                               const double* __restrict__ y,
+                                                               const double* __restrict__ w, double rho, double beta_k,
+                                                               double* __restrict__ gbar, double* __restrict__ out) {
+  const MeshDev& md = mds[0];
+  const int f = blockIdx.x * kBlock + threadIdx.x;
+  if (f >= md.m) return;
+  const long m3 = 3L * md.m;
+  double p[3][3], uc[3];
+  for (int c = 0; c < 3; ++c) {
+    const int vid = md.F[3 * f + c];
+    uc[c] = u[vid];
+    for (int d = 0; d < 3; ++d) p[c][d] = V[3 * (long)vid + d];
+  }
+  double a[3], b[3], E[3], N[3], av[3], wy[3], wz[3], zb[3];
+  for (int d = 0; d < 3; ++d) {
+    a[d] = p[1][d] - p[0][d];
+    b[d] = p[2][d] - p[0][d];
+    E[d] = uc[0] * (p[2][d] - p[1][d]) + uc[1] * (p[0][d] - p[2][d]) + uc[2] * (p[1][d] - p[0][d]);
+  }
+  N[0] = a[1] * b[2] - a[2] * b[1];
+  N[1] = a[2] * b[0] - a[0] * b[2];
+  N[2] = a[0] * b[1] - a[1] * b[0];
+  const double inv = 1.0 / (N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+  av[0] = y[3 * (long)f + 0] / rho + (N[1] * E[2] - N[2] * E[1]) * inv;
+  av[1] = y[3 * (long)f + 1] / rho + (N[2] * E[0] - N[0] * E[2]) * inv;
+  av[2] = y[3 * (long)f + 2] / rho + (N[0] * E[1] - N[1] * E[0]) * inv;
+  for (int d = 0; d < 3; ++d) {
+    wy[d] = w[3 * (long)f + d];
+    wz[d] = w[m3 + 3 * (long)f + d];
+    zb[d] = wz[d] - rho * wy[d];
+  }
+  const double na = sqrt(av[0] * av[0] + av[1] * av[1] + av[2] * av[2]);
+  if (na > 1.0) {
+    // (I - ahat ahat^T) zb / |a|
+    const double proj = (av[0] * zb[0] + av[1] * zb[1] + av[2] * zb[2]) / (na * na);
+    for (int d = 0; d < 3; ++d) zb[d] = (zb[d] - proj * av[d]) / na;
+  }
+  for (int d = 0; d < 3; ++d) {
+    gbar[3 * (long)f + d] = rho * beta_k * wy[d] + zb[d];
+    if (out) {
+      out[3 * (long)f + d] = -zb[d] / rho;
+      out[m3 + 3 * (long)f + d] = wz[d] - rho * (1.0 - beta_k) * wy[d];
+    }
+  }
+}
+
+// ubar_i = (G^T gbar)_i (+ add_i) = sum over the faces at i of <grad phi_i, gbar_f>, grad phi_i =
+// N_f x e_i / |N_f|^2; 0 at the sources.
+__global__ void __launch_bounds__(kBlock) rgd_gT_kernel(const MeshDev* __restrict__ mds, const double* __restrict__ V,
+                                                        const double* __restrict__ gbar, const double* __restrict__ add,
+                                                        const int* __restrict__ src, double* __restrict__ ubar) {
+  const MeshDev& md = mds[0];
+  const int v = blockIdx.x * kBlock + threadIdx.x;
+  if (v >= md.n) return;
+  if (src[v] != 0) {
+    ubar[v] = 0.0;
+    return;
+  }
+  double acc = add ? add[v] : 0.0;
+  const int e0 = md.incptr[v], e1 = md.incptr[v + 1];
+  for (int e = e0; e < e1; ++e) {
+    const int2 ic = md.inc[e];
+    const int f = ic.x >> 2, c = ic.x & 3;
+    double p[3][3];
+    for (int a = 0; a < 3; ++a) {
+      const int vid = md.F[3 * f + a];
+      for (int d = 0; d < 3; ++d) p[a][d] = V[3 * (long)vid + d];
+    }
+    double e1v[3], e2v[3], ec[3], N[3];
+    for (int d = 0; d < 3; ++d) {
+      e1v[d] = p[1][d] - p[0][d];
+      e2v[d] = p[2][d] - p[0][d];
+      ec[d] = p[(c + 2) % 3][d] - p[(c + 1) % 3][d];
+    }
+    N[0] = e1v[1] * e2v[2] - e1v[2] * e2v[1];
+    N[1] = e1v[2] * e2v[0] - e1v[0] * e2v[2];
+    N[2] = e1v[0] * e2v[1] - e1v[1] * e2v[0];
+    const double inv = 1.0 / (N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    const double g0 = (N[1] * ec[2] - N[2] * ec[1]) * inv;
+    const double g1 = (N[2] * ec[0] - N[0] * ec[2]) * inv;
+    const double g2 = (N[0] * ec[1] - N[1] * ec[0]) * inv;
+    acc = fma(g0, gbar[3 * (long)f + 0], acc);
+    acc = fma(g1, gbar[3 * (long)f + 1], acc);
+    acc = fma(g2, gbar[3 * (long)f + 2], acc);
+  }
+  ubar[v] = acc;
+}
+
+// out_y += cy area grad(lam), out_z += cz area grad(lam), area grad(lam) = n x E / 2 with
+// E = sum_c lam_c e_c (lam in md.lam).
+__global__ void __launch_bounds__(kBlock) rgd_lamgrad_kernel(const MeshDev* __restrict__ mds,
+                                                             const double* __restrict__ V, double cy, double cz,
+                                                             double* __restrict__ out) {
+  const MeshDev& md = mds[0];
+  const int f = blockIdx.x * kBlock + threadIdx.x;
+  if (f >= md.m) return;
+  const long m3 = 3L * md.m;
+  double p[3][3], l[3];
+  for (int c = 0; c < 3; ++c) {
+    const int vid = md.F[3 * f + c];
+    l[c] = md.lam[vid];
+    for (int d = 0; d < 3; ++d) p[c][d] = V[3 * (long)vid + d];
+  }
+  double a[3], b[3], N[3], E[3];
+  for (int d = 0; d < 3; ++d) {
+    a[d] = p[1][d] - p[0][d];
+    b[d] = p[2][d] - p[0][d];
+    E[d] = l[0] * (p[2][d] - p[1][d]) + l[1] * (p[0][d] - p[2][d]) + l[2] * (p[1][d] - p[0][d]);
+  }
+  N[0] = a[1] * b[2] - a[2] * b[1];
+  N[1] = a[2] * b[0] - a[0] * b[2];
+  N[2] = a[0] * b[1] - a[1] * b[0];
+  const double h = 0.5 / sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+  double ag[3];
+  ag[0] = (N[1] * E[2] - N[2] * E[1]) * h;
+  ag[1] = (N[2] * E[0] - N[0] * E[2]) * h;
+  ag[2] = (N[0] * E[1] - N[1] * E[0]) * h;
+  for (int d = 0; d < 3; ++d) {
+    out[3 * (long)f + d] += cy * ag[d];
+    out[m3 + 3 * (long)f + d] += cz * ag[d];
+  }
+}
+
+// Per face: the derivative of <W, G u> = N . (E x W) / |N|^2 (E = sum_c u_c e_c) with respect to
+// the corners, into gface [m][9] (u and W held fixed).
+__global__ void __launch_bounds__(kBlock) rgd_gdface_kernel(const MeshDev* __restrict__ mds,
+                                                            const double* __restrict__ V, const double* __restrict__ u,
+                                                            const double* __restrict__ W) {
+  const MeshDev& md = mds[0];
+  const int f = blockIdx.x * kBlock + threadIdx.x;
+  if (f >= md.m) return;
+  double p[3][3], uc[3];
+  for (int c = 0; c < 3; ++c) {
+    const int vid = md.F[3 * f + c];
+    uc[c] = u[vid];
+    for (int d = 0; d < 3; ++d) p[c][d] = V[3 * (long)vid + d];
+  }
+  double a[3], b[3], N[3], E[3], w[3];
+  for (int d = 0; d < 3; ++d) {
+    a[d] = p[1][d] - p[0][d];
+    b[d] = p[2][d] - p[0][d];
+    E[d] = uc[0] * (p[2][d] - p[1][d]) + uc[1] * (p[0][d] - p[2][d]) + uc[2] * (p[1][d] - p[0][d]);
+    w[d] = W[3 * (long)f + d];
+  }
+  N[0] = a[1] * b[2] - a[2] * b[1];
+  N[1] = a[2] * b[0] - a[0] * b[2];
+  N[2] = a[0] * b[1] - a[1] * b[0];
+  const double inn = 1.0 / (N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+  double wxn[3], X[3], v[3], ga[3], gb[3];
+  // through E: dE . (W x N) / |N|^2
+  wxn[0] = (w[1] * N[2] - w[2] * N[1]) * inn;
+  wxn[1] = (w[2] * N[0] - w[0] * N[2]) * inn;
+  wxn[2] = (w[0] * N[1] - w[1] * N[0]) * inn;
+  // through N: v = X / |N|^2 - 2 (N . X) N / |N|^4, X = E x W; v . dN = da . (b x v) + db . (v x a)
+  X[0] = E[1] * w[2] - E[2] * w[1];
+  X[1] = E[2] * w[0] - E[0] * w[2];
+  X[2] = E[0] * w[1] - E[1] * w[0];
+  const double sv = (N[0] * X[0] + N[1] * X[1] + N[2] * X[2]) * inn;
+  for (int d = 0; d < 3; ++d) v[d] = (X[d] - 2.0 * sv * N[d]) * inn;
+  ga[0] = b[1] * v[2] - b[2] * v[1];
+  ga[1] = b[2] * v[0] - b[0] * v[2];
+  ga[2] = b[0] * v[1] - b[1] * v[0];
+  gb[0] = v[1] * a[2] - v[2] * a[1];
+  gb[1] = v[2] * a[0] - v[0] * a[2];
+  gb[2] = v[0] * a[1] - v[1] * a[0];
+  double* out = md.gface + 9 * (long)f;
+  for (int c = 0; c < 3; ++c) {
+    const double du = uc[(c + 1) % 3] - uc[(c + 2) % 3];
+    for (int d = 0; d < 3; ++d) {
+      double g = du * wxn[d];
+      if (c == 1) g += ga[d];
+      else if (c == 2) g += gb[d];
+      else g -= ga[d] + gb[d];
+      out[3 * c + d] = g;
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_rgd_operator(const MeshDev* mds, int n, const int* src, cudaStream_t st) {
@@ -324,6 +521,43 @@ cudaError_t launch_rgd_dual(const MeshDev* mds, int n, const double* V, const do
                             const int* src, double rho, unsigned long long* dual, cudaStream_t st) {
   IG_PROF("rgd_dual", st);
   rgd_dual_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(mds, V, z, zold, src, rho, dual);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rgd_rvjp_face(const MeshDev* mds, int m, const double* V, const double* u, const double* y,
+                                 const double* w, double rho, double beta_k, double* gbar, double* out,
+                                 cudaStream_t st) {
+  IG_PROF("rgd_rvjp_face", st);
+  rgd_rvjp_face_kernel<<<(m + kBlock - 1) / kBlock, kBlock, 0, st>>>(mds, V, u, y, w, rho, beta_k, gbar, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rgd_gT(const MeshDev* mds, int n, const double* V, const double* gbar, const double* add,
+                          const int* src, double* ubar, cudaStream_t st) {
+  IG_PROF("rgd_gT", st);
+  rgd_gT_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(mds, V, gbar, add, src, ubar);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rgd_lamgrad(const MeshDev* mds, int m, const double* V, double cy, double cz, double* out,
+                               cudaStream_t st) {
+  IG_PROF("rgd_lamgrad", st);
+  rgd_lamgrad_kernel<<<(m + kBlock - 1) / kBlock, kBlock, 0, st>>>(mds, V, cy, cz, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rgd_dG(const MeshDev* mds, int n, int m, const double* V, const double* u, const double* W,
+                          double* gV, cudaStream_t st) {
+  {
+    IG_PROF("rgd_gdface", st);
+    rgd_gdface_kernel<<<(m + kBlock - 1) / kBlock, kBlock, 0, st>>>(mds, V, u, W);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  {
+    IG_PROF("rgd_dgather", st);
+    rgd_dgather_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(mds, gV);
+  }
   return cudaGetLastError();
 }
 
