@@ -54,6 +54,9 @@ def parse():
                     help="requests in the bounded sample of the serving stream")
     ap.add_argument("--variants", default="mixed,largest,batch,fairing,eigs,rgd,serve",
                     help="comma list of the extra workloads to run")
+    ap.add_argument("--oracle-timings", action="store_true",
+                    help="time the CPU oracle alone (single thread) on the ico3 and grid1024 configurations in "
+                         "full and on the 4096x2048 grid and the 256-mesh batch once each; prints one JSON line")
     return ap.parse_args()
 
 
@@ -932,8 +935,39 @@ def run_reference(args, rank, world):
                                          "d2h_bytes_per_step": 0}}
 
 
+def oracle_timings(args):
+    """The CPU oracle as it stands (single-threaded FP64 C, Jacobi-PCG to tol) on the host cores:
+    one forward + adjoint step of the small icosphere and the 1024^2 grid (best of 3 and of 1), and
+    one step each of the 4096 x 2048 grid and of the 256-mesh batch (the sum over its meshes)."""
+    import oracle
+    from paper_2602_12105_gb300 import meshgen as mg
+    oracle.build()
+
+    def step(q):
+        t0 = time.perf_counter()
+        oracle.forward_adjoint(q.V, q.F, q.B, q.t, q.T, q.b_is_V, tol=args.tol, method="pcg")
+        return time.perf_counter() - t0
+
+    out = {"kind": "oracle", "threads": oracle.num_threads(), "host_cores": len(os.sched_getaffinity(0)),
+           "tol": args.tol, "unit": UNIT, "configs": {}}
+    for name, reps in (("ico3", 3), ("grid1024", 1), ("grid4096x2048", 1)):
+        q = make_problem(name, 0)
+        dt = min(step(q) for _ in range(reps))
+        out["configs"][name] = {"n": int(q.n), "seconds_per_step": round(dt, 4), "solves_per_s": round(1.0 / dt, 5)}
+        del q
+    probs = mg.config_batch(seed=0, count=256)
+    dt = sum(step(q) for q in probs)
+    out["configs"]["batch256_icospheres"] = {"n": int(sum(q.n for q in probs)), "meshes": len(probs),
+                                             "seconds_for_all": round(dt, 3),
+                                             "solves_per_s": round(len(probs) / dt, 4)}
+    return out
+
+
 def main():
     args = parse()
+    if args.oracle_timings:
+        print(json.dumps(oracle_timings(args)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
