@@ -54,6 +54,9 @@ def parse():
                     help="requests in the bounded sample of the serving stream")
     ap.add_argument("--variants", default="mixed,largest,batch,fairing,eigs,rgd,serve",
                     help="comma list of the extra workloads to run")
+    ap.add_argument("--fma-peak", action="store_true",
+                    help="measure the FP64 and FP32 FMA throughput of this GPU (ig_measure_fma_peak) with the SM "
+                         "clock sampled during it; prints one JSON line")
     ap.add_argument("--oracle-timings", action="store_true",
                     help="time the CPU oracle alone (single thread) on the ico3 and grid1024 configurations in "
                          "full and on the 4096x2048 grid and the 256-mesh batch once each; prints one JSON line")
@@ -87,10 +90,13 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
+    _count = 0
+
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join("/tmp", f"ig_clocks_{os.getpid()}.csv")
+        ClockSampler._count += 1
+        self.path = os.path.join("/tmp", f"ig_clocks_{os.getpid()}_{ClockSampler._count}.csv")
 
     def start(self):
         try:
@@ -337,9 +343,10 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return None
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel, against the ALU peaks measured on this GPU now
+    alu = measure_alu_peaks(_native, local_rank, stream.cuda_stream)
     its_f, its_a = finfo["iterations"], ainfo["iterations"]
-    rl_all, roofline = kernel_roofline(prof, p.n, p.m, mesh.nnz, k, precision, clocks, args.workload,
+    rl_all, roofline = kernel_roofline(prof, p.n, p.m, mesh.nnz, k, precision, clocks, args.workload, alu,
                                        idx32=2 if args.workload.startswith("grid") else 4)
     step_roof = step_hbm(prof, 3, total_ms / args.steps, p.n, p.m, mesh.nnz, k, precision,
                          idx32=2 if args.workload.startswith("grid") else 4) if prof else None
@@ -365,6 +372,7 @@ def run_ours(args, rank, world, local_rank):
                        "p99": round(float(np.percentile(step_ms, 99)), 4)},
         "clocks": clocks,
         "roofline": roofline,
+        "alu_peaks": alu,
         "step_roofline": step_roof,
         "kernels": rl_all,
         "gpu_launches": gpu_launches(prof, args.steps, its_f, its_a, args.launch),
@@ -372,7 +380,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
     }
     if world == 1 and not args.no_variants:
-        out["variants"] = run_variants(args, p, U0, gV0, dev)
+        out["variants"] = run_variants(args, p, U0, gV0, dev, alu)
     return out
 
 
@@ -392,15 +400,48 @@ def gpu_launches(prof, steps, its_f, its_a, launch):
     return int(round(steps * per_step))
 
 
-def kernel_roofline(prof, n, m, nnz, k, precision, clocks, workload, idx32=4):
+def measure_alu_peaks(_native, gpu_index, stream_ptr=None):
+    """FP64 and FP32 fused multiply-add throughput of this GPU, measured by the library's
+    ig_measure_fma_peak (8 independent FMA chains per thread, one wave of resident CTAs on every
+    SM; best of 3 runs of about 0.3 s each), with the SM clock sampled while they run."""
+    import torch
+    sampler = ClockSampler(gpu_index)
+    sampler.start()
+    time.sleep(0.2)
+    r64 = max(_native.measure_fma_peak(True, steps=80000, stream=stream_ptr)[0] for _ in range(3))
+    r32 = max(_native.measure_fma_peak(False, steps=4000000, stream=stream_ptr)[0] for _ in range(3))
+    clocks = sampler.stop()
+    sms = torch.cuda.get_device_properties(gpu_index).multi_processor_count
+    mhz = clocks.get("sm_mhz")
+    out = {"fp64_tflops": round(r64 / 1e12, 4), "fp32_tflops": round(r32 / 1e12, 3), "sms": sms,
+           "sm_mhz": mhz, "clocks": clocks,
+           "how": "ig_measure_fma_peak: 8 independent FMA chains per thread, one wave of resident 256-thread CTAs on "
+                  "every SM, CUDA events, best of 3"}
+    if mhz:
+        out["fp64_fma_per_clk_per_sm"] = round(r64 / 2 / sms / (mhz * 1e6), 3)
+        out["fp32_fma_per_clk_per_sm"] = round(r32 / 2 / sms / (mhz * 1e6), 2)
+    return out
+
+
+def alu_peak_at(alu, key, sm_mhz):
+    """A measured ALU peak (TFLOP/s) scaled from the SM clock it was measured at to sm_mhz (the
+    median clock of the timed region): both are instruction rates proportional to the clock."""
+    v = alu[key]
+    if sm_mhz and alu.get("sm_mhz"):
+        v = v * sm_mhz / alu["sm_mhz"]
+    return v
+
+
+def kernel_roofline(prof, n, m, nnz, k, precision, clocks, workload, alu, idx32=4):
     """Per-kernel achieved rates from the profile pass ({name: (launches, total ms)}) and the
     roofline object of the kernel with the largest total time. FP64 kernels are held against the
-    FP64 ALU peak (152 SMs x 2 FMA/clk), FP32 ones against the measured HBM copy bandwidth and the
-    FP32 ALU peak; the bound is whichever fraction is higher."""
+    measured FP64 FMA peak, FP32 ones against the measured HBM copy bandwidth and the measured FP32
+    FMA peak (alu: measure_alu_peaks, scaled to the timed region's median SM clock); the bound is
+    whichever fraction is higher."""
     hbm_peak, peak_kind = peaks()
-    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    fp64_peak_tflops = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12     # 2 FP64 FMA / clk / SM
-    fp32_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12   # 128 FP32 FMA / clk / SM
+    sm_mhz = (clocks or {}).get("sm_mhz")
+    fp64_peak_tflops = alu_peak_at(alu, "fp64_tflops", sm_mhz)
+    fp32_peak_tflops = alu_peak_at(alu, "fp32_tflops", sm_mhz)
     rl_all = {}
     for name, (cnt, ms) in prof.items():
         is64 = name.startswith(("assemble", "vjp")) or (name.startswith("pcg_") and precision == "fp64")
@@ -420,8 +461,10 @@ def kernel_roofline(prof, n, m, nnz, k, precision, clocks, workload, idx32=4):
     if d["alu_frac"] >= d["hbm_frac"]:
         roofline = {"bound": "alu", "achieved": round(d["tflops"], 4), "peak": round(d["alu_peak"], 4),
                     "unit": "TFLOP/s", "frac": round(d["alu_frac"], 4), "traffic": measured_traffic(dom, workload),
-                    "kernel": dom, "peak_source": "derived: 152 SMs x FMA/clk x 2 x median SM clock under load "
-                                                  "(2 FMA/clk FP64, 128 FP32)",
+                    "kernel": dom,
+                    "peak_source": f"measured in this run: ig_measure_fma_peak {alu['fp64_tflops']} TFLOP/s FP64 "
+                                   f"({alu['fp32_tflops']} FP32) at a median {alu.get('sm_mhz')} MHz, scaled to the "
+                                   f"timed region's median {sm_mhz} MHz",
                     "hbm_gbs": round(d["gbs"], 1), "hbm_frac_of_measured": round(d["hbm_frac"], 4),
                     "algorithmic_bytes_per_launch": int(d["bytes"])}
     else:
@@ -513,11 +556,11 @@ def single_mesh(api, _native, dev, p, precision, tol, steps, warmup, launch="gra
             "prof": prof, "mesh": mesh}
 
 
-def variant_mixed_grid(api, _native, dev, p, tol, steps, fp64_U, fp64_gV, clocks):
+def variant_mixed_grid(api, _native, dev, p, tol, steps, fp64_U, fp64_gV, clocks, alu):
     """The headline grid in mixed precision (FP32 PCG inside FP64 refinement)."""
     r = single_mesh(api, _native, dev, p, "mixed", tol, steps, 3)
     table, roof = kernel_roofline(r["prof"], p.n, p.m, r["mesh"].nnz, p.B.shape[1], "mixed", clocks, p.name + "_mixed",
-                                  idx32=2)
+                                  alu, idx32=2)
     out = {"workload": f"{p.name} mixed: FP32 Jacobi-PCG (FP32 CSR values) inside FP64 residual refinement to {tol:g}",
            "value": round(r["solves_per_s"], 3), "unit": UNIT, "ms_per_step": round(r["ms_per_step"], 4),
            "steps": steps, "iterations": {"forward": r["finfo"]["iterations"], "adjoint": r["ainfo"]["iterations"]},
@@ -533,7 +576,7 @@ def variant_mixed_grid(api, _native, dev, p, tol, steps, fp64_U, fp64_gV, clocks
     return out
 
 
-def variant_largest(api, _native, dev, tol, steps, clocks):
+def variant_largest(api, _native, dev, tol, steps, clocks, alu):
     """The largest single mesh (4096 x 2048 grid, 8.4M vertices) in mixed precision, with its HBM
     roofline, and its error against the FP64 GPU path on the same mesh."""
     from paper_2602_12105_gb300 import meshgen as mg
@@ -541,7 +584,7 @@ def variant_largest(api, _native, dev, tol, steps, clocks):
     r = single_mesh(api, _native, dev, p, "mixed", tol, steps, 3)
     mesh = r["mesh"]
     table, roof = kernel_roofline(r["prof"], p.n, p.m, mesh.nnz, p.B.shape[1], "mixed", clocks, "grid4096x2048",
-                                  idx32=2)
+                                  alu, idx32=2)
     r64 = single_mesh(api, _native, dev, p, "fp64", tol, 1, 0, profile=False, mesh=mesh)
     out = {"workload": f"{p.name}: {p.n} vertices, {p.m} faces, k=3, t=h^2, mixed precision to {tol:g}",
            "value": round(r["solves_per_s"], 3), "unit": UNIT, "ms_per_step": round(r["ms_per_step"], 4),
@@ -855,7 +898,7 @@ def variant_serving(dev, tol, count):
             if served["p99_ms"] and plain["p99_ms"] else None}
 
 
-def run_variants(args, p, U64, gV64, dev):
+def run_variants(args, p, U64, gV64, dev, alu):
     from paper_2602_12105_gb300 import _native, api
     want = set(x.strip() for x in args.variants.split(",") if x.strip())
     sampler = ClockSampler(dev.index or 0)
@@ -864,9 +907,9 @@ def run_variants(args, p, U64, gV64, dev):
     t_start = time.perf_counter()
     clocks_guess = {"sm_mhz": None}
     if "mixed" in want:
-        out["grid1024_mixed"] = variant_mixed_grid(api, _native, dev, p, args.tol, 100, U64, gV64, clocks_guess)
+        out["grid1024_mixed"] = variant_mixed_grid(api, _native, dev, p, args.tol, 100, U64, gV64, clocks_guess, alu)
     if "largest" in want:
-        out["grid4096x2048_mixed"] = variant_largest(api, _native, dev, args.tol, 10, clocks_guess)
+        out["grid4096x2048_mixed"] = variant_largest(api, _native, dev, args.tol, 10, clocks_guess, alu)
     if "batch" in want:
         out["batch256_icospheres"] = variant_batch(api, _native, dev, args.tol, 6)
     if "fairing" in want:
@@ -901,38 +944,32 @@ def cpu_baseline(p, args):
 
 # ------------------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
+    """The oracle as it stands (single-threaded FP64 C) on the very configuration the main arm
+    names: every step is one whole forward + adjoint step of the full mesh (operator, both
+    Jacobi-PCG solves to --tol, the per-face gradient), timed on the host's wall clock."""
     if rank != 0:
         return None
     import oracle
-    from paper_2602_12105_gb300 import meshgen as mg
     oracle.build()
-    full = make_problem(args.workload, 0)
-    # bounded sample per step: the same family at a side of 128 (grid) or the icosphere itself
-    if args.workload.startswith("grid"):
-        side = 128
-        h = 1.0 / (side - 1)
-        sample = mg.problem_grid(side, side, h, h * h, seed=0, name="grid128")
-    else:
-        sample = full
-    scale = sample.n / full.n
+    p = make_problem(args.workload, 0)
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.forward_adjoint(sample.V, sample.F, sample.B, sample.t, sample.T, sample.b_is_V, tol=args.tol,
-                               method="pcg")
+        oracle.forward_adjoint(p.V, p.F, p.B, p.t, p.T, p.b_is_V, tol=args.tol, method="pcg")
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
-    per_step = float(np.sum(times)) / len(times) / scale   # seconds per full-size step, scaled by n
+    per_step = float(np.sum(times)) / len(times)
     value = 1.0 / per_step
     cpu = {"value": round(value, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-           "sample": f"{sample.name} ({sample.n} vertices) per step, time scaled by vertex count to "
-                     f"{full.name} ({full.n} vertices)"}
+           "sample": f"the full workload: {args.steps} timed steps (after {args.warmup} untimed), each one whole "
+                     f"forward + adjoint step of {p.name} ({p.n} vertices) by the single-threaded FP64 C oracle; "
+                     f"{len(os.sched_getaffinity(0))} host cores present, 1 used"}
     return {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(per_step * 1000, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(full, "fp64", args.tol)}, "impl": "reference",
-            "cpu_baseline": cpu, "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
-                                         "d2h_bytes_per_step": 0}}
+            "config": {"workload": workload_desc(p, "fp64", args.tol), "mesh": p.name, "n": p.n, "m": p.m},
+            "impl": "reference", "cpu_baseline": cpu,
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def oracle_timings(args):
@@ -967,6 +1004,13 @@ def main():
     args = parse()
     if args.oracle_timings:
         print(json.dumps(oracle_timings(args)), flush=True)
+        return
+    if args.fma_peak:
+        import torch
+
+        from paper_2602_12105_gb300 import _native
+        torch.cuda.set_device(0)
+        print(json.dumps(measure_alu_peaks(_native, 0, torch.cuda.current_stream().cuda_stream)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

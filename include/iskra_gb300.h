@@ -381,20 +381,24 @@ ig_status ig_rgd_admm_vjp(ig_mesh* mesh, const double* V_dev, const int32_t* sou
  * (CSR, each row holding its diagonal), Aval_dev [nnz] double (symmetric positive definite
  * values, e.g. from ig_operator), M_dev [n] double or NULL, B_dev [n][k] double. Output: U_dev
  * [n][k] double (must not overlap B). 1 <= k <= 4, 1 <= n <= IG_NOALLOC_MAX_ROWS. Work goes on
- * cuda_stream (a cudaStream_t; NULL = legacy default stream); the call returns after the
- * solve's loop has finished (it waits for a 4-byte flag every 16 iterations). opts may be NULL
- * (defaults; the launch mode is always one launch per kernel). info, if given, is filled as by
- * ig_solve (status IG_ERR_INVALID_ARG there means a missing or non-positive diagonal).
+ * cuda_stream (a cudaStream_t; NULL = legacy default stream). The call SYNCHRONISES that stream:
+ * its loop is driven from the host, which waits for a 4-byte flag every 16 iterations and for
+ * the error word at the end, so it returns only after the solve has finished and it must never
+ * be made while the stream (or any stream, in global capture mode) is being captured into a
+ * CUDA graph. opts may be NULL (defaults; the launch mode is always one launch per kernel).
+ * info, if given, is filled as by ig_solve.
  *
  * Scratch: all workspace lives in one static device array of about 9 MB, which every GPU that
  * loads this library holds until the process exits. The first call on a device looks up that
- * array's device address (once per device), so make the first call outside any stream capture.
- * Every call reuses the same array and overwrites what the previous call left there (the call
- * clears its counters itself); two calls that overlap on the GPU -- on different streams or
- * from different host threads -- race on the array and give wrong results.
+ * array's device address (once per device). Every call reuses the same array and overwrites
+ * what the previous call left there (the call clears its counters itself); two calls that
+ * overlap on the GPU -- on different streams or from different host threads -- race on the
+ * array and give wrong results.
  *
  * Errors: IG_ERR_INVALID_ARG for a NULL pointer, n > IG_NOALLOC_MAX_ROWS, nnz < n, k outside
- * [1, 4], overlapping B and U or bad options; IG_ERR_CUDA for a failed launch; with info,
+ * [1, 4], overlapping B and U or bad options, and -- with or without info -- for an operator
+ * with a missing or non-positive (or non-finite) diagonal entry, found on the device (the
+ * solution is then meaningless); IG_ERR_CUDA for a failed launch; with info,
  * IG_ERR_NOT_CONVERGED / IG_ERR_NONFINITE as for ig_solve. */
 ig_status ig_solve_csr_noalloc(const int32_t* rowptr_dev, const int32_t* col_dev, const double* Aval_dev,
                                const double* M_dev, int64_t n, int64_t nnz, const double* B_dev, int k,
@@ -418,6 +422,19 @@ ig_status ig_profile_enable(int enable);
 /* Synchronise on the recorded events and copy up to max per-kernel records into out; returns
  * the number of kernel names recorded (which may exceed max). */
 int ig_profile_read(ig_kernel_stat* out, int max);
+
+/* ---- measured arithmetic peak ------------------------------------------------------------- */
+
+/* Measure the device's fused multiply-add throughput, the ceiling of kernels bound by arithmetic
+ * instructions rather than by memory (on this GPU the FP64 ones: assembly, the per-face gradient
+ * and the FP64 solver loop). A grid of one wave of resident CTAs on every SM (current device) runs
+ * 8 independent FMA chains per thread for `steps` steps (2 flops per FMA) after a short warm-up,
+ * timed with CUDA events on cuda_stream. precision: IG_PRECISION_FP64 for double FMA,
+ * IG_PRECISION_MIXED for float FMA. flops_per_s receives the measured rate, seconds (may be NULL)
+ * the kernel's duration. Synchronises; allocates a small output buffer for the call. The rate
+ * follows the SM clock: sample the clock alongside it.
+ * Errors: IG_ERR_INVALID_ARG (NULL flops_per_s, steps < 1, bad precision), IG_ERR_OOM, IG_ERR_CUDA. */
+ig_status ig_measure_fma_peak(int precision, int steps, void* cuda_stream, double* flops_per_s, double* seconds);
 
 #ifdef __cplusplus
 }

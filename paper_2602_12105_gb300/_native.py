@@ -103,6 +103,7 @@ SIGNATURES = {
                                      _P(SolveInfo)]),
     "ig_profile_enable": (_i32, [_i32]),
     "ig_profile_read": (_i32, [_P(KernelStat), _i32]),
+    "ig_measure_fma_peak": (_i32, [_i32, _i32, _vp, _P(_dbl), _P(_dbl)]),
 }
 
 _lib = None
@@ -147,6 +148,19 @@ def check(status: int, ctx=None):
 
 def profile_enable(on: bool = True):
     load().ig_profile_enable(1 if on else 0)
+
+
+def measure_fma_peak(fp64: bool = True, steps: int = 0, stream=None):
+    """(flops/s, seconds) of the FMA-throughput kernel (see ig_measure_fma_peak) on `stream` (a
+    cudaStream_t as an int, or None for the legacy default stream)."""
+    lib = load()
+    if steps <= 0:
+        steps = 50000 if fp64 else 1000000
+    rate, secs = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    check(lib.ig_measure_fma_peak(IG_PRECISION_FP64 if fp64 else IG_PRECISION_MIXED, int(steps),
+                                  ctypes.c_void_p(stream) if stream else None, ctypes.byref(rate),
+                                  ctypes.byref(secs)))
+    return rate.value, secs.value
 
 
 def profile_read():

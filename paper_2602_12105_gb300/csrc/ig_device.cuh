@@ -2,6 +2,7 @@
 // deterministic CTA and cross-tile reductions, row loads, and the device-side loop control.
 #pragma once
 
+#include "ig_f32.cuh"
 #include "ig_internal.cuh"
 
 namespace ig {
@@ -133,6 +134,14 @@ __device__ __forceinline__ void load_row32(const float* __restrict__ p, long row
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 
+// A stored value in the arithmetic type: a float value of the FP32 operator is taken into FP64
+// exactly, with integer instructions (the FP64 residual of the FP32-geometry mode).
+template <typename TX, typename TA>
+__device__ __forceinline__ TX to_arith(TA a) {
+  if constexpr (sizeof(TX) == 8 && sizeof(TA) == 4) return f32_to_f64(a);
+  else return (TX)a;
+}
+
 // acc[c] = sum over the stored entries of row `row` of A[e] * X(col_e, c), where X is read by
 // the gather functor (x(col, v) fills v[0..K)). Uses the sliced-ELL layout when the mesh has one
 // (a warp's rows share one slice, so the loop count is uniform and each slot is one contiguous
@@ -191,21 +200,21 @@ __device__ __forceinline__ void row_product(const MeshDev& md, const TA* __restr
 #pragma unroll 4
       for (int j = 0; j < w; ++j) {
         const int e = base + 32 * j;
-        const TA a = __ldg(A + e);
+        const TX a = to_arith<TX>(__ldg(A + e));
         TX v[K];
         gather(__ldg(sc + e), v);
 #pragma unroll
-        for (int c = 0; c < K; ++c) acc[c] = fma_t((TX)a, v[c], acc[c]);
+        for (int c = 0; c < K; ++c) acc[c] = fma_t(a, v[c], acc[c]);
       }
     }
   } else {
     const int e0 = __ldg(md.rowptr + row), e1 = __ldg(md.rowptr + row + 1);
     for (int e = e0; e < e1; ++e) {
-      const TA a = __ldg(A + e);
+      const TX a = to_arith<TX>(__ldg(A + e));
       TX v[K];
       gather(__ldg(md.col + e), v);
 #pragma unroll
-      for (int c = 0; c < K; ++c) acc[c] = fma_t((TX)a, v[c], acc[c]);
+      for (int c = 0; c < K; ++c) acc[c] = fma_t(a, v[c], acc[c]);
     }
   }
 }

@@ -132,6 +132,17 @@ struct MeshDev {
   double* part;            // [ntiles][kPartStride] partial sums
   SolveScal* s;
   int* err;
+  // FP32 face geometry (IG_PRECISION_MIXED_GEOM32): when geom32 is set the operator is the FP32
+  // one in A32 (A is not formed; residuals read A32 exactly in FP64 arithmetic) and the face
+  // kernels work on hi/lo float splits of the FP64 vectors (x = hi + lo, hi the first 24
+  // significant bits of x, lo the rest rounded to float), so that differences of neighbouring
+  // values keep FP32 relative accuracy.
+  int geom32;
+  float* vsplit;           // [n][8]: positions, hi (x, y, z, 0) then lo (x, y, z, 0)
+  float* usplit;           // [n][8]: U, hi (k columns, padded to 4) then lo
+  float* lsplit;           // [n][8]: Lambda, the same layout
+  float* wv;               // [n]: <Lambda_v, B_v - U_v> per vertex
+  // per-face weights [m][4] float and per-face gradients [m][9] float live in facew and gface
 };
 
 // Host-side helpers (ig_api.cu).
@@ -330,8 +341,9 @@ cudaError_t launch_sell_c16(const int* sell_ptr, const int* sell_col, int n, sho
 cudaError_t launch_sell_fill(const int* rowptr, const int* col, int n, const int* sell_ptr, int* sell_col,
                              cudaStream_t st);
 
-// ig_assemble.cu (per-call V and t come from g.calls_dev)
-cudaError_t launch_assemble(Group& g, int mixed, cudaStream_t st);
+// ig_assemble.cu (per-call V and t come from g.calls_dev); mode: 0 FP64, 1 mixed (FP64 geometry
+// and operator, FP32 copy), 2 mixed with FP32 face geometry (FP32 operator only)
+cudaError_t launch_assemble(Group& g, int mode, cudaStream_t st);
 cudaError_t launch_operator_csr(const MeshDev& md, double* Acsr, cudaStream_t st);
 
 // ig_pcg.cu: see Group above
@@ -402,8 +414,10 @@ cudaError_t gmres_solve(const std::function<cudaError_t(const double*, double*)>
                         long N, int restart, int max_iter, double rel_tol, cudaStream_t st, GmresResult* res);
 
 // ig_vjp.cu
-// mode 0: solve terms; 1: solve terms and the mass weights of the calls; 2: mass weights alone
-cudaError_t launch_vjp(Group& g, int k, cudaStream_t st, int mode = 0);
+// mode 0: solve terms; 1: solve terms and the mass weights of the calls; 2: mass weights alone.
+// geom32: the group was assembled with FP32 face geometry; mode 0 then runs the FP32 per-face
+// gradient (FP64 for near-degenerate faces), the other modes the FP64 one.
+cudaError_t launch_vjp(Group& g, int k, cudaStream_t st, int mode = 0, int geom32 = 0);
 // ig_fairing.cu
 cudaError_t launch_mnorm(Group& g, const double* U, const double* T, double* G, double* w, double* loss,
                          cudaStream_t st);

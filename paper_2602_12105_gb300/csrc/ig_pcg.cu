@@ -21,7 +21,6 @@
 // handles several rows of a tile so the block reductions, which cost FP64 adds, are amortised.
 #include <cstring>
 #include <mutex>
-#include <new>
 
 #include "ig_device.cuh"
 
@@ -306,7 +305,8 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(const MeshDev* __restr
   for (int c = 0; c < K; ++c) acc[c] = 0.0;
   for (long row = t0 + threadIdx.x; row < t1; row += kBlock) {
     double ax[K];
-    row_product<K>(md, md.A, row, GatherAoS64<K>{xs}, ax);
+    if (md.geom32) row_product<K>(md, md.A32, row, GatherAoS64<K>{xs}, ax);  // the FP32 operator, exactly
+    else row_product<K>(md, md.A, row, GatherAoS64<K>{xs}, ax);
     const double mass = rhs_mass ? md.M[row] : 1.0;
 #pragma unroll
     for (int c = 0; c < K; ++c) {
@@ -806,21 +806,23 @@ extern "C" ig_status ig_solve_csr_noalloc(const int32_t* rowptr_dev, const int32
                      &reinterpret_cast<LoopCtl*>(base + kNaCtl)->nbig};
   noalloc_setup_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(md, g.mds, g.tiles, g.ntiles, ctl_init, g.ctl, md.s);
   if (cudaGetLastError() != cudaSuccess) return IG_ERR_CUDA;
-  IoTable* io = new (std::nothrow) IoTable;
-  if (!io) return IG_ERR_OOM;
-  io->in[0] = B_dev;
-  io->out[0] = U_dev;
-  cudaError_t e = group_solve(g, k, 0, *io, M_dev ? 1 : 0, o, st);
-  if (e == cudaSuccess && info) e = group_true_residual(g, k, *io, M_dev ? 1 : 0, st);
-  delete io;
+  // the pointer table lives on this thread's stack (16 KB): no host heap allocation either
+  IoTable io;
+  io.in[0] = B_dev;
+  io.out[0] = U_dev;
+  cudaError_t e = group_solve(g, k, 0, io, M_dev ? 1 : 0, o, st);
+  if (e == cudaSuccess && info) e = group_true_residual(g, k, io, M_dev ? 1 : 0, st);
   if (e != cudaSuccess) return IG_ERR_CUDA;
-  if (!info) return IG_OK;
+  // The error word is always read back (the host loop has synchronised the stream already): a
+  // missing or non-positive diagonal is a fault of the caller's operator, reported with or
+  // without info.
   SolveScal s;
   int bits = 0;
-  if (cudaMemcpyAsync(&s, md.s, sizeof(SolveScal), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+  if ((info && cudaMemcpyAsync(&s, md.s, sizeof(SolveScal), cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
       cudaMemcpyAsync(&bits, md.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return IG_ERR_CUDA;
+  if (!info) return bits ? IG_ERR_INVALID_ARG : IG_OK;
   std::memset(info, 0, sizeof(*info));
   info->status = bits ? IG_ERR_INVALID_ARG : s.status;
   info->k = k;

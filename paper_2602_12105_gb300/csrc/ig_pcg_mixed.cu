@@ -253,8 +253,8 @@ __global__ void __launch_bounds__(kBlock) resid_mixed_kernel(const MeshDev* __re
         const long nn = md.n;
         const long t0 = (long)tile * md.tile_rows32;
         const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
-        const double* __restrict__ A = md.A;
         const double* __restrict__ x = md.x;
+        const bool geom32 = md.geom32 != 0;  // the operator is the FP32 one: its values, exactly
         double acc[K];
 #pragma unroll
         for (int c = 0; c < K; ++c) acc[c] = 0.0;
@@ -263,7 +263,8 @@ __global__ void __launch_bounds__(kBlock) resid_mixed_kernel(const MeshDev* __re
           const long row = t0 + rr * kBlock + threadIdx.x;
           if (row < t1) {
             double ax[K];
-            row_product<K>(md, A, row, GatherSoA64<K>{x, nn}, ax);
+            if (geom32) row_product<K>(md, md.A32, row, GatherSoA64<K>{x, nn}, ax);
+            else row_product<K>(md, md.A, row, GatherSoA64<K>{x, nn}, ax);
 #pragma unroll
             for (int c = 0; c < K; ++c) {
               const double res = md.rhs[c * nn + row] - ax[c];

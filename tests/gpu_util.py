@@ -15,6 +15,20 @@ def rel2(a, b):
     return float(np.linalg.norm(np.asarray(a) - b) / (nb if nb > 0 else 1.0))
 
 
+def relmax(a, b):
+    """Largest elementwise error of a against b, relative to max |b|."""
+    a, b = np.asarray(a), np.asarray(b)
+    mb = np.abs(b).max() if b.size else 0.0
+    return float(np.abs(a - b).max() / (mb if mb > 0 else 1.0)) if b.size else 0.0
+
+
+def assert_close(a, b, tol, what=""):
+    """Both the relative 2-norm error and the largest elementwise error (relative to max |b|)
+    within tol: the norm alone could hide a few wrong entries of a large array."""
+    e2, em = rel2(a, b), relmax(a, b)
+    assert e2 <= tol and em <= tol, f"{what}: rel 2-norm {e2:.3e}, max elementwise {em:.3e}, tol {tol:.1e}"
+
+
 def case(name, seed=0, k=3):
     """Small cases that the oracle solves in seconds. Several span more than one 256-row tile
     with a ragged last tile (grid61x53: 3233 rows; ico5: 10242 rows)."""

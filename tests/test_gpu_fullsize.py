@@ -1,26 +1,33 @@
 """Parity at the full workload sizes, in the launch configuration the benchmark times (the
 device-side graph loop): the 1024 x 1024 grid in FP64 (1,048,576 vertices) and the 4096 x 2048 grid
-in mixed precision (8,388,608 vertices). The oracle cannot solve these in seconds, so the checks
-use what it computes one vertex at a time, and properties that hold at any size:
+in mixed precision (8,388,608 vertices), each against the CPU oracle run on the WHOLE mesh (its
+operator, its forward and adjoint Jacobi-PCG solves to 1e-13, its closed-form per-face gradient).
+The oracle takes a few seconds on the first mesh and well under two minutes on the second.
 
-- operator rows and masses at sampled vertices against the oracle run on the sampled vertices'
-  1-rings (a vertex's row of L and its mass depend on its incident faces only);
-- the FP64 residual of the GPU solutions (recomputed by the library in FP64), and the residual
-  rows at the sampled vertices under the oracle's rows;
-- dl/dV at the sampled vertices against the oracle's closed-form VJP on the same 1-rings, fed with
-  the GPU's U and an independently solved adjoint Lambda (a vertex's gradient depends on its
-  incident faces only);
-- in mixed precision, the solution against the FP64 GPU solution of the same mesh.
+Checked element by element (largest entrywise error relative to the largest reference entry,
+with the relative 2-norm beside it):
+
+- the operator A and the mass M: within 1e-12 (the same pattern, bit for bit);
+- with both sides solved to 1e-13: U and dl/dV within 1e-10 (FP64) and within the same 1e-10
+  in mixed precision, whose refinement residual uses the FP64 operator;
+- at the benchmark's tolerance (1e-10), the solver's own contract: the residual of the GPU's U
+  under the oracle's operator within 1e-10 (1 + 1e-3) per column, and the FP64 residuals the
+  library recomputes for both solves. The distance to the exact solution then depends on the
+  operator's conditioning (and, entry by entry, on how the error spreads over the mesh), so U and
+  dl/dV are only held to a coarse 1e-8 in relative 2-norm there.
+These sizes reach paths that the small tests do not: FP64 tiles of 1728 rows dealt cyclically to
+the CTAs (meshes of at least 2^20 rows), slices of one width, and 16-bit column offsets in the
+mixed-precision SpMV.
 """
 import numpy as np
 import pytest
 
 import oracle
+from gpu_util import assert_close, rel2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
-NSAMPLE = 48
 
 
 @pytest.fixture(scope="module")
@@ -35,103 +42,60 @@ def _t(a, dtype=torch.float64):
     return torch.from_numpy(np.ascontiguousarray(a)).to(device=DEV, dtype=dtype)
 
 
-def _samples(n, nx, seed):
-    """Corner, edge and interior vertices of the grid, plus random ones."""
-    rng = np.random.default_rng(seed)
-    fixed = [0, nx - 1, n - nx, n - 1, nx // 2, n // 2 + nx // 3, (n // nx // 2) * nx]
-    return np.unique(np.concatenate([fixed, rng.integers(0, n, NSAMPLE - len(fixed))])).astype(np.int64)
+def _reference(p):
+    """The oracle's whole path on the whole mesh: operator, U = A^-1 M B, Lambda = A^-1 (U - T),
+    dl/dV, each solve to a relative residual of 1e-13."""
+    return oracle.forward_adjoint(p.V, p.F, p.B, p.t, p.T, False, tol=1e-13, method="pcg")
 
 
-def _patch(F, idx):
-    """The faces incident to the sampled vertices, renumbered to their own vertices."""
-    mask = np.isin(F, idx).any(axis=1)
-    Fl = F[mask]
-    verts, inv = np.unique(Fl, return_inverse=True)
-    return verts, inv.reshape(-1, 3).astype(np.int32)
-
-
-def _rows(rowptr, col, val, idx):
-    """{vertex: {column: value}} for the given rows of a CSR matrix on the device."""
-    rp = rowptr.cpu().numpy()
-    out = {}
-    for i in idx:
-        a, b = int(rp[i]), int(rp[i + 1])
-        out[int(i)] = dict(zip(col[a:b].cpu().numpy().tolist(), val[a:b].cpu().numpy().tolist()))
-    return out
-
-
-def _check(api, p, precision, tol, sol_tol):
-    n = p.n
-    nx = p.meta["nx"]
-    idx = _samples(n, nx, seed=n % 1000)
-    mesh = api.Mesh(_t(p.F, torch.int32), n)
+def _check(api, p, precision):
+    ref = _reference(p)
+    mesh = api.Mesh(_t(p.F, torch.int32), p.n)
     V, B, T = _t(p.V), _t(p.B), _t(p.T)
     mesh.assemble(V, p.t, precision)
-    opts = api.make_opts(rel_tol=tol)
+
+    # the operator, entry by entry on the (bit-identical) pattern
+    rowptr, col = mesh.pattern()
+    assert np.array_equal(rowptr.cpu().numpy().astype(np.int64), ref["rowptr"])
+    assert np.array_equal(col.cpu().numpy(), ref["col"])
+    A, M = mesh.operator()
+    assert_close(A.cpu().numpy(), ref["Aval"], 1e-12, "A")
+    assert_close(M.cpu().numpy(), ref["M"], 1e-12, "M")
+
+    # both sides to 1e-13
+    tight = api.make_opts(rel_tol=1e-13)
+    U, finfo = mesh.solve(B, opts=tight, info=True)
+    gV, _, _, ainfo = mesh.adjoint(V, B, False, U, U - T, opts=tight, info=True)
+    assert finfo["status"] == 0 and ainfo["status"] == 0, (finfo, ainfo)
+    assert_close(U.cpu().numpy(), ref["U"], 1e-10, "U (1e-13 solves)")
+    assert_close(gV.cpu().numpy(), ref["gV"], 1e-10, "dl/dV (1e-13 solves)")
+
+    # the benchmark's configuration: 1e-10
+    opts = api.make_opts(rel_tol=1e-10)
     U, finfo = mesh.solve(B, opts=opts, info=True)
     gV, _, _, ainfo = mesh.adjoint(V, B, False, U, U - T, opts=opts, info=True)
     assert finfo["status"] == 0 and ainfo["status"] == 0, (finfo, ainfo)
-    assert max(finfo["true_rel_residual"]) <= tol * (1 + 1e-3)
-    assert max(ainfo["true_rel_residual"]) <= tol * (1 + 1e-3)
-
-    # operator rows and masses against the oracle on the sampled 1-rings
-    verts, Fl = _patch(p.F, idx)
-    o_rowptr, o_col, o_A, o_L, o_M = oracle.operator(p.V[verts], Fl, p.t)
-    A, M = mesh.operator()
-    rowptr, col = mesh.pattern()
-    g_rows = _rows(rowptr, col, A, idx)
-    loc = {int(v): i for i, v in enumerate(verts)}
-    Mh = M.cpu().numpy()
-    for v in idx:
-        li = loc[int(v)]
-        a, b = o_rowptr[li], o_rowptr[li + 1]
-        ref = {int(verts[c]): x for c, x in zip(o_col[a:b], o_A[a:b])}
-        rmax = max(abs(x) for x in ref.values())
-        assert set(ref) == set(g_rows[int(v)]), v
-        for c, x in ref.items():
-            assert abs(g_rows[int(v)][c] - x) <= 1e-12 * rmax, (v, c)
-        assert abs(Mh[v] - o_M[li]) <= 1e-12 * o_M[li], v
-
-    # residual rows of the GPU solution at the samples, under the oracle's rows
+    assert max(finfo["true_rel_residual"]) <= 1e-10 * (1 + 1e-3)
+    assert max(ainfo["true_rel_residual"]) <= 1e-10 * (1 + 1e-3)
     Uh = U.cpu().numpy()
-    R = Mh[:, None] * p.B
-    rnorm = np.linalg.norm(R, axis=0)
-    for v in idx:
-        li = loc[int(v)]
-        a, b = o_rowptr[li], o_rowptr[li + 1]
-        au = sum(x * Uh[int(verts[c])] for c, x in zip(o_col[a:b], o_A[a:b]))
-        assert np.all(np.abs(R[v] - au) <= tol * rnorm * (1 + 1e-3)), v
-
-    # dl/dV at the samples: the oracle's VJP on the 1-rings with the GPU's U and an adjoint solved
-    # here in FP64 to sol_tol (A Lam = G, as A Lam = M (G / M))
-    G = U - T
-    if precision != "fp64":
-        mesh.assemble(V, p.t, "fp64")
-    Lam = mesh.solve(G / M[:, None], opts=api.make_opts(rel_tol=sol_tol))
-    o_gV, _, _ = oracle.vjp(p.V[verts], Fl, p.t, Uh[verts], Lam.cpu().numpy()[verts], p.B[verts], False)
-    gVh = gV.cpu().numpy()
-    ref = np.array([o_gV[loc[int(v)]] for v in idx])
-    got = gVh[idx]
-    scale = np.abs(ref).max()
-    return mesh, U, got, ref, scale
+    res = ref["R"] - oracle.spmv(ref["rowptr"], ref["col"], ref["Aval"], Uh)
+    rel = np.linalg.norm(res, axis=0) / np.linalg.norm(ref["R"], axis=0)
+    assert rel.max() <= 1e-10 * (1 + 1e-3), rel
+    assert rel2(Uh, ref["U"]) <= 1e-8
+    assert rel2(gV.cpu().numpy(), ref["gV"]) <= 1e-8
+    return mesh, U
 
 
 def test_fullsize_grid1024_fp64(api):
     from paper_2602_12105_gb300 import meshgen as mg
-    p = mg.config_grid1024(0)
-    mesh, U, got, ref, scale = _check(api, p, "fp64", 1e-10, 1e-13)
-    # the GPU adjoint stopped at a relative residual of 1e-10, the one solved here at 1e-13; with
-    # t = h^2 the operator's condition number is at most 9 (eigenvalues between h^2 and 9 h^2), so
-    # the two gradients agree to within about 9e-10 of max |gV|
-    assert np.abs(got - ref).max() <= 2e-9 * scale, (np.abs(got - ref).max(), scale)
+    _check(api, mg.config_grid1024(0), "fp64")
 
 
 def test_fullsize_grid4096x2048_mixed(api):
     from paper_2602_12105_gb300 import meshgen as mg
     p = mg.config_grid4096x2048(0)
-    mesh, U, got, ref, scale = _check(api, p, "mixed", 1e-10, 1e-13)
-    assert np.abs(got - ref).max() <= 1e-8 * scale, (np.abs(got - ref).max(), scale)
-    # the mixed solution against the FP64 GPU solution of the same mesh (assembled in FP64 above)
+    mesh, U = _check(api, p, "mixed")
+    # the mixed solution against the FP64 GPU solution of the same mesh at the same tolerance
+    mesh.assemble(_t(p.V), p.t, "fp64")
     U64 = mesh.solve(_t(p.B), opts=api.make_opts(rel_tol=1e-10))
-    rel = float(torch.linalg.vector_norm(U - U64) / torch.linalg.vector_norm(U64))
-    assert rel <= 1e-9, rel
+    assert rel2(U.cpu().numpy(), U64.cpu().numpy()) <= 1e-9

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import case, rel2
+from gpu_util import assert_close, case, rel2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -46,14 +46,14 @@ def test_mixed_forward_adjoint_match_oracle(api, name):
     assert max(info["true_rel_residual"]) <= 1e-13 * (1 + 1e-3) * 10
     o_rowptr, o_col, o_A, o_L, o_M = oracle.operator(V, F, t)
     U_ref = _oracle_solve(o_rowptr, o_col, o_A, o_M[:, None] * B)
-    assert rel2(U.cpu().numpy(), U_ref) <= 1e-10
+    assert_close(U.cpu().numpy(), U_ref, 1e-10, "U")
     gV, gB, gt, ainfo = mesh.adjoint(_t(V), _t(B), False, U, U - _t(T), want_gB=True, want_gt=True, opts=opts,
                                      info=True)
     assert ainfo["status"] == 0, ainfo
     Lam_ref = _oracle_solve(o_rowptr, o_col, o_A, U_ref - T)
     gV_ref, gB_ref, gt_ref = oracle.vjp(V, F, t, U_ref, Lam_ref, B, False)
-    assert rel2(gV.cpu().numpy(), gV_ref) <= 1e-10
-    assert rel2(gB.cpu().numpy(), gB_ref) <= 1e-10
+    assert_close(gV.cpu().numpy(), gV_ref, 1e-10, "gV")
+    assert_close(gB.cpu().numpy(), gB_ref, 1e-10, "gB")
     assert abs(gt.item() - gt_ref) <= 1e-10 * abs(gt_ref)
 
 

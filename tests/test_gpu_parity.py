@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import CASES, case, rel2
+from gpu_util import CASES, assert_close, case, rel2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -83,15 +83,15 @@ def test_forward_and_adjoint(api, name):
     assert info["status"] == 0, info
     o_rowptr, o_col, o_A, o_L, o_M = oracle.operator(V, F, t)
     U_ref = _oracle_solve(o_rowptr, o_col, o_A, o_M[:, None] * B)
-    assert rel2(U.cpu().numpy(), U_ref) <= 1e-10
+    assert_close(U.cpu().numpy(), U_ref, 1e-10, "U")
     # adjoint for l = 0.5 ||U - T||^2, both sides using their own U
     G = U - _t(T)
     gV, gB, gt, ainfo = mesh.adjoint(_t(V), _t(B), False, U, G, want_gB=True, want_gt=True, opts=opts, info=True)
     assert ainfo["status"] == 0, ainfo
     Lam_ref = _oracle_solve(o_rowptr, o_col, o_A, U_ref - T)
     gV_ref, gB_ref, gt_ref = oracle.vjp(V, F, t, U_ref, Lam_ref, B, False)
-    assert rel2(gV.cpu().numpy(), gV_ref) <= gtol
-    assert rel2(gB.cpu().numpy(), gB_ref) <= 1e-10
+    assert_close(gV.cpu().numpy(), gV_ref, gtol, "gV")
+    assert_close(gB.cpu().numpy(), gB_ref, 1e-10, "gB")
     assert abs(gt.item() - gt_ref) <= gtol * max(abs(gt_ref), 1e-300)
 
 
@@ -104,12 +104,12 @@ def test_column_counts(api, k):
     U = mesh.solve(_t(B), opts=opts)
     o_rowptr, o_col, o_A, o_L, o_M = oracle.operator(V, F, t)
     U_ref = _oracle_solve(o_rowptr, o_col, o_A, o_M[:, None] * B)
-    assert rel2(U.cpu().numpy(), U_ref) <= 1e-10
+    assert_close(U.cpu().numpy(), U_ref, 1e-10, "U")
     gV, gB, gt = mesh.adjoint(_t(V), _t(B), False, U, U - _t(T), want_gB=True, want_gt=True, opts=opts)
     Lam_ref = _oracle_solve(o_rowptr, o_col, o_A, U_ref - T)
     gV_ref, gB_ref, gt_ref = oracle.vjp(V, F, t, U_ref, Lam_ref, B, False)
-    assert rel2(gV.cpu().numpy(), gV_ref) <= 1e-10
-    assert rel2(gB.cpu().numpy(), gB_ref) <= 1e-10
+    assert_close(gV.cpu().numpy(), gV_ref, 1e-10, "gV")
+    assert_close(gB.cpu().numpy(), gB_ref, 1e-10, "gB")
 
 
 def test_b_is_V_autograd_matches_oracle(api):
@@ -123,8 +123,8 @@ def test_b_is_V_autograd_matches_oracle(api):
     loss = 0.5 * ((U - _t(p.T)) ** 2).sum()
     loss.backward()
     ref = oracle.forward_adjoint(p.V, p.F, p.B, p.t, p.T, True)
-    assert rel2(U.detach().cpu().numpy(), ref["U"]) <= 1e-10
-    assert rel2(V.grad.cpu().numpy(), ref["gV"]) <= 1e-10
+    assert_close(U.detach().cpu().numpy(), ref["U"], 1e-10, "U")
+    assert_close(V.grad.cpu().numpy(), ref["gV"], 1e-10, "gV")
     assert abs(loss.item() - ref["loss"]) <= 1e-10 * ref["loss"]
 
 
@@ -137,8 +137,8 @@ def test_autograd_b_and_t(api):
     U = api.smooth(mesh, Vt, Bt, tt, opts=api.make_opts(rel_tol=1e-13))
     (0.5 * ((U - _t(T)) ** 2).sum()).backward()
     ref = oracle.forward_adjoint(V, F, B, t, T, False)
-    assert rel2(Vt.grad.cpu().numpy(), ref["gV"]) <= 1e-10
-    assert rel2(Bt.grad.cpu().numpy(), ref["gB"]) <= 1e-10
+    assert_close(Vt.grad.cpu().numpy(), ref["gV"], 1e-10, "gV")
+    assert_close(Bt.grad.cpu().numpy(), ref["gB"], 1e-10, "gB")
     assert abs(tt.grad.item() - ref["gt"]) <= 1e-10 * abs(ref["gt"])
 
 

@@ -213,3 +213,27 @@ def test_admm_vjp_does_not_depend_on_rho_and_is_translation_invariant():
     g2 = oracle.rgd_admm_vjp(V, F, [0], y2, z2, 5.0, beta, bk, c)[0]
     assert np.abs(g1 - g2).max() <= 1e-8 * np.abs(g1).max()
     assert np.abs(g1.sum(axis=0)).max() <= 1e-10 * np.abs(g1).max()
+
+
+def test_over_relaxation_changes_the_path_not_the_fixed_point():
+    """The dual step's over-relaxation term rho ((beta_k - 1)(z_old - G u)) changes the path of the
+    rounds but not their fixed points: at a fixed point z_new = z_old = z and y_new = y, so the dual
+    step reads rho beta_k (G u - z) = 0, i.e. G u = z, and the z-step z = P(y / rho + G u); neither
+    condition involves beta_k (beta_k != 0). The converged distance and the gradient through the
+    fixed point must therefore agree at beta_k = 1 and 1.5, while the paths differ. A sign error in
+    the term moves the fixed point (to z = beta_k G u / (2 - beta_k) with the sign of the
+    (1 - beta_k) z_old part flipped), which this catches at beta_k = 1.5."""
+    V, F = _bumpy_grid(5, 5, seed=6)
+    rho, beta = 2.0, 0.5
+    c = np.random.default_rng(9).standard_normal(V.shape[0])
+    u1, y1, z1 = _converged(V, F, rho, beta, 1.0)
+    u15, y15, z15 = _converged(V, F, rho, beta, 1.5)
+    assert np.abs(u1 - u15).max() <= 1e-10 * np.abs(u1).max()
+    assert np.abs(z1 - z15).max() <= 1e-9
+    g1 = oracle.rgd_admm_vjp(V, F, [0], y1, z1, rho, beta, 1.0, c)[0]
+    g15 = oracle.rgd_admm_vjp(V, F, [0], y15, z15, rho, beta, 1.5, c)[0]
+    assert np.abs(g1 - g15).max() <= 1e-10 * np.abs(g1).max()
+    # the paths differ: after the same few rounds from the same start the iterates are apart
+    a = oracle.rgd_admm(V, F, [0], rho, beta, 1.0, 5)
+    b = oracle.rgd_admm(V, F, [0], rho, beta, 1.5, 5)
+    assert np.abs(a[1] - b[1]).max() > 1e-3
