@@ -200,9 +200,37 @@ def algorithmic(kernel, n, m, nnz, k, prec, idx32=4):
     elif kernel == "assemble_face":
         flops = 60 * m
         byts = 12 * m + 24 * n + 32 * m
+    elif kernel == "assemble_rows":
+        # incidence offsets and entries (8 B per corner), the per-face weights, row offsets and
+        # diagonal slots; A (and its FP32 copy in mixed precision), M and 1/A_ii written
+        flops = 0
+        byts = 4 * n + 24 * m + 32 * m + 8 * n + 4 * n + 8 * nnz + 16 * n + (4 * nnz + 4 * n if prec == "mixed" else 0)
     elif kernel == "vjp_face":
         flops = 330 * m
         byts = 12 * m + 24 * n + 3 * 8 * k * n + 72 * m
+    elif kernel == "vjp_gather":
+        # incidence offsets and entries, the per-corner gradients (24 B each), M; gV written
+        flops = 0
+        byts = 4 * n + 24 * m + 72 * m + 8 * n + 24 * n
+    # FP32 face geometry: the split vertex passes, the FP32 face kernels and the FP32 gathers
+    elif kernel == "assemble_split32":
+        flops = 0
+        byts = 24 * n + 32 * n
+    elif kernel == "assemble_face32":
+        flops = 60 * m
+        byts = 12 * m + 32 * n + 16 * m
+    elif kernel == "assemble_rows32":
+        flops = 0
+        byts = 4 * n + 24 * m + 16 * m + 8 * n + 4 * n + 4 * nnz + 8 * n + 4 * n
+    elif kernel == "vjp_split32":
+        flops = 0
+        byts = 3 * 8 * k * n + 32 * n + 32 * n + 4 * n
+    elif kernel == "vjp_face32":
+        flops = 330 * m
+        byts = 12 * m + 3 * 32 * n + 4 * n + 48 * m
+    elif kernel == "vjp_gather32":
+        flops = 0
+        byts = 4 * n + 24 * m + 48 * m + 24 * n
     else:
         return None, None
     return float(flops), float(byts)
@@ -444,8 +472,10 @@ def kernel_roofline(prof, n, m, nnz, k, precision, clocks, workload, alu, idx32=
     fp32_peak_tflops = alu_peak_at(alu, "fp32_tflops", sm_mhz)
     rl_all = {}
     for name, (cnt, ms) in prof.items():
-        is64 = name.startswith(("assemble", "vjp")) or (name.startswith("pcg_") and precision == "fp64")
-        fl, by = algorithmic(name, n, m, nnz, k, "fp64" if is64 else "fp32", idx32)
+        is64 = (name.startswith(("assemble", "vjp")) and not name.endswith("32")) or \
+            (name.startswith("pcg_") and precision == "fp64")
+        fl, by = algorithmic(name, n, m, nnz, k, precision if name == "assemble_rows" else ("fp64" if is64 else "fp32"),
+                             idx32)
         if fl is None or cnt == 0 or ms <= 0:
             continue
         avg_s = ms / cnt / 1000.0
@@ -486,8 +516,10 @@ def step_hbm(prof, nsteps, ms_per_step, n, m, nnz, k, precision, idx32=4):
     hbm_peak, peak_kind = peaks()
     total, counted = 0.0, []
     for name, (cnt, _) in prof.items():
-        is64 = name.startswith(("assemble", "vjp")) or (name.startswith("pcg_") and precision == "fp64")
-        _, by = algorithmic(name, n, m, nnz, k, "fp64" if is64 else "fp32", idx32)
+        is64 = (name.startswith(("assemble", "vjp")) and not name.endswith("32")) or \
+            (name.startswith("pcg_") and precision == "fp64")
+        _, by = algorithmic(name, n, m, nnz, k, precision if name == "assemble_rows" else ("fp64" if is64 else "fp32"),
+                            idx32)
         if by is None or cnt == 0:
             continue
         total += by * cnt / nsteps
@@ -505,6 +537,13 @@ def _rel(a, b):
     import torch
     den = float(torch.linalg.vector_norm(b))
     return float(torch.linalg.vector_norm(a - b)) / (den if den > 0 else 1.0)
+
+
+def _relmax(a, b):
+    """Largest elementwise error of a against b, relative to max |b|."""
+    import torch
+    den = float(b.abs().max())
+    return float((a - b).abs().max()) / (den if den > 0 else 1.0)
 
 
 def _dev_problem(p, dev):
@@ -598,6 +637,25 @@ def variant_largest(api, _native, dev, tol, steps, clocks, alu):
            "step_roofline": step_hbm(r["prof"], 1, r["ms_per_step"], p.n, p.m, mesh.nnz, p.B.shape[1], "mixed",
                                      idx32=2),
            "kernels": table}
+    # the same mesh with FP32 face geometry (FP64 for slivers): the FP32 operator solved exactly
+    r32 = single_mesh(api, _native, dev, p, "mixed32", tol, steps, 3, mesh=mesh)
+    table32, roof32 = kernel_roofline(r32["prof"], p.n, p.m, mesh.nnz, p.B.shape[1], "mixed", clocks,
+                                      "grid4096x2048_mixed32", alu, idx32=2)
+    out["fp32_geometry"] = {
+        "workload": f"{p.name}, mixed precision with FP32 face geometry (cotangents, areas and the per-face "
+                    f"gradient in FP32; FP64 for faces with sin(theta_min) < 1e-2), FP32 operator solved to {tol:g}",
+        "value": round(r32["solves_per_s"], 3), "unit": UNIT, "ms_per_step": round(r32["ms_per_step"], 4),
+        "steps": steps,
+        "iterations": {"forward": r32["finfo"]["iterations"], "adjoint": r32["ainfo"]["iterations"]},
+        "true_rel_residual_own_operator": {"forward": max(r32["finfo"]["true_rel_residual"]),
+                                           "adjoint": max(r32["ainfo"]["true_rel_residual"])},
+        "rel_err_vs_fp64_gpu": {"U": _rel(r32["U"], r64["U"]), "gV": _rel(r32["gV"], r64["gV"]),
+                                "U_max_elementwise": _relmax(r32["U"], r64["U"]),
+                                "gV_max_elementwise": _relmax(r32["gV"], r64["gV"])},
+        "roofline": roof32,
+        "step_roofline": step_hbm(r32["prof"], 1, r32["ms_per_step"], p.n, p.m, mesh.nnz, p.B.shape[1], "mixed",
+                                  idx32=2),
+        "kernels": table32}
     mesh.close()
     return out
 

@@ -50,7 +50,20 @@ typedef enum {
   IG_ERR_STATE = 8               /* call out of order (e.g. solve before assemble) */
 } ig_status;
 
-enum { IG_PRECISION_FP64 = 0, IG_PRECISION_MIXED = 1 };
+/* Precision of the assembled operator and of the solves (ig_assemble):
+ *   IG_PRECISION_FP64        FP64 geometry, FP64 operator, FP64 Jacobi-PCG.
+ *   IG_PRECISION_MIXED       FP64 geometry and FP64 operator; the solves iterate in FP32 on an
+ *                            FP32 copy inside FP64 residual refinement against the FP64 operator,
+ *                            so they reach the FP64 solution (same accuracy as FP64).
+ *   IG_PRECISION_MIXED_GEOM32  FP32 face geometry as well: cotangents, areas and the per-face
+ *                            gradient in FP32, FP64 only for near-degenerate faces (smallest
+ *                            corner with sin < 1e-2); the operator is the FP32 one (A32), and the
+ *                            FP64 refinement solves it to rel_tol exactly. Results differ from the
+ *                            FP64 path by the FP32 rounding of the operator (about 1e-7 relative
+ *                            in its entries, amplified by its condition number). For the smoothing
+ *                            step (ig_solve, ig_adjoint, ig_vjp and the batch and serving calls)
+ *                            only. */
+enum { IG_PRECISION_FP64 = 0, IG_PRECISION_MIXED = 1, IG_PRECISION_MIXED_GEOM32 = 2 };
 enum { IG_LAUNCH_GRAPH = 0, IG_LAUNCH_HOST = 1 };
 
 typedef struct ig_ctx ig_ctx;
@@ -121,7 +134,10 @@ ig_status ig_mesh_pattern(ig_mesh* mesh, int32_t* rowptr_dev, int32_t* col_dev);
 /* Assemble A = M(V) + t L(V) for positions V_dev [n][3] (§7.1: L(v), M(v) recomputed
  * whenever v changes). precision = IG_PRECISION_FP64 keeps A in FP64; IG_PRECISION_MIXED also
  * keeps an FP32 copy of A and its diagonal for the inner iterations (the FP64 operator is
- * still the one every residual is measured against). Asynchronous; a zero-area face or a
+ * still the one every residual is measured against); IG_PRECISION_MIXED_GEOM32 computes the
+ * face geometry in FP32 (FP64 for faces whose smallest corner has sin < 1e-2) and keeps only
+ * the FP32 operator, which ig_operator then returns (its values are exact in FP64); positions
+ * must lie within the float range in this mode. Asynchronous; a zero-area face or a
  * non-finite coordinate is reported by the next synchronising call (ig_solve with info, or
  * ig_check), as IG_ERR_DEGENERATE_FACE / IG_ERR_NONFINITE.
  * Errors: IG_ERR_INVALID_ARG (t < 0 or not finite, bad precision), IG_ERR_OOM, IG_ERR_CUDA. */
@@ -230,7 +246,7 @@ ig_status ig_mass_vjp(ig_mesh* mesh, const double* V_dev, const double* w_dev, d
  *   loss = 1/2 sum_i M_i |T_i - U_i|^2 (the M-norm objective against targets T_dev [n][3]);
  *   g = dloss/dV by the adjoint rule (Eq. 3; with B = V) plus the direct mass term;
  *   Sobolev H^1 preconditioning with the same operator, g~ = A^-1 g; V <- V - eta g~.
- * V_dev [n][3] is updated in place. precision as for ig_assemble. loss_host (may be NULL)
+ * V_dev [n][3] is updated in place. precision: IG_PRECISION_FP64 or IG_PRECISION_MIXED. loss_host (may be NULL)
  * receives the loss at the positions the step started from (synchronises). info3 (may be NULL)
  * is an array of 3 ig_solve_info for the forward, adjoint and preconditioning solves
  * (synchronises). Workspace (13 n doubles) is allocated on the mesh at the first call.
@@ -260,7 +276,8 @@ ig_status ig_fairing_step(ig_mesh* mesh, double* V_dev, const double* T_dev, dou
  * allocated on the mesh at the first call. Errors: IG_ERR_STATE (not assembled), IG_ERR_INVALID_ARG (NULL U_dev, k or iters
  * out of range), IG_ERR_NONFINITE (a Gram matrix was not positive definite: the start columns
  * were dependent or not finite; reported when lambda_host or info is given), the errors of
- * ig_solve, IG_ERR_OOM, IG_ERR_CUDA. The gradient through this fixed point: ig_eigs_vjp. */
+ * ig_solve, IG_ERR_OOM, IG_ERR_CUDA; IG_ERR_STATE also for a mesh assembled with
+ * IG_PRECISION_MIXED_GEOM32. The gradient through this fixed point: ig_eigs_vjp. */
 ig_status ig_eigs(ig_mesh* mesh, int k, int iters, double* U_dev, double* lambda_host, const ig_solve_opts* opts,
                   ig_solve_info* info);
 

@@ -24,6 +24,7 @@ IG_ERR_STATE = 8
 
 IG_PRECISION_FP64 = 0
 IG_PRECISION_MIXED = 1
+IG_PRECISION_MIXED_GEOM32 = 2
 IG_LAUNCH_GRAPH = 0
 IG_LAUNCH_HOST = 1
 

@@ -16,7 +16,10 @@ import torch
 
 from . import _native as N
 
-_PREC = {"fp64": N.IG_PRECISION_FP64, "mixed": N.IG_PRECISION_MIXED}
+# "fp64": FP64 throughout; "mixed": FP32 iterations inside FP64 refinement against the FP64
+# operator (the FP64 answer); "mixed32": also FP32 face geometry (FP64 for near-degenerate faces),
+# the FP32 operator solved exactly (see IG_PRECISION_MIXED_GEOM32 in the C header)
+_PREC = {"fp64": N.IG_PRECISION_FP64, "mixed": N.IG_PRECISION_MIXED, "mixed32": N.IG_PRECISION_MIXED_GEOM32}
 
 
 def _ptr(t: Optional[torch.Tensor]):

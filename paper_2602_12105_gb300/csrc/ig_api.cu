@@ -254,6 +254,30 @@ cudaError_t mesh_ensure_mixed(ig_mesh* mesh, cudaStream_t st) {
   return group_upload_mds(mesh->group, st);
 }
 
+// The buffers of FP32 face geometry (once per mesh): split positions, split U and Lambda and the
+// per-vertex weights of the gradient; the per-face weights and gradients reuse facew and gface.
+cudaError_t mesh_ensure_geom32(ig_mesh* mesh, cudaStream_t st) {
+  cudaError_t e = mesh_ensure_mixed(mesh, st);
+  if (e != cudaSuccess) return e;
+  MeshDev& md = mesh->md;
+  if (md.vsplit) return cudaSuccess;
+  const size_t n = (size_t)mesh->n;
+  if ((e = mesh_alloc(mesh, &md.vsplit, 8 * n)) != cudaSuccess) return e;
+  if ((e = mesh_alloc(mesh, &md.usplit, 8 * n)) != cudaSuccess) return e;
+  if ((e = mesh_alloc(mesh, &md.lsplit, 8 * n)) != cudaSuccess) return e;
+  if ((e = mesh_alloc(mesh, &md.wv, n)) != cudaSuccess) return e;
+  mesh->group.host_mds[0] = md;
+  return group_upload_mds(mesh->group, st);
+}
+
+// Record the geometry mode of the next assembly in the mesh's descriptor (host and device copies).
+cudaError_t mesh_set_geom32(ig_mesh* mesh, int geom32, cudaStream_t st) {
+  if (mesh->md.geom32 == geom32) return cudaSuccess;
+  mesh->md.geom32 = geom32;
+  mesh->group.host_mds[0] = mesh->md;
+  return group_upload_mds(mesh->group, st);
+}
+
 }  // namespace ig
 
 // =============================================================================================
@@ -444,15 +468,16 @@ ig_status ig_mesh_upload(ig_ctx* ctx, const int32_t* F_dev, int64_t m, int64_t n
   md.nnz = nnz;
   // Solver tiles (whole warps, at least kBlock rows): the choice depends on n and the device only,
   // never on a batch.
-  // Mixed precision: 256..1024 rows; a mesh that fills the GPU gets a tile count that is a whole
-  // multiple of the resident CTA slots S of the solver kernels, so every launch ends in full waves.
+  // Mixed precision: 256..kMaxTileRows32 rows, one wave of tiles over the resident CTA slots S
+  // of the solver kernels where the mesh allows (a CTA takes its tile in passes of kTileRows
+  // rows and reduces once per tile, so few large tiles cost few barriers and few partial sums).
   auto choose_tiles = [ni](long S, int& tile_rows, int& ntiles) {
     if (S < 1) S = 1;
-    long waves = ((long)ni + S * kTileRows - 1) / (S * kTileRows);
+    long waves = ((long)ni + S * kMaxTileRows32 - 1) / (S * kMaxTileRows32);
     if (waves < 1) waves = 1;
     long rows = ((long)ni + S * waves - 1) / (S * waves);
     if (rows < kBlock) rows = kBlock;
-    if (rows > kTileRows) rows = kTileRows;
+    if (rows > kMaxTileRows32) rows = kMaxTileRows32;
     rows = (rows + 31) / 32 * 32;
     tile_rows = (int)rows;
     ntiles = (int)(((long)ni + rows - 1) / rows);
@@ -563,17 +588,19 @@ ig_status ig_assemble(ig_mesh* mesh, const double* V_dev, double t, int precisio
   ig_ctx* ctx = mesh->ctx;
   if (!V_dev) return bad_arg(ctx, "V is NULL");
   if (!(t >= 0.0) || !std::isfinite(t)) return bad_arg(ctx, "t must be finite and >= 0");
-  if (precision != IG_PRECISION_FP64 && precision != IG_PRECISION_MIXED) return bad_arg(ctx, "unknown precision");
+  if (precision != IG_PRECISION_FP64 && precision != IG_PRECISION_MIXED && precision != IG_PRECISION_MIXED_GEOM32)
+    return bad_arg(ctx, "unknown precision");
   DeviceGuard guard(ctx->device);
-  const int mixed = precision == IG_PRECISION_MIXED;
-  if (mixed) IG_CK(ctx, mesh_ensure_mixed(mesh, ctx->stream), "alloc");
+  if (precision == IG_PRECISION_MIXED) IG_CK(ctx, mesh_ensure_mixed(mesh, ctx->stream), "alloc");
+  if (precision == IG_PRECISION_MIXED_GEOM32) IG_CK(ctx, mesh_ensure_geom32(mesh, ctx->stream), "alloc");
+  IG_CK(ctx, mesh_set_geom32(mesh, precision == IG_PRECISION_MIXED_GEOM32 ? 1 : 0, ctx->stream), "upload");
   CallDev call{};
   call.V = V_dev;
   call.t = t;
   IG_CK(ctx, group_set_calls(mesh->group, &call, ctx->stream), "upload");
   IG_CK(ctx, cudaMemsetAsync(mesh->md.err, 0, sizeof(int), ctx->stream), "memset");
-  IG_CK(ctx, launch_assemble(mesh->group, mixed, ctx->stream), "assemble");
-  mesh->assembled = mixed ? 2 : 1;
+  IG_CK(ctx, launch_assemble(mesh->group, precision, ctx->stream), "assemble");
+  mesh->assembled = precision + 1;  // 1 FP64, 2 mixed, 3 mixed with FP32 geometry
   mesh->t = t;
   return IG_OK;
 }
@@ -622,7 +649,7 @@ ig_status ig_solve(ig_mesh* mesh, const double* B_dev, int k, double* U_dev, con
   auto io = std::make_unique<IoTable>();
   io->in[0] = B_dev;
   io->out[0] = U_dev;
-  IG_CK(ctx, group_solve(mesh->group, k, mesh->assembled == 2, *io, 1, o, ctx->stream), "solve");
+  IG_CK(ctx, group_solve(mesh->group, k, mesh->assembled >= 2, *io, 1, o, ctx->stream), "solve");
   if (!info) return IG_OK;
   IG_CK(ctx, group_true_residual(mesh->group, k, *io, 1, ctx->stream), "residual");
   return collect_info(mesh, k, info);
@@ -648,7 +675,7 @@ ig_status ig_adjoint(ig_mesh* mesh, const double* V_dev, const double* B_dev, in
   auto io = std::make_unique<IoTable>();
   io->in[0] = G_dev;
   io->out[0] = mesh->md.lam;
-  IG_CK(ctx, group_solve(mesh->group, k, mesh->assembled == 2, *io, 0, o, ctx->stream), "adjoint solve");
+  IG_CK(ctx, group_solve(mesh->group, k, mesh->assembled >= 2, *io, 0, o, ctx->stream), "adjoint solve");
   CallDev call{};
   call.V = V_dev;
   call.B = b_is_V ? V_dev : B_dev;
@@ -660,7 +687,7 @@ ig_status ig_adjoint(ig_mesh* mesh, const double* V_dev, const double* B_dev, in
   call.b_is_V = b_is_V ? 1 : 0;
   call.bstride = b_is_V ? 3 : k;
   IG_CK(ctx, group_set_calls(mesh->group, &call, ctx->stream), "upload");
-  IG_CK(ctx, launch_vjp(mesh->group, k, ctx->stream), "vjp");
+  IG_CK(ctx, launch_vjp(mesh->group, k, ctx->stream, 0, mesh->assembled == 3), "vjp");
   if (!info) return IG_OK;
   IG_CK(ctx, group_true_residual(mesh->group, k, *io, 0, ctx->stream), "residual");
   return collect_info(mesh, k, info);
@@ -682,7 +709,7 @@ ig_status ig_solve_begin(ig_mesh* mesh, const double* in_dev, int k, int rhs_mas
   auto io = std::make_unique<IoTable>();
   io->in[0] = in_dev;
   io->out[0] = nullptr;
-  IG_CK(ctx, group_begin(mesh->group, k, mesh->assembled == 2, *io, rhs_mass ? 1 : 0, o, ctx->stream),
+  IG_CK(ctx, group_begin(mesh->group, k, mesh->assembled >= 2, *io, rhs_mass ? 1 : 0, o, ctx->stream),
         "solve begin");
   return IG_OK;
 }
@@ -722,7 +749,7 @@ ig_status ig_vjp(ig_mesh* mesh, const double* V_dev, const double* B_dev, int b_
   call.b_is_V = b_is_V ? 1 : 0;
   call.bstride = b_is_V ? 3 : k;
   IG_CK(ctx, group_set_calls(mesh->group, &call, ctx->stream), "upload");
-  IG_CK(ctx, launch_vjp(mesh->group, k, ctx->stream), "vjp");
+  IG_CK(ctx, launch_vjp(mesh->group, k, ctx->stream, 0, mesh->assembled == 3), "vjp");
   return IG_OK;
 }
 
@@ -746,6 +773,8 @@ ig_status ig_fairing_step(ig_mesh* mesh, double* V_dev, const double* T_dev, dou
   ig_ctx* ctx = mesh->ctx;
   if (!V_dev || !T_dev) return bad_arg(ctx, "V and T must be non-NULL");
   if (!(eta >= 0.0) || !(eta < 1e300)) return bad_arg(ctx, "eta must be finite and >= 0");
+  if (precision != IG_PRECISION_FP64 && precision != IG_PRECISION_MIXED)
+    return bad_arg(ctx, "the fairing step runs in FP64 or mixed precision");
   const ig_solve_opts o = resolve_opts(opts);
   ig_status cs = check_opts(ctx, o);
   if (cs != IG_OK) return cs;
@@ -804,8 +833,8 @@ ig_status ig_eigs(ig_mesh* mesh, int k, int iters, double* U_dev, double* lambda
                   ig_solve_info* info) {
   if (!mesh) return IG_ERR_INVALID_ARG;
   ig_ctx* ctx = mesh->ctx;
-  if (!mesh->assembled) {
-    set_error(ctx, "eigs before assemble");
+  if (!mesh->assembled || mesh->assembled == 3) {
+    set_error(ctx, "eigs needs a mesh assembled in FP64 or mixed precision");
     return IG_ERR_STATE;
   }
   if (!U_dev) return bad_arg(ctx, "U must be non-NULL");
@@ -861,8 +890,8 @@ ig_status ig_eigs_vjp(ig_mesh* mesh, const double* V_dev, int k, int iters, cons
                       double* gV_dev, const ig_solve_opts* opts) {
   if (!mesh) return IG_ERR_INVALID_ARG;
   ig_ctx* ctx = mesh->ctx;
-  if (!mesh->assembled) {
-    set_error(ctx, "eigs_vjp before assemble");
+  if (!mesh->assembled || mesh->assembled == 3) {
+    set_error(ctx, "eigs_vjp needs a mesh assembled in FP64 or mixed precision");
     return IG_ERR_STATE;
   }
   if (!V_dev || !U_dev || !gU_dev || !gV_dev) return bad_arg(ctx, "V, U, gU and gV must be non-NULL");

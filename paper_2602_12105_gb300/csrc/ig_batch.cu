@@ -144,18 +144,20 @@ ig_status ig_batch_assemble(ig_batch* b, const double* const* V_dev, const doubl
   if (!b) return IG_ERR_INVALID_ARG;
   ig_ctx* ctx = b->ctx;
   if (!V_dev || !t) return bad(ctx, "V and t arrays are required");
-  if (precision != IG_PRECISION_FP64 && precision != IG_PRECISION_MIXED) return bad(ctx, "unknown precision");
+  if (precision != IG_PRECISION_FP64 && precision != IG_PRECISION_MIXED && precision != IG_PRECISION_MIXED_GEOM32)
+    return bad(ctx, "unknown precision");
   const int nm = (int)b->meshes.size();
   for (int i = 0; i < nm; ++i) {
     if (!V_dev[i]) return bad(ctx, "a V pointer is NULL");
     if (!(t[i] >= 0.0) || !std::isfinite(t[i])) return bad(ctx, "every t must be finite and >= 0");
   }
   BatchDevice guard(ctx->device);
-  const int mixed = precision == IG_PRECISION_MIXED;
   std::vector<CallDev> calls(nm);
   for (int i = 0; i < nm; ++i) {
     ig_mesh* m = b->meshes[i];
-    if (mixed) BT_CK(ctx, mesh_ensure_mixed(m, ctx->stream), "alloc");
+    if (precision == IG_PRECISION_MIXED) BT_CK(ctx, mesh_ensure_mixed(m, ctx->stream), "alloc");
+    if (precision == IG_PRECISION_MIXED_GEOM32) BT_CK(ctx, mesh_ensure_geom32(m, ctx->stream), "alloc");
+    BT_CK(ctx, mesh_set_geom32(m, precision == IG_PRECISION_MIXED_GEOM32 ? 1 : 0, ctx->stream), "upload");
     BT_CK(ctx, cudaMemsetAsync(m->md.err, 0, sizeof(int), ctx->stream), "memset");
     calls[i] = CallDev{};
     calls[i].V = V_dev[i];
@@ -163,9 +165,9 @@ ig_status ig_batch_assemble(ig_batch* b, const double* const* V_dev, const doubl
   }
   BT_CK(ctx, refresh(b, ctx->stream), "upload");
   BT_CK(ctx, group_set_calls(b->group, calls.data(), ctx->stream), "upload");
-  BT_CK(ctx, launch_assemble(b->group, mixed, ctx->stream), "batch assemble");
+  BT_CK(ctx, launch_assemble(b->group, precision, ctx->stream), "batch assemble");
   for (int i = 0; i < nm; ++i) {
-    b->meshes[i]->assembled = mixed ? 2 : 1;
+    b->meshes[i]->assembled = precision + 1;
     b->meshes[i]->t = t[i];
   }
   return IG_OK;
@@ -198,7 +200,7 @@ ig_status ig_batch_solve(ig_batch* b, const double* const* B_dev, int k, double*
     io->out[i] = U_dev[i];
   }
   BT_CK(ctx, refresh(b, ctx->stream), "upload");
-  BT_CK(ctx, group_solve(b->group, k, prec == 2, *io, 1, o, ctx->stream), "batch solve");
+  BT_CK(ctx, group_solve(b->group, k, prec >= 2, *io, 1, o, ctx->stream), "batch solve");
   if (!infos) return IG_OK;
   BT_CK(ctx, group_true_residual(b->group, k, *io, 1, ctx->stream), "residual");
   return batch_info(b, k, infos);
@@ -246,9 +248,9 @@ ig_status ig_batch_adjoint(ig_batch* b, const double* const* V_dev, const double
     c.bstride = b_is_V ? 3 : k;
   }
   BT_CK(ctx, refresh(b, ctx->stream), "upload");
-  BT_CK(ctx, group_solve(b->group, k, prec == 2, *io, 0, o, ctx->stream), "batch adjoint solve");
+  BT_CK(ctx, group_solve(b->group, k, prec >= 2, *io, 0, o, ctx->stream), "batch adjoint solve");
   BT_CK(ctx, group_set_calls(b->group, calls.data(), ctx->stream), "upload");
-  BT_CK(ctx, launch_vjp(b->group, k, ctx->stream), "batch vjp");
+  BT_CK(ctx, launch_vjp(b->group, k, ctx->stream, 0, prec == 3), "batch vjp");
   if (!infos) return IG_OK;
   BT_CK(ctx, group_true_residual(b->group, k, *io, 0, ctx->stream), "residual");
   return batch_info(b, k, infos);
@@ -269,7 +271,7 @@ ig_status ig_batch_iterate(ig_batch* b, int k, int max_iters, int* done_host) {
   }
   BatchDevice guard(ctx->device);
   BT_CK(ctx, refresh(b, ctx->stream), "upload");
-  BT_CK(ctx, group_iterate(b->group, k, prec == 2, max_iters, done_host, ctx->stream), "batch iterate");
+  BT_CK(ctx, group_iterate(b->group, k, prec >= 2, max_iters, done_host, ctx->stream), "batch iterate");
   return IG_OK;
 }
 

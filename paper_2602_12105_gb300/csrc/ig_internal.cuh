@@ -34,7 +34,8 @@ namespace ig {
 
 constexpr int kBlock = 256;          // threads per CTA of every row- or face-parallel kernel
 constexpr int kRowsPerThread = 4;    // rows per thread in the mixed-precision solver kernels
-constexpr int kTileRows = kBlock * kRowsPerThread;
+constexpr int kTileRows = kBlock * kRowsPerThread;  // one pass of the mixed-precision solver kernels
+constexpr int kMaxTileRows32 = 64 * kTileRows;      // the largest mixed-precision tile (passes of kTileRows)
 constexpr int kMaxPasses64 = 8;      // FP64 solver tiles: at most 8 passes of kBlock rows
 constexpr int kTileRows64 = kBlock * kMaxPasses64;
 constexpr int kMaxK = 4;
@@ -287,6 +288,8 @@ cudaError_t group_solve(Group& g, int k, int mixed, const IoTable& io, int rhs_m
                         cudaStream_t st);
 cudaError_t group_true_residual(Group& g, int k, const IoTable& io, int rhs_mass, cudaStream_t st);
 cudaError_t mesh_ensure_mixed(ig_mesh* mesh, cudaStream_t st);
+cudaError_t mesh_ensure_geom32(ig_mesh* mesh, cudaStream_t st);
+cudaError_t mesh_set_geom32(ig_mesh* mesh, int geom32, cudaStream_t st);
 int solver_blocks_per_sm();        // ig_pcg.cu: min resident CTAs per SM of the FP64 loop kernels
 int solver_blocks_per_sm_mixed();  // ig_pcg_mixed.cu: same for the mixed-precision loop kernels
 cudaError_t group_solve_mixed(Group& g, int k, const IoTable& io, int rhs_mass, const ig_solve_opts& o,
@@ -309,7 +312,7 @@ struct ig_mesh {
   ig_ctx* ctx = nullptr;
   int64_t n = 0, m = 0, nnz = 0;
   int64_t bytes = 0;
-  int assembled = 0;        // 0 none, 1 FP64, 2 mixed
+  int assembled = 0;        // 0 none, 1 FP64, 2 mixed, 3 mixed with FP32 face geometry
   double t = 0.0;
   int ws_k = 0;             // solver vectors allocated for this many columns
   ig::MeshDev md{};         // host copy of the device pointers

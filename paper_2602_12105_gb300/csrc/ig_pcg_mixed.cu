@@ -26,6 +26,29 @@ struct KPm {
   static constexpr int v = (K == 3) ? 4 : K;
 };
 
+// A tile of the mixed-precision kernels is one wave's share of a mesh (up to kMaxTileRows32 rows),
+// taken in passes of kTileRows rows (kRowsPerThread per thread). Each thread adds its per-pass
+// FP32 partial sums into a running sum with the rounding error of every addition carried along
+// (compensated summation), so a tile of many passes keeps the accuracy of a short sum; the tile's
+// sums then go through the usual warp and tile reduction (FP64 across warps and tiles).
+template <int NV>
+struct CompSum {
+  float s[NV], c[NV];
+  __device__ __forceinline__ CompSum() {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) s[i] = c[i] = 0.f;
+  }
+  __device__ __forceinline__ void add(const float (&x)[NV]) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const float y = x[i] - c[i];
+      const float t = s[i] + y;
+      c[i] = (t - s[i]) - y;
+      s[i] = t;
+    }
+  }
+};
+
 // ------------------------------------------------------------------------------- bookkeeping
 __device__ __noinline__ void finish_init_mixed(SolveScal* s, int k, const double* acc, double tol, double inner_tol,
                                                int max_iter, int max_refine) {
@@ -186,18 +209,20 @@ __global__ void __launch_bounds__(kBlock) init_mixed_kernel(const MeshDev* __res
   double acc[K];
 #pragma unroll
   for (int c = 0; c < K; ++c) acc[c] = 0.0;
+  for (long base = t0; base < t1; base += kTileRows) {
 #pragma unroll
-  for (int rr = 0; rr < kRowsPerThread; ++rr) {
-    const long row = t0 + rr * kBlock + threadIdx.x;
-    if (row < t1) {
-      const double mass = rhs_mass ? md.M[row] : 1.0;
+    for (int rr = 0; rr < kRowsPerThread; ++rr) {
+      const long row = base + rr * kBlock + threadIdx.x;
+      if (row < t1) {
+        const double mass = rhs_mass ? md.M[row] : 1.0;
 #pragma unroll
-      for (int c = 0; c < K; ++c) {
-        const double b = rhs_mass ? mass * src[row * K + c] : src[row * K + c];
-        md.rhs[c * nn + row] = b;
-        md.r[c * nn + row] = b;
-        md.x[c * nn + row] = 0.0;
-        acc[c] = fma(b, b, acc[c]);
+        for (int c = 0; c < K; ++c) {
+          const double b = rhs_mass ? mass * src[row * K + c] : src[row * K + c];
+          md.rhs[c * nn + row] = b;
+          md.r[c * nn + row] = b;
+          md.x[c * nn + row] = 0.0;
+          acc[c] = fma(b, b, acc[c]);
+        }
       }
     }
   }
@@ -217,25 +242,29 @@ __global__ void __launch_bounds__(kBlock, 4) spmv_mixed_kernel(const MeshDev* __
         const float* __restrict__ A = md.A32;
         const float* __restrict__ p = md.p32;
         float* __restrict__ q32 = md.q32;
-        float pq[K];
+        CompSum<K> sum;
+        for (long base = t0; base < t1; base += kTileRows) {
+          float pq[K];
 #pragma unroll
-        for (int c = 0; c < K; ++c) pq[c] = 0.f;
+          for (int c = 0; c < K; ++c) pq[c] = 0.f;
 #pragma unroll
-        for (int rr = 0; rr < kRowsPerThread; ++rr) {
-          const long row = t0 + rr * kBlock + threadIdx.x;
-          if (row < t1) {
-            float q[K];
-            row_product<K>(md, A, row, GatherP32<K>{p}, q);
-            float pi[K];
-            load_row32<K>(p, row, pi);
+          for (int rr = 0; rr < kRowsPerThread; ++rr) {
+            const long row = base + rr * kBlock + threadIdx.x;
+            if (row < t1) {
+              float q[K];
+              row_product<K>(md, A, row, GatherP32<K>{p}, q);
+              float pi[K];
+              load_row32<K>(p, row, pi);
 #pragma unroll
-            for (int c = 0; c < K; ++c) {
-              q32[c * nn + row] = q[c];
-              pq[c] = fmaf(pi[c], q[c], pq[c]);
+              for (int c = 0; c < K; ++c) {
+                q32[c * nn + row] = q[c];
+                pq[c] = fmaf(pi[c], q[c], pq[c]);
+              }
             }
           }
+          sum.add(pq);
         }
-        tile_reduce<K>(pq, red, out);
+        tile_reduce<K>(sum.s, red, out);
       },
       [](const MeshDev& md, const SolveScal& cur, const double* v) { finish_spmv(md.s, cur, K, v); });
 }
@@ -258,18 +287,20 @@ __global__ void __launch_bounds__(kBlock) resid_mixed_kernel(const MeshDev* __re
         double acc[K];
 #pragma unroll
         for (int c = 0; c < K; ++c) acc[c] = 0.0;
+        for (long base = t0; base < t1; base += kTileRows) {
 #pragma unroll
-        for (int rr = 0; rr < kRowsPerThread; ++rr) {
-          const long row = t0 + rr * kBlock + threadIdx.x;
-          if (row < t1) {
-            double ax[K];
-            if (geom32) row_product<K>(md, md.A32, row, GatherSoA64<K>{x, nn}, ax);
-            else row_product<K>(md, md.A, row, GatherSoA64<K>{x, nn}, ax);
+          for (int rr = 0; rr < kRowsPerThread; ++rr) {
+            const long row = base + rr * kBlock + threadIdx.x;
+            if (row < t1) {
+              double ax[K];
+              if (geom32) row_product<K>(md, md.A32, row, GatherSoA64<K>{x, nn}, ax);
+              else row_product<K>(md, md.A, row, GatherSoA64<K>{x, nn}, ax);
 #pragma unroll
-            for (int c = 0; c < K; ++c) {
-              const double res = md.rhs[c * nn + row] - ax[c];
-              md.r[c * nn + row] = res;
-              acc[c] = fma(res, res, acc[c]);
+              for (int c = 0; c < K; ++c) {
+                const double res = md.rhs[c * nn + row] - ax[c];
+                md.r[c * nn + row] = res;
+                acc[c] = fma(res, res, acc[c]);
+              }
             }
           }
         }
@@ -291,9 +322,7 @@ __global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* 
         const long nn = md.n;
         const long t0 = (long)tile * md.tile_rows32;
         const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
-        float acc[2 * K];
-#pragma unroll
-        for (int i = 0; i < 2 * K; ++i) acc[i] = 0.f;
+        CompSum<2 * K> sum;
         const float* __restrict__ D32 = md.Dinv32;
         float* __restrict__ x32 = md.x32;
         float* __restrict__ r32 = md.r32;
@@ -301,39 +330,47 @@ __global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* 
           const float* __restrict__ p32 = md.p32;
           const float* __restrict__ q32 = md.q32;
           const int n32 = md.n;
+          float alpha[K];
+#pragma unroll
+          for (int c = 0; c < K; ++c) alpha[c] = (float)tc.sn.alpha[c];
           constexpr int RB = 2;
+          for (long base = t0; base < t1; base += kTileRows) {
+            float acc[2 * K];
 #pragma unroll
-          for (int r0 = 0; r0 < kRowsPerThread; r0 += RB) {
-            float d[RB], pi[RB][K], xs[RB][K], qs[RB][K], rs[RB][K];
+            for (int i = 0; i < 2 * K; ++i) acc[i] = 0.f;
 #pragma unroll
-            for (int u = 0; u < RB; ++u) {
-              const int row = (int)t0 + (r0 + u) * kBlock + threadIdx.x;
-              if (row < (int)t1) {
-                d[u] = D32[row];
-                load_row32<K>(p32, row, pi[u]);
+            for (int r0 = 0; r0 < kRowsPerThread; r0 += RB) {
+              float d[RB], pi[RB][K], xs[RB][K], qs[RB][K], rs[RB][K];
 #pragma unroll
-                for (int c = 0; c < K; ++c) {
-                  xs[u][c] = x32[(long)c * n32 + row];
-                  qs[u][c] = q32[(long)c * n32 + row];
-                  rs[u][c] = r32[(long)c * n32 + row];
+              for (int u = 0; u < RB; ++u) {
+                const int row = (int)base + (r0 + u) * kBlock + threadIdx.x;
+                if (row < (int)t1) {
+                  d[u] = D32[row];
+                  load_row32<K>(p32, row, pi[u]);
+#pragma unroll
+                  for (int c = 0; c < K; ++c) {
+                    xs[u][c] = x32[(long)c * n32 + row];
+                    qs[u][c] = q32[(long)c * n32 + row];
+                    rs[u][c] = r32[(long)c * n32 + row];
+                  }
+                }
+              }
+#pragma unroll
+              for (int u = 0; u < RB; ++u) {
+                const int row = (int)base + (r0 + u) * kBlock + threadIdx.x;
+                if (row < (int)t1) {
+#pragma unroll
+                  for (int c = 0; c < K; ++c) {
+                    const float rv = fmaf(-alpha[c], qs[u][c], rs[u][c]);
+                    x32[(long)c * n32 + row] = fmaf(alpha[c], pi[u][c], xs[u][c]);
+                    r32[(long)c * n32 + row] = rv;
+                    acc[c] = fmaf(rv, d[u] * rv, acc[c]);
+                    acc[K + c] = fmaf(rv, rv, acc[K + c]);
+                  }
                 }
               }
             }
-#pragma unroll
-            for (int u = 0; u < RB; ++u) {
-              const int row = (int)t0 + (r0 + u) * kBlock + threadIdx.x;
-              if (row < (int)t1) {
-#pragma unroll
-                for (int c = 0; c < K; ++c) {
-                  const float a = (float)tc.sn.alpha[c];
-                  const float rv = fmaf(-a, qs[u][c], rs[u][c]);
-                  x32[(long)c * n32 + row] = fmaf(a, pi[u][c], xs[u][c]);
-                  r32[(long)c * n32 + row] = rv;
-                  acc[c] = fmaf(rv, d[u] * rv, acc[c]);
-                  acc[K + c] = fmaf(rv, rv, acc[K + c]);
-                }
-              }
-            }
+            sum.add(acc);
           }
         } else {
           // Restart: r32 = r64 / ||r64|| for columns still above tol, d = 0
@@ -345,23 +382,29 @@ __global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* 
             inv[c] = 1.0 / tc.sn.scale[c];
           }
           const double* __restrict__ r64 = md.r;
+          for (long base = t0; base < t1; base += kTileRows) {
+            float acc[2 * K];
 #pragma unroll
-          for (int rr = 0; rr < kRowsPerThread; ++rr) {
-            const long row = t0 + rr * kBlock + threadIdx.x;
-            if (row < t1) {
-              const float dinv = D32[row];
+            for (int i = 0; i < 2 * K; ++i) acc[i] = 0.f;
 #pragma unroll
-              for (int c = 0; c < K; ++c) {
-                const float rv = act[c] ? (float)(r64[c * nn + row] * inv[c]) : 0.f;
-                r32[c * nn + row] = rv;
-                x32[c * nn + row] = 0.f;
-                acc[c] = fmaf(rv, dinv * rv, acc[c]);
-                acc[K + c] = fmaf(rv, rv, acc[K + c]);
+            for (int rr = 0; rr < kRowsPerThread; ++rr) {
+              const long row = base + rr * kBlock + threadIdx.x;
+              if (row < t1) {
+                const float dinv = D32[row];
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                  const float rv = act[c] ? (float)(r64[c * nn + row] * inv[c]) : 0.f;
+                  r32[c * nn + row] = rv;
+                  x32[c * nn + row] = 0.f;
+                  acc[c] = fmaf(rv, dinv * rv, acc[c]);
+                  acc[K + c] = fmaf(rv, rv, acc[K + c]);
+                }
               }
             }
+            sum.add(acc);
           }
         }
-        tile_reduce<2 * K>(acc, red, out);
+        tile_reduce<2 * K>(sum.s, red, out);
       },
       [](const MeshDev& md, const SolveScal& cur, const double* v) {
         if (cur.phase == kPhaseInner) finish_update_mixed(md.s, cur, K, v);
@@ -389,24 +432,26 @@ __global__ void __launch_bounds__(kBlock, 4) pupdate_mixed_kernel(const MeshDev*
                       const float* __restrict__ r32 = md.r32;
                       float* __restrict__ p32 = md.p32;
                       constexpr int R = kRowsPerThread;
-                      float d[R], pi[R][K], rs[R][K];
+                      for (long base = t0; base < t1; base += kTileRows) {
+                        float d[R], pi[R][K], rs[R][K];
 #pragma unroll
-                      for (int u = 0; u < R; ++u) {
-                        const long row = t0 + u * kBlock + threadIdx.x;
-                        if (row < t1) {
-                          d[u] = D32[row];
-                          load_row32<K>(p32, row, pi[u]);
+                        for (int u = 0; u < R; ++u) {
+                          const long row = base + u * kBlock + threadIdx.x;
+                          if (row < t1) {
+                            d[u] = D32[row];
+                            load_row32<K>(p32, row, pi[u]);
 #pragma unroll
-                          for (int c = 0; c < K; ++c) rs[u][c] = r32[c * nn + row];
+                            for (int c = 0; c < K; ++c) rs[u][c] = r32[c * nn + row];
+                          }
                         }
-                      }
 #pragma unroll
-                      for (int u = 0; u < R; ++u) {
-                        const long row = t0 + u * kBlock + threadIdx.x;
-                        if (row < t1) {
+                        for (int u = 0; u < R; ++u) {
+                          const long row = base + u * kBlock + threadIdx.x;
+                          if (row < t1) {
 #pragma unroll
-                          for (int c = 0; c < K; ++c)
-                            p32[row * KPm<K>::v + c] = fmaf(beta[c], pi[u][c], d[u] * rs[u][c]);
+                            for (int c = 0; c < K; ++c)
+                              p32[row * KPm<K>::v + c] = fmaf(beta[c], pi[u][c], d[u] * rs[u][c]);
+                          }
                         }
                       }
                     } else {
@@ -415,13 +460,15 @@ __global__ void __launch_bounds__(kBlock, 4) pupdate_mixed_kernel(const MeshDev*
                       for (int c = 0; c < K; ++c) sc[c] = tc.sn.scale[c];
                       const float* __restrict__ x32 = md.x32;
                       double* __restrict__ x = md.x;
+                      for (long base = t0; base < t1; base += kTileRows) {
 #pragma unroll
-                      for (int rr = 0; rr < kRowsPerThread; ++rr) {
-                        const long row = t0 + rr * kBlock + threadIdx.x;
-                        if (row < t1) {
+                        for (int rr = 0; rr < kRowsPerThread; ++rr) {
+                          const long row = base + rr * kBlock + threadIdx.x;
+                          if (row < t1) {
 #pragma unroll
-                          for (int c = 0; c < K; ++c)
-                            x[c * nn + row] = fma(sc[c], (double)x32[c * nn + row], x[c * nn + row]);
+                            for (int c = 0; c < K; ++c)
+                              x[c * nn + row] = fma(sc[c], (double)x32[c * nn + row], x[c * nn + row]);
+                          }
                         }
                       }
                     }

@@ -94,3 +94,85 @@ def test_mixed_refinement_cap(api):
     assert info["status"] == N.IG_ERR_NOT_CONVERGED and info["refinements"] == 1
     # the best iterate is still written and is a good approximation
     assert max(info["true_rel_residual"]) < 1e-3
+
+
+# ------------------------------------------------------------------------------- FP32 face geometry
+# The mixed32 mode computes cotangents, areas and the per-face gradient in FP32 (FP64 for faces
+# whose smallest corner has sin < 1e-2) and solves the FP32 operator A32 exactly (FP64 refinement).
+# Its error against the FP64 oracle is that of the operator's FP32 rounding:
+#   - each weight t cot / 2 and area / 3 is a few FP32 operations on edges that are exact to one
+#     FP32 rounding (hi/lo split positions), so within about 4 u = 2.4e-7 of its value (u = 2^-24);
+#     a row of A sums up to ~12 of them, so A and M are held to 1e-6 of max |A| and max |M|;
+#   - U solves A32 U = M32 B, so its relative error is at most cond(A) times that of the operator;
+#     with t small against the squared mesh spacing, cond(A) is a few, and U is held to 1e-6;
+#   - dl/dV is a sum of per-face FP32 terms built from the same split data and U, Lambda, so it is
+#     held to 2e-6 (relative to max |dl/dV|), and dl/dt to 1e-6.
+# The translated meshes check that positions far from the origin keep that accuracy (the split
+# takes differences of neighbouring vertices exactly; a plain FP32 copy of the positions would
+# lose about |x| / |edge| ulps there).
+R1_CASES = ["tetra", "octa", "ico3", "grid61x53", "planar_jitter", "ico5", "ico5_shifted", "grid61x53_shifted"]
+
+
+@pytest.mark.parametrize("name", R1_CASES)
+def test_fp32_geometry_matches_oracle(api, name):
+    V, F, t, B, T = case(name.replace("_shifted", ""), seed=21)
+    if name.endswith("_shifted"):
+        V = V + np.array([1000.0, -2000.0, 500.0])
+    mesh = api.Mesh(_t(F, torch.int32), V.shape[0])
+    mesh.assemble(_t(V), t, precision="mixed32")
+    A, M = mesh.operator()
+    o_rowptr, o_col, o_A, o_L, o_M = oracle.operator(V, F, t)
+    assert_close(A.cpu().numpy(), o_A, 1e-6, "A32")
+    assert_close(M.cpu().numpy(), o_M, 1e-6, "M")
+    opts = api.make_opts(rel_tol=1e-13)
+    U, info = mesh.solve(_t(B), opts=opts, info=True)
+    assert info["status"] == 0, info
+    # solved exactly for its own operator: the FP64 residual under A32 (as ig_operator returns it)
+    R = M.cpu().numpy()[:, None] * B
+    res = R - oracle.spmv(o_rowptr, o_col, A.cpu().numpy(), U.cpu().numpy())
+    assert (np.linalg.norm(res, axis=0) / np.linalg.norm(R, axis=0)).max() <= 1e-13 * (1 + 1e-3)
+    ref = oracle.forward_adjoint(V, F, B, t, T, False, tol=1e-14)
+    assert_close(U.cpu().numpy(), ref["U"], 1e-6, "U")
+    gV, gB, gt, ainfo = mesh.adjoint(_t(V), _t(B), False, U, U - _t(T), want_gB=True, want_gt=True, opts=opts,
+                                     info=True)
+    assert ainfo["status"] == 0, ainfo
+    assert_close(gV.cpu().numpy(), ref["gV"], 2e-6, "dl/dV")
+    assert_close(gB.cpu().numpy(), ref["gB"], 1e-6, "dl/dB")
+    assert abs(gt.item() - ref["gt"]) <= 1e-6 * abs(ref["gt"])
+
+
+def test_fp32_geometry_symmetric_operator_and_batch_bits(api):
+    """A32 is exactly symmetric (each edge's two weights are added in the same order by both of
+    its rows), and a mesh gives the same bits alone and inside a batch in this mode too."""
+    V, F, t, B, T = case("ico5", seed=22)
+    n = V.shape[0]
+    mesh = api.Mesh(_t(F, torch.int32), n)
+    mesh.assemble(_t(V), t, precision="mixed32")
+    A, M = mesh.operator()
+    rowptr, col = mesh.pattern()
+    rp, cl, a = rowptr.cpu().numpy(), col.cpu().numpy(), A.cpu().numpy()
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    vals = dict(zip(zip(rows.tolist(), cl.tolist()), a.tolist()))
+    assert all(vals[(j, i)] == v for (i, j), v in vals.items())
+    U1 = mesh.solve(_t(B))
+    gV1, _, _ = mesh.adjoint(_t(V), _t(B), False, U1, U1 - _t(T))
+    V2, F2, t2, B2, T2 = case("grid61x53", seed=23)
+    other = api.Mesh(_t(F2, torch.int32), V2.shape[0])
+    batch = api.Batch([other, mesh])
+    batch.assemble([_t(V2), _t(V)], [t2, t], precision="mixed32")
+    Us = batch.solve([_t(B2), _t(B)])
+    gVs, _, _ = batch.adjoint([_t(V2), _t(V)], [_t(B2), _t(B)], False, Us, [Us[0] - _t(T2), Us[1] - _t(T)])
+    assert torch.equal(Us[1], U1) and torch.equal(gVs[1], gV1)
+
+
+def test_fp32_geometry_sliver_faces_take_the_fp64_path(api):
+    """On the sliver mesh (a corner with sin = 2e-4, about 0.01 degrees) the weights of the sliver faces come
+    from the FP64 path: the FP32 operator is within FP32 rounding (6e-8) of the FP64 one, where
+    FP32 arithmetic on that face would lose a factor of about 1 / sin(theta) = 5e3 in accuracy."""
+    V, F, t, B, T = case("sliver")
+    mesh = api.Mesh(_t(F, torch.int32), V.shape[0])
+    mesh.assemble(_t(V), t, precision="mixed32")
+    A, M = mesh.operator()
+    o_rowptr, o_col, o_A, o_L, o_M = oracle.operator(V, F, t)
+    assert_close(A.cpu().numpy(), o_A, 2e-7, "A32 with slivers")
+    assert_close(M.cpu().numpy(), o_M, 2e-7, "M with slivers")
