@@ -143,6 +143,18 @@ ig_status ig_mesh_pattern(ig_mesh* mesh, int32_t* rowptr_dev, int32_t* col_dev);
  * Errors: IG_ERR_INVALID_ARG (t < 0 or not finite, bad precision), IG_ERR_OOM, IG_ERR_CUDA. */
 ig_status ig_assemble(ig_mesh* mesh, const double* V_dev, double t, int precision);
 
+/* Cotangent clamp: with enable != 0, every corner's cotangent enters L as max(cot, clamp_min) --
+ * the cotangent weights with a minimum (clamp_min) of the paper's §4 ARAP listing, applied per
+ * corner before the two corners of an edge are added -- and a clamped corner (cot < clamp_min)
+ * adds nothing to dl/dV (the clamp is constant there), while dl/dt uses clamp_min for it. With
+ * clamp_min >= 0 every off-diagonal entry of L is <= -clamp_min / 2. enable = 0 restores the
+ * plain cotangents. It applies to every later assembly of this mesh, in every precision, and to
+ * the gradients of those assemblies; the mesh must be assembled again after the call
+ * (IG_ERR_STATE otherwise). The geodesic calls (ig_rgd_*), whose identity L = D G needs the plain
+ * cotangents, return IG_ERR_STATE on a mesh with the clamp on.
+ * Errors: IG_ERR_INVALID_ARG (NULL mesh, clamp_min not finite). */
+ig_status ig_mesh_set_cot_clamp(ig_mesh* mesh, int enable, double clamp_min);
+
 /* Synchronise and return the first error the device recorded for this mesh since upload
  * (assembly or solve), or IG_OK. */
 ig_status ig_check(ig_mesh* mesh);
@@ -346,13 +358,17 @@ ig_status ig_rgd_u_step_vjp(ig_mesh* mesh, const double* V_dev, const int32_t* s
  * residuals after every round (one synchronisation per round); with neither, exactly max_rounds
  * rounds run without synchronising.
  * y_dev and z_dev [m][3]: the start (e.g. zeros) on entry, the last iterates on return. u_dev [n]:
- * the last u. stats_host (may be NULL; synchronises): 4 doubles, the rounds run, the primal and
- * dual residuals of the last round, and the final rho. rho > 0, beta >= 0, beta_k in [0, 2]
- * (over-relaxation), max_rounds >= 1, tol >= 0. The operator is built once (as in ig_rgd_u_step)
- * and each round is one Laplacian solve to opts->rel_tol; the mesh must be assembled again before
- * other solves. Solver statuses of the rounds are not reported (call ig_rgd_u_step with info on
- * the final y and z to check the last solve).
- * Errors: as ig_rgd_u_step, and IG_ERR_INVALID_ARG for max_rounds, rho, beta_k or tol out of range. */
+ * the last u. stats_host (may be NULL): 5 doubles, the rounds run, the primal and dual residuals
+ * of the last round, the final rho, and the rounds that needed no solve (below). rho > 0,
+ * beta >= 0, beta_k in [0, 2] (over-relaxation), max_rounds >= 1, tol >= 0. The operator is built
+ * once (as in ig_rgd_u_step); each round after the first warm-starts its Laplacian solve from the
+ * previous round's u (it solves A d = b - A u for the correction, to the tolerance that leaves
+ * |b - A (u + d)| <= opts->rel_tol |b|, the criterion of a cold solve, and skips the solve when u
+ * already meets it), which reads one scalar back per round (the call synchronises every round).
+ * The mesh must be assembled again before other solves.
+ * Errors: as ig_rgd_u_step, and IG_ERR_INVALID_ARG for max_rounds, rho, beta_k or tol out of
+ * range. IG_ERR_NOT_CONVERGED / IG_ERR_NONFINITE when a round's solve ended so (the worst over the
+ * rounds); the rounds still run to the end and every output is written. */
 ig_status ig_rgd_admm(ig_mesh* mesh, const double* V_dev, const int32_t* sources_host, int nsrc, double rho, double beta,
                       double beta_k, int max_rounds, double tol, int adapt_rho, double* u_dev, double* y_dev,
                       double* z_dev, double* stats_host, const ig_solve_opts* opts);
@@ -412,10 +428,13 @@ ig_status ig_rgd_admm_vjp(ig_mesh* mesh, const double* V_dev, const int32_t* sou
  * overlap on the GPU -- on different streams or from different host threads -- race on the
  * array and give wrong results.
  *
- * Errors: IG_ERR_INVALID_ARG for a NULL pointer, n > IG_NOALLOC_MAX_ROWS, nnz < n, k outside
- * [1, 4], overlapping B and U or bad options, and -- with or without info -- for an operator
- * with a missing or non-positive (or non-finite) diagonal entry, found on the device (the
- * solution is then meaningless); IG_ERR_CUDA for a failed launch; with info,
+ * Before solving, a set-up kernel checks the caller's pattern on the device (the call reads the
+ * result back and returns without solving, U untouched, when it fails):
+ * IG_ERR_INDEX_OUT_OF_RANGE for a row range outside [0, nnz) or a column outside [0, n);
+ * IG_ERR_INVALID_ARG for a missing or non-positive (or non-finite) diagonal entry. These are
+ * reported with or without info (info->status carries them too).
+ * Other errors: IG_ERR_INVALID_ARG for a NULL pointer, n > IG_NOALLOC_MAX_ROWS, nnz < n, k
+ * outside [1, 4], overlapping B and U or bad options; IG_ERR_CUDA for a failed launch; with info,
  * IG_ERR_NOT_CONVERGED / IG_ERR_NONFINITE as for ig_solve. */
 ig_status ig_solve_csr_noalloc(const int32_t* rowptr_dev, const int32_t* col_dev, const double* Aval_dev,
                                const double* M_dev, int64_t n, int64_t nnz, const double* B_dev, int k,

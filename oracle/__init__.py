@@ -60,6 +60,9 @@ def lib():
             L.orc_dense_cholesky_solve.argtypes = [i64, vp, vp, vp, i32, vp, vp]
             L.orc_pcg_solve.argtypes = [i64, vp, vp, vp, i32, vp, vp, dbl, i32, vp, vp]
             L.orc_vjp.argtypes = [i64, vp, i64, vp, dbl, i32, vp, vp, vp, i32, vp, vp, vp]
+            L.orc_laplacian_csr_clamp.argtypes = [i64, vp, i64, vp, dbl, vp, vp, vp, i64]
+            L.orc_laplacian_csr_clamp.restype = i64
+            L.orc_vjp_clamp.argtypes = [i64, vp, i64, vp, dbl, i32, vp, vp, vp, i32, dbl, vp, vp, vp]
             L.orc_mass_vjp.argtypes = [i64, vp, i64, vp, vp, vp]
             _lib = L
     return _lib
@@ -93,15 +96,20 @@ def face_geometry(V, F):
     return cot, area
 
 
-def laplacian(V, F):
-    """Cotangent Laplacian (PSD convention) as CSR: (rowptr int64[n+1], col int32, val f64)."""
+def laplacian(V, F, clamp_min=None):
+    """Cotangent Laplacian (PSD convention) as CSR: (rowptr int64[n+1], col int32, val f64).
+    With clamp_min, every corner's cotangent is clamped from below first (the cotangent weights
+    with a minimum of the §4 ARAP listing, read per corner)."""
     V, F = _f64(V), _i32(F)
     n, m = V.shape[0], F.shape[0]
     cap = n + 6 * m
     rowptr = np.empty(n + 1, dtype=np.int64)
     col = np.empty(cap, dtype=np.int32)
     val = np.empty(cap)
-    nnz = lib().orc_laplacian_csr(n, _p(V), m, _p(F), _p(rowptr), _p(col), _p(val), cap)
+    if clamp_min is None:
+        nnz = lib().orc_laplacian_csr(n, _p(V), m, _p(F), _p(rowptr), _p(col), _p(val), cap)
+    else:
+        nnz = lib().orc_laplacian_csr_clamp(n, _p(V), m, _p(F), float(clamp_min), _p(rowptr), _p(col), _p(val), cap)
     if nnz < 0:
         raise OracleError(-nnz, "laplacian_csr")
     return rowptr, col[:nnz].copy(), val[:nnz].copy()
@@ -117,9 +125,9 @@ def mass(V, F):
     return M
 
 
-def operator(V, F, t):
+def operator(V, F, t, clamp_min=None):
     """A = M + t L on L's pattern. Returns (rowptr, col, Aval, Lval, M)."""
-    rowptr, col, Lval = laplacian(V, F)
+    rowptr, col, Lval = laplacian(V, F, clamp_min)
     M = mass(V, F)
     Aval = np.empty_like(Lval)
     lib().orc_operator(M.shape[0], _p(rowptr), _p(col), _p(Lval), _p(M), float(t), _p(Aval))
@@ -169,31 +177,37 @@ def solve(rowptr, col, Aval, R, tol=1e-14, method="auto", max_iter=100000):
     return X
 
 
-def vjp(V, F, t, U, Lam, B, b_is_V):
-    """Closed-form per-face gradient of the loss w.r.t. V (see orc_vjp). Returns (gV, gB, gt)."""
+def vjp(V, F, t, U, Lam, B, b_is_V, clamp_min=None):
+    """Closed-form per-face gradient of the loss w.r.t. V (see orc_vjp; with clamp_min, of the
+    step assembled from clamped cotangents, orc_vjp_clamp). Returns (gV, gB, gt)."""
     V, F, U, Lam = _f64(V), _i32(F), _f64(U), _f64(Lam)
     n, k = U.shape
     Bc = None if b_is_V else _f64(B)
     gV = np.empty((n, 3))
     gB = None if b_is_V else np.empty((n, k))
     gt = ctypes.c_double(0.0)
-    st = lib().orc_vjp(n, _p(V), F.shape[0], _p(F), float(t), k, _p(U), _p(Lam), _p(Bc), int(bool(b_is_V)),
-                       _p(gV), _p(gB), ctypes.byref(gt))
+    if clamp_min is None:
+        st = lib().orc_vjp(n, _p(V), F.shape[0], _p(F), float(t), k, _p(U), _p(Lam), _p(Bc), int(bool(b_is_V)),
+                           _p(gV), _p(gB), ctypes.byref(gt))
+    else:
+        st = lib().orc_vjp_clamp(n, _p(V), F.shape[0], _p(F), float(t), k, _p(U), _p(Lam), _p(Bc),
+                                 int(bool(b_is_V)), float(clamp_min), _p(gV), _p(gB), ctypes.byref(gt))
     if st:
         raise OracleError(st, "vjp")
     return gV, gB, gt.value
 
 
-def forward_adjoint(V, F, B, t, T, b_is_V, tol=1e-14, method="auto"):
+def forward_adjoint(V, F, B, t, T, b_is_V, tol=1e-14, method="auto", clamp_min=None):
     """The whole path for loss l = 0.5 ||U - T||^2: assemble, solve A U = M B, adjoint
-    A Lambda = U - T, gradient. Returns a dict with U, Lam, gV, gB, gt, loss and the operator."""
-    rowptr, col, Aval, Lval, M = operator(V, F, t)
+    A Lambda = U - T, gradient. Returns a dict with U, Lam, gV, gB, gt, loss and the operator.
+    clamp_min: assemble from clamped cotangents (and differentiate that step)."""
+    rowptr, col, Aval, Lval, M = operator(V, F, t, clamp_min)
     Bv = _f64(V) if b_is_V else _f64(B)
     R = M[:, None] * Bv
     U = solve(rowptr, col, Aval, R, tol=tol, method=method)
     G = U - T
     Lam = solve(rowptr, col, Aval, G, tol=tol, method=method)
-    gV, gB, gt = vjp(V, F, t, U, Lam, B, b_is_V)
+    gV, gB, gt = vjp(V, F, t, U, Lam, B, b_is_V, clamp_min)
     return dict(U=U, Lam=Lam, gV=gV, gB=gB, gt=gt, loss=0.5 * float(np.sum(G * G)), rowptr=rowptr, col=col,
                 Aval=Aval, Lval=Lval, M=M, R=R, G=G)
 

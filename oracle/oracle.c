@@ -23,7 +23,9 @@
  * the gradient. No blocking, fusion or reordering beyond that.
  *
  * Readings where the paper is silent: barycentric lumping M_ii = sum over faces at i of
- * area/3; no cotangent clamp on this path; a face with zero area is an error (status 3).
+ * area/3; no cotangent clamp on this path unless asked for (the *_clamp variants: every
+ * corner's cotangent clamped from below, the cotangent weights with a minimum of the paper's
+ * §4 ARAP listing); a face with zero area is an error (status 3).
  */
 #include <math.h>
 #include <stdint.h>
@@ -113,9 +115,11 @@ static int triplet_cmp(const void* pa, const void* pb) {
  * edge (a, b), adds w = cot_c / 2 as four triplets: (a,b) -w, (b,a) -w, (a,a) +w, (b,b) +w.
  * Triplets are sorted by (row, col, generation order) and equal keys are summed, so every
  * entry is summed in face order. rowptr has n+1 entries; col and val need capacity
- * cap >= n + 6m. Returns nnz (> 0) or minus an error code. */
-int64_t orc_laplacian_csr(int64_t n, const double* V, int64_t m, const int32_t* F, int64_t* rowptr,
-                          int32_t* col, double* val, int64_t cap) {
+ * cap >= n + 6m. With clamp non-NULL every corner's cotangent is first clamped from below,
+ * cot_c <- max(cot_c, *clamp) (the cotangent weights with a minimum of the paper's §4 ARAP
+ * listing, read per corner). Returns nnz (> 0) or minus an error code. */
+static int64_t laplacian_csr(int64_t n, const double* V, int64_t m, const int32_t* F, const double* clamp,
+                             int64_t* rowptr, int32_t* col, double* val, int64_t cap) {
   double* cot = (double*)malloc(sizeof(double) * 3 * (size_t)m);
   double* area = (double*)malloc(sizeof(double) * (size_t)m);
   orc_triplet* T = (orc_triplet*)malloc(sizeof(orc_triplet) * 12 * (size_t)m);
@@ -126,7 +130,9 @@ int64_t orc_laplacian_csr(int64_t n, const double* V, int64_t m, const int32_t* 
   for (int64_t f = 0; f < m; ++f) {
     for (int c = 0; c < 3; ++c) {
       int64_t a = F[3 * f + (c + 1) % 3], b = F[3 * f + (c + 2) % 3];
-      double w = 0.5 * cot[3 * f + c];
+      double ct = cot[3 * f + c];
+      if (clamp && ct < *clamp) ct = *clamp;
+      double w = 0.5 * ct;
       orc_triplet t0 = {a, b, nt, -w}; T[nt++] = t0;
       orc_triplet t1 = {b, a, nt, -w}; T[nt++] = t1;
       orc_triplet t2 = {a, a, nt, w}; T[nt++] = t2;
@@ -150,6 +156,17 @@ int64_t orc_laplacian_csr(int64_t n, const double* V, int64_t m, const int32_t* 
   for (int64_t r = 0; r < n; ++r) rowptr[r + 1] += rowptr[r];
   free(cot); free(area); free(T);
   return nnz;
+}
+
+int64_t orc_laplacian_csr(int64_t n, const double* V, int64_t m, const int32_t* F, int64_t* rowptr,
+                          int32_t* col, double* val, int64_t cap) {
+  return laplacian_csr(n, V, m, F, NULL, rowptr, col, val, cap);
+}
+
+/* The same with every corner's cotangent clamped from below at clamp_min. */
+int64_t orc_laplacian_csr_clamp(int64_t n, const double* V, int64_t m, const int32_t* F, double clamp_min,
+                                int64_t* rowptr, int32_t* col, double* val, int64_t cap) {
+  return laplacian_csr(n, V, m, F, &clamp_min, rowptr, col, val, cap);
 }
 
 /* Barycentric lumped mass: M_ii = sum over faces containing i of area / 3 (face order). */
@@ -319,8 +336,12 @@ int orc_pcg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const do
  * When B is V itself (b_is_V), M Lambda is added to gV (the explicit dependence of M V on V).
  * Other outputs: gB = M Lambda (when B is independent of V; may be NULL) and
  * gt = -<Lambda, L U> (may be NULL). U, Lam, B are [n][k]; gV is [n][3]. */
-int orc_vjp(int64_t n, const double* V, int64_t m, const int32_t* F, double t, int k, const double* U,
-            const double* Lam, const double* B, int b_is_V, double* gV, double* gB, double* gt) {
+/* With clamp non-NULL the operator was assembled from the clamped cotangents max(cot_c, *clamp):
+ * a clamped corner (cot_c < *clamp) holds a constant, so it adds nothing to dl/dV, and dl/dt
+ * uses the clamped value. */
+static int vjp(int64_t n, const double* V, int64_t m, const int32_t* F, double t, int k, const double* U,
+               const double* Lam, const double* B, int b_is_V, const double* clamp, double* gV, double* gB,
+               double* gt) {
   if (b_is_V && k != 3) return ORC_ERR_ARG;
   const double* Bsrc = b_is_V ? V : B;
   double* M = (double*)calloc((size_t)n, sizeof(double));
@@ -363,6 +384,10 @@ int orc_vjp(int64_t n, const double* V, int64_t m, const int32_t* F, double t, i
       double lu = 0.0;
       for (int c = 0; c < k; ++c)
         lu += (Lam[vid[cj] * k + c] - Lam[vid[ck] * k + c]) * (U[vid[cj] * k + c] - U[vid[ck] * k + c]);
+      if (clamp && cot < *clamp) {
+        gt_acc -= 0.5 * (*clamp) * lu;
+        continue;
+      }
       gt_acc -= 0.5 * cot * lu;
       double w = -t * 0.5 * lu;
       double ekxn[3], nxej[3], dj[3], dk[3];
@@ -389,6 +414,18 @@ int orc_vjp(int64_t n, const double* V, int64_t m, const int32_t* F, double t, i
   if (gt) *gt = gt_acc;
   free(M);
   return ORC_OK;
+}
+
+int orc_vjp(int64_t n, const double* V, int64_t m, const int32_t* F, double t, int k, const double* U,
+            const double* Lam, const double* B, int b_is_V, double* gV, double* gB, double* gt) {
+  return vjp(n, V, m, F, t, k, U, Lam, B, b_is_V, NULL, gV, gB, gt);
+}
+
+/* The gradient of the step assembled with clamped cotangents (orc_laplacian_csr_clamp). */
+int orc_vjp_clamp(int64_t n, const double* V, int64_t m, const int32_t* F, double t, int k, const double* U,
+                  const double* Lam, const double* B, int b_is_V, double clamp_min, double* gV, double* gB,
+                  double* gt) {
+  return vjp(n, V, m, F, t, k, U, Lam, B, b_is_V, &clamp_min, gV, gB, gt);
 }
 
 /* Gradient of the mass term sum_i M_i(v) w_i (M_i = sum over the faces at i of area/3) with

@@ -10,7 +10,9 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libiskra_gb300.so")
+# ISKRA_GB300_CHECK=1 selects the bounds-checked build (libiskra_gb300_check.so, -DIG_CHECK)
+CHECKED = os.environ.get("ISKRA_GB300_CHECK", "0") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "libiskra_gb300_check.so" if CHECKED else "libiskra_gb300.so")
 
 IG_OK = 0
 IG_ERR_INVALID_ARG = 1
@@ -105,6 +107,7 @@ SIGNATURES = {
     "ig_profile_enable": (_i32, [_i32]),
     "ig_profile_read": (_i32, [_P(KernelStat), _i32]),
     "ig_measure_fma_peak": (_i32, [_i32, _i32, _vp, _P(_dbl), _P(_dbl)]),
+    "ig_mesh_set_cot_clamp": (_i32, [_vp, _i32, _dbl]),
 }
 
 _lib = None
@@ -117,10 +120,10 @@ def load(path: str = LIB_PATH):
     with _lock:
         if _lib is not None:
             return _lib
-        if not os.path.exists(path):
+        if not os.path.exists(path) or (CHECKED and path == LIB_PATH):
             try:
                 from . import build as _build
-                _build.build()
+                _build.build(checked=CHECKED and path == LIB_PATH)
             except Exception as exc:  # noqa: BLE001 - re-raised with context
                 raise NativeLibraryError(f"libiskra_gb300.so is missing and could not be built: {exc}") from exc
         try:

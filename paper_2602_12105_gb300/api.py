@@ -120,6 +120,17 @@ class Mesh:
             pass
 
     # -- library calls
+    def set_cot_clamp(self, clamp_min: Optional[float]):
+        """Clamp every corner's cotangent from below at clamp_min in later assemblies (and their
+        gradients), or restore the plain cotangents with None (ig_mesh_set_cot_clamp). The mesh
+        must be assembled again afterwards."""
+        self.ctx.sync_stream()
+        on = clamp_min is not None
+        self.ctx.check(self.ctx.lib.ig_mesh_set_cot_clamp(self.h, 1 if on else 0, float(clamp_min) if on else 0.0))
+        self.clamp_min = clamp_min
+        self._token = None
+        return self
+
     def assemble(self, V: torch.Tensor, t: float, precision: str = "fp64"):
         V = self._dev(V, 3, "V")
         self.ctx.sync_stream()
@@ -229,7 +240,10 @@ class Mesh:
         """Rounds of the regularized-geodesic ADMM (see ig_rgd_admm) from y and z (zeros when not
         given), at most max_rounds, stopping early at tol when tol > 0, with residual balancing of
         rho when adapt_rho. Returns (u [n], y [m][3], z [m][3], stats) with stats a dict of the
-        rounds run, the last primal and dual residuals and the final rho."""
+        rounds run, the last primal and dual residuals, the final rho, the rounds whose warm-started
+        u already met the solver tolerance (no solve), whether the rounds met tol ("converged") and
+        the worst status of the u-step solves ("solve_status": 0, or IG_ERR_NOT_CONVERGED with a
+        warning; other failures raise)."""
         V = self._dev(V, 3, "V")
         dev = self.ctx.device
         y = torch.zeros((self.m, 3), dtype=torch.float64, device=dev) if y is None else \
@@ -238,7 +252,7 @@ class Mesh:
             z.to(dev, torch.float64).contiguous().clone()
         src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).ravel())
         u = torch.empty(self.n, dtype=torch.float64, device=dev)
-        stats = (ctypes.c_double * 4)()
+        stats = (ctypes.c_double * 5)()
         self.ctx.sync_stream()
         st = self.ctx.lib.ig_rgd_admm(self.h, _ptr(V), src.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(src.size),
                                       float(rho), float(beta), float(beta_k), int(max_rounds), float(tol),
@@ -246,8 +260,13 @@ class Mesh:
                                       ctypes.byref(opts) if opts is not None else None)
         self._token = None
         self.t = None
-        self.ctx.check(st)
-        return u, y, z, {"rounds": int(stats[0]), "primal": stats[1], "dual": stats[2], "rho": stats[3]}
+        if st == N.IG_ERR_NOT_CONVERGED:
+            warnings.warn("rgd_admm: a u-step solve stopped at max_iter above rel_tol")
+        else:
+            self.ctx.check(st)
+        return u, y, z, {"rounds": int(stats[0]), "primal": stats[1], "dual": stats[2], "rho": stats[3],
+                         "warm_rounds_without_solve": int(stats[4]),
+                         "converged": bool(tol > 0.0 and stats[1] <= tol and stats[2] <= tol), "solve_status": st}
 
     def rgd_u_step_vjp(self, V: torch.Tensor, sources, y: torch.Tensor, z: torch.Tensor, rho: float, beta: float,
                        u: torch.Tensor, gu: torch.Tensor, opts=None):

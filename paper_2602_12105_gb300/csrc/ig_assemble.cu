@@ -42,10 +42,9 @@ __global__ void __launch_bounds__(256) face_kernel(const MeshDev* __restrict__ m
   if (f >= md.m) return;
   const double* __restrict__ V = calls[tl.x].V;
   const double half_t = 0.5 * calls[tl.x].t;
-  const int* __restrict__ F = md.F;
   double* __restrict__ facew = md.facew;
   int* err = md.err;
-  const int i0 = __ldg(F + 3 * f), i1 = __ldg(F + 3 * f + 1), i2 = __ldg(F + 3 * f + 2);
+  const int i0 = face_vertex(md, f, 0), i1 = face_vertex(md, f, 1), i2 = face_vertex(md, f, 2);
   double p0[3], p1[3], p2[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -76,6 +75,12 @@ __global__ void __launch_bounds__(256) face_kernel(const MeshDev* __restrict__ m
     w.y = h * (d2[0] * d0[0] + d2[1] * d0[1] + d2[2] * d0[2]);
     w.z = h * (d0[0] * d1[0] + d0[1] * d1[1] + d0[2] * d1[2]);
     w.w = s2 * inv_s * (1.0 / 6.0);
+    if (md.clamp_on) {  // w_c = (t/2) cot_c >= (t/2) clamp_min
+      const double wmin = half_t * md.clamp_min;
+      w.x = fmax(w.x, wmin);
+      w.y = fmax(w.y, wmin);
+      w.z = fmax(w.z, wmin);
+    }
   }
   double2* out = reinterpret_cast<double2*>(facew + 4 * (long)f);
   out[0] = make_double2(w.x, w.y);
@@ -105,7 +110,7 @@ __global__ void __launch_bounds__(256) split_v_kernel(const MeshDev* __restrict_
 // The FP64 weights of one face (as face_kernel), rounded to float; flags a degenerate or
 // non-finite face.
 __device__ __noinline__ float4 face_weights64(const double* __restrict__ V, int i0, int i1, int i2, double half_t,
-                                              int* err) {
+                                              int* err, int clamp_on, double clamp_min) {
   double p0[3], p1[3], p2[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -131,10 +136,16 @@ __device__ __noinline__ float4 face_weights64(const double* __restrict__ V, int 
   }
   const double inv_s = rsqrt(s2);
   const double h = -half_t * inv_s;
-  return make_float4((float)(h * (d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2])),
-                     (float)(h * (d2[0] * d0[0] + d2[1] * d0[1] + d2[2] * d0[2])),
-                     (float)(h * (d0[0] * d1[0] + d0[1] * d1[1] + d0[2] * d1[2])),
-                     (float)(s2 * inv_s * (1.0 / 6.0)));
+  double w0 = h * (d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2]);
+  double w1 = h * (d2[0] * d0[0] + d2[1] * d0[1] + d2[2] * d0[2]);
+  double w2 = h * (d0[0] * d1[0] + d0[1] * d1[1] + d0[2] * d1[2]);
+  if (clamp_on) {
+    const double wmin = half_t * clamp_min;
+    w0 = fmax(w0, wmin);
+    w1 = fmax(w1, wmin);
+    w2 = fmax(w2, wmin);
+  }
+  return make_float4((float)w0, (float)w1, (float)w2, (float)(s2 * inv_s * (1.0 / 6.0)));
 }
 
 // K1 with FP32 geometry: per face the float weights (t cot_c / 2, area / 3) into facew viewed as
@@ -146,8 +157,7 @@ __global__ void __launch_bounds__(256) face32_kernel(const MeshDev* __restrict__
   const MeshDev& md = mds[tl.x];
   const int f = tl.y * 256 + threadIdx.x;
   if (f >= md.m) return;
-  const int* __restrict__ F = md.F;
-  const int i0 = __ldg(F + 3 * f), i1 = __ldg(F + 3 * f + 1), i2 = __ldg(F + 3 * f + 2);
+  const int i0 = face_vertex(md, f, 0), i1 = face_vertex(md, f, 1), i2 = face_vertex(md, f, 2);
   const float4* __restrict__ vs = reinterpret_cast<const float4*>(md.vsplit);
   const float4 h0 = __ldg(vs + 2 * (long)i0), l0 = __ldg(vs + 2 * (long)i0 + 1);
   const float4 h1 = __ldg(vs + 2 * (long)i1), l1 = __ldg(vs + 2 * (long)i1 + 1);
@@ -167,16 +177,25 @@ __global__ void __launch_bounds__(256) face32_kernel(const MeshDev* __restrict__
   const float pmax = fmaxf(fmaxf(e1 * e2, e2 * e0), e0 * e1);
   float4 w;
   if (!(s2 >= kSliverSin2 * pmax) || !(s2 > 0.f) || !(pmax < 3.0e38f)) {
-    w = face_weights64(calls[tl.x].V, i0, i1, i2, 0.5 * calls[tl.x].t, md.err);
+    w = face_weights64(calls[tl.x].V, i0, i1, i2, 0.5 * calls[tl.x].t, md.err, md.clamp_on, md.clamp_min);
   } else {
     float th, tl32;
     split_f64(calls[tl.x].t, th, tl32);  // t as a float without an FP64 conversion instruction
     const float inv_s = rsqrtf(s2);
-    const float h = -0.5f * (th + tl32) * inv_s;
+    const float half_t = 0.5f * (th + tl32);
+    const float h = -half_t * inv_s;
     w.x = h * (d1x * d2x + d1y * d2y + d1z * d2z);
     w.y = h * (d2x * d0x + d2y * d0y + d2z * d0z);
     w.z = h * (d0x * d1x + d0y * d1y + d0z * d1z);
     w.w = s2 * inv_s * (1.0f / 6.0f);
+    if (md.clamp_on) {
+      float ch, cl;
+      split_f64(md.clamp_min, ch, cl);
+      const float wmin = half_t * (ch + cl);
+      w.x = fmaxf(w.x, wmin);
+      w.y = fmaxf(w.y, wmin);
+      w.z = fmaxf(w.z, wmin);
+    }
   }
   reinterpret_cast<float4*>(md.facew)[f] = w;
 }
@@ -195,7 +214,10 @@ __global__ void __launch_bounds__(256) row32_kernel(const MeshDev* __restrict__ 
   if (v >= md.n) return;
   const int r0 = __ldg(md.rowptr + v);
   const int len = __ldg(md.rowptr + v + 1) - r0;
-  const int dslot = __ldg(md.diagpos + v) - r0;
+  int dslot = __ldg(md.diagpos + v) - r0;
+#ifdef IG_CHECK
+  if (!IG_IN_RANGE(dslot, len, md.err)) dslot = 0;
+#endif
   const int sl = v >> 5;
   const int sbase = __ldg(md.sell_ptr + sl) + (v & 31);
   const int width = (__ldg(md.sell_ptr + sl + 1) - __ldg(md.sell_ptr + sl)) >> 5;
@@ -208,14 +230,18 @@ __global__ void __launch_bounds__(256) row32_kernel(const MeshDev* __restrict__ 
   }
   float mass = 0.f, diag = 0.f;
   const float4* __restrict__ fw4 = reinterpret_cast<const float4*>(md.facew);
-  const int e0 = __ldg(md.incptr + v), e1 = __ldg(md.incptr + v + 1);
+  int e0, e1;
+  inc_range(md, v, e0, e1);
   for (int e = e0; e < e1; ++e) {
     const int2 ic = __ldg(md.inc + e);
-    const int f = ic.x >> 2, c = ic.x & 3;
+    const int f = inc_face(md, ic.x), c = ic.x & 3;
     const float4 w = __ldg(fw4 + f);
     const float w_next = (c == 0) ? w.z : (c == 1 ? w.x : w.y);
     const float w_prev = (c == 0) ? w.y : (c == 1 ? w.z : w.x);
     const int sn = ic.y & 0xffff, sp = ic.y >> 16;
+#ifdef IG_CHECK
+    if (!IG_IN_RANGE(sn, len, md.err) || !IG_IN_RANGE(sp, len, md.err)) continue;
+#endif
     if (in_smem) {
       acc[sn][threadIdx.x] -= w_next;
       acc[sp][threadIdx.x] -= w_prev;
@@ -249,7 +275,10 @@ __global__ void __launch_bounds__(256) row_kernel(const MeshDev* __restrict__ md
   if (v >= md.n) return;
   const int r0 = __ldg(md.rowptr + v);
   const int len = __ldg(md.rowptr + v + 1) - r0;
-  const int dslot = __ldg(md.diagpos + v) - r0;
+  int dslot = __ldg(md.diagpos + v) - r0;
+#ifdef IG_CHECK
+  if (!IG_IN_RANGE(dslot, len, md.err)) dslot = 0;
+#endif
   const int sl = v >> 5;
   const int sbase = __ldg(md.sell_ptr + sl) + (v & 31);
   const int width = (__ldg(md.sell_ptr + sl + 1) - __ldg(md.sell_ptr + sl)) >> 5;
@@ -261,16 +290,20 @@ __global__ void __launch_bounds__(256) row_kernel(const MeshDev* __restrict__ md
     for (int j = 0; j < len; ++j) gA[sbase + 32 * j] = 0.0;
   }
   double mass = 0.0, diag = 0.0;
-  const int e0 = __ldg(md.incptr + v), e1 = __ldg(md.incptr + v + 1);
+  int e0, e1;
+  inc_range(md, v, e0, e1);
   for (int e = e0; e < e1; ++e) {
     const int2 ic = __ldg(md.inc + e);
-    const int f = ic.x >> 2, c = ic.x & 3;
+    const int f = inc_face(md, ic.x), c = ic.x & 3;
     const double2* fw = reinterpret_cast<const double2*>(md.facew + 4 * (long)f);
     const double2 a = __ldg(fw), b = __ldg(fw + 1);
     // corner c+2 is opposite the edge (v, next); corner c+1 is opposite the edge (v, prev)
     const double w_next = (c == 0) ? b.x : (c == 1 ? a.x : a.y);
     const double w_prev = (c == 0) ? a.y : (c == 1 ? b.x : a.x);
     const int sn = ic.y & 0xffff, sp = ic.y >> 16;
+#ifdef IG_CHECK
+    if (!IG_IN_RANGE(sn, len, md.err) || !IG_IN_RANGE(sp, len, md.err)) continue;
+#endif
     if (in_smem) {
       acc[sn][threadIdx.x] -= w_next;
       acc[sp][threadIdx.x] -= w_prev;

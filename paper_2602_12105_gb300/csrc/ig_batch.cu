@@ -75,7 +75,9 @@ ig_status batch_info(ig_batch* b, int k, ig_solve_info* infos) {
   ig_status worst = IG_OK;
   for (size_t i = 0; i < nm; ++i) {
     ig_status st = (ig_status)ss[i].status;
-    if (bits[i]) st = (bits[i] & kErrNonfinite) ? IG_ERR_NONFINITE : IG_ERR_DEGENERATE_FACE;
+    if (bits[i])
+      st = (bits[i] & kErrBounds) ? IG_ERR_INDEX_OUT_OF_RANGE
+                                  : ((bits[i] & kErrNonfinite) ? IG_ERR_NONFINITE : IG_ERR_DEGENERATE_FACE);
     if (st != IG_OK && worst == IG_OK) worst = st;
     if (infos) {
       ig_solve_info& inf = infos[i];
@@ -105,6 +107,7 @@ ig_solve_opts opts_or_default(const ig_solve_opts* o) {
 extern "C" {
 
 ig_status ig_batch_create(ig_ctx* ctx, ig_mesh* const* meshes, int count, ig_batch** out) {
+  IG_NVTX("ig_batch_create");
   if (!ctx || !out) return IG_ERR_INVALID_ARG;
   *out = nullptr;
   if (!meshes || count < 1 || count > kMaxIo) return bad(ctx, "need 1 <= count <= 1024 meshes");
@@ -131,6 +134,7 @@ ig_status ig_batch_create(ig_ctx* ctx, ig_mesh* const* meshes, int count, ig_bat
 }
 
 ig_status ig_batch_free(ig_batch* b) {
+  IG_NVTX("ig_batch_free");
   if (!b) return IG_ERR_INVALID_ARG;
   BatchDevice guard(b->ctx->device);
   cudaStreamSynchronize(b->ctx->stream);
@@ -141,6 +145,7 @@ ig_status ig_batch_free(ig_batch* b) {
 }
 
 ig_status ig_batch_assemble(ig_batch* b, const double* const* V_dev, const double* t, int precision) {
+  IG_NVTX("ig_batch_assemble");
   if (!b) return IG_ERR_INVALID_ARG;
   ig_ctx* ctx = b->ctx;
   if (!V_dev || !t) return bad(ctx, "V and t arrays are required");
@@ -175,6 +180,7 @@ ig_status ig_batch_assemble(ig_batch* b, const double* const* V_dev, const doubl
 
 ig_status ig_batch_solve(ig_batch* b, const double* const* B_dev, int k, double* const* U_dev,
                          const ig_solve_opts* opts, ig_solve_info* infos) {
+  IG_NVTX("ig_batch_solve");
   if (!b) return IG_ERR_INVALID_ARG;
   ig_ctx* ctx = b->ctx;
   const int nm = (int)b->meshes.size();
@@ -210,6 +216,7 @@ ig_status ig_batch_adjoint(ig_batch* b, const double* const* V_dev, const double
                            const double* const* U_dev, const double* const* G_dev, int k, double* const* gV_dev,
                            double* const* gB_dev, double* gt_dev, const ig_solve_opts* opts,
                            ig_solve_info* infos) {
+  IG_NVTX("ig_batch_adjoint");
   if (!b) return IG_ERR_INVALID_ARG;
   ig_ctx* ctx = b->ctx;
   const int nm = (int)b->meshes.size();
@@ -257,6 +264,7 @@ ig_status ig_batch_adjoint(ig_batch* b, const double* const* V_dev, const double
 }
 
 ig_status ig_batch_iterate(ig_batch* b, int k, int max_iters, int* done_host) {
+  IG_NVTX("ig_batch_iterate");
   if (!b) return IG_ERR_INVALID_ARG;
   ig_ctx* ctx = b->ctx;
   if (k < 1 || k > kMaxK) return bad(ctx, "k must be in [1, 4]");

@@ -191,7 +191,7 @@ __device__ __forceinline__ void row_product(const MeshDev& md, const TA* __restr
         for (int u = 0; u < 8; ++u)
           if (j0 + u < w) {
             TX v[K];
-            gather(cj[u], v);
+            gather(IG_IN_RANGE(cj[u], md.n, md.err) ? cj[u] : 0, v);
 #pragma unroll
             for (int c = 0; c < K; ++c) acc[c] = fma_t((TX)aj[u], v[c], acc[c]);
           }
@@ -202,7 +202,8 @@ __device__ __forceinline__ void row_product(const MeshDev& md, const TA* __restr
         const int e = base + 32 * j;
         const TX a = to_arith<TX>(__ldg(A + e));
         TX v[K];
-        gather(__ldg(sc + e), v);
+        const int cj = __ldg(sc + e);
+        gather(IG_IN_RANGE(cj, md.n, md.err) ? cj : 0, v);
 #pragma unroll
         for (int c = 0; c < K; ++c) acc[c] = fma_t(a, v[c], acc[c]);
       }
@@ -212,7 +213,8 @@ __device__ __forceinline__ void row_product(const MeshDev& md, const TA* __restr
     for (int e = e0; e < e1; ++e) {
       const TX a = to_arith<TX>(__ldg(A + e));
       TX v[K];
-      gather(__ldg(md.col + e), v);
+      const int cj = __ldg(md.col + e);
+      gather(IG_IN_RANGE(cj, md.n, md.err) ? cj : 0, v);
 #pragma unroll
       for (int c = 0; c < K; ++c) acc[c] = fma_t(a, v[c], acc[c]);
     }
@@ -361,6 +363,13 @@ __device__ __forceinline__ void tile_reduce(T (&v)[NV], double* red, double* out
 }
 
 // ------------------------------------------------------------------------------- persistent tiles
+// The tilings of a mesh: 0 the FP64 solver's, 1 the mixed-precision SpMV's and p-update's, 2 the
+// mixed-precision update's (one wave of large tiles on meshes of at least kBigRows rows, the
+// tiling 1 otherwise, so that the chunked lists of smaller meshes serve both).
+__device__ __forceinline__ int tile_count(const MeshDev& md, int tiling) {
+  return tiling == 0 ? md.ntiles : (tiling == 1 ? md.ntiles32 : md.ntiles32u);
+}
+
 // Per-CTA view of the mesh whose tiles the CTA is working on: a copy of its MeshDev and of the
 // scalars the kernels read, taken once per mesh switch. Every CTA of a launch reads the same few
 // scalars; reading them through one thread per CTA keeps them off a single hot L2 line, and the
@@ -413,7 +422,7 @@ __device__ __forceinline__ void load_mesh(const MeshDev* __restrict__ mds, int i
 template <int NV, typename Finish>
 __device__ __forceinline__ void flush_tiles(TileCtx& tc, int tiling, unsigned run, int cnt_idx,
                                             const Finish& finish) {
-  const int ntiles = tiling ? tc.md.ntiles32 : tc.md.ntiles;
+  const int ntiles = tile_count(tc.md, tiling);
   unsigned int* cnt = &tc.md.s->cnt[cnt_idx];
   if (threadIdx.x < NV) __threadfence();  // the tile sums this thread wrote, before the count
   __syncthreads();
@@ -646,7 +655,7 @@ struct TileWalk {
 
 // body(md, tile, red, out) does the tile's work and sums its NV values into out with
 // tile_reduce(v, red, out); active(sn) says whether a mesh takes part in this launch (uniform per
-// CTA). tiling 0: FP64 solver tiles, 1: mixed-precision tiles; cnt_idx selects the mesh counter.
+// CTA). tiling: see tile_count; cnt_idx selects the mesh counter.
 template <int NV, typename Active, typename Body, typename Finish>
 __device__ __forceinline__ void tile_loop(const MeshDev* __restrict__ mds, const ListRef& L, int tiling, int cnt_idx,
                                           TileCtx& tc, const Active& active, const Body& body,
@@ -662,7 +671,7 @@ __device__ __forceinline__ void tile_loop(const MeshDev* __restrict__ mds, const
       run = 0;
       load_mesh(mds, cur, tc);
     }
-    const int nt = tiling ? tc.md.ntiles32 : tc.md.ntiles;
+    const int nt = tile_count(tc.md, tiling);
     if (!w.here(L, nt)) continue;
     if (active(tc.sn)) {
       body(tc.md, w.lt, tc.red[buf], tc.md.part + (long)w.lt * kPartStride);
@@ -686,7 +695,7 @@ __device__ __forceinline__ void tile_loop_plain(const MeshDev* __restrict__ mds,
       cur = w.mi;
       load_mesh(mds, cur, tc);
     }
-    const int nt = tiling ? tc.md.ntiles32 : tc.md.ntiles;
+    const int nt = tile_count(tc.md, tiling);
     if (!w.here(L, nt)) continue;
     if (active(tc.sn)) body(tc.md, w.lt);
     w.next(L, nt);

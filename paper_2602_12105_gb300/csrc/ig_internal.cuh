@@ -22,6 +22,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <functional>
@@ -49,7 +50,34 @@ enum : int {
   kErrValence = 8,
   kErrDegenerate = 16,
   kErrNonfinite = 32,
+  kErrBounds = 64,  // bounds-checked build only: an index read from device data was out of range
 };
+
+// Bounds-checked build (compiled with -DIG_CHECK, a separate library): the indices the kernels
+// read from device data (pattern columns, face vertices, incidence entries, row slots) are tested
+// before use; one out of range sets kErrBounds in the mesh's error word and the access is skipped,
+// so a corrupted structure is reported (as IG_ERR_INDEX_OUT_OF_RANGE by the next synchronising
+// call) instead of faulting. The default build compiles the tests away.
+__device__ __forceinline__ bool in_range_checked(long long i, long long size, int* err) {
+  if (i >= 0 && i < size) return true;
+  if (err) atomicOr(err, kErrBounds);
+  return false;
+}
+#ifdef IG_CHECK
+#define IG_IN_RANGE(i, size, errp) ::ig::in_range_checked((long long)(i), (long long)(size), (errp))
+#else
+#define IG_IN_RANGE(i, size, errp) true
+#endif
+
+// NVTX range around a C ABI call (visible in Nsight timelines; costs a function-pointer call
+// when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define IG_NVTX(name) ::ig::NvtxRange ig_nvtx_range_(name)
 
 // Solver state of one mesh, resident in device memory. The "last CTA" of each reduction
 // (detected with a counter) writes the scalars; every other field is read-only for kernels.
@@ -91,6 +119,7 @@ struct MeshDev {
   int n, m, nnz, ntiles;   // ntiles = ceil(n / tile_rows)
   int tile_rows;           // rows per FP64 solver tile (<= kTileRows64, a multiple of 32), chosen at upload
   int ntiles32, tile_rows32;  // the same for the mixed-precision kernels (their own occupancy)
+  int ntiles32u, tile_rows32u;  // the mixed-precision update's tiles (one wave on meshes of kBigRows or more)
   int nnz_sell;            // stored entries of the sliced layout (0: A is plain CSR on rowptr/col)
   int sell_w;              // every slice has this many entries per row (0: widths differ)
   const int* sell_ptr;     // [ceil(n/32)+1] slice offsets, or null for plain CSR
@@ -144,7 +173,35 @@ struct MeshDev {
   float* lsplit;           // [n][8]: Lambda, the same layout
   float* wv;               // [n]: <Lambda_v, B_v - U_v> per vertex
   // per-face weights [m][4] float and per-face gradients [m][9] float live in facew and gface
+  // Cotangent clamp (ig_mesh_set_cot_clamp): when clamp_on, every corner's cotangent enters the
+  // operator as max(cot, clamp_min), and a clamped corner adds nothing to dl/dV.
+  int clamp_on;
+  double clamp_min;
 };
+
+// Topology reads through the bounds checks of the checked build (plain loads otherwise): a bad
+// value is reported in md.err and replaced by one that keeps the access inside its array.
+// The incidence range of vertex v (within [0, 3m)):
+__device__ __forceinline__ void inc_range(const MeshDev& md, int v, int& e0, int& e1) {
+  e0 = __ldg(md.incptr + v);
+  e1 = __ldg(md.incptr + v + 1);
+#ifdef IG_CHECK
+  if (!(e0 >= 0 && e0 <= e1 && e1 <= 3 * md.m)) {
+    atomicOr(md.err, kErrBounds);
+    e0 = e1 = 0;
+  }
+#endif
+}
+// Vertex c of face f (within [0, n)):
+__device__ __forceinline__ int face_vertex(const MeshDev& md, int f, int c) {
+  const int v = __ldg(md.F + 3 * f + c);
+  return IG_IN_RANGE(v, md.n, md.err) ? v : 0;
+}
+// The face of an incidence entry (within [0, m)):
+__device__ __forceinline__ int inc_face(const MeshDev& md, int fc) {
+  const int f = fc >> 2;
+  return IG_IN_RANGE(f, md.m, md.err) ? f : 0;
+}
 
 // Host-side helpers (ig_api.cu).
 void set_error(ig_ctx* ctx, const std::string& msg);
@@ -380,6 +437,12 @@ cudaError_t eig_vjp_massw(int k, double* ws, long n, cudaStream_t st);  // wm = 
 cudaError_t launch_rgd_operator(const MeshDev* mds, int n, const int* src, cudaStream_t st);
 cudaError_t launch_rgd_rhs(const MeshDev* mds, int n, const double* V, const double* y, const double* z, double rho,
                            double beta, const int* src, double* b, cudaStream_t st);
+// warm start of a u-step solve: rhs = b - A u and *ratio = |b| / |rhs| (device scalar)
+cudaError_t launch_rgd_warm(const MeshDev* mds, long n, const double* b, const double* u, double* rhs, double* ratio,
+                            cudaStream_t st);
+cudaError_t launch_rgd_axpy(double* u, const double* d, long n, cudaStream_t st);  // u += d
+// *worst = max(*worst, status of the mesh's last solve)
+cudaError_t launch_rgd_note_status(const MeshDev* mds, int* worst, cudaStream_t st);
 // out = x with zeros on the sources (add_s = 0), or x + s (add_s = 1)
 cudaError_t launch_rgd_vec(const double* x, const int* src, int n, int add_s, double s, double* out, cudaStream_t st);
 // one ADMM z-step and dual step per face (primal: max_f |G u - z| as double bits, may be null)

@@ -698,14 +698,23 @@ constexpr size_t kNoAllocBytes = align256(kNaStart + sizeof(int4) * (kNoAllocMax
 std::mutex g_noalloc_mu;
 void* g_noalloc_base[64] = {};
 
-// Preconditioner from the operator's diagonal, solver state cleared, tile table written.
+// The caller's pattern checked (row ranges within [0, nnz), columns within [0, n)), the preconditioner
+// from the operator's diagonal, solver state cleared, tile table written.
 __global__ void __launch_bounds__(256) noalloc_setup_kernel(MeshDev md, MeshDev* md_out, int2* tiles, int ntiles,
                                                             LoopCtl ctl_init, LoopCtl* ctl, SolveScal* s) {
   const long row = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (row < md.n) {
     double d = 0.0;
-    for (int e = md.rowptr[row]; e < md.rowptr[row + 1]; ++e)
-      if (md.col[e] == row) d = md.A[e];
+    const int e0 = md.rowptr[row], e1 = md.rowptr[row + 1];
+    if (e0 < 0 || e1 < e0 || e1 > md.nnz) {
+      atomicOr(md.err, kErrIndex);  // a row range outside the caller's [0, nnz)
+    } else {
+      for (int e = e0; e < e1; ++e) {
+        const int c = md.col[e];
+        if (c < 0 || c >= md.n) atomicOr(md.err, kErrIndex);  // a column outside [0, n)
+        else if (c == row) d = md.A[e];
+      }
+    }
     if (!positive_finite(d)) atomicOr(md.err, kErrDegenerate);
     md.Dinv[row] = positive_finite(d) ? 1.0 / d : 0.0;
 #pragma unroll
@@ -731,6 +740,7 @@ extern "C" ig_status ig_solve_csr_noalloc(const int32_t* rowptr_dev, const int32
                                           const double* M_dev, int64_t n, int64_t nnz, const double* B_dev, int k,
                                           double* U_dev, void* cuda_stream, const ig_solve_opts* opts,
                                           ig_solve_info* info) {
+  IG_NVTX("ig_solve_csr_noalloc");
   using namespace ig;
   if (!rowptr_dev || !col_dev || !Aval_dev || !B_dev || !U_dev) return IG_ERR_INVALID_ARG;
   if (n < 1 || n > kNoAllocMaxRows || nnz < n || nnz > (int64_t)INT32_MAX) return IG_ERR_INVALID_ARG;
@@ -806,6 +816,23 @@ extern "C" ig_status ig_solve_csr_noalloc(const int32_t* rowptr_dev, const int32
                      &reinterpret_cast<LoopCtl*>(base + kNaCtl)->nbig};
   noalloc_setup_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(md, g.mds, g.tiles, g.ntiles, ctl_init, g.ctl, md.s);
   if (cudaGetLastError() != cudaSuccess) return IG_ERR_CUDA;
+  // The caller's pattern is validated before the solve touches it: a row range outside [0, nnz)
+  // or a column outside [0, n) would send the SpMV's loads out of the caller's arrays.
+  {
+    int bits0 = 0;
+    if (cudaMemcpyAsync(&bits0, md.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return IG_ERR_CUDA;
+    if (bits0) {
+      const ig_status bad = (bits0 & kErrIndex) ? IG_ERR_INDEX_OUT_OF_RANGE : IG_ERR_INVALID_ARG;
+      if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->status = bad;
+        info->k = k;
+      }
+      return bad;
+    }
+  }
   // the pointer table lives on this thread's stack (16 KB): no host heap allocation either
   IoTable io;
   io.in[0] = B_dev;

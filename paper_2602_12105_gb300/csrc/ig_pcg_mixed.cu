@@ -26,26 +26,19 @@ struct KPm {
   static constexpr int v = (K == 3) ? 4 : K;
 };
 
-// A tile of the mixed-precision kernels is one wave's share of a mesh (up to kMaxTileRows32 rows),
-// taken in passes of kTileRows rows (kRowsPerThread per thread). Each thread adds its per-pass
-// FP32 partial sums into a running sum with the rounding error of every addition carried along
-// (compensated summation), so a tile of many passes keeps the accuracy of a short sum; the tile's
-// sums then go through the usual warp and tile reduction (FP64 across warps and tiles).
+// The mixed-precision kernels take a tile in passes of kTileRows rows (kRowsPerThread per thread);
+// a thread adds its rows' FP32 products across the passes of a tile (at most 64 passes, 256
+// terms), the warps add their lanes in FP32 and the tile's warps and tiles are added in FP64.
 template <int NV>
-struct CompSum {
-  float s[NV], c[NV];
-  __device__ __forceinline__ CompSum() {
+struct PassSum {
+  float s[NV];
+  __device__ __forceinline__ PassSum() {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) s[i] = c[i] = 0.f;
+    for (int i = 0; i < NV; ++i) s[i] = 0.f;
   }
   __device__ __forceinline__ void add(const float (&x)[NV]) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      const float y = x[i] - c[i];
-      const float t = s[i] + y;
-      c[i] = (t - s[i]) - y;
-      s[i] = t;
-    }
+    for (int i = 0; i < NV; ++i) s[i] += x[i];
   }
 };
 
@@ -242,7 +235,7 @@ __global__ void __launch_bounds__(kBlock, 4) spmv_mixed_kernel(const MeshDev* __
         const float* __restrict__ A = md.A32;
         const float* __restrict__ p = md.p32;
         float* __restrict__ q32 = md.q32;
-        CompSum<K> sum;
+        PassSum<K> sum;
         for (long base = t0; base < t1; base += kTileRows) {
           float pq[K];
 #pragma unroll
@@ -316,13 +309,13 @@ __global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* 
     cudaGraphConditionalHandle handle, int use_graph) {
   __shared__ TileCtx tc;
   tile_loop<2 * K>(
-      mds, L, 1, 1, tc,
+      mds, L, 2, 1, tc,
       [](const ScalSnap& x) { return !x.done && x.phase != kPhaseApply; },
       [&](const MeshDev& md, int tile, double* red, double* out) {
         const long nn = md.n;
-        const long t0 = (long)tile * md.tile_rows32;
-        const long t1 = t0 + md.tile_rows32 < nn ? t0 + md.tile_rows32 : nn;
-        CompSum<2 * K> sum;
+        const long t0 = (long)tile * md.tile_rows32u;
+        const long t1 = t0 + md.tile_rows32u < nn ? t0 + md.tile_rows32u : nn;
+        PassSum<2 * K> sum;
         const float* __restrict__ D32 = md.Dinv32;
         float* __restrict__ x32 = md.x32;
         float* __restrict__ r32 = md.r32;

@@ -84,14 +84,15 @@ __global__ void __launch_bounds__(kBlock) rgd_rhs_kernel(const MeshDev* __restri
     return;
   }
   double div = 0.0;
-  const int e0 = md.incptr[v], e1 = md.incptr[v + 1];
+  int e0, e1;
+  inc_range(md, v, e0, e1);
   for (int e = e0; e < e1; ++e) {
     const int2 ic = md.inc[e];
-    const int f = ic.x >> 2, c = ic.x & 3;
+    const int f = inc_face(md, ic.x), c = ic.x & 3;
     double p[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const int vid = md.F[3 * f + a];
+      const int vid = face_vertex(md, f, a);
 #pragma unroll
       for (int d = 0; d < 3; ++d) p[a][d] = V[3 * (long)vid + d];
     }
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(kBlock) rgd_dface_kernel(const MeshDev* __rest
   if (f >= md.m) return;
   double p[3][3], l[3];
   for (int c = 0; c < 3; ++c) {
-    const int vid = md.F[3 * f + c];
+    const int vid = face_vertex(md, f, c);
     l[c] = md.lam[vid];
     for (int d = 0; d < 3; ++d) p[c][d] = V[3 * (long)vid + d];
   }
@@ -196,10 +197,11 @@ __global__ void __launch_bounds__(kBlock) rgd_dgather_kernel(const MeshDev* __re
   const int v = blockIdx.x * kBlock + threadIdx.x;
   if (v >= md.n) return;
   double g[3] = {0.0, 0.0, 0.0};
-  const int e0 = md.incptr[v], e1 = md.incptr[v + 1];
+  int e0, e1;
+  inc_range(md, v, e0, e1);
   for (int e = e0; e < e1; ++e) {
     const int2 ic = md.inc[e];
-    const int f = ic.x >> 2, c = ic.x & 3;
+    const int f = inc_face(md, ic.x), c = ic.x & 3;
     for (int d = 0; d < 3; ++d) g[d] += md.gface[9 * (long)f + 3 * c + d];
   }
   for (int d = 0; d < 3; ++d) gV[3 * (long)v + d] += g[d];
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(kBlock) rgd_zy_kernel(const MeshDev* __restric
   if (f >= md.m) return;
   double p[3][3], uc[3];
   for (int c = 0; c < 3; ++c) {
-    const int vid = md.F[3 * f + c];
+    const int vid = face_vertex(md, f, c);
     uc[c] = u[vid];
     for (int d = 0; d < 3; ++d) p[c][d] = V[3 * (long)vid + d];
   }
@@ -261,13 +263,14 @@ __global__ void __launch_bounds__(kBlock) rgd_dual_kernel(const MeshDev* __restr
   const int v = blockIdx.x * kBlock + threadIdx.x;
   if (v >= md.n || src[v] != 0) return;
   double div = 0.0;
-  const int e0 = md.incptr[v], e1 = md.incptr[v + 1];
+  int e0, e1;
+  inc_range(md, v, e0, e1);
   for (int e = e0; e < e1; ++e) {
     const int2 ic = md.inc[e];
-    const int f = ic.x >> 2, c = ic.x & 3;
+    const int f = inc_face(md, ic.x), c = ic.x & 3;
     double p[3][3];
     for (int a = 0; a < 3; ++a) {
-      const int vid = md.F[3 * f + a];
+      const int vid = face_vertex(md, f, a);
       for (int d = 0; d < 3; ++d) p[a][d] = V[3 * (long)vid + d];
     }
     double e1v[3], e2v[3], ec[3], N[3];
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(kBlock) rgd_rvjp_face_kernel(const MeshDev* __
   const long m3 = 3L * md.m;
   double p[3][3], uc[3];
   for (int c = 0; c < 3; ++c) {
-    const int vid = md.F[3 * f + c];
+    const int vid = face_vertex(md, f, c);
     uc[c] = u[vid];
     for (int d = 0; d < 3; ++d) p[c][d] = V[3 * (long)vid + d];
   }
@@ -356,13 +359,14 @@ __global__ void __launch_bounds__(kBlock) rgd_gT_kernel(const MeshDev* __restric
     return;
   }
   double acc = add ? add[v] : 0.0;
-  const int e0 = md.incptr[v], e1 = md.incptr[v + 1];
+  int e0, e1;
+  inc_range(md, v, e0, e1);
   for (int e = e0; e < e1; ++e) {
     const int2 ic = md.inc[e];
-    const int f = ic.x >> 2, c = ic.x & 3;
+    const int f = inc_face(md, ic.x), c = ic.x & 3;
     double p[3][3];
     for (int a = 0; a < 3; ++a) {
-      const int vid = md.F[3 * f + a];
+      const int vid = face_vertex(md, f, a);
       for (int d = 0; d < 3; ++d) p[a][d] = V[3 * (long)vid + d];
     }
     double e1v[3], e2v[3], ec[3], N[3];
@@ -396,7 +400,7 @@ __global__ void __launch_bounds__(kBlock) rgd_lamgrad_kernel(const MeshDev* __re
   const long m3 = 3L * md.m;
   double p[3][3], l[3];
   for (int c = 0; c < 3; ++c) {
-    const int vid = md.F[3 * f + c];
+    const int vid = face_vertex(md, f, c);
     l[c] = md.lam[vid];
     for (int d = 0; d < 3; ++d) p[c][d] = V[3 * (long)vid + d];
   }
@@ -430,7 +434,7 @@ __global__ void __launch_bounds__(kBlock) rgd_gdface_kernel(const MeshDev* __res
   if (f >= md.m) return;
   double p[3][3], uc[3];
   for (int c = 0; c < 3; ++c) {
-    const int vid = md.F[3 * f + c];
+    const int vid = face_vertex(md, f, c);
     uc[c] = u[vid];
     for (int d = 0; d < 3; ++d) p[c][d] = V[3 * (long)vid + d];
   }
@@ -475,6 +479,45 @@ __global__ void __launch_bounds__(kBlock) rgd_gdface_kernel(const MeshDev* __res
   }
 }
 
+// Warm start of a u-step solve from the previous round's u: rhs = b - A u with the constrained
+// operator (the solve then finds the correction), and ratio = |b| / |rhs|, so that solving the
+// correction to a relative tolerance of tol * ratio leaves |b - A u| <= tol |b|, the criterion of
+// a cold solve. Tiles of kTileRows rows, 4 per thread; deterministic sums (last CTA, tile order).
+__global__ void __launch_bounds__(kBlock) rgd_warm_kernel(const MeshDev* __restrict__ mds, const double* __restrict__ b,
+                                                          const double* __restrict__ u, double* __restrict__ rhs,
+                                                          double* ratio) {
+  __shared__ double sh[2 * kBlock];
+  const MeshDev& md = mds[0];
+  const long n = md.n;
+  const int ntile = (int)((n + kTileRows - 1) / kTileRows);
+  double acc[2] = {0.0, 0.0};
+#pragma unroll
+  for (int rr = 0; rr < kRowsPerThread; ++rr) {
+    const long row = (long)blockIdx.x * kTileRows + rr * kBlock + threadIdx.x;
+    if (row < n) {
+      double au[1];
+      row_product<1>(md, md.A, row, GatherAoS64<1>{u}, au);
+      const double bb = b[row], r = bb - au[0];
+      rhs[row] = r;
+      acc[0] = fma(bb, bb, acc[0]);
+      acc[1] = fma(r, r, acc[1]);
+    }
+  }
+  if (reduce_tiles<2>(acc, md.part, blockIdx.x, ntile, &md.s->cnt[2], sh) && threadIdx.x == 0)
+    *ratio = acc[1] > 0.0 ? sqrt(acc[0] / acc[1]) : 1e300;
+}
+
+__global__ void __launch_bounds__(kBlock) rgd_axpy_kernel(double* __restrict__ u, const double* __restrict__ d, long n) {
+  const long i = (long)blockIdx.x * kBlock + threadIdx.x;
+  if (i < n) u[i] += d[i];
+}
+
+// The worst status of the solves so far (codes grow with severity: 0 ok, NOT_CONVERGED, NONFINITE).
+__global__ void rgd_note_status_kernel(const MeshDev* __restrict__ mds, int* worst) {
+  const int st = mds[0].s->status;
+  if (st > *worst) *worst = st;
+}
+
 }  // namespace
 
 cudaError_t launch_rgd_operator(const MeshDev* mds, int n, const int* src, cudaStream_t st) {
@@ -487,6 +530,23 @@ cudaError_t launch_rgd_rhs(const MeshDev* mds, int n, const double* V, const dou
                            double beta, const int* src, double* b, cudaStream_t st) {
   IG_PROF("rgd_rhs", st);
   rgd_rhs_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(mds, V, y, z, rho, 1.0 / (beta + rho), src, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rgd_warm(const MeshDev* mds, long n, const double* b, const double* u, double* rhs, double* ratio,
+                            cudaStream_t st) {
+  IG_PROF("rgd_warm", st);
+  rgd_warm_kernel<<<(unsigned)((n + kTileRows - 1) / kTileRows), kBlock, 0, st>>>(mds, b, u, rhs, ratio);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rgd_axpy(double* u, const double* d, long n, cudaStream_t st) {
+  rgd_axpy_kernel<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(u, d, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rgd_note_status(const MeshDev* mds, int* worst, cudaStream_t st) {
+  rgd_note_status_kernel<<<1, 1, 0, st>>>(mds, worst);
   return cudaGetLastError();
 }
 

@@ -57,13 +57,15 @@ __global__ void __launch_bounds__(256) vjp_face_kernel(const MeshDev* __restrict
   const int ntl = (md.m + kFaceTile - 1) / kFaceTile;
   const int f = tl.y * kFaceTile + threadIdx.x;
   const double* __restrict__ lam = md.lam;
+  const int clamp_on = md.clamp_on;
+  const double clamp_min = md.clamp_min;
   double gt_part = 0.0;
   if (f < md.m) {
     int vid[3];
     double P[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      vid[c] = __ldg(md.F + 3 * f + c);
+      vid[c] = face_vertex(md, f, c);
 #pragma unroll
       for (int d = 0; d < 3; ++d) P[c][d] = __ldg(V + 3 * (long)vid[c] + d);
     }
@@ -108,9 +110,15 @@ __global__ void __launch_bounds__(256) vjp_face_kernel(const MeshDev* __restrict
         double lu = 0.0;
 #pragma unroll
         for (int k = 0; k < K; ++k) lu = fma(L[a][k] - L[b][k], Uv[a][k] - Uv[b][k], lu);
-        omega[c] = mt2 * lu;
         // dl/dt = -<Lambda, L U> = -sum_c (cot_c / 2) lu_c = sum_c (dot_c / s / 2) lu_c
-        if (gt) gt_part = fma(0.5 * dot[c] * inv_s, lu, gt_part);
+        if (clamp_on && -dot[c] * inv_s < clamp_min) {
+          // a clamped corner holds cot = clamp_min: no term in dl/dV, clamp_min in dl/dt
+          omega[c] = 0.0;
+          if (gt) gt_part = fma(-0.5 * clamp_min, lu, gt_part);
+        } else {
+          omega[c] = mt2 * lu;
+          if (gt) gt_part = fma(0.5 * dot[c] * inv_s, lu, gt_part);
+        }
       }
     }
     if constexpr (MODE != 0) wa += (__ldg(cl.wm + vid[0]) + __ldg(cl.wm + vid[1])) + __ldg(cl.wm + vid[2]);
@@ -179,10 +187,11 @@ __global__ void __launch_bounds__(256) vjp_gather_kernel(const MeshDev* __restri
   double* __restrict__ gV = calls[tl.x].gV;
   double* __restrict__ gB = calls[tl.x].gB;
   double g0 = 0.0, g1 = 0.0, g2 = 0.0;
-  const int e0 = __ldg(md.incptr + v), e1 = __ldg(md.incptr + v + 1);
+  int e0, e1;
+  inc_range(md, v, e0, e1);
   for (int e = e0; e < e1; ++e) {
     const int fc = __ldg(&md.inc[e].x);
-    const double* src = md.gface + 9 * (long)(fc >> 2) + 3 * (fc & 3);
+    const double* src = md.gface + 9 * (long)inc_face(md, fc) + 3 * (fc & 3);
     g0 += src[0];
     g1 += src[1];
     g2 += src[2];
@@ -283,8 +292,13 @@ __device__ __noinline__ double face_grad64(const MeshDev& md, const CallDev& cl,
     double lu = 0.0;
 #pragma unroll
     for (int k = 0; k < K; ++k) lu = fma(L[a][k] - L[b][k], Uv[a][k] - Uv[b][k], lu);
-    omega[c] = mt2 * lu;
-    gt_part = fma(0.5 * dot[c] * inv_s, lu, gt_part);
+    if (md.clamp_on && -dot[c] * inv_s < md.clamp_min) {
+      omega[c] = 0.0;
+      gt_part = fma(-0.5 * md.clamp_min, lu, gt_part);
+    } else {
+      omega[c] = mt2 * lu;
+      gt_part = fma(0.5 * dot[c] * inv_s, lu, gt_part);
+    }
   }
   wa *= (1.0 / 3.0);
   const double Pv = -(omega[0] * dot[0] + omega[1] * dot[1] + omega[2] * dot[2]);
@@ -307,7 +321,7 @@ __device__ __noinline__ double face_grad64(const MeshDev& md, const CallDev& cl,
 __device__ __forceinline__ float hl_diff(float ha, float la, float hb, float lb) { return (ha - hb) + (la - lb); }
 
 template <int K>
-__global__ void __launch_bounds__(256) vjp32_face_kernel(const MeshDev* __restrict__ mds,
+__global__ void __launch_bounds__(256, 3) vjp32_face_kernel(const MeshDev* __restrict__ mds,
                                                          const CallDev* __restrict__ calls,
                                                          const int2* __restrict__ ftiles) {
   __shared__ double sh[8];
@@ -323,7 +337,7 @@ __global__ void __launch_bounds__(256) vjp32_face_kernel(const MeshDev* __restri
   if (f < md.m) {
     int vid[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) vid[c] = __ldg(md.F + 3 * f + c);
+    for (int c = 0; c < 3; ++c) vid[c] = face_vertex(md, f, c);
     const float4* __restrict__ vs = reinterpret_cast<const float4*>(md.vsplit);
     float4 ph[3], pl[3];
 #pragma unroll
@@ -380,6 +394,13 @@ __global__ void __launch_bounds__(256) vjp32_face_kernel(const MeshDev* __restri
       float th, tl32;
       split_f64(cl.t, th, tl32);
       const float mt2 = -0.5f * (th + tl32);
+      const bool clamp_on = md.clamp_on != 0;
+      float cmin = 0.f;
+      if (clamp_on) {
+        float ch, cl2;
+        split_f64(md.clamp_min, ch, cl2);
+        cmin = ch + cl2;
+      }
       float omega[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -389,8 +410,13 @@ __global__ void __launch_bounds__(256) vjp32_face_kernel(const MeshDev* __restri
         for (int k = 0; k < K; ++k)
           lu = fmaf(hl_diff(lh[a][k], ll[a][k], lh[b][k], ll[b][k]), hl_diff(uh[a][k], ul[a][k], uh[b][k], ul[b][k]),
                     lu);
-        omega[c] = mt2 * lu;
-        gt_part = fmaf(0.5f * dot[c] * inv_s, lu, gt_part);
+        if (clamp_on && -dot[c] * inv_s < cmin) {
+          omega[c] = 0.f;
+          gt_part = fmaf(-0.5f * cmin, lu, gt_part);
+        } else {
+          omega[c] = mt2 * lu;
+          gt_part = fmaf(0.5f * dot[c] * inv_s, lu, gt_part);
+        }
       }
       wa *= (1.0f / 3.0f);
       const float Pv = -(omega[0] * dot[0] + omega[1] * dot[1] + omega[2] * dot[2]);
@@ -464,10 +490,11 @@ __global__ void __launch_bounds__(256) vjp32_gather_kernel(const MeshDev* __rest
   double* __restrict__ gB = calls[tl.x].gB;
   const float4* __restrict__ gf = reinterpret_cast<const float4*>(md.gface);
   float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-  const int e0 = __ldg(md.incptr + v), e1 = __ldg(md.incptr + v + 1);
+  int e0, e1;
+  inc_range(md, v, e0, e1);
   for (int e = e0; e < e1; ++e) {
     const int fc = __ldg(&md.inc[e].x);
-    const float4 x = __ldg(gf + 3 * (long)(fc >> 2) + (fc & 3));
+    const float4 x = __ldg(gf + 3 * (long)inc_face(md, fc) + (fc & 3));
     g0 += x.x;
     g1 += x.y;
     g2 += x.z;

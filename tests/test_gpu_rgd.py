@@ -165,3 +165,32 @@ def test_admm_stopping_and_rho_balancing_match_oracle(api):
     assert st["rounds"] == rst[0] and st["rho"] == rst[3], (st, rst)
     assert st["primal"] <= 1e-3 and st["dual"] <= 1e-3
     assert np.abs(u.cpu().numpy() - ru).max() <= 1e-7 * np.abs(ru).max()
+
+
+def test_admm_reports_unconverged_u_steps(api):
+    """A u-step solve that stops at its iteration cap is reported (the worst status over the
+    rounds: a warning and solve_status in Python, IG_ERR_NOT_CONVERGED from the C ABI), and the
+    rounds still run and write their outputs."""
+    from paper_2602_12105_gb300 import _native as N
+    V, F, src = _case("grid70x50")
+    mesh = api.Mesh(_t(F, torch.int32), V.shape[0])
+    with pytest.warns(UserWarning, match="max_iter"):
+        u, y, z, st = mesh.rgd_admm(_t(V), src, 5.0, 0.1, 1.0, 3, opts=api.make_opts(rel_tol=1e-13, max_iter=2))
+    assert st["solve_status"] == N.IG_ERR_NOT_CONVERGED and st["rounds"] == 3
+    assert bool(torch.isfinite(u).all())
+    u, y, z, st = mesh.rgd_admm(_t(V), src, 5.0, 0.1, 1.0, 3, opts=api.make_opts(rel_tol=1e-10))
+    assert st["solve_status"] == N.IG_OK
+
+
+def test_admm_warm_start_skips_solves_near_the_fixed_point(api):
+    """Started from converged iterates, every round after the first finds the previous u already
+    within the solver tolerance and needs no solve; u stays the oracle's."""
+    from paper_2602_12105_gb300 import meshgen as mg
+    p = mg.config_grid(17, 17, seed=0, t=1.0)
+    V = p.V.copy()
+    V[:, 2] = 0.0
+    ru, ry, rz, rst = oracle.rgd_admm(V, p.F, [0], 1.0, 0.0, 1.0, 20000, tol=1e-12)
+    mesh = api.Mesh(_t(p.F, torch.int32), p.n)
+    u, y, z, st = mesh.rgd_admm(_t(V), [0], 1.0, 0.0, 1.0, 5, y=_t(ry), z=_t(rz), opts=api.make_opts(rel_tol=1e-8))
+    assert st["warm_rounds_without_solve"] >= 3, st
+    assert np.abs(u.cpu().numpy() - ru).max() <= 1e-7 * np.abs(ru).max()

@@ -9,8 +9,9 @@ it passes both alone in a fresh process and after the rest of the suite.
 Cases: a ragged multi-tile grid and an icosphere (two calls in a row each, plus the right-hand side
 given directly), k = 4 columns, and n = IG_NOALLOC_MAX_ROWS = 65536 rows (a 256 x 256 grid: the
 largest tile table, start table and partial-sum block the static layout allows), each checked
-element by element against the oracle's Jacobi-PCG solved to 1e-14; and an operator with a zero
-diagonal entry, which the call reports as IG_ERR_INVALID_ARG with and without info.
+element by element against the oracle's Jacobi-PCG solved to 1e-14; and faulty caller operators,
+which the call reports before solving: a zero diagonal entry (IG_ERR_INVALID_ARG), a column outside
+[0, n) and a row range beyond nnz (IG_ERR_INDEX_OUT_OF_RANGE), with and without info.
 """
 import ctypes
 
@@ -116,9 +117,8 @@ def test_noalloc_at_the_row_limit(env):
 
 
 def test_noalloc_reports_a_zero_diagonal(env):
-    """A caller operator whose row 5 has a zero diagonal entry: the setup kernel flags it, and the
-    call returns IG_ERR_INVALID_ARG whether or not info is asked for. The iteration cap keeps the
-    (meaningless) solve short."""
+    """A caller operator whose row 5 has a zero diagonal entry: the set-up kernel flags it, and the
+    call returns IG_ERR_INVALID_ARG, without solving, whether or not info is asked for."""
     api, N, lib = env
     V, F, t, B, T = case("grid61x53", seed=9)
     mesh, rowptr, col, A, M, stream = _setup(api, V, F, t)
@@ -136,6 +136,30 @@ def test_noalloc_reports_a_zero_diagonal(env):
     assert st == N.IG_ERR_INVALID_ARG
     # the next call with the good operator starts clean
     st, info = _call(lib, N, rowptr, col, A, M, V.shape[0], mesh.nnz, Bt, U, stream, api.make_opts(rel_tol=1e-12))
+    assert st == N.IG_OK, info
+
+
+def test_noalloc_rejects_out_of_range_columns_before_solving(env):
+    """A column index outside [0, n) in the caller's pattern is found by the set-up kernel (which
+    reads every row's columns once, within the row ranges it has checked against nnz) and the call
+    returns IG_ERR_INDEX_OUT_OF_RANGE without launching the solve: U keeps its contents."""
+    api, N, lib = env
+    V, F, t, B, T = case("grid61x53", seed=10)
+    mesh, rowptr, col, A, M, stream = _setup(api, V, F, t)
+    col_bad = col.clone()
+    col_bad[7] = V.shape[0] + 5
+    Bt = torch.from_numpy(B).to("cuda:0")
+    U = torch.full_like(Bt, 3.0)
+    st, info = _call(lib, N, rowptr, col_bad, A, M, V.shape[0], mesh.nnz, Bt, U, stream, api.make_opts(rel_tol=1e-10))
+    assert st == N.IG_ERR_INDEX_OUT_OF_RANGE and info["status"] == N.IG_ERR_INDEX_OUT_OF_RANGE, (st, info)
+    assert bool((U == 3.0).all())
+    # a row range beyond nnz
+    rp_bad = rowptr.clone()
+    rp_bad[-1] = mesh.nnz + 4
+    st, _ = _call(lib, N, rp_bad, col, A, M, V.shape[0], mesh.nnz, Bt, U, stream, api.make_opts(rel_tol=1e-10),
+                  want_info=False)
+    assert st == N.IG_ERR_INDEX_OUT_OF_RANGE
+    st, info = _call(lib, N, rowptr, col, A, M, V.shape[0], mesh.nnz, Bt, U, stream, api.make_opts(rel_tol=1e-10))
     assert st == N.IG_OK, info
 
 
