@@ -536,7 +536,9 @@ ig_status ig_mesh_upload(ig_ctx* ctx, const int32_t* F_dev, int64_t m, int64_t n
   md.inc = inc;
   md.err = err;
   const size_t nv = (size_t)n * kMaxK;
-  const size_t npart = std::max(std::max((size_t)md.ntiles, (size_t)md.ntiles32) * kPartStride,
+  // partial sums: the loop kernels' tiles (twice over for the cluster loop of small meshes, which
+  // keeps the SpMV's and the update's partials apart), and the VJP's per-face-tile sums of dl/dt
+  const size_t npart = std::max(std::max((size_t)md.ntiles, (size_t)md.ntiles32) * 2 * kPartStride,
                                 (size_t)(mi + 255) / 256) + 8;
   UP_CK(mesh_alloc(M, &md.facew, 4 * (size_t)m), "alloc");
   UP_CK(mesh_alloc(M, &md.A, (size_t)nnz_sell), "alloc");

@@ -34,6 +34,9 @@ __device__ __forceinline__ bool positive_finite(double x) {
   return b > 0 && (b & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
 }
 
+// CLAMP: some mesh of the group clamps its cotangents (the check is compiled out otherwise: this
+// kernel is bound by FP64 instructions).
+template <bool CLAMP>
 __global__ void __launch_bounds__(256) face_kernel(const MeshDev* __restrict__ mds, const CallDev* __restrict__ calls,
                                                    const int2* __restrict__ ftiles) {
   const int2 tl = ftiles[blockIdx.x];
@@ -75,7 +78,7 @@ __global__ void __launch_bounds__(256) face_kernel(const MeshDev* __restrict__ m
     w.y = h * (d2[0] * d0[0] + d2[1] * d0[1] + d2[2] * d0[2]);
     w.z = h * (d0[0] * d1[0] + d0[1] * d1[1] + d0[2] * d1[2]);
     w.w = s2 * inv_s * (1.0 / 6.0);
-    if (md.clamp_on) {  // w_c = (t/2) cot_c >= (t/2) clamp_min
+    if (CLAMP && md.clamp_on) {  // w_c = (t/2) cot_c >= (t/2) clamp_min
       const double wmin = half_t * md.clamp_min;
       w.x = fmax(w.x, wmin);
       w.y = fmax(w.y, wmin);
@@ -370,7 +373,8 @@ cudaError_t launch_assemble(Group& g, int mode, cudaStream_t st) {
   }
   {
     IG_PROF("assemble_face", st);
-    face_kernel<<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
+    if (group_any_clamp(g)) face_kernel<true><<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
+    else face_kernel<false><<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   {

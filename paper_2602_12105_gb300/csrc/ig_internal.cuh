@@ -40,6 +40,7 @@ constexpr int kMaxTileRows32 = 64 * kTileRows;      // the largest mixed-precisi
 constexpr int kMaxPasses64 = 8;      // FP64 solver tiles: at most 8 passes of kBlock rows
 constexpr int kTileRows64 = kBlock * kMaxPasses64;
 constexpr int kMaxK = 4;
+constexpr int kSmallTiles = 16;      // a single mesh of at most this many FP64 tiles loops in one cluster
 constexpr int kPartStride = 8;       // doubles per tile in the partial-sum arrays
 
 // Device error word bits (OR-ed by kernels, decoded on the host).
@@ -337,6 +338,12 @@ struct Group {
   std::vector<MeshDev> host_mds;  // host copy of mds
 };
 
+// Does some mesh of the group clamp its cotangents (host copy of the descriptors)?
+inline bool group_any_clamp(const Group& g) {
+  for (const MeshDev& md : g.host_mds)
+    if (md.clamp_on) return true;
+  return false;
+}
 cudaError_t group_init(Group& g, const MeshDev* host_mds, int nmesh, int slots64, int slots32, cudaStream_t st);
 cudaError_t group_upload_mds(Group& g, cudaStream_t st);
 cudaError_t group_set_calls(Group& g, const CallDev* calls, cudaStream_t st);

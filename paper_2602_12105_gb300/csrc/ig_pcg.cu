@@ -287,6 +287,110 @@ __global__ void __launch_bounds__(kBlock, 4) update_kernel(const MeshDev* __rest
   }
 }
 
+// ------------------------------------------------------------------------------- small meshes
+// The whole iteration loop of a small single mesh (at most kSmallTiles FP64 tiles) in one
+// thread-block cluster with one CTA per tile. A CTA runs its tile through the tile bodies of the
+// multi-CTA kernels and publishes the tile's partial sums; after a cluster barrier every CTA adds
+// all the partials in tile order and runs the finish step on its own shared-memory copy of the
+// solve state (the same inputs and arithmetic in every CTA, so the copies stay equal), and goes
+// on. Two cluster barriers per iteration replace the kernel boundaries, the last-CTA hand-offs
+// and the graph loop's node transitions, which make up most of an iteration of a mesh of a few
+// tiles. The arithmetic and its order are those of the multi-CTA path: the same bits. The SpMV's
+// and the update's partials live in separate halves of the partial buffer, so a CTA that runs
+// ahead never overwrites partials that another CTA is still adding.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <int NV, typename Finish>
+__device__ __forceinline__ void finish_cluster(TileCtx& tc, SolveScal& st, const double* part, int nt,
+                                               const Finish& finish) {
+  double v[NV];
+  gather_partials<NV>(part, nt, v);
+  if (threadIdx.x < (int)(sizeof(SolveScal) / 4))
+    reinterpret_cast<unsigned*>(&tc.cur)[threadIdx.x] = reinterpret_cast<const unsigned*>(&st)[threadIdx.x];
+  tile_reduce<NV>(v, tc.red[0], tc.tot);
+  __syncthreads();
+  if (threadIdx.x < 32) finish(&st, tc.cur, tc.tot);
+  __syncthreads();
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) solve_cluster_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl) {
+  __shared__ TileCtx tc;
+  __shared__ SolveScal st;
+  load_mesh(mds, 0, tc);
+  const int nt = tc.md.ntiles, tile = blockIdx.x;
+  static_assert(sizeof(SolveScal) % 4 == 0 && sizeof(SolveScal) / 4 <= kBlock, "SolveScal copy");
+  if (threadIdx.x < (int)(sizeof(SolveScal) / 4))
+    reinterpret_cast<unsigned*>(&st)[threadIdx.x] = __ldcg(reinterpret_cast<const unsigned*>(tc.md.s) + threadIdx.x);
+  __syncthreads();
+  double* part_spmv = tc.md.part;
+  double* part_upd = tc.md.part + (long)nt * kPartStride;
+  const int cap = __ldcg(&ctl->cap);
+  int it = 0;
+  for (; it < cap && !st.done; ++it) {
+    if (threadIdx.x < kMaxK) tc.sn.beta[threadIdx.x] = st.beta[threadIdx.x];
+    __syncthreads();
+    spmv_tile<K>(tc.md, tile, tc.sn, tc.red[1], part_spmv + (long)tile * kPartStride);
+    cluster_sync_all();
+    finish_cluster<K>(tc, st, part_spmv, nt,
+                      [](SolveScal* s, const SolveScal& cur, const double* v) { finish_spmv(s, cur, K, v); });
+    if (threadIdx.x < kMaxK) tc.sn.alpha[threadIdx.x] = st.alpha[threadIdx.x];
+    __syncthreads();
+    update_tile<K>(tc.md, tile, tc.sn, tc.red[1], part_upd + (long)tile * kPartStride);
+    cluster_sync_all();
+    finish_cluster<2 * K>(tc, st, part_upd, nt,
+                          [](SolveScal* s, const SolveScal& cur, const double* v) { finish_update(s, cur, K, v); });
+  }
+  if (blockIdx.x == 0) {
+    if (threadIdx.x < (int)(sizeof(SolveScal) / 4))
+      reinterpret_cast<unsigned*>(tc.md.s)[threadIdx.x] = reinterpret_cast<const unsigned*>(&st)[threadIdx.x];
+    if (threadIdx.x == 0) {
+      ctl->iter = it;
+      ctl->all_done = 1;
+    }
+  }
+}
+
+// Launch of the cluster loop: one cluster of ntiles CTAs (non-portable sizes above 8 allowed).
+// Returns false, with nothing launched, when the device refuses that cluster.
+template <int K>
+bool launch_cluster_loop(Group& g, cudaStream_t st) {
+  const int nt = g.host_mds[0].ntiles;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(solve_cluster_kernel<K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    attr_set = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nt, 1, 1);
+  cfg.blockDim = dim3(kBlock, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nt;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, solve_cluster_kernel<K>, &cfg) != cudaSuccess || clusters < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaLaunchKernelEx(&cfg, solve_cluster_kernel<K>, (const MeshDev*)g.mds, g.ctl) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
 // ------------------------------------------------------------------------------- true residual
 // trueres = ||rhs - A x|| / ||rhs|| per column with x = io.out (the written solution).
 template <int K>
@@ -404,6 +508,9 @@ cudaError_t host_loop_k(Group& g, int max_it, int poll, cudaStream_t st) {
 
 template <int K>
 cudaError_t loop_k(Group& g, const ig_solve_opts& o, cudaStream_t st) {
+  if (o.launch == IG_LAUNCH_GRAPH && !prof_on() && g.nmesh == 1 && g.host_mds[0].ntiles <= kSmallTiles &&
+      launch_cluster_loop<K>(g, st))
+    return cudaSuccess;
   if (o.launch == IG_LAUNCH_GRAPH && !prof_on()) {
     SolvePlan& pl = g.plans[0][K];
     if (!pl.exec) {

@@ -39,7 +39,9 @@ namespace {
 constexpr int kFaceTile = 256;
 
 // MODE 0: the solve terms; 1: the solve terms and the mass weights; 2: the mass weights alone.
-template <int K, int MODE>
+// CLAMP: some mesh of the group clamps its cotangents (compiled out otherwise: this kernel is bound
+// by FP64 instructions).
+template <int K, int MODE, bool CLAMP>
 __global__ void __launch_bounds__(256) vjp_face_kernel(const MeshDev* __restrict__ mds,
                                                        const CallDev* __restrict__ calls,
                                                        const int2* __restrict__ ftiles) {
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(256) vjp_face_kernel(const MeshDev* __restrict
 #pragma unroll
         for (int k = 0; k < K; ++k) lu = fma(L[a][k] - L[b][k], Uv[a][k] - Uv[b][k], lu);
         // dl/dt = -<Lambda, L U> = -sum_c (cot_c / 2) lu_c = sum_c (dot_c / s / 2) lu_c
-        if (clamp_on && -dot[c] * inv_s < clamp_min) {
+        if (CLAMP && clamp_on && -dot[c] * inv_s < clamp_min) {
           // a clamped corner holds cot = clamp_min: no term in dl/dV, clamp_min in dl/dt
           omega[c] = 0.0;
           if (gt) gt_part = fma(-0.5 * clamp_min, lu, gt_part);
@@ -541,9 +543,13 @@ template <int K>
 cudaError_t vjp_k(Group& g, int mode, cudaStream_t st) {
   {
     IG_PROF("vjp_face", st);
-    if (mode == 0) vjp_face_kernel<K, 0><<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
-    else if (mode == 1) vjp_face_kernel<K, 1><<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
-    else vjp_face_kernel<K, 2><<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
+    const bool cl = group_any_clamp(g);
+    if (mode == 0 && cl) vjp_face_kernel<K, 0, true><<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
+    else if (mode == 0) vjp_face_kernel<K, 0, false><<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
+    else if (mode == 1 && cl)
+      vjp_face_kernel<K, 1, true><<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
+    else if (mode == 1) vjp_face_kernel<K, 1, false><<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
+    else vjp_face_kernel<K, 2, false><<<g.nface_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.face_tiles);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

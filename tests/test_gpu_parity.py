@@ -248,3 +248,23 @@ def test_error_statuses(api):
     with pytest.raises(N.IgError) as e:
         mesh.solve(_t(np.zeros((Vc.shape[0], 5))))
     assert e.value.status == N.IG_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name", ["tetra", "ico3", "planar_jitter", "sliver", "grid61x53"])
+def test_small_mesh_cluster_loop_same_bits(api, name):
+    """A single mesh of at most 16 FP64 tiles runs its whole iteration loop in one thread-block
+    cluster (the graph launch mode; grid61x53 has 13 tiles); the host-launched mode runs the
+    multi-CTA kernels. Same tile bodies, same partial sums in the same order: the same bits,
+    forward and adjoint, and the same iteration counts."""
+    V, F, t, B, T = case(name, seed=31)
+    mesh = api.Mesh(_t(F, torch.int32), V.shape[0])
+    mesh.assemble(_t(V), t)
+    res = {}
+    for launch in ("graph", "host"):
+        opts = api.make_opts(rel_tol=1e-12, launch=launch)
+        U, fi = mesh.solve(_t(B), opts=opts, info=True)
+        gV, gB, gt, ai = mesh.adjoint(_t(V), _t(B), False, U, U - _t(T), want_gt=True, opts=opts, info=True)
+        res[launch] = (U, gV, gt, fi["iterations"], ai["iterations"])
+    a, b = res["graph"], res["host"]
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
+    assert a[3:] == b[3:]

@@ -126,3 +126,24 @@ def test_round_budget_is_never_exceeded(mods, nmesh):
         assert info1["iterations"] == iters
         assert torch.equal(U, U1)
     batch.close()
+
+
+def test_served_results_match_the_oracle(mods):
+    """Served requests (mixed precision, continuous batching, solved to 1e-10) against the CPU
+    oracle solved to 1e-13 on the same inputs. The served solves stop at a relative residual of
+    1e-10, so U is within cond(A) 1e-10 of the exact solution: A = M + t L has cond(A) about
+    1 + 8 t / h^2, at most about 60 for these meshes (grid sides up to 89, t = 1e-3; icospheres of
+    levels 2..4, t = 3e-3). U is held to 1e-8 and dl/dV (two solves) to 1e-7, relative 2-norm and
+    largest entry."""
+    import oracle
+    from gpu_util import assert_close
+    api, meshgen, serve = mods
+    reqs = _requests(meshgen, serve, 6, 0.05, seed=3)
+    srv = serve.Server(precision="mixed", quantum=8, keep_results=True)
+    done = srv.run(reqs, realtime=True)
+    assert all(r.status == 0 for r in done)
+    for r in done:
+        p = next(q for q in reqs if q.rid == r.rid).make()
+        ref = oracle.forward_adjoint(p.V, p.F, p.B, p.t, p.T, False, tol=1e-13, method="pcg")
+        assert_close(r.U.cpu().numpy(), ref["U"], 1e-8, f"U of request {r.rid}")
+        assert_close(r.gV.cpu().numpy(), ref["gV"], 1e-7, f"dl/dV of request {r.rid}")
