@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="grid1024",
                     help="grid1024 (default), ico3, grid4096x2048, or any gridS / gridXxY of the same family")
-    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "mixed32"])
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -52,7 +52,7 @@ def parse():
                     help="skip the other workloads (mixed grid, largest mesh, 256-mesh batch, serving)")
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="requests in the bounded sample of the serving stream")
-    ap.add_argument("--variants", default="mixed,largest,batch,fairing,eigs,rgd,serve",
+    ap.add_argument("--variants", default="small,mixed,largest,batch,fairing,eigs,rgd,serve",
                     help="comma list of the extra workloads to run")
     ap.add_argument("--fma-peak", action="store_true",
                     help="measure the FP64 and FP32 FMA throughput of this GPU (ig_measure_fma_peak) with the SM "
@@ -615,6 +615,21 @@ def variant_mixed_grid(api, _native, dev, p, tol, steps, fp64_U, fp64_gV, clocks
     return out
 
 
+def variant_small(api, _native, dev, steps=300):
+    """The small single mesh of the plain FP64 configuration: the noisy level-3 icosphere (642
+    vertices), B = V, loss 1/2 |U - clean sphere|^2, forward + adjoint to 1e-12; a mesh of three
+    FP64 tiles, whose solves loop inside one thread-block cluster."""
+    from paper_2602_12105_gb300 import meshgen as mg
+    p = mg.config_ico3(0)
+    r = single_mesh(api, _native, dev, p, "fp64", 1e-12, steps, 10, profile=False)
+    r["mesh"].close()
+    return {"workload": f"{p.name}: {p.n} vertices, {p.m} faces, B = V, FP64, forward + adjoint to 1e-12",
+            "unit": UNIT, "value": round(r["solves_per_s"], 2), "ms_per_step": round(r["ms_per_step"], 4),
+            "steps": steps, "iterations": {"forward": r["finfo"]["iterations"], "adjoint": r["ainfo"]["iterations"]},
+            "true_rel_residual": {"forward": max(r["finfo"]["true_rel_residual"]),
+                                  "adjoint": max(r["ainfo"]["true_rel_residual"])}}
+
+
 def variant_largest(api, _native, dev, tol, steps, clocks, alu):
     """The largest single mesh (4096 x 2048 grid, 8.4M vertices) in mixed precision, with its HBM
     roofline, and its error against the FP64 GPU path on the same mesh."""
@@ -1014,6 +1029,8 @@ def run_variants(args, p, U64, gV64, dev, alu):
     out = {}
     t_start = time.perf_counter()
     clocks_guess = {"sm_mhz": None}
+    if "small" in want:
+        out["ico3_fp64"] = variant_small(api, _native, dev)
     if "mixed" in want:
         out["grid1024_mixed"] = variant_mixed_grid(api, _native, dev, p, args.tol, 100, U64, gV64, clocks_guess, alu)
     if "largest" in want:

@@ -235,29 +235,26 @@ __global__ void __launch_bounds__(kBlock, 4) spmv_mixed_kernel(const MeshDev* __
         const float* __restrict__ A = md.A32;
         const float* __restrict__ p = md.p32;
         float* __restrict__ q32 = md.q32;
-        PassSum<K> sum;
-        for (long base = t0; base < t1; base += kTileRows) {
-          float pq[K];
+        float pq[K];
 #pragma unroll
-          for (int c = 0; c < K; ++c) pq[c] = 0.f;
+        for (int c = 0; c < K; ++c) pq[c] = 0.f;
+        // the SpMV's tiles have at most kTileRows rows: one pass
 #pragma unroll
-          for (int rr = 0; rr < kRowsPerThread; ++rr) {
-            const long row = base + rr * kBlock + threadIdx.x;
-            if (row < t1) {
-              float q[K];
-              row_product<K>(md, A, row, GatherP32<K>{p}, q);
-              float pi[K];
-              load_row32<K>(p, row, pi);
+        for (int rr = 0; rr < kRowsPerThread; ++rr) {
+          const long row = t0 + rr * kBlock + threadIdx.x;
+          if (row < t1) {
+            float q[K];
+            row_product<K>(md, A, row, GatherP32<K>{p}, q);
+            float pi[K];
+            load_row32<K>(p, row, pi);
 #pragma unroll
-              for (int c = 0; c < K; ++c) {
-                q32[c * nn + row] = q[c];
-                pq[c] = fmaf(pi[c], q[c], pq[c]);
-              }
+            for (int c = 0; c < K; ++c) {
+              q32[c * nn + row] = q[c];
+              pq[c] = fmaf(pi[c], q[c], pq[c]);
             }
           }
-          sum.add(pq);
         }
-        tile_reduce<K>(sum.s, red, out);
+        tile_reduce<K>(pq, red, out);
       },
       [](const MeshDev& md, const SolveScal& cur, const double* v) { finish_spmv(md.s, cur, K, v); });
 }
@@ -280,20 +277,19 @@ __global__ void __launch_bounds__(kBlock) resid_mixed_kernel(const MeshDev* __re
         double acc[K];
 #pragma unroll
         for (int c = 0; c < K; ++c) acc[c] = 0.0;
-        for (long base = t0; base < t1; base += kTileRows) {
+        // tiles of at most kTileRows rows: one pass
 #pragma unroll
-          for (int rr = 0; rr < kRowsPerThread; ++rr) {
-            const long row = base + rr * kBlock + threadIdx.x;
-            if (row < t1) {
-              double ax[K];
-              if (geom32) row_product<K>(md, md.A32, row, GatherSoA64<K>{x, nn}, ax);
-              else row_product<K>(md, md.A, row, GatherSoA64<K>{x, nn}, ax);
+        for (int rr = 0; rr < kRowsPerThread; ++rr) {
+          const long row = t0 + rr * kBlock + threadIdx.x;
+          if (row < t1) {
+            double ax[K];
+            if (geom32) row_product<K>(md, md.A32, row, GatherSoA64<K>{x, nn}, ax);
+            else row_product<K>(md, md.A, row, GatherSoA64<K>{x, nn}, ax);
 #pragma unroll
-              for (int c = 0; c < K; ++c) {
-                const double res = md.rhs[c * nn + row] - ax[c];
-                md.r[c * nn + row] = res;
-                acc[c] = fma(res, res, acc[c]);
-              }
+            for (int c = 0; c < K; ++c) {
+              const double res = md.rhs[c * nn + row] - ax[c];
+              md.r[c * nn + row] = res;
+              acc[c] = fma(res, res, acc[c]);
             }
           }
         }
@@ -424,27 +420,25 @@ __global__ void __launch_bounds__(kBlock, 4) pupdate_mixed_kernel(const MeshDev*
                       const float* __restrict__ D32 = md.Dinv32;
                       const float* __restrict__ r32 = md.r32;
                       float* __restrict__ p32 = md.p32;
-                      constexpr int R = kRowsPerThread;
-                      for (long base = t0; base < t1; base += kTileRows) {
-                        float d[R], pi[R][K], rs[R][K];
+                      constexpr int R = kRowsPerThread;  // one pass: tiles of at most kTileRows rows
+                      float d[R], pi[R][K], rs[R][K];
 #pragma unroll
-                        for (int u = 0; u < R; ++u) {
-                          const long row = base + u * kBlock + threadIdx.x;
-                          if (row < t1) {
-                            d[u] = D32[row];
-                            load_row32<K>(p32, row, pi[u]);
+                      for (int u = 0; u < R; ++u) {
+                        const long row = t0 + u * kBlock + threadIdx.x;
+                        if (row < t1) {
+                          d[u] = D32[row];
+                          load_row32<K>(p32, row, pi[u]);
 #pragma unroll
-                            for (int c = 0; c < K; ++c) rs[u][c] = r32[c * nn + row];
-                          }
+                          for (int c = 0; c < K; ++c) rs[u][c] = r32[c * nn + row];
                         }
+                      }
 #pragma unroll
-                        for (int u = 0; u < R; ++u) {
-                          const long row = base + u * kBlock + threadIdx.x;
-                          if (row < t1) {
+                      for (int u = 0; u < R; ++u) {
+                        const long row = t0 + u * kBlock + threadIdx.x;
+                        if (row < t1) {
 #pragma unroll
-                            for (int c = 0; c < K; ++c)
-                              p32[row * KPm<K>::v + c] = fmaf(beta[c], pi[u][c], d[u] * rs[u][c]);
-                          }
+                          for (int c = 0; c < K; ++c)
+                            p32[row * KPm<K>::v + c] = fmaf(beta[c], pi[u][c], d[u] * rs[u][c]);
                         }
                       }
                     } else {
@@ -453,15 +447,13 @@ __global__ void __launch_bounds__(kBlock, 4) pupdate_mixed_kernel(const MeshDev*
                       for (int c = 0; c < K; ++c) sc[c] = tc.sn.scale[c];
                       const float* __restrict__ x32 = md.x32;
                       double* __restrict__ x = md.x;
-                      for (long base = t0; base < t1; base += kTileRows) {
 #pragma unroll
-                        for (int rr = 0; rr < kRowsPerThread; ++rr) {
-                          const long row = base + rr * kBlock + threadIdx.x;
-                          if (row < t1) {
+                      for (int rr = 0; rr < kRowsPerThread; ++rr) {
+                        const long row = t0 + rr * kBlock + threadIdx.x;
+                        if (row < t1) {
 #pragma unroll
-                            for (int c = 0; c < K; ++c)
-                              x[c * nn + row] = fma(sc[c], (double)x32[c * nn + row], x[c * nn + row]);
-                          }
+                          for (int c = 0; c < K; ++c)
+                            x[c * nn + row] = fma(sc[c], (double)x32[c * nn + row], x[c * nn + row]);
                         }
                       }
                     }
