@@ -64,7 +64,8 @@ __device__ __noinline__ void finish_init(SolveScal* s, int k, const double* acc,
 
 // Convergence test per column (recursive residual), beta_c = rz_new / rz, iteration count. Runs on
 // warp 0 of the CTA that completes the mesh: lane c takes column c, lane 0 the mesh's fields.
-__device__ __noinline__ void finish_update(SolveScal* s, const SolveScal& cur, int k, const double* acc) {
+// Returns (on lane 0) whether the mesh is now done.
+__device__ __noinline__ int finish_update(SolveScal* s, const SolveScal& cur, int k, const double* acc) {
   const int c = threadIdx.x & 31;
   int act = 0, bad = 0;
   if (c < k && cur.active[c] != 0) {
@@ -87,19 +88,22 @@ __device__ __noinline__ void finish_update(SolveScal* s, const SolveScal& cur, i
   }
   const int nact = __popc(__ballot_sync(0xffffffffu, act));
   const int anybad = __any_sync(0xffffffffu, bad);
+  int done = 0;
   if (c == 0) {
     const int it = cur.iter + 1;
     s->iter = it;
     if (anybad) {
       s->status = IG_ERR_NONFINITE;
-      s->done = 1;
+      done = 1;
     } else if (nact == 0) {
-      s->done = 1;
+      done = 1;
     } else if (it >= cur.max_iter) {
       s->status = IG_ERR_NOT_CONVERGED;
-      s->done = 1;
+      done = 1;
     }
+    if (done) s->done = 1;
   }
+  return done;
 }
 
 // ------------------------------------------------------------------------------- init
@@ -244,15 +248,17 @@ __device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const S
 }
 
 // Loop control of a group of one mesh, on lane 0 of the CTA that completes the mesh, right after
-// its finish step: the loop stops when the mesh is done or the cap is reached. A launch in which
-// the mesh takes no part is stopped by its CTA 0 at entry, so every launch either completes the
-// mesh (and counts towards the cap) or stops the loop. (A group of several meshes needs every CTA
-// of the launch to have finished, for the list rebuilds: loop_control.)
-__device__ __noinline__ void single_loop_control(const SolveScal* s, LoopCtl* ctl, cudaGraphConditionalHandle handle,
-                                                 int use_graph) {
-  const int it = __ldcg(&ctl->iter) + 1;
+// its finish step: the loop stops when the mesh is done or the cap is reached. The iteration
+// counter and the cap were read at the kernel's entry (only this step writes the counter), and
+// done is the finish step's own result, so the step makes no global read. A launch in which the
+// mesh takes no part is stopped by its CTA 0 at entry, so every launch either completes the mesh
+// (and counts towards the cap) or stops the loop. (A group of several meshes needs every CTA of
+// the launch to have finished, for the list rebuilds: loop_control.)
+__device__ __forceinline__ void single_loop_control(int done, int iter, int cap, LoopCtl* ctl,
+                                                    cudaGraphConditionalHandle handle, int use_graph) {
+  const int it = iter + 1;
   ctl->iter = it;
-  if (s->done || it >= __ldcg(&ctl->cap)) {  // done: this thread's own write in the finish step
+  if (done || it >= cap) {
     ctl->all_done = 1;
     if (use_graph) cudaGraphSetConditional(handle, 0u);
   }
@@ -262,10 +268,13 @@ template <int K>
 __global__ void __launch_bounds__(kBlock, 4) update_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L,
     cudaGraphConditionalHandle handle, int use_graph) {
   __shared__ TileCtx tc;
-  __shared__ int s_single, s_stop;
+  __shared__ int s_single, s_stop, s_iter, s_cap, s_done;
   if (threadIdx.x == 0) {
     s_single = (__ldcg(&ctl->nmesh) == 1);
     s_stop = __ldcg(&ctl->all_done);
+    s_iter = __ldcg(&ctl->iter);
+    s_cap = __ldcg(&ctl->cap);
+    s_done = 0;
     // a group of one mesh whose mesh takes no part in this launch (done, or the loop stopped):
     // no CTA completes it, so the loop is stopped here
     if (s_single && blockIdx.x == 0 && (s_stop || __ldcg(&mds[0].s->done))) {
@@ -278,12 +287,15 @@ __global__ void __launch_bounds__(kBlock, 4) update_kernel(const MeshDev* __rest
   tile_loop<2 * K>(
       mds, L, 0, 1, tc, [&](const ScalSnap& x) { return !x.done && !s_stop; },
       [&](const MeshDev& md, int tile, double* red, double* out) { update_tile<K>(md, tile, tc.sn, red, out); },
-      [](const MeshDev& md, const SolveScal& cur, const double* v) { finish_update(md.s, cur, K, v); });
+      [&](const MeshDev& md, const SolveScal& cur, const double* v) {
+        const int done = finish_update(md.s, cur, K, v);
+        if (threadIdx.x == 0) s_done = done;
+      });
   if (!s_single) {
     loop_control(mds, ctl, handle, use_graph);
   } else if (tc.last && threadIdx.x == 0) {
     // the CTA that completed the mesh (its finish step is done: flush_tiles ends in a barrier)
-    single_loop_control(tc.md.s, ctl, handle, use_graph);
+    single_loop_control(s_done, s_iter, s_cap, ctl, handle, use_graph);
   }
 }
 
