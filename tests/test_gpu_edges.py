@@ -94,3 +94,28 @@ def test_batch_column_counts_and_single_mesh_batch(api, k):
             ref = _oracle_solve(q.V, q.F, q.t, B.cpu().numpy())
             assert rel2(U.cpu().numpy(), ref) <= 1e-10
         batch.close()
+
+
+@pytest.mark.parametrize("max_iter", [1, 2, 3, 7])
+def test_iteration_cap_is_exact_on_a_multi_tile_mesh(api, max_iter):
+    """A solve that cannot meet its tolerance stops after exactly max_iter iterations with
+    NOT_CONVERGED: in the graph loop (two iterations per pass of its WHILE body, so an odd cap ends
+    inside a pass, and the completing CTA decides from the counter and cap it read at entry) and
+    in the host loop, with the same bits. The iterate is the oracle's Jacobi-PCG iterate after as
+    many iterations (the same algorithm in FP64; only the order of the sums differs)."""
+    from paper_2602_12105_gb300 import _native as N
+    from paper_2602_12105_gb300 import meshgen as mg
+    p = mg.config_grid(160, 150, seed=5)  # 24,000 rows: many FP64 tiles, the multi-CTA loop
+    B = np.random.default_rng(6).uniform(-1, 1, (p.n, 3))
+    mesh = api.Mesh(_t(p.F, torch.int32), p.n)
+    mesh.assemble(_t(p.V), p.t)
+    out = {}
+    for launch in ("graph", "host"):
+        U, info = mesh.solve(_t(B), opts=api.make_opts(rel_tol=1e-300, max_iter=max_iter, launch=launch), info=True)
+        assert info["status"] == N.IG_ERR_NOT_CONVERGED and info["iterations"] == max_iter, (launch, info)
+        out[launch] = U.cpu().numpy()
+    assert np.array_equal(out["graph"], out["host"])
+    rowptr, col, A, L, M = oracle.operator(p.V, p.F, p.t)
+    X, iters, _, st = oracle.pcg_solve(rowptr, col, A, M[:, None] * B, tol=1e-300, max_iter=max_iter)
+    assert st == oracle.ERR_NOT_CONVERGED and list(iters) == [max_iter] * 3
+    assert rel2(out["graph"], X) <= 1e-12
