@@ -247,23 +247,6 @@ __device__ __forceinline__ void update_tile(const MeshDev& md, int tile, const S
   tile_reduce<2 * K>(acc, red, out);
 }
 
-// Loop control of a group of one mesh, on lane 0 of the CTA that completes the mesh, right after
-// its finish step: the loop stops when the mesh is done or the cap is reached. The iteration
-// counter and the cap were read at the kernel's entry (only this step writes the counter), and
-// done is the finish step's own result, so the step makes no global read. A launch in which the
-// mesh takes no part is stopped by its CTA 0 at entry, so every launch either completes the mesh
-// (and counts towards the cap) or stops the loop. (A group of several meshes needs every CTA of
-// the launch to have finished, for the list rebuilds: loop_control.)
-__device__ __forceinline__ void single_loop_control(int done, int iter, int cap, LoopCtl* ctl,
-                                                    cudaGraphConditionalHandle handle, int use_graph) {
-  const int it = iter + 1;
-  ctl->iter = it;
-  if (done || it >= cap) {
-    ctl->all_done = 1;
-    if (use_graph) cudaGraphSetConditional(handle, 0u);
-  }
-}
-
 template <int K>
 __global__ void __launch_bounds__(kBlock, 4) update_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L,
     cudaGraphConditionalHandle handle, int use_graph) {

@@ -121,8 +121,8 @@ __device__ __noinline__ void finish_residual(SolveScal* s, const SolveScal& cur,
   }
 }
 
-// After forming r32 = r64 / scale: start a new inner solve.
-__device__ __noinline__ void finish_restart(SolveScal* s, const SolveScal& cur, int k, const double* acc) {
+// After forming r32 = r64 / scale: start a new inner solve. Returns (on lane 0) the new phase.
+__device__ __noinline__ int finish_restart(SolveScal* s, const SolveScal& cur, int k, const double* acc) {
   const int c = threadIdx.x & 31;
   int act = 0;
   if (c < k) {
@@ -135,14 +135,17 @@ __device__ __noinline__ void finish_restart(SolveScal* s, const SolveScal& cur, 
     s->relres_inner[c] = act ? 1.0 : 0.0;
   }
   const int nact = __popc(__ballot_sync(0xffffffffu, act));
+  const int phase = nact ? kPhaseInner : kPhaseApply;
   if (c == 0) {
     s->inner_iter = 0;
-    s->phase = nact ? kPhaseInner : kPhaseApply;
+    s->phase = phase;
   }
+  return phase;
 }
 
 // Inner FP32 iteration: inner convergence test, beta, switch to Apply when the inner solve is done.
-__device__ __noinline__ void finish_update_mixed(SolveScal* s, const SolveScal& cur, int k, const double* acc) {
+// Returns (on lane 0) the phase after it, or -1 when the mesh is done (a non-finite sum).
+__device__ __noinline__ int finish_update_mixed(SolveScal* s, const SolveScal& cur, int k, const double* acc) {
   const int c = threadIdx.x & 31;
   int act = 0, bad = 0;
   if (c < k && cur.active[c] != 0) {
@@ -165,6 +168,7 @@ __device__ __noinline__ void finish_update_mixed(SolveScal* s, const SolveScal& 
   }
   const int nact = __popc(__ballot_sync(0xffffffffu, act));
   const int anybad = __any_sync(0xffffffffu, bad);
+  int phase = kPhaseInner;
   if (c == 0) {
     const int it = cur.iter + 1, inner = cur.inner_iter + 1;
     s->iter = it;
@@ -172,10 +176,13 @@ __device__ __noinline__ void finish_update_mixed(SolveScal* s, const SolveScal& 
     if (anybad) {
       s->status = IG_ERR_NONFINITE;
       s->done = 1;
+      phase = -1;
     } else if (nact == 0 || inner >= cur.inner_cap || it >= cur.max_iter) {
       s->phase = kPhaseApply;
+      phase = kPhaseApply;
     }
   }
+  return phase;
 }
 
 // ------------------------------------------------------------------------------- kernels
@@ -304,6 +311,21 @@ template <int K>
 __global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L,
     cudaGraphConditionalHandle handle, int use_graph) {
   __shared__ TileCtx tc;
+  __shared__ int s_single, s_iter, s_cap, s_phase;
+  if (threadIdx.x == 0) {
+    s_single = (__ldcg(&ctl->nmesh) == 1);
+    s_iter = __ldcg(&ctl->iter);
+    s_cap = __ldcg(&ctl->cap);
+    s_phase = kPhaseInner;
+    tc.last = 0;
+    // a group of one mesh that takes no part in this launch (done: its residual met the tolerance
+    // in this iteration, or the loop stopped): no CTA completes it, so the loop is stopped here
+    if (s_single && blockIdx.x == 0 && (__ldcg(&ctl->all_done) || __ldcg(&mds[0].s->done))) {
+      ctl->all_done = 1;
+      if (use_graph) cudaGraphSetConditional(handle, 0u);
+    }
+  }
+  __syncthreads();
   tile_loop<2 * K>(
       mds, L, 2, 1, tc,
       [](const ScalSnap& x) { return !x.done && x.phase != kPhaseApply; },
@@ -395,18 +417,38 @@ __global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* 
         }
         tile_reduce<2 * K>(sum.s, red, out);
       },
-      [](const MeshDev& md, const SolveScal& cur, const double* v) {
-        if (cur.phase == kPhaseInner) finish_update_mixed(md.s, cur, K, v);
-        else finish_restart(md.s, cur, K, v);
+      [&](const MeshDev& md, const SolveScal& cur, const double* v) {
+        const int phase = cur.phase == kPhaseInner ? finish_update_mixed(md.s, cur, K, v)
+                                                   : finish_restart(md.s, cur, K, v);
+        if (threadIdx.x == 0) s_phase = phase;
       });
-  loop_control(mds, ctl, handle, use_graph);
+  if (!s_single) {
+    loop_control(mds, ctl, handle, use_graph);
+  } else if (tc.last) {
+    // the CTA that completed the mesh (flush_tiles ended in a barrier, so s_phase is visible): the
+    // next iteration recomputes the FP64 residual when the inner solve just ended; the Apply list
+    // is rebuilt by the whole CTA
+    const int apply = s_phase == kPhaseApply;
+    if (apply && ctl->app_mesh) rebuild_apply(mds, ctl);
+    if (threadIdx.x == 0) {
+      ctl->any_apply = apply;
+      single_loop_control(s_phase < 0, s_iter, s_cap, ctl, handle, use_graph);
+    }
+  }
 }
 
 // Inner phase: p32 = D^-1 r32 + beta p32 (loads of a thread's rows before its stores). Apply
 // phase: x64 += ||r64|| x32.
 template <int K>
-__global__ void __launch_bounds__(kBlock, 4) pupdate_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L) {
+// In the graph loop (use_graph), CTA 0 also sets the condition of the IF node that holds the next
+// iteration's residual kernel: whether some mesh recomputes its FP64 residual then (any_apply, as
+// the update launch before this one left it). Iterations without a refinement so skip that launch.
+__global__ void __launch_bounds__(kBlock, 4) pupdate_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L,
+                                                                  cudaGraphConditionalHandle apply_handle,
+                                                                  int use_graph) {
   __shared__ TileCtx tc;
+  if (use_graph && blockIdx.x == 0 && threadIdx.x == 0)
+    cudaGraphSetConditional(apply_handle, __ldcg(&ctl->any_apply) ? 1u : 0u);
   tile_loop_plain(mds, L, 1, tc,
                   [](const ScalSnap& x) { return !x.done && (x.phase == kPhaseInner || x.phase == kPhaseApply); },
                   [&](const MeshDev& md, int tile) {
@@ -478,14 +520,36 @@ cudaError_t build_plan_mixed(Group& g, SolvePlan& pl) {
   if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   cudaStream_t cs = g.capture_stream;
-  e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  // The body: an IF node holding the residual kernel (its condition set by the p-update of the
+  // iteration before; the value it starts a solve with is irrelevant, since no mesh recomputes its
+  // residual in a solve's first iteration and the kernel itself returns when none does), then the
+  // SpMV, the update and the p-update.
+  cudaGraphConditionalHandle apply_handle;
+  e = cudaGraphConditionalHandleCreate(&apply_handle, body, 1u, 0u);
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  cudaGraphNodeParams ip = {};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = apply_handle;
+  ip.conditional.type = cudaGraphCondTypeIf;
+  ip.conditional.size = 1;
+  cudaGraphNode_t if_node;
+  e = cudaGraphAddNode(&if_node, body, nullptr, nullptr, 0, &ip);
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  cudaGraph_t resid_body = ip.conditional.phGraph_out[0];
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamBeginCaptureToGraph(cs, resid_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
   resid_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.listapp);
+  cudaError_t le = cudaGetLastError();
+  e = cudaStreamEndCapture(cs, &captured);
+  if (le != cudaSuccess) e = le;
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  e = cudaStreamBeginCaptureToGraph(cs, body, &if_node, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
   spmv_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.list32);
   update_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.list32, handle, 1);
-  pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.list32);
-  cudaError_t le = cudaGetLastError();
-  cudaGraph_t captured = nullptr;
+  pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.list32, apply_handle, 1);
+  le = cudaGetLastError();
   e = cudaStreamEndCapture(cs, &captured);
   if (le != cudaSuccess) e = le;
   if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
@@ -527,7 +591,7 @@ cudaError_t host_loop_mixed_k(Group& g, int max_it, int poll, cudaStream_t st) {
     }
     {
       IG_PROF("pcg32_pupdate", st);
-      pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.ctl, g.list32);
+      pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, st>>>(g.mds, g.ctl, g.list32, cudaGraphConditionalHandle{}, 0);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
