@@ -205,9 +205,15 @@ def algorithmic(kernel, n, m, nnz, k, prec, idx32=4):
         # diagonal slots; A (and its FP32 copy in mixed precision), M and 1/A_ii written
         flops = 0
         byts = 4 * n + 24 * m + 32 * m + 8 * n + 4 * n + 8 * nnz + 16 * n + (4 * nnz + 4 * n if prec == "mixed" else 0)
+    elif kernel == "vjp_vertex":
+        # Lambda, B and U per vertex; <Lambda_v, B_v - U_v> written
+        flops = 4 * k * n
+        byts = 3 * 8 * k * n + 8 * n
     elif kernel == "vjp_face":
-        flops = 330 * m
-        byts = 12 * m + 24 * n + 3 * 8 * k * n + 72 * m
+        # faces, V, U and Lambda at the vertices (each once from DRAM), the per-vertex weights;
+        # the per-corner gradients written
+        flops = 300 * m
+        byts = 12 * m + 24 * n + 2 * 8 * k * n + 8 * n + 72 * m
     elif kernel == "vjp_gather":
         # incidence offsets and entries, the per-corner gradients (24 B each), M; gV written
         flops = 0

@@ -51,8 +51,7 @@ __global__ void __launch_bounds__(256) vjp_face_kernel(const MeshDev* __restrict
   const MeshDev& md = mds[tl.x];
   const CallDev& cl = calls[tl.x];
   const double* __restrict__ V = cl.V;
-  const double* __restrict__ Bsrc = cl.b_is_V ? cl.V : cl.B;
-  const int bstride = cl.bstride;
+  const double* __restrict__ wvert = md.z;  // per-vertex weights (vjp_vertex_kernel)
   const double* __restrict__ U = cl.U;
   double* __restrict__ gt = cl.gt;
   const double tval = cl.t;
@@ -95,6 +94,8 @@ __global__ void __launch_bounds__(256) vjp_face_kernel(const MeshDev* __restrict
     double wa = 0.0;
     double omega[3] = {0.0, 0.0, 0.0};
     if constexpr (MODE != 2) {
+      // <Lambda_v, B_v - U_v> of the three vertices, formed once per vertex by vjp_vertex_kernel
+      wa = (__ldg(wvert + vid[0]) + __ldg(wvert + vid[1])) + __ldg(wvert + vid[2]);
       double L[3][K], Uv[3][K];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -102,7 +103,6 @@ __global__ void __launch_bounds__(256) vjp_face_kernel(const MeshDev* __restrict
         for (int k = 0; k < K; ++k) {
           L[c][k] = lam[(long)vid[c] * K + k];
           Uv[c][k] = U[(long)vid[c] * K + k];
-          wa = fma(L[c][k], Bsrc[(long)vid[c] * bstride + k] - Uv[c][k], wa);
         }
       }
       const double mt2 = -0.5 * tval;
@@ -175,6 +175,27 @@ __global__ void __launch_bounds__(256) vjp_face_kernel(const MeshDev* __restrict
     *gt = all;
     md.s->cnt[3] = 0u;
   }
+}
+
+// K6a's per-vertex part: w_v = <Lambda_v, B_v - U_v> (the gradient of the face area's weight
+// comes from these three per face), formed once per vertex instead of once per incident face. It
+// goes to the solver's z vector, which no kernel reads between the adjoint solve and the next
+// solve's initialisation.
+template <int K>
+__global__ void __launch_bounds__(256) vjp_vertex_kernel(const MeshDev* __restrict__ mds,
+                                                         const CallDev* __restrict__ calls,
+                                                         const int2* __restrict__ rtiles) {
+  const int2 tl = rtiles[blockIdx.x];
+  const MeshDev& md = mds[tl.x];
+  const int v = tl.y * 256 + threadIdx.x;
+  if (v >= md.n) return;
+  const CallDev& cl = calls[tl.x];
+  const double* __restrict__ Bsrc = cl.b_is_V ? cl.V : cl.B;
+  double w = 0.0;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    w = fma(md.lam[(long)v * K + k], Bsrc[(long)v * cl.bstride + k] - cl.U[(long)v * K + k], w);
+  md.z[v] = w;
 }
 
 template <int K>
@@ -541,6 +562,10 @@ cudaError_t vjp32_k(Group& g, cudaStream_t st) {
 
 template <int K>
 cudaError_t vjp_k(Group& g, int mode, cudaStream_t st) {
+  if (mode != 2) {
+    IG_PROF("vjp_vertex", st);
+    vjp_vertex_kernel<K><<<g.nrow_tiles, 256, 0, st>>>(g.mds, g.calls_dev, g.row_tiles);
+  }
   {
     IG_PROF("vjp_face", st);
     const bool cl = group_any_clamp(g);
