@@ -440,9 +440,10 @@ __global__ void __launch_bounds__(kBlock, 4) update_mixed_kernel(const MeshDev* 
 // Inner phase: p32 = D^-1 r32 + beta p32 (loads of a thread's rows before its stores). Apply
 // phase: x64 += ||r64|| x32.
 template <int K>
-// In the graph loop (use_graph), CTA 0 also sets the condition of the IF node that holds the next
-// iteration's residual kernel: whether some mesh recomputes its FP64 residual then (any_apply, as
-// the update launch before this one left it). Iterations without a refinement so skip that launch.
+// In the graph loop of a single mesh (use_graph), CTA 0 also sets the condition of the IF node that
+// holds the next iteration's residual kernel: whether the mesh recomputes its FP64 residual then
+// (any_apply, as the update launch before this one left it). Iterations without a refinement so
+// skip that launch.
 __global__ void __launch_bounds__(kBlock, 4) pupdate_mixed_kernel(const MeshDev* __restrict__ mds, LoopCtl* ctl, ListRef L,
                                                                   cudaGraphConditionalHandle apply_handle,
                                                                   int use_graph) {
@@ -520,35 +521,44 @@ cudaError_t build_plan_mixed(Group& g, SolvePlan& pl) {
   if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   cudaStream_t cs = g.capture_stream;
-  // The body: an IF node holding the residual kernel (its condition set by the p-update of the
-  // iteration before; the value it starts a solve with is irrelevant, since no mesh recomputes its
-  // residual in a solve's first iteration and the kernel itself returns when none does), then the
-  // SpMV, the update and the p-update.
-  cudaGraphConditionalHandle apply_handle;
-  e = cudaGraphConditionalHandleCreate(&apply_handle, body, 1u, 0u);
-  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
-  cudaGraphNodeParams ip = {};
-  ip.type = cudaGraphNodeTypeConditional;
-  ip.conditional.handle = apply_handle;
-  ip.conditional.type = cudaGraphCondTypeIf;
-  ip.conditional.size = 1;
-  cudaGraphNode_t if_node;
-  e = cudaGraphAddNode(&if_node, body, nullptr, nullptr, 0, &ip);
-  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
-  cudaGraph_t resid_body = ip.conditional.phGraph_out[0];
+  // A group of one mesh: the body is an IF node holding the residual kernel (its condition set by
+  // the p-update of the iteration before; the value it starts a solve with is irrelevant, since no
+  // mesh recomputes its residual in a solve's first iteration and the kernel itself returns when
+  // none does), then the SpMV, the update and the p-update. A group of many meshes has some mesh
+  // refining in most iterations, where the IF node costs more than it saves: its body launches the
+  // residual kernel every iteration.
+  const bool use_if = g.nmesh == 1;
+  cudaGraphConditionalHandle apply_handle{};
+  cudaGraphNode_t if_node = nullptr;
   cudaGraph_t captured = nullptr;
-  e = cudaStreamBeginCaptureToGraph(cs, resid_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  cudaError_t le = cudaSuccess;
+  if (use_if) {
+    e = cudaGraphConditionalHandleCreate(&apply_handle, body, 1u, 0u);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = apply_handle;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    e = cudaGraphAddNode(&if_node, body, nullptr, nullptr, 0, &ip);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+    cudaGraph_t resid_body = ip.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(cs, resid_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+    resid_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.listapp);
+    le = cudaGetLastError();
+    e = cudaStreamEndCapture(cs, &captured);
+    if (le != cudaSuccess) e = le;
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+    e = cudaStreamBeginCaptureToGraph(cs, body, &if_node, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+  } else {
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  }
   if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
-  resid_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.listapp);
-  cudaError_t le = cudaGetLastError();
-  e = cudaStreamEndCapture(cs, &captured);
-  if (le != cudaSuccess) e = le;
-  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
-  e = cudaStreamBeginCaptureToGraph(cs, body, &if_node, nullptr, 1, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) { cudaGraphDestroy(graph); return e; }
+  if (!use_if) resid_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.listapp);
   spmv_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.list32);
   update_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.list32, handle, 1);
-  pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.list32, apply_handle, 1);
+  pupdate_mixed_kernel<K><<<g.grid32, kBlock, 0, cs>>>(g.mds, g.ctl, g.list32, apply_handle, use_if ? 1 : 0);
   le = cudaGetLastError();
   e = cudaStreamEndCapture(cs, &captured);
   if (le != cudaSuccess) e = le;
