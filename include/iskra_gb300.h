@@ -163,6 +163,13 @@ ig_status ig_check(ig_mesh* mesh);
  * M_dev [n] (the lumped mass). Either pointer may be NULL. */
 ig_status ig_operator(ig_mesh* mesh, double* Aval_dev, double* M_dev);
 
+/* Copy the FP32 operator of a mixed-precision assembly (IG_PRECISION_MIXED or
+ * IG_PRECISION_MIXED_GEOM32) on the pattern: Aval_dev [nnz] floats, in the order of ig_operator.
+ * With IG_PRECISION_MIXED each value is the FP64 value rounded to nearest (ties to even).
+ * Errors: IG_ERR_INVALID_ARG (NULL mesh or pointer), IG_ERR_STATE (no mixed-precision
+ * assembly). */
+ig_status ig_operator32(ig_mesh* mesh, float* Aval_dev);
+
 /* Solve A U = M B (the forward smoothing step of §7.1) by Jacobi-preconditioned conjugate
  * gradients, x0 = 0, every column to opts->rel_tol (FP64 operator; in mixed precision the
  * iterations run in FP32 and the residual is recomputed in FP64 between refinements).

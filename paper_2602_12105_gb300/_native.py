@@ -79,6 +79,7 @@ SIGNATURES = {
     "ig_assemble": (_i32, [_vp, _vp, _dbl, _i32]),
     "ig_check": (_i32, [_vp]),
     "ig_operator": (_i32, [_vp, _vp, _vp]),
+    "ig_operator32": (_i32, [_vp, _vp]),
     "ig_solve": (_i32, [_vp, _vp, _i32, _vp, _P(SolveOpts), _P(SolveInfo)]),
     "ig_adjoint": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _P(SolveOpts), _P(SolveInfo)]),
     "ig_batch_create": (_i32, [_vp, _P(_vp), _i32, _P(_vp)]),

@@ -150,6 +150,13 @@ class Mesh:
         self.ctx.check(self.ctx.lib.ig_operator(self.h, _ptr(A), _ptr(M)))
         return A, M
 
+    def operator32(self):
+        """The FP32 operator of a mixed-precision assembly, on the pattern (ig_operator32)."""
+        A = torch.empty(self.nnz, dtype=torch.float32, device=self.ctx.device)
+        self.ctx.sync_stream()
+        self.ctx.check(self.ctx.lib.ig_operator32(self.h, _ptr(A)))
+        return A
+
     def mass(self):
         """The lumped mass M [n] of the assembled operator."""
         M = torch.empty(self.n, dtype=torch.float64, device=self.ctx.device)

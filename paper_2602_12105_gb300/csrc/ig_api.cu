@@ -667,6 +667,19 @@ ig_status ig_operator(ig_mesh* mesh, double* Aval_dev, double* M_dev) {
   return IG_OK;
 }
 
+ig_status ig_operator32(ig_mesh* mesh, float* Aval_dev) {
+  IG_NVTX("ig_operator32");
+  if (!mesh || !Aval_dev) return IG_ERR_INVALID_ARG;
+  ig_ctx* ctx = mesh->ctx;
+  if (mesh->assembled < 2) {
+    set_error(ctx, "FP32 operator requested before a mixed-precision assembly");
+    return IG_ERR_STATE;
+  }
+  DeviceGuard guard(ctx->device);
+  IG_CK(ctx, launch_operator32_csr(mesh->md, Aval_dev, ctx->stream), "copy A32");
+  return IG_OK;
+}
+
 ig_status ig_solve(ig_mesh* mesh, const double* B_dev, int k, double* U_dev, const ig_solve_opts* opts,
                    ig_solve_info* info) {
   IG_NVTX("ig_solve");

@@ -319,17 +319,19 @@ __global__ void __launch_bounds__(256) row_kernel(const MeshDev* __restrict__ md
   }
   const double aii = mass + diag;
   const double dinv = 1.0 / aii;
+  // the FP32 copies round to nearest with integer instructions (f64_to_f32_rn), not the
+  // conversion instruction, which issues at the FP64 rate
   if (in_smem) {
     acc[dslot][threadIdx.x] = aii;
     for (int j = 0; j < len; ++j) {
       const double x = acc[j][threadIdx.x];
       gA[sbase + 32 * j] = x;
-      if (mixed) md.A32[sbase + 32 * j] = (float)x;
+      if (mixed) md.A32[sbase + 32 * j] = f64_to_f32_rn(x);
     }
   } else {
     gA[sbase + 32 * dslot] = aii;
     if (mixed)
-      for (int j = 0; j < len; ++j) md.A32[sbase + 32 * j] = (float)gA[sbase + 32 * j];
+      for (int j = 0; j < len; ++j) md.A32[sbase + 32 * j] = f64_to_f32_rn(gA[sbase + 32 * j]);
   }
   for (int j = len; j < width; ++j) {
     gA[sbase + 32 * j] = 0.0;
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(256) row_kernel(const MeshDev* __restrict__ md
   }
   md.M[v] = mass;
   md.Dinv[v] = dinv;
-  if (mixed) md.Dinv32[v] = (float)dinv;
+  if (mixed) md.Dinv32[v] = f64_to_f32_rn(dinv);
 }
 
 // Copy of A in CSR order (the order of ig_mesh_pattern); with FP32 geometry the FP32 operator.
@@ -348,6 +350,15 @@ __global__ void __launch_bounds__(256) operator_csr_kernel(MeshDev md, double* _
   const int sbase = md.sell_ptr[v >> 5] + (v & 31);
   for (int j = 0; j < len; ++j)
     out[r0 + j] = md.geom32 ? f32_to_f64(md.A32[sbase + 32 * j]) : md.A[sbase + 32 * j];
+}
+
+// The FP32 operator (mixed precision) in CSR order.
+__global__ void __launch_bounds__(256) operator32_csr_kernel(MeshDev md, float* __restrict__ out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= md.n) return;
+  const int r0 = md.rowptr[v], len = md.rowptr[v + 1] - r0;
+  const int sbase = md.sell_ptr[v >> 5] + (v & 31);
+  for (int j = 0; j < len; ++j) out[r0 + j] = md.A32[sbase + 32 * j];
 }
 
 }  // namespace
@@ -381,6 +392,11 @@ cudaError_t launch_assemble(Group& g, int mode, cudaStream_t st) {
     IG_PROF("assemble_rows", st);
     row_kernel<<<g.nrow_tiles, 256, 0, st>>>(g.mds, g.row_tiles, mode);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_operator32_csr(const MeshDev& md, float* Acsr, cudaStream_t st) {
+  operator32_csr_kernel<<<(md.n + 255) / 256, 256, 0, st>>>(md, Acsr);
   return cudaGetLastError();
 }
 

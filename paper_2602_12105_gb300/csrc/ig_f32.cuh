@@ -37,6 +37,22 @@ __device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
   }
 }
 
+// x rounded to float, to nearest with ties to even (IEEE 754 binary64 -> binary32): the 29
+// mantissa bits that binary32 drops decide the rounding; a carry out of the kept 23 bits moves into
+// the exponent field, and past the largest float it gives infinity, as the rule requires. Zeros,
+// results below the float normal range, infinities and NaNs (rare in the operator) take the
+// hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned top = (unsigned)(b >> 32), bot = (unsigned)b;
+  const unsigned e = (top >> 20) & 0x7ffu;  // biased FP64 exponent
+  if (e < 897u || e > 1150u) return __double2float_rn(x);
+  const unsigned m = ((top & 0xfffffu) << 3) | (bot >> 29);  // the kept 23 mantissa bits
+  const unsigned rest = bot & 0x1fffffffu;                    // the dropped 29
+  const unsigned up = (rest > 0x10000000u) | ((rest == 0x10000000u) & (m & 1u));
+  return __uint_as_float(((top & 0x80000000u) | ((e - 896u) << 23) | m) + up);
+}
+
 // The FP64 value of a float, exactly (denormal floats are taken as zero).
 __device__ __forceinline__ double f32_to_f64(float f) {
   const unsigned u = __float_as_uint(f);

@@ -412,6 +412,7 @@ cudaError_t launch_sell_fill(const int* rowptr, const int* col, int n, const int
 // and operator, FP32 copy), 2 mixed with FP32 face geometry (FP32 operator only)
 cudaError_t launch_assemble(Group& g, int mode, cudaStream_t st);
 cudaError_t launch_operator_csr(const MeshDev& md, double* Acsr, cudaStream_t st);
+cudaError_t launch_operator32_csr(const MeshDev& md, float* Acsr, cudaStream_t st);
 
 // ig_pcg.cu: see Group above
 

@@ -96,6 +96,24 @@ def test_mixed_refinement_cap(api):
     assert max(info["true_rel_residual"]) < 1e-3
 
 
+@pytest.mark.parametrize("name,t_scale", [("ico5", 1.0), ("grid61x53", 1.0), ("planar_jitter", 1.0), ("sliver", 1.0),
+                                          ("ico5", 1e-40), ("ico5", 1e41)])
+def test_fp32_operator_is_the_fp64_operator_rounded_to_nearest(api, name, t_scale):
+    """In mixed precision the FP32 copy of A is the FP64 operator rounded to nearest, ties to even,
+    entry by entry: the assembly rounds with integer instructions, and numpy's float64 -> float32
+    cast is that rounding. The scaled t puts off-diagonal entries below the float normal range
+    (1e-40: float subnormals) and past the largest float (1e41: infinities)."""
+    V, F, t, B, T = case(name, seed=21)
+    mesh = api.Mesh(_t(F, torch.int32), V.shape[0])
+    mesh.assemble(_t(V), t * t_scale, precision="mixed")
+    A64, _ = mesh.operator()
+    a64 = A64.cpu().numpy()
+    a32 = mesh.operator32().cpu().numpy()
+    with np.errstate(over="ignore"):
+        ref = a64.astype(np.float32)
+    assert np.array_equal(a32.view(np.uint32), ref.view(np.uint32))
+
+
 # ------------------------------------------------------------------------------- FP32 face geometry
 # The mixed32 mode computes cotangents, areas and the per-face gradient in FP32 (FP64 for faces
 # whose smallest corner has sin < 1e-2) and solves the FP32 operator A32 exactly (FP64 refinement).
