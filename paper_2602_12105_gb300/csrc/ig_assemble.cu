@@ -66,28 +66,28 @@ __global__ void __launch_bounds__(256) face_kernel(const MeshDev* __restrict__ m
   const double ny = d1[2] * d2[0] - d1[0] * d2[2];
   const double nz = d1[0] * d2[1] - d1[1] * d2[0];
   const double s2 = nx * nx + ny * ny + nz * nz;
-  double4 w;
+  double wx, wy, wz, ww;  // the three corner weights and the face area / 3
   if (!positive_finite(s2)) {
     const long long b = __double_as_longlong(s2);
     atomicOr(err, (b & 0x7ff0000000000000ll) == 0x7ff0000000000000ll ? kErrNonfinite : kErrDegenerate);
-    w = make_double4(0.0, 0.0, 0.0, 0.0);
+    wx = wy = wz = ww = 0.0;
   } else {
     const double inv_s = rsqrt(s2);
     const double h = -half_t * inv_s;
-    w.x = h * (d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2]);
-    w.y = h * (d2[0] * d0[0] + d2[1] * d0[1] + d2[2] * d0[2]);
-    w.z = h * (d0[0] * d1[0] + d0[1] * d1[1] + d0[2] * d1[2]);
-    w.w = s2 * inv_s * (1.0 / 6.0);
+    wx = h * (d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2]);
+    wy = h * (d2[0] * d0[0] + d2[1] * d0[1] + d2[2] * d0[2]);
+    wz = h * (d0[0] * d1[0] + d0[1] * d1[1] + d0[2] * d1[2]);
+    ww = s2 * inv_s * (1.0 / 6.0);
     if (CLAMP && md.clamp_on) {  // w_c = (t/2) cot_c >= (t/2) clamp_min
       const double wmin = half_t * md.clamp_min;
-      w.x = fmax(w.x, wmin);
-      w.y = fmax(w.y, wmin);
-      w.z = fmax(w.z, wmin);
+      wx = fmax(wx, wmin);
+      wy = fmax(wy, wmin);
+      wz = fmax(wz, wmin);
     }
   }
   double2* out = reinterpret_cast<double2*>(facew + 4 * (long)f);
-  out[0] = make_double2(w.x, w.y);
-  out[1] = make_double2(w.z, w.w);
+  out[0] = make_double2(wx, wy);
+  out[1] = make_double2(wz, ww);
 }
 
 // sin^2 of the smallest corner below this: the face is a sliver and is computed in FP64.
